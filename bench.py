@@ -1,0 +1,333 @@
+"""Benchmark of the superblock H*psi + Lanczos hot path on GB300.
+
+Workload (default): the 2 x 32 Hubbard ladder at m = 1000 kept states,
+N_up = N_dn = 28 (1/8 hole doping), 16 superblocks with U = 4 .. 12 that
+share every operator block (isometry-grown, seeded; see workloads/grown.py).
+
+One timed step = the whole hot path for the 16-member batch: a ground-state
+solve (dmrg_lanczos_ground: products, float64 Lanczos scalars, CGS2 full
+reorthogonalisation, tridiagonal test, CUDA graphs; mixed precision followed
+by float64 refinement when a tensor-core precision is selected) plus the
+Hellmann-Feynman gradient (dmrg_energy_grad).  value = algorithmic H*psi
+flops executed in the step / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own batch (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("H·ψ TFLOP/s & Lanczos steps/s at m=1000, mixed vs FP64 same GPU, "
+          "|ΔE0|≤1e-8")
+WORKLOAD = "hubbard_ladder_2x32_m1000_U4-12_batch16"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-iter", type=int, default=300)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_workload(batch, rank):
+    from workloads.grown import ladder_m1000
+    return ladder_m1000(batch=batch, seed=rank)
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands, on the host cores: a bounded sample of the
+    same workload (two batch members: a few blocked products and Lanczos
+    iterations), scaled to the metric's unit."""
+    if rank != 0:
+        return 0
+    from oracle import superblock as osb
+    from workloads.superblock import seeded_normal
+    sb = make_workload(args.batch, 0)
+    flops_member = osb.matvec_flops(sb)
+    cores = len(os.sched_getaffinity(0))
+    x = seeded_normal(0, sb.dim)
+    osb.apply_H(sb, x, 0)  # warm-up
+    times = []
+    n = 0
+    t_end = time.perf_counter() + 20.0
+    for step in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        for b in (0, 1):
+            x = osb.apply_H(sb, x, b)
+            x /= np.linalg.norm(x)
+            n += 1
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end:
+            break
+    sec = sum(times)
+    tflops = n * flops_member / sec / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": len(times), "warmup": 1, "ms_per_step": 1000 * sec / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "2 members x 1 product per step"},
+            "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} blocked float64 products of single members (NumPy), D={sb.dim}"},
+            "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(sb):
+    from oracle import superblock as osb
+    from workloads.superblock import seeded_normal
+    flops = osb.matvec_flops(sb)
+    x = seeded_normal(1, sb.dim)
+    osb.apply_H(sb, x, 0)
+    n = 0
+    t0 = time.perf_counter()
+    while n < 3 or time.perf_counter() - t0 < 10.0:
+        x = osb.apply_H(sb, x, n % sb.batch)
+        x /= np.linalg.norm(x)
+        n += 1
+        if n >= 200:
+            break
+    sec = time.perf_counter() - t0
+    return {"value": n * flops / sec / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": f"{n} blocked float64 products (one member each, NumPy) of the same "
+                                        f"workload, {sec:.1f} s"}
+
+
+# ------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_0902_3185_gb300 import binding
+    from workloads.superblock import seeded_normal
+
+    sb = make_workload(args.batch, rank)
+    g = binding.GpuSuperblock(sb, device=dev)
+    prec = args.prec
+    if prec == "auto":
+        prec = "fp64"
+        try:
+            g.apply_H(g.empty().zero_(), prec="bf16x3")
+            prec = "bf16x3"
+        except binding.DmrgError:
+            pass
+    flops_mv = g.info["flops_per_matvec"]
+    X0 = np.stack([seeded_normal(1000 * rank + b, sb.dim) for b in range(sb.batch)])
+    x0 = torch.from_numpy(X0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(x):
+        e0, psi, infos, st = g.lanczos_ground(x, tol=args.tol, max_iter=args.max_iter, prec=prec,
+                                              refine=True, refine_tol=args.tol, graph_iters=8)
+        dEdc = g.energy_grad(psi)
+        return e0, psi, infos, dEdc
+
+    for _ in range(max(3, args.warmup)):
+        e0, psi, infos, dEdc = step(x0)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev = []
+    mv_count = 0
+    it_count = 0
+    launches = 0
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between timed steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e0, psi, infos, dEdc = step(x0)
+        b.record(stream)
+        ev.append((a, b))
+        mv_count += max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
+        it_count += max(i["iters"] + i["refine_iters"] for i in infos)
+        launches += infos[0]["kernel_launches"] + 4
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * mv_count * flops_mv / (ms / 1e3) / 1e12
+
+    # kernel-only product timing (events on the launching stream)
+    y = g.empty()
+    reps = 20
+    for _ in range(3):
+        g.apply_H(x0, y, prec=prec)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.apply_H(x0, y, prec=prec)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    mv_ms = a.elapsed_time(b) / reps
+    mv64_ms = mv_ms
+    if prec != "fp64":
+        a.record(stream)
+        for _ in range(3):
+            g.apply_H(x0, y, prec="fp64")
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        mv64_ms = a.elapsed_time(b) / 3
+
+    # end to end through the public API with host buffers
+    xh = torch.from_numpy(X0).pin_memory()
+    ph = torch.empty_like(xh).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd = xh.to(dev, non_blocking=True)
+        e0h, psi, infos, dEdc = step(xd)
+        ph.copy_(psi, non_blocking=True)
+        dh = dEdc.cpu()
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": world * mv_count / args.steps * flops_mv / e2e_s / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(X0.nbytes), "d2h_bytes_per_step": int(X0.nbytes + dh.numel() * 8)}
+
+    peaks, kind = measured_peaks()
+    if prec == "fp64":
+        peak = peaks["bf16_tflops"] * 1.25 / 2250.0
+        bound, pk_note = "alu", f"float64 = {kind} bf16 peak x nominal 1.25/2250"
+    elif prec == "tf32":
+        peak = peaks["bf16_tflops"] * 1100.0 / 2250.0
+        bound, pk_note = "tensor", f"tf32 = {kind} bf16 peak x nominal 1100/2250"
+    else:
+        peak = peaks["bf16_tflops"] / 3.0
+        bound, pk_note = "tensor", f"{kind} bf16 peak / 3 (three bf16 products per algorithmic product)"
+    achieved = flops_mv / (mv_ms / 1e3) / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "superblock product (all launches of one dmrg_apply_H)",
+            "peak_source": pk_note}
+
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == "fp64" else f"{prec}+f32acc (products), f64 (Lanczos)",
+           "data": "synthetic (seeded isometry-grown superblocks)",
+           "config": {"workload": WORKLOAD, "batch": sb.batch, "D": sb.dim, "m": 1000,
+                      "sectors": sb.n_sectors, "pairs": len(sb.pairs), "prec": prec, "tol": args.tol,
+                      "l2": "256 MB flush between timed steps; Krylov basis > L2"},
+           "lanczos_steps_per_s": world * it_count / (ms / 1e3),
+           "matvec_ms": mv_ms, "matvec_tflops": achieved, "matvec_fp64_ms": mv64_ms,
+           "matvec_fp64_tflops": flops_mv / (mv64_ms / 1e3) / 1e12,
+           "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
+           "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline_sample(sb)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

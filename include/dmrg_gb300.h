@@ -1,0 +1,158 @@
+/*
+ * dmrg_gb300.h -- C ABI of the GB300 superblock H*psi + Lanczos library.
+ *
+ * The operation (G. Alvarez, DMRG++ paper, Sec. 3.3): the Lanczos solver
+ * needs only x += H y, with the superblock Hamiltonian
+ *     H = H_S' (x) 1 + 1 (x) H_E' + sum_k c_k A_k (x) B_k
+ * acting on a wavefunction that is blocked by the effective quantum number
+ * (Sec. 3.2).  Sector s pairs the S' states of quantum number q_s with the
+ * E' states of Q_target - q_s; its block Psi_s is r[s] x c[s], row-major,
+ * and the flat vector is the concatenation of the blocks in sector order
+ * (D = sum_s r[s] c[s]).  Every (term k, sector pair) with a nonzero block
+ * contributes
+ *     Y[s_out] += c_k * A[s_out,s_in] * Psi[s_in] * B[s_out,s_in]^T
+ * because (A (x) B) vec(Psi) = vec(A Psi B^T).  H_S' (x) 1 and 1 (x) H_E'
+ * are pairs whose B (respectively A) is the identity (flags below).
+ *
+ * Conventions shared by every call:
+ *  - All vectors are float64, device pointers, laid out [batch][D]; the
+ *    library never keeps or frees caller memory.
+ *  - Calls are ordered on the given CUDA stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Calls that return host scalars
+ *    (e0, info) synchronise that stream before returning.
+ *  - Errors never cross the ABI as exceptions: every call returns a
+ *    dmrg_status; dmrg_last_error gives a message for the superblock.
+ *  - A superblock is not thread safe: calls on one dmrg_sb must not overlap
+ *    (they share its workspace).
+ */
+#ifndef DMRG_GB300_H
+#define DMRG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrg_sb dmrg_sb;
+
+typedef enum {
+  DMRG_OK = 0,
+  DMRG_EINVAL = 1,      /* bad argument or descriptor */
+  DMRG_ENOMEM = 2,      /* device or host allocation failed */
+  DMRG_ECUDA = 3,       /* a CUDA runtime call failed */
+  DMRG_ENOCONV = 4,     /* Lanczos hit max_iter before the tolerance */
+  DMRG_EBREAKDOWN = 5,  /* (informational) Krylov space became invariant: result exact */
+  DMRG_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  DMRG_ENAN = 7,        /* NaN or Inf met in a Lanczos scalar */
+  DMRG_EUNSUPPORTED = 8 /* precision or feature not built for this device */
+} dmrg_status;
+
+typedef enum {
+  DMRG_FP64 = 0,   /* float64 products on the CUDA cores */
+  DMRG_TF32 = 1,   /* tensor cores, TF32 operands, FP32 accumulation */
+  DMRG_BF16X3 = 2  /* tensor cores, x = hi + lo in BF16, hi*hi + hi*lo + lo*hi, FP32 accumulation */
+} dmrg_prec;
+
+enum { DMRG_ID_A = 1, /* A is the identity (1 (x) B term; r[s_out] == r[s_in]) */
+       DMRG_ID_B = 2  /* B is the identity (A (x) 1 term; c[s_out] == c[s_in]) */ };
+
+/* One (term, sector pair).  A: r[s_out] x r[s_in] row-major with leading
+ * dimension lda >= r[s_in]; B: c[s_out] x c[s_in] with ldb >= c[s_in].
+ * Pointers are host or device memory (dmrg_sb_desc.blocks_on_device); they
+ * are read during dmrg_create_superblock and not kept. */
+typedef struct {
+  int32_t term, s_out, s_in, flags;
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+} dmrg_pair;
+
+typedef struct {
+  int32_t n_sectors;
+  const int32_t* r;        /* host, [n_sectors], >= 0 */
+  const int32_t* c;        /* host, [n_sectors], >= 0 */
+  int32_t n_terms;
+  const double* coeffs;    /* host, [batch][n_terms] */
+  int32_t n_pairs;
+  const dmrg_pair* pairs;  /* host, [n_pairs] */
+  int32_t blocks_on_device;
+} dmrg_sb_desc;
+
+typedef struct {
+  int64_t dim;              /* D per batch member */
+  int32_t batch, n_sectors, n_terms, n_pairs;
+  double flops_per_matvec;  /* algorithmic flops of one H*psi, all batch members */
+  double op_bytes_f64;      /* bytes of the stored float64 operator blocks */
+  double op_bytes_mixed;    /* bytes of the tensor-core operand copies (TF32 layout) */
+} dmrg_sb_info;
+
+typedef struct {
+  double tol;          /* stop when beta_j |s_j| <= tol * max(1, |theta|) */
+  int32_t max_iter;    /* Krylov dimension cap (clamped to D) */
+  int32_t prec;        /* dmrg_prec of the products in the main solve */
+  int32_t refine;      /* 1: after a mixed-precision solve, restart FP64 Lanczos from its psi */
+  double refine_tol;   /* tolerance of the FP64 refinement */
+  int32_t check_every; /* run the tridiagonal test every this many iterations (>= 1) */
+  int32_t graph_iters; /* iterations captured per CUDA graph launch (>= 1) */
+} dmrg_lanczos_opts;
+
+typedef struct {     /* one per batch member */
+  double e0;
+  double residual;        /* beta_j |s_j| at exit */
+  int32_t iters;          /* Lanczos iterations of the main solve */
+  int32_t refine_iters;   /* FP64 iterations of the refinement */
+  int32_t mixed_matvecs;
+  int32_t fp64_matvecs;
+  int32_t status;         /* dmrg_status of this member */
+  int32_t breakdown;
+  int32_t kernel_launches; /* kernels the whole call launched (all members, graph nodes counted) */
+  int32_t pad;
+} dmrg_lanczos_info;
+
+/* Sec. 3.2-3.3: build the sector tables, the (term, sector pair) task lists,
+ * device copies of every operator block (float64 and tensor-core layouts)
+ * and the workspace.  batch >= 1 superblocks share all blocks and differ only
+ * in coeffs.  Returns DMRG_EINVAL for inconsistent shapes (identity flag with
+ * r_out != r_in, sector out of range, ld too small, NULL block). */
+dmrg_status dmrg_create_superblock(const dmrg_sb_desc* d, int32_t batch, dmrg_sb** out);
+void dmrg_destroy_superblock(dmrg_sb* sb);
+const char* dmrg_last_error(const dmrg_sb* sb);
+dmrg_status dmrg_query(const dmrg_sb* sb, dmrg_sb_info* info);
+
+/* Replace the coefficient table (host, [batch][n_terms]) without rebuilding:
+ * coupling sweeps and finite differences. Stream-ordered after previous work. */
+dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs);
+
+/* Sec. 3.3 x += H y: y = H psi (accumulate = 0) or y += H psi (accumulate =
+ * 1) for every batch member.  psi, y: device [batch][D], must not overlap. */
+dmrg_status dmrg_apply_H(dmrg_sb* sb, const double* psi, double* y, int32_t accumulate,
+                         int32_t prec, void* stream);
+
+/* Reverse mode of y = H(c) psi for a cotangent g (device [batch][D]):
+ * dpsi = H^T g (device [batch][D]) and dc[b][k] = <g_b, (A_k (x) B_k) psi_b>
+ * (device [batch][n_terms]).  Either output may be NULL. */
+dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* g,
+                                  double* dpsi, double* dc, int32_t prec, void* stream);
+
+/* Sec. 3.3 (diagonalize / Lanczos): lowest eigenpair of every batch member,
+ * Lanczos with float64 scalars and full reorthogonalisation (CGS2), the
+ * iteration captured in CUDA graphs.  psi0: device [batch][D] start vectors;
+ * psi_out: device [batch][D], normalised; e0: host [batch]; info: host
+ * [batch] or NULL.  Returns the worst member status (DMRG_OK if all met the
+ * tolerance; DMRG_EBREAKDOWN is reported in info only). */
+dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0,
+                                const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info,
+                                void* stream);
+
+/* Hellmann-Feynman: dE0/dc_k = <psi, (A_k (x) B_k) psi> / <psi, psi> for
+ * every batch member.  psi: device [batch][D]; dE_dc: device [batch][n_terms]. */
+dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int32_t prec,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMRG_GB300_H */

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of ``libdmrg_gb300.so`` (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module converts
+a :class:`workloads.superblock.Superblock` into the C descriptor, passes
+device pointers of torch tensors, and raises on any non-OK status.  There is
+no CPU fallback: without the built library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdmrg_gb300.so")
+
+FP64, TF32, BF16X3 = 0, 1, 2
+PREC = {"fp64": FP64, "tf32": TF32, "bf16x3": BF16X3}
+ID_A, ID_B = 1, 2
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN",
+          6: "ETIMEOUT", 7: "ENAN", 8: "EUNSUPPORTED"}
+
+# exported symbols, as declared in include/dmrg_gb300.h
+SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error", "dmrg_query",
+           "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
+           "dmrg_energy_grad"]
+
+
+class DmrgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Pair(C.Structure):
+    _fields_ = [("term", C.c_int32), ("s_out", C.c_int32), ("s_in", C.c_int32), ("flags", C.c_int32),
+                ("A", C.c_void_p), ("lda", C.c_int64), ("B", C.c_void_p), ("ldb", C.c_int64)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_sectors", C.c_int32), ("r", C.c_void_p), ("c", C.c_void_p), ("n_terms", C.c_int32),
+                ("coeffs", C.c_void_p), ("n_pairs", C.c_int32), ("pairs", C.c_void_p),
+                ("blocks_on_device", C.c_int32)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("dim", C.c_int64), ("batch", C.c_int32), ("n_sectors", C.c_int32), ("n_terms", C.c_int32),
+                ("n_pairs", C.c_int32), ("flops_per_matvec", C.c_double), ("op_bytes_f64", C.c_double),
+                ("op_bytes_mixed", C.c_double)]
+
+
+class LanczosOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32), ("refine", C.c_int32),
+                ("refine_tol", C.c_double), ("check_every", C.c_int32), ("graph_iters", C.c_int32)]
+
+
+class LanczosInfo(C.Structure):
+    _fields_ = [("e0", C.c_double), ("residual", C.c_double), ("iters", C.c_int32),
+                ("refine_iters", C.c_int32), ("mixed_matvecs", C.c_int32), ("fp64_matvecs", C.c_int32),
+                ("status", C.c_int32), ("breakdown", C.c_int32), ("kernel_launches", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load the library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH}")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, dp = C.c_void_p, C.c_int32, C.c_void_p
+    lib.dmrg_create_superblock.argtypes = [C.POINTER(_Desc), i32, C.POINTER(vp)]
+    lib.dmrg_destroy_superblock.argtypes = [vp]
+    lib.dmrg_destroy_superblock.restype = None
+    lib.dmrg_last_error.argtypes = [vp]
+    lib.dmrg_last_error.restype = C.c_char_p
+    lib.dmrg_query.argtypes = [vp, C.POINTER(_Info)]
+    lib.dmrg_set_coeffs.argtypes = [vp, dp]
+    lib.dmrg_apply_H.argtypes = [vp, dp, dp, i32, i32, vp]
+    lib.dmrg_apply_H_backward.argtypes = [vp, dp, dp, dp, dp, i32, vp]
+    lib.dmrg_lanczos_ground.argtypes = [vp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
+    lib.dmrg_energy_grad.argtypes = [vp, dp, dp, i32, vp]
+    for name in SYMBOLS:
+        if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+class GpuSuperblock:
+    """Device-resident superblock: operator blocks, task lists and workspace."""
+
+    def __init__(self, sb, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.lib = load()
+        self.device = torch.device(device or "cuda")
+        self.sb = sb
+        self.batch = sb.batch
+        self.n_terms = sb.n_terms
+        self.dim = sb.dim
+        r = np.ascontiguousarray(sb.r, dtype=np.int32)
+        c = np.ascontiguousarray(sb.c, dtype=np.int32)
+        coeffs = np.ascontiguousarray(sb.coeffs, dtype=np.float64)
+        keep = []
+        pairs = (_Pair * max(1, len(sb.pairs)))()
+        for i, p in enumerate(sb.pairs):
+            flags = (ID_A if p.A is None else 0) | (ID_B if p.B is None else 0)
+            A = None if p.A is None else np.ascontiguousarray(p.A, dtype=np.float64)
+            B = None if p.B is None else np.ascontiguousarray(p.B, dtype=np.float64)
+            keep += [A, B]
+            pairs[i] = _Pair(p.term, p.s_out, p.s_in, flags,
+                             None if A is None else A.ctypes.data, 0 if A is None else A.shape[1],
+                             None if B is None else B.ctypes.data, 0 if B is None else B.shape[1])
+        desc = _Desc(sb.n_sectors, r.ctypes.data, c.ctypes.data, sb.n_terms, coeffs.ctypes.data,
+                     len(sb.pairs), C.cast(pairs, C.c_void_p), 0)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.dmrg_create_superblock(C.byref(desc), sb.batch, C.byref(h))
+        if st != 0:
+            raise DmrgError(st, "dmrg_create_superblock failed (see stderr)")
+        self.h = h
+        info = _Info()
+        self._check(self.lib.dmrg_query(self.h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in _Info._fields_}
+
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.dmrg_last_error(self.h) if getattr(self, "h", None) else b""
+            raise DmrgError(st, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmrg_destroy_superblock(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- calls
+    def empty(self):
+        return torch.empty(self.batch, self.dim, dtype=torch.float64, device=self.device)
+
+    def set_coeffs(self, coeffs):
+        c = np.ascontiguousarray(np.broadcast_to(np.asarray(coeffs, dtype=np.float64),
+                                                 (self.batch, self.n_terms)))
+        self._check(self.lib.dmrg_set_coeffs(self.h, c.ctypes.data))
+
+    def apply_H(self, psi, y=None, accumulate=False, prec="fp64", stream=None):
+        if y is None:
+            y = self.empty()
+        self._check(self.lib.dmrg_apply_H(self.h, _ptr(psi), _ptr(y), int(accumulate), _prec(prec),
+                                          _stream(stream)))
+        return y
+
+    def apply_H_backward(self, psi, g, want_dpsi=True, want_dc=True, prec="fp64", stream=None):
+        dpsi = self.empty() if want_dpsi else None
+        dc = torch.empty(self.batch, self.n_terms, dtype=torch.float64, device=self.device) if want_dc else None
+        self._check(self.lib.dmrg_apply_H_backward(self.h, _ptr(psi), _ptr(g), _ptr(dpsi), _ptr(dc),
+                                                   _prec(prec), _stream(stream)))
+        return dpsi, dc
+
+    def energy_grad(self, psi, prec="fp64", stream=None):
+        out = torch.empty(self.batch, self.n_terms, dtype=torch.float64, device=self.device)
+        self._check(self.lib.dmrg_energy_grad(self.h, _ptr(psi), _ptr(out), _prec(prec), _stream(stream)))
+        return out
+
+    def lanczos_ground(self, psi0, tol=1e-12, max_iter=300, prec="fp64", refine=True, refine_tol=1e-10,
+                       check_every=1, graph_iters=8, psi_out=None, stream=None):
+        if psi_out is None:
+            psi_out = self.empty()
+        e0 = np.zeros(self.batch)
+        info = (LanczosInfo * self.batch)()
+        opts = LanczosOpts(tol, max_iter, _prec(prec), int(refine), refine_tol, check_every, graph_iters)
+        st = self.lib.dmrg_lanczos_ground(self.h, _ptr(psi0), _ptr(psi_out), e0.ctypes.data, C.byref(opts),
+                                          info, _stream(stream))
+        infos = [{k: getattr(info[b], k) for k, _ in LanczosInfo._fields_} for b in range(self.batch)]
+        if st not in (0, 4):
+            self._check(st)
+        return e0, psi_out, infos, st
+
+
+class ApplyH(torch.autograd.Function):
+    """y = H(c) psi through the library; backward gives H^T g and <g, (A_k (x) B_k) psi>."""
+
+    @staticmethod
+    def forward(ctx, psi, coeffs, gsb: GpuSuperblock, prec="fp64"):
+        gsb.set_coeffs(coeffs.detach().cpu().numpy())
+        ctx.gsb = gsb
+        ctx.prec = prec
+        ctx.save_for_backward(psi)
+        return gsb.apply_H(psi.contiguous(), prec=prec)
+
+    @staticmethod
+    def backward(ctx, g):
+        (psi,) = ctx.saved_tensors
+        need_psi, need_c = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        dpsi, dc = ctx.gsb.apply_H_backward(psi, g.contiguous(), want_dpsi=need_psi, want_dc=need_c,
+                                            prec=ctx.prec)
+        return dpsi, dc, None, None
+
+
+def apply_H(psi, coeffs, gsb: GpuSuperblock, prec="fp64"):
+    return ApplyH.apply(psi, coeffs, gsb, prec)

@@ -1,0 +1,747 @@
+// C ABI of the superblock library: descriptor validation, device arenas,
+// the (term, sector pair) task lists, the product, its reverse mode, the
+// Hellmann-Feynman gradient and the graph-captured Lanczos driver.
+//
+// Paper Sec. 3.2 (symmetry blocks, partition), Sec. 3.3 (the on-the-fly
+// superblock product x += H y as system, environment and connection tasks;
+// Lanczos needs only that product).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "internal.h"
+#include "lanczos.h"
+#include "tc.h"
+
+using namespace dmrg;
+
+namespace {
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) throw CudaError{e_, #x}; \
+  } while (0)
+
+struct Invalid {
+  std::string msg;
+};
+
+template <class T>
+T* dalloc(size_t n) {
+  if (n == 0) n = 1;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, n * sizeof(T)));
+  return static_cast<T*>(p);
+}
+
+template <class T>
+void upload(T*& d, const std::vector<T>& h) {
+  if (d) cudaFree(d);
+  d = dalloc<T>(h.size());
+  if (!h.empty()) CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+template <class F>
+dmrg_status guard(dmrg_sb* sb, F&& fn) {
+  try {
+    return fn();
+  } catch (const CudaError& ce) {
+    if (sb) sb->err = std::string(ce.what) + ": " + cudaGetErrorString(ce.e);
+    return ce.e == cudaErrorMemoryAllocation ? DMRG_ENOMEM : DMRG_ECUDA;
+  } catch (const Invalid& iv) {
+    if (sb) sb->err = iv.msg;
+    return DMRG_EINVAL;
+  } catch (const std::bad_alloc&) {
+    if (sb) sb->err = "host allocation failed";
+    return DMRG_ENOMEM;
+  }
+}
+
+// ----------------------------------------------------------- task building
+struct SegSpec {
+  int32_t l_buf;
+  int64_t l_off;
+  int32_t ldl, l_trans;
+  int32_t r_buf;
+  int64_t r_off;
+  int32_t ldr, r_trans;
+  int32_t K, coef;
+};
+
+SegF64 mkseg(const SegSpec& s) {
+  SegF64 g{};
+  g.l_off = s.l_off;
+  g.r_off = s.r_off;
+  g.l_buf = s.l_buf;
+  g.r_buf = s.r_buf;
+  g.ldl = s.ldl;
+  g.ldr = s.ldr;
+  g.K = s.K;
+  g.l_trans = s.l_trans;
+  g.r_trans = s.r_trans;
+  g.coef = s.coef;
+  return g;
+}
+
+// Append the tiles of one M x N output and its segment list; returns the
+// positions (before sorting) of the new tiles.
+void add_output(TaskListF64& tl, int32_t c_buf, int64_t c_off, int32_t ldc, int32_t M, int32_t N, int32_t mode,
+                const std::vector<SegF64>& segs, std::vector<int64_t>* ids) {
+  if (M <= 0 || N <= 0) return;
+  const int32_t sb = (int32_t)tl.h_segs.size();
+  tl.h_segs.insert(tl.h_segs.end(), segs.begin(), segs.end());
+  const int32_t se = (int32_t)tl.h_segs.size();
+  for (int32_t m0 = 0; m0 < M; m0 += 64)
+    for (int32_t n0 = 0; n0 < N; n0 += 64) {
+      TileF64 t{};
+      t.c_off = c_off;
+      t.c_buf = c_buf;
+      t.ldc = ldc;
+      t.M = M;
+      t.N = N;
+      t.m0 = m0;
+      t.n0 = n0;
+      t.seg_begin = sb;
+      t.seg_end = se;
+      t.mode = mode;
+      if (ids) ids->push_back((int64_t)tl.h_tiles.size());
+      tl.h_tiles.push_back(t);
+    }
+}
+
+// Heaviest tiles first (one CTA per tile); returns new position of each old tile.
+std::vector<int64_t> sort_tiles(TaskListF64& tl) {
+  const size_t n = tl.h_tiles.size();
+  std::vector<int64_t> w(n), perm(n), where(n);
+  for (size_t i = 0; i < n; ++i) {
+    int64_t k = 0;
+    for (int32_t s = tl.h_tiles[i].seg_begin; s < tl.h_tiles[i].seg_end; ++s) k += tl.h_segs[s].K;
+    w[i] = k;
+  }
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return w[a] > w[b]; });
+  std::vector<TileF64> nt(n);
+  for (size_t i = 0; i < n; ++i) {
+    nt[i] = tl.h_tiles[perm[i]];
+    where[perm[i]] = (int64_t)i;
+  }
+  tl.h_tiles.swap(nt);
+  return where;
+}
+
+void finish(TaskListF64& tl) {
+  tl.n_tiles = (int64_t)tl.h_tiles.size();
+  upload(tl.d_tiles, tl.h_tiles);
+  upload(tl.d_segs, tl.h_segs);
+}
+
+void free_tl(TaskListF64& tl) {
+  if (tl.d_tiles) cudaFree(tl.d_tiles);
+  if (tl.d_segs) cudaFree(tl.d_segs);
+  tl.d_tiles = nullptr;
+  tl.d_segs = nullptr;
+}
+
+bool is_gemm_pair(const PairH& p) { return (p.flags & (DMRG_ID_A | DMRG_ID_B)) == 0; }
+
+void build_f64_tasks(dmrg_sb* sb) {
+  const int nt = sb->n_terms;
+  const auto& r = sb->r;
+  const auto& c = sb->c;
+  // intermediate offsets (per member), forward and transposed orders
+  std::vector<int64_t> toff_f(sb->pairs.size(), -1), toff_b(sb->pairs.size(), -1);
+  std::vector<int32_t> border(sb->pairs.size(), 0);
+  int64_t Tf = 0, Tb = 0;
+  for (size_t i = 0; i < sb->pairs.size(); ++i) {
+    const PairH& p = sb->pairs[i];
+    if (!is_gemm_pair(p)) continue;
+    const int64_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
+    toff_f[i] = Tf;
+    Tf += p.order == 0 ? ro * ci : ri * co;
+    const double c0 = 2.0 * ri * ro * co + 2.0 * ri * co * ci;  // (A^T G) B first
+    const double c1 = 2.0 * ro * co * ci + 2.0 * ri * ro * ci;  // A^T (G B) first
+    border[i] = c0 <= c1 ? 0 : 1;
+    toff_b[i] = Tb;
+    Tb += border[i] == 0 ? ri * co : ro * ci;
+  }
+  const int64_t Tm = std::max(Tf, Tb);
+  sb->T_elems = Tm * sb->batch;
+  if (sb->d_T) cudaFree(sb->d_T);
+  sb->d_T = dalloc<double>((size_t)sb->T_elems);
+
+  std::vector<std::vector<size_t>> by_out(sb->S), by_in(sb->S);
+  for (size_t i = 0; i < sb->pairs.size(); ++i) {
+    by_out[sb->pairs[i].s_out].push_back(i);
+    by_in[sb->pairs[i].s_in].push_back(i);
+  }
+  std::vector<int64_t> dot_ids;                 // tile id (pre-sort) per recorded entry
+  std::vector<std::vector<int64_t>> dot_list((size_t)sb->batch * nt);
+
+  for (int b = 0; b < sb->batch; ++b) {
+    const int64_t xb = (int64_t)b * sb->D;
+    const int64_t tb = (int64_t)b * Tm;
+    auto coef = [&](const PairH& p) { return b * nt + p.term; };
+    auto X = [&](int s) { return xb + sb->off[s]; };
+    // ---------------- forward and dot phase 1
+    for (size_t i = 0; i < sb->pairs.size(); ++i) {
+      const PairH& p = sb->pairs[i];
+      if (!is_gemm_pair(p)) continue;
+      const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
+      for (int pass = 0; pass < 2; ++pass) {
+        TaskListF64& tl = pass == 0 ? sb->f64_fwd1 : sb->f64_dot1;
+        const int32_t cf = pass == 0 ? coef(p) : -1;
+        if (p.order == 0) {  // T = A Psi_in  (r_out x c_in)
+          add_output(tl, BUF_T, tb + toff_f[i], ci, ro, ci, TM_STORE,
+                     {mkseg({BUF_OPS, p.a_off, ri, 0, BUF_X, X(p.s_in), ci, 0, ri, cf})}, nullptr);
+        } else {  // T = Psi_in B^T  (r_in x c_out)
+          add_output(tl, BUF_T, tb + toff_f[i], co, ri, co, TM_STORE,
+                     {mkseg({BUF_X, X(p.s_in), ci, 0, BUF_OPS, p.b_off, ci, 1, ci, cf})}, nullptr);
+        }
+      }
+    }
+    // forward phase-2 segments of one pair (coefficient cf for identity pairs)
+    auto fwd_seg = [&](size_t i, int32_t cf) {
+      const PairH& p = sb->pairs[i];
+      const int32_t ri = r[p.s_in], ci = c[p.s_in], co = c[p.s_out];
+      if (p.flags & DMRG_ID_B)
+        return mkseg({BUF_OPS, p.a_off, ri, 0, BUF_X, X(p.s_in), ci, 0, ri, cf});
+      if (p.flags & DMRG_ID_A)
+        return mkseg({BUF_X, X(p.s_in), ci, 0, BUF_OPS, p.b_off, ci, 1, ci, cf});
+      if (p.order == 0)
+        return mkseg({BUF_T, tb + toff_f[i], ci, 0, BUF_OPS, p.b_off, ci, 1, ci, -1});
+      return mkseg({BUF_OPS, p.a_off, ri, 0, BUF_T, tb + toff_f[i], co, 0, ri, -1});
+    };
+    // ---------------- forward phase 2: one output per sector
+    for (int s = 0; s < sb->S; ++s) {
+      if ((int64_t)r[s] * c[s] == 0) continue;
+      std::vector<SegF64> segs;
+      for (size_t i : by_out[s]) segs.push_back(fwd_seg(i, coef(sb->pairs[i])));
+      add_output(sb->f64_fwd2, BUF_Y, X(s), c[s], r[s], c[s], TM_STORE, segs, nullptr);
+    }
+    // ---------------- dot phase 2: one output per pair, dotted with G
+    for (size_t i = 0; i < sb->pairs.size(); ++i) {
+      const PairH& p = sb->pairs[i];
+      std::vector<int64_t> ids;
+      add_output(sb->f64_dot2, BUF_G, X(p.s_out), c[p.s_out], r[p.s_out], c[p.s_out], TM_DOT, {fwd_seg(i, -1)},
+                 &ids);
+      for (int64_t id : ids) dot_list[(size_t)b * nt + p.term].push_back(id);
+    }
+    // ---------------- transposed product: dpsi[s_in] += c A^T G[s_out] B
+    for (size_t i = 0; i < sb->pairs.size(); ++i) {
+      const PairH& p = sb->pairs[i];
+      if (!is_gemm_pair(p)) continue;
+      const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
+      if (border[i] == 0)  // T = c A^T G  (r_in x c_out)
+        add_output(sb->f64_bwd1, BUF_T, tb + toff_b[i], co, ri, co, TM_STORE,
+                   {mkseg({BUF_OPS, p.a_off, ri, 1, BUF_X, X(p.s_out), co, 0, ro, coef(p)})}, nullptr);
+      else  // T = c G B  (r_out x c_in)
+        add_output(sb->f64_bwd1, BUF_T, tb + toff_b[i], ci, ro, ci, TM_STORE,
+                   {mkseg({BUF_X, X(p.s_out), co, 0, BUF_OPS, p.b_off, ci, 0, co, coef(p)})}, nullptr);
+    }
+    for (int s = 0; s < sb->S; ++s) {
+      if ((int64_t)r[s] * c[s] == 0) continue;
+      std::vector<SegF64> segs;
+      for (size_t i : by_in[s]) {
+        const PairH& p = sb->pairs[i];
+        const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
+        if (p.flags & DMRG_ID_B)
+          segs.push_back(mkseg({BUF_OPS, p.a_off, ri, 1, BUF_X, X(p.s_out), co, 0, ro, coef(p)}));
+        else if (p.flags & DMRG_ID_A)
+          segs.push_back(mkseg({BUF_X, X(p.s_out), co, 0, BUF_OPS, p.b_off, ci, 0, co, coef(p)}));
+        else if (border[i] == 0)
+          segs.push_back(mkseg({BUF_T, tb + toff_b[i], co, 0, BUF_OPS, p.b_off, ci, 0, co, -1}));
+        else
+          segs.push_back(mkseg({BUF_OPS, p.a_off, ri, 1, BUF_T, tb + toff_b[i], ci, 0, ro, -1}));
+      }
+      add_output(sb->f64_bwd2, BUF_Y, X(s), c[s], r[s], c[s], TM_STORE, segs, nullptr);
+    }
+  }
+  sort_tiles(sb->f64_fwd1);
+  sort_tiles(sb->f64_fwd2);
+  sort_tiles(sb->f64_dot1);
+  sort_tiles(sb->f64_bwd1);
+  sort_tiles(sb->f64_bwd2);
+  const std::vector<int64_t> where = sort_tiles(sb->f64_dot2);
+  std::vector<int32_t> ptr(1, 0), idx;
+  for (auto& lst : dot_list) {
+    for (int64_t id : lst) idx.push_back((int32_t)where[id]);
+    ptr.push_back((int32_t)idx.size());
+  }
+  upload(sb->d_dot_red_ptr, ptr);
+  upload(sb->d_dot_red_idx, idx);
+  if (sb->d_dot_partial) cudaFree(sb->d_dot_partial);
+  sb->d_dot_partial = dalloc<double>((size_t)std::max<int64_t>(1, (int64_t)sb->f64_dot2.h_tiles.size()));
+  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1, &sb->f64_bwd2})
+    finish(*tl);
+}
+
+// ------------------------------------------------------------- products
+void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
+            cudaStream_t st) {
+  if (prec == DMRG_FP64) {
+    Bufs bufs{{const_cast<double*>(x), y, sb->d_T, sb->d_ops, nullptr}};
+    launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, 0, nullptr, skip, st);
+    launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, accumulate, nullptr, skip, st);
+  } else {
+    tc_matvec(sb, prec, x, y, accumulate, skip, st);
+  }
+  CK(cudaGetLastError());
+}
+
+void term_dots(dmrg_sb* sb, const double* psi, const double* g, double* dc, cudaStream_t st) {
+  Bufs bufs{{const_cast<double*>(psi), nullptr, sb->d_T, sb->d_ops, const_cast<double*>(g)}};
+  launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
+  launch_seg_gemm_f64(sb->f64_dot2, bufs, sb->d_coeffs, 0, sb->d_dot_partial, nullptr, st);
+  lz_launch_reduce_terms(sb->d_dot_partial, sb->d_dot_red_ptr, sb->d_dot_red_idx, dc, sb->batch * sb->n_terms, st);
+  CK(cudaGetLastError());
+}
+
+// --------------------------------------------------------------- Lanczos
+void lz_free(dmrg_sb* sb) {
+  for (int i = 0; i < 8; ++i)
+    if (sb->lz_graphs[i]) {
+      cudaGraphExecDestroy((cudaGraphExec_t)sb->lz_graphs[i]);
+      sb->lz_graphs[i] = nullptr;
+      sb->lz_graph_key[i] = 0;
+    }
+  for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_ab, sb->lz_s, sb->lz_out})
+    if (p) cudaFree(p);
+  if (sb->lz_ctl) cudaFree(sb->lz_ctl);
+  if (sb->h_ctl) cudaFreeHost(sb->h_ctl);
+  sb->lz_V = sb->lz_w = sb->lz_vcur = sb->lz_partial = sb->lz_h = sb->lz_ab = sb->lz_s = sb->lz_out = nullptr;
+  sb->lz_ctl = nullptr;
+  sb->h_ctl = nullptr;
+  sb->lz_cap = 0;
+}
+
+void lz_alloc(dmrg_sb* sb, int cap) {
+  if (cap <= sb->lz_cap) return;
+  lz_free(sb);
+  const int64_t D = sb->D, B = sb->batch;
+  sb->lz_nchunk = lz_nchunk(D);
+  sb->lz_V = dalloc<double>((size_t)(cap * B * D));
+  sb->lz_w = dalloc<double>((size_t)(B * D));
+  sb->lz_vcur = dalloc<double>((size_t)(B * D));
+  sb->lz_partial = dalloc<double>((size_t)(B * sb->lz_nchunk * cap));
+  sb->lz_h = dalloc<double>((size_t)(2 * B * cap));
+  sb->lz_ab = dalloc<double>((size_t)(2 * B * cap));
+  sb->lz_s = dalloc<double>((size_t)(B * cap));
+  sb->lz_out = dalloc<double>((size_t)(4 * B + 1));
+  sb->lz_ctl = dalloc<int32_t>((size_t)(LZ_CTL_MEMBER + 2 * B));
+  void* hp = nullptr;
+  CK(cudaMallocHost(&hp, sizeof(int32_t) * (LZ_CTL_MEMBER + 2 * B)));
+  sb->h_ctl = static_cast<int32_t*>(hp);
+  CK(cudaMemset(sb->lz_ab, 0, sizeof(double) * 2 * B * cap));
+  sb->lz_cap = cap;
+}
+
+// one Lanczos iteration for every running member (all on stream st)
+void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
+  const int64_t D = sb->D;
+  const int B = sb->batch, cap = sb->lz_cap, nch = sb->lz_nchunk;
+  int32_t* ctl = sb->lz_ctl;
+  matvec(sb, prec, sb->lz_vcur, sb->lz_w, 0, ctl + LZ_CTL_ALLDONE, st);
+  double* h1 = sb->lz_h;
+  double* h2 = sb->lz_h + (size_t)B * cap;
+  double* npart = sb->lz_partial;  // reused: the norm partials fit in the row partials
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, nch, st);
+  lz_launch_reduce_rows(sb->lz_partial, h1, ctl, nch, cap, B, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, h1, nullptr, ctl, D, B, cap, nch, st);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, nch, st);
+  lz_launch_reduce_rows(sb->lz_partial, h2, ctl, nch, cap, B, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, h2, npart, ctl, D, B, cap, nch, st);
+  lz_launch_finalize_ab(sb->lz_h, npart, sb->lz_ab, ctl, B, cap, nch, st);
+  lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, ctl, sb->lz_out + 4 * B, B, cap, D, st);  // tol at out[4B]
+  lz_launch_next_vector(sb->lz_w, sb->lz_ab, sb->lz_V, sb->lz_vcur, ctl, D, B, cap, st);
+  lz_launch_advance(ctl, B, st);
+  CK(cudaGetLastError());
+}
+
+cudaGraphExec_t lz_graph(dmrg_sb* sb, int prec, int K) {
+  const int key = 1 + prec * 1024 + K;
+  for (int i = 0; i < 8; ++i)
+    if (sb->lz_graphs[i] && sb->lz_graph_key[i] == key) return (cudaGraphExec_t)sb->lz_graphs[i];
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  try {
+    for (int k = 0; k < K; ++k) lz_enqueue_iteration(sb, prec, cs);
+  } catch (...) {
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    throw;
+  }
+  CK(cudaStreamEndCapture(cs, &g));
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  CK(e);
+  int slot = 0;
+  for (int i = 0; i < 8; ++i)
+    if (!sb->lz_graphs[i]) { slot = i; break; }
+  if (sb->lz_graphs[slot]) cudaGraphExecDestroy((cudaGraphExec_t)sb->lz_graphs[slot]);
+  sb->lz_graphs[slot] = ge;
+  sb->lz_graph_key[slot] = key;
+  return ge;
+}
+
+struct LzRun {
+  std::vector<int32_t> code, iters;
+  std::vector<double> theta, resid;
+  int64_t launches = 0;
+};
+
+int matvec_launches(const dmrg_sb* sb, int prec) {
+  if (prec == DMRG_FP64) return (sb->f64_fwd1.n_tiles > 0) + (sb->f64_fwd2.n_tiles > 0);
+  return tc_launches(sb, prec);
+}
+constexpr int LZ_KERNELS_PER_ITER = 10;  // everything in lz_enqueue_iteration besides the product
+
+// Lanczos from psi0 (device [batch][D]) to psi_out; returns per-member results.
+LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double tol, int max_iter,
+               int check_every, int graph_iters, cudaStream_t st) {
+  const int64_t D = sb->D;
+  const int B = sb->batch;
+  max_iter = (int)std::min<int64_t>(std::min(std::max(1, max_iter), 1024), D);
+  lz_alloc(sb, max_iter + 1);
+  const int cap = sb->lz_cap, nch = sb->lz_nchunk;
+  // v_0 = psi0 / |psi0|
+  double* part = sb->lz_partial;
+  double* nrm2 = sb->d_scratch;
+  lz_launch_sumsq(psi0, part, D, B, nch, st);
+  lz_launch_sum_chunks(part, nrm2, nch, B, st);
+  lz_launch_scale_unit(psi0, nrm2, sb->lz_V, sb->lz_vcur, D, B, st);
+  std::vector<int32_t> hc(LZ_CTL_MEMBER + 2 * B, 0);
+  hc[LZ_CTL_MAXIT] = max_iter;
+  hc[LZ_CTL_CHECK] = std::max(1, check_every);
+  CK(cudaMemcpyAsync(sb->lz_ctl, hc.data(), hc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sb->lz_out + 4 * B, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // host vectors above are stack memory
+  const int K = std::max(1, std::min(graph_iters, max_iter));
+  cudaGraphExec_t ge = lz_graph(sb, prec, K);
+  int launched = 0;
+  for (;;) {
+    CK(cudaGraphLaunch(ge, st));
+    launched += K;
+    CK(cudaMemcpyAsync(sb->h_ctl, sb->lz_ctl, sizeof(int32_t) * (LZ_CTL_MEMBER + 2 * B), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (sb->h_ctl[LZ_CTL_ALLDONE]) break;
+    if (launched > max_iter + K) throw Invalid{"Lanczos control did not terminate"};
+  }
+  lz_launch_ritz(sb->lz_V, sb->lz_s, sb->lz_ctl, psi_out, D, B, cap, st);
+  lz_launch_sumsq(psi_out, part, D, B, nch, st);
+  lz_launch_sum_chunks(part, nrm2, nch, B, st);
+  lz_launch_scale_unit(psi_out, nrm2, psi_out, nullptr, D, B, st);
+  std::vector<double> out(4 * B);
+  CK(cudaMemcpyAsync(out.data(), sb->lz_out, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  LzRun r;
+  r.launches = 3 + (int64_t)launched * (LZ_KERNELS_PER_ITER + matvec_launches(sb, prec)) + 4;
+  for (int b = 0; b < B; ++b) {
+    r.code.push_back(sb->h_ctl[LZ_CTL_MEMBER + b]);
+    r.iters.push_back(sb->h_ctl[LZ_CTL_MEMBER + B + b]);
+    r.theta.push_back(out[4 * b]);
+    r.resid.push_back(out[4 * b + 1]);
+  }
+  return r;
+}
+
+dmrg_status code_to_status(int code) {
+  switch (code) {
+    case LZ_CONVERGED: return DMRG_OK;
+    case LZ_BREAKDOWN: return DMRG_EBREAKDOWN;
+    case LZ_NAN: return DMRG_ENAN;
+    case LZ_CAP: return DMRG_ENOCONV;
+    default: return DMRG_ENOCONV;
+  }
+}
+
+void validate_and_copy(dmrg_sb* sb, const dmrg_sb_desc* d, int32_t batch) {
+  if (!d) throw Invalid{"null descriptor"};
+  if (batch < 1) throw Invalid{"batch must be >= 1"};
+  if (d->n_sectors < 0 || d->n_terms < 1 || d->n_pairs < 0) throw Invalid{"bad counts"};
+  if (d->n_sectors > 0 && (!d->r || !d->c)) throw Invalid{"null sector dims"};
+  if (!d->coeffs) throw Invalid{"null coeffs"};
+  if (d->n_pairs > 0 && !d->pairs) throw Invalid{"null pair list"};
+  sb->S = d->n_sectors;
+  sb->n_terms = d->n_terms;
+  sb->batch = batch;
+  sb->r.assign(d->r, d->r + sb->S);
+  sb->c.assign(d->c, d->c + sb->S);
+  sb->off.assign(sb->S + 1, 0);
+  for (int s = 0; s < sb->S; ++s) {
+    if (sb->r[s] < 0 || sb->c[s] < 0) throw Invalid{"negative sector dimension"};
+    sb->off[s + 1] = sb->off[s] + (int64_t)sb->r[s] * sb->c[s];
+  }
+  sb->D = sb->off[sb->S];
+  if (sb->D == 0) throw Invalid{"empty target space (D = 0)"};
+  sb->coeffs.assign(d->coeffs, d->coeffs + (size_t)batch * sb->n_terms);
+  // pairs: validate, lay out the float64 arena (ld = number of columns)
+  std::vector<const dmrg_pair*> keep;
+  int64_t ops = 0;
+  for (int i = 0; i < d->n_pairs; ++i) {
+    const dmrg_pair& p = d->pairs[i];
+    char buf[160];
+    if (p.term < 0 || p.term >= sb->n_terms || p.s_out < 0 || p.s_out >= sb->S || p.s_in < 0 || p.s_in >= sb->S) {
+      snprintf(buf, sizeof buf, "pair %d: term or sector out of range", i);
+      throw Invalid{buf};
+    }
+    if ((p.flags & DMRG_ID_A) && (p.flags & DMRG_ID_B)) {
+      snprintf(buf, sizeof buf, "pair %d: both sides identity", i);
+      throw Invalid{buf};
+    }
+    const int64_t ro = sb->r[p.s_out], ri = sb->r[p.s_in], co = sb->c[p.s_out], ci = sb->c[p.s_in];
+    if ((p.flags & DMRG_ID_A) && ro != ri) {
+      snprintf(buf, sizeof buf, "pair %d: identity A needs r[s_out] == r[s_in]", i);
+      throw Invalid{buf};
+    }
+    if ((p.flags & DMRG_ID_B) && co != ci) {
+      snprintf(buf, sizeof buf, "pair %d: identity B needs c[s_out] == c[s_in]", i);
+      throw Invalid{buf};
+    }
+    if (!(p.flags & DMRG_ID_A) && ro * ri > 0 && (!p.A || p.lda < ri)) {
+      snprintf(buf, sizeof buf, "pair %d: A missing or lda < r[s_in]", i);
+      throw Invalid{buf};
+    }
+    if (!(p.flags & DMRG_ID_B) && co * ci > 0 && (!p.B || p.ldb < ci)) {
+      snprintf(buf, sizeof buf, "pair %d: B missing or ldb < c[s_in]", i);
+      throw Invalid{buf};
+    }
+    if (ro * co == 0 || ri * ci == 0) continue;  // touches an empty sector: contributes nothing
+    keep.push_back(&p);
+    if (!(p.flags & DMRG_ID_A)) ops += ro * ri;
+    if (!(p.flags & DMRG_ID_B)) ops += co * ci;
+  }
+  sb->ops_elems = ops;
+  std::vector<double> host((size_t)std::max<int64_t>(ops, 1));
+  int64_t pos = 0;
+  sb->flops = 0;
+  for (const dmrg_pair* pp : keep) {
+    const dmrg_pair& p = *pp;
+    PairH h{};
+    h.term = p.term;
+    h.s_out = p.s_out;
+    h.s_in = p.s_in;
+    h.flags = p.flags & (DMRG_ID_A | DMRG_ID_B);
+    const int64_t ro = sb->r[p.s_out], ri = sb->r[p.s_in], co = sb->c[p.s_out], ci = sb->c[p.s_in];
+    h.a_off = h.b_off = -1;
+    auto copy_block = [&](const double* src, int64_t ld, int64_t rows, int64_t cols) {
+      const int64_t at = pos;
+      if (d->blocks_on_device) {
+        CK(cudaMemcpy2D(host.data() + pos, cols * sizeof(double), src, ld * sizeof(double), cols * sizeof(double),
+                        rows, cudaMemcpyDeviceToHost));
+      } else {
+        for (int64_t i = 0; i < rows; ++i) memcpy(host.data() + pos + i * cols, src + i * ld, cols * sizeof(double));
+      }
+      pos += rows * cols;
+      return at;
+    };
+    if (!(h.flags & DMRG_ID_A)) h.a_off = copy_block(p.A, p.lda, ro, ri);
+    if (!(h.flags & DMRG_ID_B)) h.b_off = copy_block(p.B, p.ldb, co, ci);
+    if (h.flags & DMRG_ID_A) sb->flops += 2.0 * ro * ci * co;
+    else if (h.flags & DMRG_ID_B) sb->flops += 2.0 * ro * ri * co;
+    else {
+      const double c0 = 2.0 * ro * ri * ci + 2.0 * ro * ci * co;  // (A Psi) B^T
+      const double c1 = 2.0 * ri * ci * co + 2.0 * ro * ri * co;  // A (Psi B^T)
+      h.order = c0 <= c1 ? 0 : 1;
+      sb->flops += std::min(c0, c1);
+    }
+    sb->pairs.push_back(h);
+  }
+  sb->d_ops = dalloc<double>((size_t)std::max<int64_t>(ops, 1));
+  if (ops) CK(cudaMemcpy(sb->d_ops, host.data(), ops * sizeof(double), cudaMemcpyHostToDevice));
+  upload(sb->d_coeffs, sb->coeffs);
+  sb->d_scratch = dalloc<double>((size_t)(4 * batch + 16));
+  sb->d_red = dalloc<double>((size_t)batch * lz_nchunk(sb->D));
+}
+
+void destroy(dmrg_sb* sb) {
+  if (!sb) return;
+  lz_free(sb);
+  tc_free(sb);
+  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1, &sb->f64_bwd2})
+    free_tl(*tl);
+  for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red})
+    if (p) cudaFree(p);
+  if (sb->d_dot_red_ptr) cudaFree(sb->d_dot_red_ptr);
+  if (sb->d_dot_red_idx) cudaFree(sb->d_dot_red_idx);
+  delete sb;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+dmrg_status dmrg_create_superblock(const dmrg_sb_desc* d, int32_t batch, dmrg_sb** out) {
+  if (!out) return DMRG_EINVAL;
+  *out = nullptr;
+  dmrg_sb* sb = new (std::nothrow) dmrg_sb();
+  if (!sb) return DMRG_ENOMEM;
+  const dmrg_status st = guard(sb, [&] {
+    validate_and_copy(sb, d, batch);
+    build_f64_tasks(sb);
+    tc_build(sb);
+    CK(cudaDeviceSynchronize());
+    return DMRG_OK;
+  });
+  if (st != DMRG_OK) {
+    static thread_local std::string last;
+    last = sb->err;
+    destroy(sb);
+    fprintf(stderr, "dmrg_create_superblock: %s\n", last.c_str());
+    return st;
+  }
+  *out = sb;
+  return DMRG_OK;
+}
+
+void dmrg_destroy_superblock(dmrg_sb* sb) { destroy(sb); }
+
+const char* dmrg_last_error(const dmrg_sb* sb) { return sb ? sb->err.c_str() : "null superblock"; }
+
+dmrg_status dmrg_query(const dmrg_sb* sb, dmrg_sb_info* info) {
+  if (!sb || !info) return DMRG_EINVAL;
+  info->dim = sb->D;
+  info->batch = sb->batch;
+  info->n_sectors = sb->S;
+  info->n_terms = sb->n_terms;
+  info->n_pairs = (int32_t)sb->pairs.size();
+  info->flops_per_matvec = sb->flops * sb->batch;
+  info->op_bytes_f64 = (double)sb->ops_elems * 8.0;
+  info->op_bytes_mixed = tc_operand_bytes(sb);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs) {
+  if (!sb || !coeffs) return DMRG_EINVAL;
+  return guard(sb, [&] {
+    sb->coeffs.assign(coeffs, coeffs + (size_t)sb->batch * sb->n_terms);
+    CK(cudaMemcpy(sb->d_coeffs, sb->coeffs.data(), sb->coeffs.size() * sizeof(double), cudaMemcpyHostToDevice));
+    tc_set_coeffs(sb);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_apply_H(dmrg_sb* sb, const double* psi, double* y, int32_t accumulate, int32_t prec,
+                         void* stream) {
+  if (!sb) return DMRG_EINVAL;
+  if (!psi || !y || psi == y) {
+    sb->err = "apply_H: null or aliased psi / y";
+    return DMRG_EINVAL;
+  }
+  if (prec < DMRG_FP64 || prec > DMRG_BF16X3) {
+    sb->err = "apply_H: unknown precision";
+    return DMRG_EINVAL;
+  }
+  if (prec != DMRG_FP64 && !tc_available(sb)) {
+    sb->err = "apply_H: tensor-core path not available on this device";
+    return DMRG_EUNSUPPORTED;
+  }
+  return guard(sb, [&] {
+    matvec(sb, prec, psi, y, accumulate ? 1 : 0, nullptr, (cudaStream_t)stream);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* g, double* dpsi, double* dc,
+                                  int32_t prec, void* stream) {
+  if (!sb) return DMRG_EINVAL;
+  if (!g || (dc && !psi) || (dpsi && dpsi == g)) {
+    sb->err = "apply_H_backward: bad pointers";
+    return DMRG_EINVAL;
+  }
+  if (prec < DMRG_FP64 || prec > DMRG_BF16X3) return DMRG_EINVAL;
+  return guard(sb, [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dpsi) {
+      if (prec == DMRG_FP64 || !tc_available(sb)) {
+        Bufs bufs{{const_cast<double*>(g), dpsi, sb->d_T, sb->d_ops, nullptr}};
+        launch_seg_gemm_f64(sb->f64_bwd1, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
+        launch_seg_gemm_f64(sb->f64_bwd2, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
+      } else {
+        tc_matvec_T(sb, prec, g, dpsi, st);
+      }
+    }
+    if (dc) term_dots(sb, psi, g, dc, st);
+    CK(cudaGetLastError());
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int32_t prec, void* stream) {
+  if (!sb || !psi || !dE_dc) return DMRG_EINVAL;
+  (void)prec;
+  return guard(sb, [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    term_dots(sb, psi, psi, dE_dc, st);
+    const int nch = lz_nchunk(sb->D);
+    lz_launch_sumsq(psi, sb->d_red, sb->D, sb->batch, nch, st);
+    lz_launch_sum_chunks(sb->d_red, sb->d_scratch, nch, sb->batch, st);
+    lz_launch_div_rows(dE_dc, sb->d_scratch, sb->n_terms, sb->batch, st);
+    CK(cudaGetLastError());
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0,
+                                const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info, void* stream) {
+  if (!sb || !psi0 || !psi_out || !e0 || !opts) return DMRG_EINVAL;
+  if (opts->prec < DMRG_FP64 || opts->prec > DMRG_BF16X3 || !(opts->tol > 0) || opts->max_iter < 1) {
+    sb->err = "lanczos: bad options";
+    return DMRG_EINVAL;
+  }
+  if (opts->prec != DMRG_FP64 && !tc_available(sb)) {
+    sb->err = "lanczos: tensor-core path not available on this device";
+    return DMRG_EUNSUPPORTED;
+  }
+  return guard(sb, [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = sb->batch;
+    const int ge = std::max(1, opts->graph_iters);
+    LzRun r = lz_solve(sb, psi0, psi_out, opts->prec, opts->tol, opts->max_iter, opts->check_every, ge, st);
+    std::vector<int32_t> refine_iters(B, 0);
+    LzRun rr;
+    const bool refine = opts->prec != DMRG_FP64 && opts->refine;
+    if (refine) {
+      rr = lz_solve(sb, psi_out, psi_out, DMRG_FP64, opts->refine_tol > 0 ? opts->refine_tol : 1e-10,
+                    opts->max_iter, opts->check_every, ge, st);
+    }
+    dmrg_status worst = DMRG_OK;
+    for (int b = 0; b < B; ++b) {
+      const LzRun& fin = refine ? rr : r;
+      dmrg_status s = code_to_status(fin.code[b]);
+      const dmrg_status report = s == DMRG_EBREAKDOWN ? DMRG_OK : s;
+      if (report != DMRG_OK && worst == DMRG_OK) worst = report;
+      e0[b] = fin.theta[b];
+      if (info) {
+        info[b].e0 = fin.theta[b];
+        info[b].residual = fin.resid[b];
+        info[b].iters = r.iters[b];
+        info[b].refine_iters = refine ? rr.iters[b] : 0;
+        info[b].mixed_matvecs = opts->prec != DMRG_FP64 ? r.iters[b] : 0;
+        info[b].fp64_matvecs = opts->prec == DMRG_FP64 ? r.iters[b] : (refine ? rr.iters[b] : 0);
+        info[b].status = s;
+        info[b].breakdown = fin.code[b] == LZ_BREAKDOWN;
+        info[b].kernel_launches = (int32_t)(r.launches + (refine ? rr.launches : 0));
+      }
+    }
+    return worst;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal types of the superblock library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dmrg_gb300.h"
+
+namespace dmrg {
+
+// ---------------------------------------------------------------- FP64 path
+// Buffers a task can address.  Offsets are in elements, so one task list
+// serves every call whatever the caller's pointers are.
+enum BufId : int32_t { BUF_X = 0, BUF_Y = 1, BUF_T = 2, BUF_OPS = 3, BUF_G = 4, NBUF = 5 };
+
+struct Bufs {
+  double* p[NBUF];
+};
+
+// One product L (M x K) * R (K x N) scaled by `scale`, added into the tile.
+struct SegF64 {
+  int64_t l_off, r_off;
+  int32_t l_buf, r_buf;
+  int32_t ldl, ldr;
+  int32_t K;
+  int32_t l_trans;  // 0: L(m,k) = X[m*ldl + k]; 1: L(m,k) = X[k*ldl + m]
+  int32_t r_trans;  // 0: R(k,n) = X[k*ldr + n]; 1: R(k,n) = X[n*ldr + k]
+  int32_t coef;     // index into the coefficient table, -1 = 1.0
+};
+
+// One output tile C[m0:m0+64, n0:n0+64] of an M x N matrix.
+enum TileMode : int32_t { TM_STORE = 0, TM_DOT = 2 };
+struct TileF64 {
+  int64_t c_off;
+  int32_t c_buf, ldc;
+  int32_t M, N, m0, n0;
+  int32_t seg_begin, seg_end;
+  int32_t mode;  // TM_STORE: C = acc (or C += acc when the launch accumulates); TM_DOT: sum(acc .* C)
+  int32_t pad;
+};
+
+struct TaskListF64 {
+  std::vector<TileF64> h_tiles;
+  std::vector<SegF64> h_segs;
+  TileF64* d_tiles = nullptr;
+  SegF64* d_segs = nullptr;
+  int64_t n_tiles = 0;
+};
+
+// skip: optional device flag; when *skip != 0 the launch does nothing
+void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef,
+                         int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
+
+// ------------------------------------------------------------ host pair info
+struct PairH {
+  int32_t term, s_out, s_in, flags;
+  int64_t a_off, b_off;  // element offsets in the FP64 operator arena (ld = cols)
+  int32_t order;         // two-GEMM pairs: 0 = (A Psi) B^T first A, 1 = A (Psi B^T)
+};
+
+}  // namespace dmrg
+
+// ------------------------------------------------------------ the superblock
+struct dmrg_sb {
+  int32_t S = 0, n_terms = 0, batch = 0;
+  std::vector<int32_t> r, c;
+  std::vector<int64_t> off;  // [S+1]
+  int64_t D = 0;
+  std::vector<double> coeffs;  // host [batch][n_terms]
+  double* d_coeffs = nullptr;  // device [batch][n_terms]
+  std::vector<dmrg::PairH> pairs;
+  double* d_ops = nullptr;     // FP64 operator arena
+  int64_t ops_elems = 0;
+  double flops = 0;            // algorithmic flops of one product, one member
+
+  // FP64 task lists
+  dmrg::TaskListF64 f64_fwd1, f64_fwd2;   // forward: phase 1 (intermediates), phase 2 (outputs)
+  dmrg::TaskListF64 f64_bwd1, f64_bwd2;   // H^T g
+  dmrg::TaskListF64 f64_dot1, f64_dot2;   // per-pair <g, A psi B^T>
+  double* d_T = nullptr;                  // FP64 intermediate workspace
+  int64_t T_elems = 0;
+  // term reduction of dot tiles: for (b, k): tile range [dot_red_ptr[bk], dot_red_ptr[bk+1])
+  int32_t* d_dot_red_ptr = nullptr;
+  int32_t* d_dot_red_idx = nullptr;
+  double* d_dot_partial = nullptr;
+  double* d_scratch = nullptr;  // small reduction scratch (batch norms)
+  double* d_red = nullptr;      // [batch][chunks] reduction partials outside Lanczos
+
+  // Lanczos state (allocated on first use)
+  int32_t lz_cap = 0;  // Krylov capacity (max_iter + 1)
+  double* lz_V = nullptr;        // [lz_cap][batch][D]
+  double* lz_w = nullptr;        // [batch][D]
+  double* lz_vcur = nullptr;     // [batch][D]
+  double* lz_partial = nullptr;  // [batch][nchunk][lz_cap]
+  double* lz_h = nullptr;        // [2][batch][lz_cap]
+  double* lz_ab = nullptr;       // alpha [batch][lz_cap], beta [batch][lz_cap]
+  double* lz_s = nullptr;        // Ritz vector [batch][lz_cap]
+  double* lz_out = nullptr;      // per member: theta, resid
+  int32_t* lz_ctl = nullptr;     // device control words
+  int32_t* h_ctl = nullptr;      // pinned host mirror
+  int32_t lz_nchunk = 0;
+  void* lz_graphs[8] = {};       // cached cudaGraphExec_t per (prec, K) slot
+  int32_t lz_graph_key[8] = {};
+
+  void* tc = nullptr;            // tensor-core path state (matvec_tc.cu)
+
+  std::string err;
+};

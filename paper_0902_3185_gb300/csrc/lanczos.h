@@ -1,0 +1,46 @@
+// Launchers and constants of the float64 Lanczos kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace dmrg {
+
+constexpr int LZ_THREADS = 256;   // threads of the vector kernels
+constexpr int LZ_EPT = 4;         // elements per thread
+constexpr int LZ_CHUNK = LZ_THREADS * LZ_EPT;
+constexpr int LZ_ROWS = 4;        // Krylov rows reduced together in k_multidot
+constexpr int LZ_TRI = 64;        // threads of the tridiagonal multisection
+
+enum LzCtl : int { LZ_CTL_J = 0, LZ_CTL_MAXIT = 1, LZ_CTL_CHECK = 2, LZ_CTL_ALLDONE = 3, LZ_CTL_MEMBER = 4 };
+enum LzCode : int { LZ_RUNNING = 0, LZ_CONVERGED = 1, LZ_BREAKDOWN = 2, LZ_NAN = 3, LZ_CAP = 4 };
+
+inline int lz_nchunk(int64_t D) { return (int)((D + LZ_CHUNK - 1) / LZ_CHUNK); }
+
+void lz_launch_multidot(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
+                        int batch, int cap, int nchunk, cudaStream_t st);
+void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
+                           int batch, cudaStream_t st);
+void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
+                         const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, cudaStream_t st);
+void lz_launch_finalize_ab(const double* h, const double* norm_partial, double* ab, const int32_t* ctl,
+                           int batch, int cap, int nchunk, cudaStream_t st);
+void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
+                       int cap, int64_t D, cudaStream_t st);
+void lz_launch_next_vector(const double* w, const double* ab, double* V, double* vcur, const int32_t* ctl,
+                           int64_t D, int batch, int cap, cudaStream_t st);
+void lz_launch_advance(int32_t* ctl, int batch, cudaStream_t st);
+void lz_launch_sumsq(const double* x, double* part, int64_t D, int batch, int nchunk, cudaStream_t st);
+void lz_launch_dot(const double* x, const double* y, double* part, int64_t D, int batch, int nchunk,
+                   cudaStream_t st);
+void lz_launch_sum_chunks(const double* part, double* res, int nchunk, int batch, cudaStream_t st);
+void lz_launch_scale_unit(const double* x, const double* nrm2, double* y, double* y2, int64_t D, int batch,
+                          cudaStream_t st);
+void lz_launch_ritz(const double* V, const double* s, const int32_t* ctl, double* out, int64_t D, int batch,
+                    int cap, cudaStream_t st);
+void lz_launch_div_rows(double* v, const double* nrm2, int n_terms, int batch, cudaStream_t st);
+void lz_launch_reduce_terms(const double* part, const int32_t* ptr, const int32_t* idx, double* out, int n,
+                            cudaStream_t st);
+
+}  // namespace dmrg

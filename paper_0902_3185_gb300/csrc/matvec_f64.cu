@@ -1,0 +1,132 @@
+// Grouped FP64 sector GEMM: every (term, sector pair) product of the
+// superblock Hamiltonian in one launch, on the CUDA cores in float64.
+//
+// Paper Sec. 3.3: the product x += H y is done per symmetry block, on the
+// fly, as system, environment and connection parts.  Here each output tile
+// of a block Y_s (or of an intermediate A Psi / Psi B^T) walks over a list of
+// segments, each a plain product L (M x K) * R (K x N) with its own layout
+// and coefficient, and accumulates them in registers.  One tile writes each
+// output element exactly once, so results do not depend on scheduling.
+//
+// Tile 64 x 64, K step 16, 256 threads with a 4 x 4 register block each
+// (rows ty + 16 i, cols tx + 16 j).  GB300 runs float64 at a small fraction
+// of its FP32 rate, so this kernel is bound by DFMA issue, not by memory.
+
+#include "internal.h"
+
+namespace dmrg {
+
+constexpr int F64_BM = 64, F64_BN = 64, F64_BK = 16, F64_THREADS = 256;
+
+__global__ void __launch_bounds__(F64_THREADS)
+seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs,
+                    Bufs bufs, const double* __restrict__ coef, int accumulate,
+                    double* __restrict__ dot_out, const int32_t* __restrict__ skip) {
+  __shared__ double Ls[F64_BK][F64_BM + 1];
+  __shared__ double Rs[F64_BK][F64_BN + 1];
+  __shared__ double red[F64_THREADS / 32];
+
+  if (skip && *skip) return;
+  const TileF64 t = tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int sg = t.seg_begin; sg < t.seg_end; ++sg) {
+    const SegF64 s = segs[sg];
+    const double* L = bufs.p[s.l_buf] + s.l_off;
+    const double* R = bufs.p[s.r_buf] + s.r_off;
+    const double scale = s.coef >= 0 ? coef[s.coef] : 1.0;
+    for (int k0 = 0; k0 < s.K; k0 += F64_BK) {
+#pragma unroll
+      for (int e = 0; e < (F64_BM * F64_BK) / F64_THREADS; ++e) {
+        const int idx = tid + e * F64_THREADS;
+        int m, k;
+        if (s.l_trans) { k = idx / F64_BM; m = idx % F64_BM; }
+        else { m = idx / F64_BK; k = idx % F64_BK; }
+        const int gm = t.m0 + m, gk = k0 + k;
+        double v = 0.0;
+        if (gm < t.M && gk < s.K)
+          v = s.l_trans ? L[(int64_t)gk * s.ldl + gm] : L[(int64_t)gm * s.ldl + gk];
+        Ls[k][m] = v * scale;
+      }
+#pragma unroll
+      for (int e = 0; e < (F64_BN * F64_BK) / F64_THREADS; ++e) {
+        const int idx = tid + e * F64_THREADS;
+        int n, k;
+        if (s.r_trans) { n = idx / F64_BK; k = idx % F64_BK; }
+        else { k = idx / F64_BN; n = idx % F64_BN; }
+        const int gn = t.n0 + n, gk = k0 + k;
+        double v = 0.0;
+        if (gn < t.N && gk < s.K)
+          v = s.r_trans ? R[(int64_t)gn * s.ldr + gk] : R[(int64_t)gk * s.ldr + gn];
+        Rs[k][n] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < F64_BK; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = Ls[k][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Rs[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+
+  double* C = bufs.p[t.c_buf] + t.c_off;
+  if (t.mode == TM_STORE) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = t.m0 + ty + 16 * i;
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = t.n0 + tx + 16 * j;
+        if (n >= t.N) continue;
+        double* p = C + (int64_t)m * t.ldc + n;
+        *p = accumulate ? *p + acc[i][j] : acc[i][j];
+      }
+    }
+  } else {  // TM_DOT: sum over the tile of acc .* C, fixed-order block reduction
+    double part = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = t.m0 + ty + 16 * i;
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = t.n0 + tx + 16 * j;
+        if (n >= t.N) continue;
+        part = fma(acc[i][j], C[(int64_t)m * t.ldc + n], part);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < F64_THREADS / 32; ++w) tot += red[w];
+      dot_out[blockIdx.x] = tot;
+    }
+  }
+}
+
+void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef,
+                         int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st) {
+  if (tl.n_tiles == 0) return;
+  seg_gemm_f64_kernel<<<(unsigned)tl.n_tiles, F64_THREADS, 0, st>>>(
+      tl.d_tiles, tl.d_segs, bufs, coef, accumulate, dot_out, skip);
+}
+
+}  // namespace dmrg

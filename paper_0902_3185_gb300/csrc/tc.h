@@ -1,0 +1,22 @@
+// Tensor-core (tcgen05) path of the superblock product: mixed precision.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+struct dmrg_sb;
+
+namespace dmrg {
+
+void tc_build(dmrg_sb* sb);      // operand panels and task lists (no-op when unsupported)
+void tc_free(dmrg_sb* sb);
+bool tc_available(const dmrg_sb* sb);
+void tc_set_coeffs(dmrg_sb* sb);
+double tc_operand_bytes(const dmrg_sb* sb);
+int tc_launches(const dmrg_sb* sb, int prec);  // kernels one product launches
+void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
+               cudaStream_t st);
+void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st);
+
+}  // namespace dmrg

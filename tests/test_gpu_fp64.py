@@ -1,0 +1,176 @@
+"""GPU parity of the float64 path against the CPU oracle, through the C ABI.
+
+Tolerances (float64 products, different summation order than NumPy):
+element-wise |y_gpu - y_oracle| <= 1e-12 * max|y_oracle| for the product,
+its transpose and the term dots; |dE0| <= 1e-10 * |E0| for Lanczos
+(the paper's solver tolerance is the residual; the energy error is its
+square over the gap), and psi within 1e-7 up to sign.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dmrg, grad as ograd, lanczos as olz, superblock as osb
+from workloads.grown import grown_hubbard_superblock, ladder_m1000
+from workloads.superblock import seeded_normal
+from workloads.synthetic import ragged_small, random_sectored
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0902_3185_gb300 import binding
+    binding.load()
+    return torch.device("cuda:0")
+
+
+def gpu_sb(sb):
+    from paper_0902_3185_gb300.binding import GpuSuperblock
+    return GpuSuperblock(sb)
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def close(a, b, rel=1e-12):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = max(1.0, float(np.abs(b).max()) if b.size else 1.0)
+    return float(np.abs(a - b).max() if a.size else 0.0) <= rel * scale
+
+
+def heis16_superblock():
+    model = dmrg.heisenberg_chain()
+    steps, _, _ = dmrg.infinite_dmrg(model, 16, m=32, keep_superblocks=True)
+    return steps[-1].superblock
+
+
+CASES = {
+    "ragged": lambda: ragged_small(seed=1, batch=3),
+    "random16": lambda: random_sectored(seed=4, n_sectors=16, dmin=1, dmax=200, identity_terms=True, batch=2),
+    "heis16_m32": heis16_superblock,
+    "hub_ladder_grown": lambda: grown_hubbard_superblock(12, "ladder", 5, 5, m=60, cut=6, U_values=[4.0, 8.0]),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_H_fp64(dev, name):
+    sb = CASES[name]()
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(10 + b, sb.dim) for b in range(sb.batch)])
+    y = g.apply_H(to_dev(X)).cpu().numpy()
+    for b in range(sb.batch):
+        assert close(y[b], osb.apply_H(sb, X[b], b)), (name, b)
+    # accumulate mode: y += H psi
+    y0 = np.stack([seeded_normal(50 + b, sb.dim) for b in range(sb.batch)])
+    yt = to_dev(y0)
+    g.apply_H(to_dev(X), y=yt, accumulate=True)
+    yt = yt.cpu().numpy()
+    for b in range(sb.batch):
+        assert close(yt[b], y0[b] + osb.apply_H(sb, X[b], b))
+
+
+@pytest.mark.parametrize("name", ["ragged", "random16", "hub_ladder_grown"])
+def test_backward_and_term_dots_fp64(dev, name):
+    sb = CASES[name]()
+    g = gpu_sb(sb)
+    P = np.stack([seeded_normal(20 + b, sb.dim) for b in range(sb.batch)])
+    G = np.stack([seeded_normal(30 + b, sb.dim) for b in range(sb.batch)])
+    dpsi, dc = g.apply_H_backward(to_dev(P), to_dev(G))
+    dpsi, dc = dpsi.cpu().numpy(), dc.cpu().numpy()
+    for b in range(sb.batch):
+        assert close(dpsi[b], osb.apply_HT(sb, G[b], b))
+        assert close(dc[b], osb.term_products(sb, G[b], P[b]))
+
+
+def test_empty_and_uncoupled_sectors(dev):
+    sb = ragged_small(seed=3)
+    g = gpu_sb(sb)
+    y = g.apply_H(to_dev(seeded_normal(0, sb.dim)[None])).cpu().numpy()[0]
+    off = sb.offsets()
+    assert np.all(y[off[6]:off[7]] == 0.0)
+
+
+def test_energy_grad_fp64(dev):
+    sb = CASES["hub_ladder_grown"]()
+    g = gpu_sb(sb)
+    P = np.stack([seeded_normal(7 + b, sb.dim) for b in range(sb.batch)])
+    out = g.energy_grad(to_dev(P)).cpu().numpy()
+    for b in range(sb.batch):
+        assert close(out[b], ograd.hf_grad(sb.with_coeffs(sb.coeffs[b:b + 1]), P[b]))
+
+
+@pytest.mark.parametrize("name", ["heis16_m32", "hub_ladder_grown"])
+def test_lanczos_fp64_matches_oracle(dev, name):
+    sb = CASES[name]()
+    g = gpu_sb(sb)
+    P0 = np.stack([seeded_normal(b, sb.dim) for b in range(sb.batch)])
+    e0, psi, infos, st = g.lanczos_ground(to_dev(P0), tol=1e-12, max_iter=300, prec="fp64")
+    assert st == 0, infos
+    psi = psi.cpu().numpy()
+    for b in range(sb.batch):
+        ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v, b), P0[b], tol=1e-12, max_iter=300)
+        assert abs(e0[b] - ref.e0) <= 1e-10 * abs(ref.e0), (b, e0[b], ref.e0)
+        d = min(np.linalg.norm(psi[b] - ref.psi), np.linalg.norm(psi[b] + ref.psi))
+        assert d < 1e-7
+        th, res = olz.rayleigh(lambda v: osb.apply_H(sb, v, b), psi[b])
+        assert res < 1e-9 * max(1.0, abs(th))
+
+
+def test_lanczos_fp64_heis16_against_exact(dev):
+    # last infinite-DMRG superblock of the L = 16, m = 32 chain: variational,
+    # within the truncation error of the exact energy -6.911737145575
+    sb = CASES["heis16_m32"]()
+    g = gpu_sb(sb)
+    e0, _, _, st = g.lanczos_ground(to_dev(seeded_normal(0, sb.dim)[None]), tol=1e-12)
+    assert st == 0
+    assert -6.911737145575 - 1e-10 <= e0[0] < -6.911737145575 + 1e-3
+
+
+def test_lanczos_cap_reports_noconv(dev):
+    sb = CASES["hub_ladder_grown"]()
+    g = gpu_sb(sb)
+    e0, psi, infos, st = g.lanczos_ground(to_dev(seeded_normal(0, sb.dim)[None].repeat(sb.batch, 0)),
+                                          tol=1e-14, max_iter=3)
+    assert st == 4 and all(i["status"] == 4 and i["iters"] == 3 for i in infos)
+
+
+def test_lanczos_breakdown_exact(dev):
+    # a start vector inside a small invariant subspace: the Krylov space closes
+    sb = ragged_small(seed=1)
+    g = gpu_sb(sb)
+    off = sb.offsets()
+    x = np.zeros(sb.dim)
+    x[off[0]:off[1]] = 1.0  # 1x1 sector 0: H maps it into sectors it couples to
+    e0, psi, infos, st = g.lanczos_ground(to_dev(x[None]), tol=1e-13, max_iter=400)
+    ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v), x, tol=1e-13, max_iter=400)
+    assert abs(e0[0] - ref.e0) <= 1e-9 * max(1, abs(ref.e0))
+
+
+def test_set_coeffs_and_autograd(dev):
+    from paper_0902_3185_gb300.binding import apply_H
+    sb = ragged_small(seed=2, tiny=True)
+    g = gpu_sb(sb)
+    psi = torch.from_numpy(seeded_normal(0, sb.dim)[None]).cuda().requires_grad_(True)
+    c = torch.from_numpy(sb.coeffs.copy()).cuda().requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda p, cc: apply_H(p, cc, g), (psi, c), eps=1e-6, atol=1e-7)
+    c2 = sb.coeffs * 1.7
+    g.set_coeffs(c2)
+    y = g.apply_H(psi.detach()).cpu().numpy()[0]
+    assert close(y, osb.apply_H(sb.with_coeffs(c2), psi.detach().cpu().numpy()[0]))
+
+
+@pytest.mark.slow
+def test_full_size_ladder_m1000_sampled(dev):
+    """The 2 x 32 ladder at m = 1000, 16 members: float64 product of two
+    members against the oracle, every element."""
+    sb = ladder_m1000(batch=16)
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(100 + b, sb.dim) for b in range(sb.batch)])
+    y = g.apply_H(to_dev(X)).cpu().numpy()
+    for b in (0, 15):
+        assert close(y[b], osb.apply_H(sb, X[b], b))
