@@ -220,9 +220,11 @@ class ApplyH(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, psi, coeffs, gsb: GpuSuperblock, prec="fp64"):
-        gsb.set_coeffs(coeffs.detach().cpu().numpy())
+        c = coeffs.detach().cpu().numpy().copy()
+        gsb.set_coeffs(c)
         ctx.gsb = gsb
         ctx.prec = prec
+        ctx.coeffs = c  # the library holds one coefficient table: restore it for backward
         ctx.save_for_backward(psi)
         return gsb.apply_H(psi.contiguous(), prec=prec)
 
@@ -230,6 +232,7 @@ class ApplyH(torch.autograd.Function):
     def backward(ctx, g):
         (psi,) = ctx.saved_tensors
         need_psi, need_c = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        ctx.gsb.set_coeffs(ctx.coeffs)
         dpsi, dc = ctx.gsb.apply_H_backward(psi, g.contiguous(), want_dpsi=need_psi, want_dc=need_c,
                                             prec=ctx.prec)
         return dpsi, dc, None, None

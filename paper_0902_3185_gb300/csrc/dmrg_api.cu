@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <numeric>
 
 #include "internal.h"
@@ -33,6 +34,9 @@ struct CudaError {
   } while (0)
 
 struct Invalid {
+  std::string msg;
+};
+struct Timeout {
   std::string msg;
 };
 
@@ -61,6 +65,15 @@ dmrg_status guard(dmrg_sb* sb, F&& fn) {
   } catch (const Invalid& iv) {
     if (sb) sb->err = iv.msg;
     return DMRG_EINVAL;
+  } catch (const Timeout& to) {
+    if (sb) sb->err = to.msg;
+    return DMRG_ETIMEOUT;
+  } catch (const std::logic_error& le) {
+    if (sb) sb->err = le.what();
+    return DMRG_EINVAL;
+  } catch (const std::runtime_error& re) {
+    if (sb) sb->err = re.what();
+    return DMRG_ECUDA;
   } catch (const std::bad_alloc&) {
     if (sb) sb->err = "host allocation failed";
     return DMRG_ENOMEM;
@@ -446,9 +459,12 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
   lz_launch_sum_chunks(part, nrm2, nch, B, st);
   lz_launch_scale_unit(psi_out, nrm2, psi_out, nullptr, D, B, st);
   std::vector<double> out(4 * B);
+  int32_t tc_err = 0;
   CK(cudaMemcpyAsync(out.data(), sb->lz_out, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&tc_err, sb->d_tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
+  if (tc_err) throw Timeout{"a tensor-core kernel gave up a bounded wait"};
   LzRun r;
   r.launches = 3 + (int64_t)launched * (LZ_KERNELS_PER_ITER + matvec_launches(sb, prec)) + 4;
   for (int b = 0; b < B; ++b) {
@@ -564,6 +580,9 @@ void validate_and_copy(dmrg_sb* sb, const dmrg_sb_desc* d, int32_t batch) {
   }
   sb->d_ops = dalloc<double>((size_t)std::max<int64_t>(ops, 1));
   if (ops) CK(cudaMemcpy(sb->d_ops, host.data(), ops * sizeof(double), cudaMemcpyHostToDevice));
+  sb->h_ops = std::move(host);
+  sb->d_tc_err = dalloc<int32_t>(1);
+  CK(cudaMemset(sb->d_tc_err, 0, sizeof(int32_t)));
   upload(sb->d_coeffs, sb->coeffs);
   sb->d_scratch = dalloc<double>((size_t)(4 * batch + 16));
   sb->d_red = dalloc<double>((size_t)batch * lz_nchunk(sb->D));
@@ -577,6 +596,7 @@ void destroy(dmrg_sb* sb) {
     free_tl(*tl);
   for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red})
     if (p) cudaFree(p);
+  if (sb->d_tc_err) cudaFree(sb->d_tc_err);
   if (sb->d_dot_red_ptr) cudaFree(sb->d_dot_red_ptr);
   if (sb->d_dot_red_idx) cudaFree(sb->d_dot_red_idx);
   delete sb;
@@ -596,6 +616,8 @@ dmrg_status dmrg_create_superblock(const dmrg_sb_desc* d, int32_t batch, dmrg_sb
     validate_and_copy(sb, d, batch);
     build_f64_tasks(sb);
     tc_build(sb);
+    sb->h_ops.clear();
+    sb->h_ops.shrink_to_fit();
     CK(cudaDeviceSynchronize());
     return DMRG_OK;
   });

@@ -106,6 +106,8 @@ struct dmrg_sb {
   int32_t lz_graph_key[8] = {};
 
   void* tc = nullptr;            // tensor-core path state (matvec_tc.cu)
+  int32_t* d_tc_err = nullptr;   // set by a tensor-core kernel whose bounded wait gave up
+  std::vector<double> h_ops;     // host copy of the float64 arena during creation only
 
   std::string err;
 };

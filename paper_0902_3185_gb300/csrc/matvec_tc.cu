@@ -1,14 +1,856 @@
-// Tensor-core path: not built yet.
+// Mixed-precision superblock product on the tcgen05 tensor cores.
+//
+// Paper Sec. 3.3: x += H y as system, environment and connection tasks, each
+// a product of sector blocks, formed on the fly.  With batch members that
+// share every operator block (coupling sweeps), the member wavefunctions are
+// stacked along the M dimension of every product, so that the small, uneven
+// sector blocks of a DMRG superblock become GEMMs with M = batch x dim:
+//
+//   order R pairs (A last):  X_b = Psi_b[s_in] B^T         (phase 1)
+//                            Y_b^T += X_b^T A^T              (group S)
+//   order L pairs (B last):  Z_b^T = Psi_b[s_in]^T A^T      (phase 1)
+//                            Y_b += Z_b B^T                  (group E)
+//   1 (x) B terms:           Y_b += (c Psi_b) B^T            (group E)
+//   A (x) 1 terms:           Y_b^T += (c Psi_b)^T A^T        (group S)
+//
+// Every product is D = L R^T with both operands K-major, so operands are
+// kept in HBM already in the tensor cores' shared-memory image ("panels"):
+// 8-row atoms of 128-byte rows with the 128-byte swizzle, atoms of one
+// 128-byte K chunk stored contiguously.  A tile load is then one contiguous
+// cp.async.bulk per operand and no tensor maps are needed.  Zero padding in
+// K is written once; padding rows only feed accumulator rows/columns that
+// are never stored.
+//
+// One persistent kernel runs a list of output tiles (128 x up to 256) per
+// launch: warp 0 streams operand tiles through a multi-stage shared-memory
+// ring, warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator,
+// warps 2-5 drain the accumulator (tcgen05.ld) and either write the float64
+// output block or the next phase's operand panel (scaled by the member's
+// coefficient, rounded to TF32 or split into BF16 hi + lo).
+//
+// Precisions: TF32 (kind::tf32), and BF16x3: x = hi + lo, products
+// hi*hi + hi*lo + lo*hi in kind::f16 with an FP32 accumulator.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <vector>
+
+#include <cuda_bf16.h>
+
 #include "internal.h"
 #include "tc.h"
+#include "tc_kernel.cuh"
 
 namespace dmrg {
-void tc_build(dmrg_sb*) {}
-void tc_free(dmrg_sb*) {}
-bool tc_available(const dmrg_sb*) { return false; }
-void tc_set_coeffs(dmrg_sb*) {}
-double tc_operand_bytes(const dmrg_sb*) { return 0.0; }
-int tc_launches(const dmrg_sb*, int) { return 0; }
-void tc_matvec(dmrg_sb*, int, const double*, double*, int, const int32_t*, cudaStream_t) {}
-void tc_matvec_T(dmrg_sb*, int, const double*, double*, cudaStream_t) {}
+
+// ----------------------------------------------------------- task structs
+struct TcSeg {
+  const char* l;      // L panel (hi)
+  const char* r;      // R panel (hi)
+  int64_t l_lo, r_lo; // byte offset hi -> lo panel (BF16x3)
+  int32_t l_atoms, r_atoms;  // atoms per K chunk in each panel
+  int32_t kchunks;
+  int32_t pad;
+};
+
+struct TcTile {
+  int32_t m0, n0, ntile, la, ra;  // la / ra: atoms to load from L / R
+  int32_t seg_begin, seg_end, out;
+};
+
+enum OutKind : int32_t { OUT_Y_ROW = 0, OUT_Y_COL = 1, OUT_PANEL = 2 };
+
+struct TcOut {
+  int32_t kind;
+  int32_t Rm;      // accumulator rows per batch member
+  int32_t M, N;    // valid accumulator rows / columns
+  int32_t ldy;     // Y: row length of the output block
+  int32_t add;     // Y: accumulate into y (second group of a sector)
+  int32_t term;    // panel: coefficient column, -1 = 1
+  int32_t p_atoms; // panel: atoms per K chunk
+  int64_t y_off;   // Y: element offset of the sector block in a member
+  char* p;         // panel (hi)
+  int64_t p_lo;
+};
+
+struct StageJob {
+  int64_t src_off;  // sector block offset inside a member
+  int32_t r, c;     // source block dims
+  int32_t transpose, term;
+  char* p;
+  int64_t p_lo;
+  int32_t atoms, pad;
+};
+struct StageWork {
+  int32_t job, tile;  // tile = 32 x 32 block of the source, row-major over the source tiles
+};
+
+// byte offset of element (row, k) inside a panel
+__host__ __device__ inline int64_t panel_off(int64_t row, int64_t k, int64_t atoms, int es) {
+  const int64_t kce = 128 / es;
+  const int64_t kc = k / kce, kk = k - kc * kce;
+  const int64_t atom = row >> 3, r8 = row & 7;
+  const int64_t byte = kk * es;
+  const int64_t chunk = (byte >> 4) ^ r8;
+  return (kc * atoms + atom) * 1024 + r8 * 128 + (chunk << 4) + (byte & 15);
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_panel(char* p, int64_t p_lo, int64_t row, int64_t k, int atoms, float v) {
+  if (PREC == DMRG_TF32) {
+    *reinterpret_cast<float*>(p + panel_off(row, k, atoms, 4)) = tc::round_tf32(v);
+  } else {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int64_t o = panel_off(row, k, atoms, 2);
+    *reinterpret_cast<__nv_bfloat16*>(p + o) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(p + p_lo + o) = lo;
+  }
+}
+
+// ---------------------------------------------------------------- staging
+// float64 psi blocks -> operand panels (optionally transposed and scaled by
+// the member's coefficient).  One block = one 32 x 32 tile of one job.
+template <int PREC>
+__global__ void __launch_bounds__(256)
+tc_stage_kernel(const StageJob* __restrict__ jobs, const StageWork* __restrict__ work, const double* __restrict__ x,
+                int64_t D, const double* __restrict__ coef, int n_terms, const int32_t* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double t[32][33];
+  const StageWork w = work[blockIdx.x];
+  const StageJob j = jobs[w.job];
+  const int b = blockIdx.y;
+  const int tc_ = (j.c + 31) / 32;
+  const int a0 = (w.tile / tc_) * 32, b0 = (w.tile % tc_) * 32;
+  const double sc = j.term >= 0 ? coef[(int64_t)b * n_terms + j.term] : 1.0;
+  const double* src = x + (int64_t)b * D + j.src_off;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int e = ty; e < 32; e += 8) {
+    const int a = a0 + e, c = b0 + tx;
+    t[e][tx] = (a < j.r && c < j.c) ? src[(int64_t)a * j.c + c] * sc : 0.0;
+  }
+  __syncthreads();
+  constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
+  for (int e = ty; e < 32; e += 8) {
+    if (!j.transpose) {  // row = b*r + a, k = c
+      const int a = a0 + e, c = b0 + tx;
+      if (a < j.r && c < j.c)
+        store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, c, j.atoms, (float)t[e][tx]);
+    } else {  // row = b*c + c', k = a
+      const int c = b0 + e, a = a0 + tx;
+      if (a < j.r && c < j.c)
+        store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + c, a, j.atoms, (float)t[tx][e]);
+    }
+  }
+  (void)es;
+}
+
+// ------------------------------------------------------ grouped tile GEMM
+constexpr int TC_THREADS = 192;
+constexpr int L_TILE_BYTES = 128 * 128;  // 128 rows x 128 B
+
+template <int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
+               const TcOut* __restrict__ outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
+               int n_terms, int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
+               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(1024) char smem_raw[];
+  // control block, then 1024-aligned stage ring
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + 8;
+  uint64_t* acc_full = empty + 8;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t base_u32 = tc::smem_u32(smem_raw);
+  char* ring = smem_raw + (((base_u32 + 256 + 1023) & ~1023u) - base_u32);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&acc_full[a], 1);
+      tc::mbar_init(&acc_empty[a], 4);
+    }
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, (uint32_t)tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int acc_stride = tmem_cols / 2;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued = 0;  // bit s: stage s has a copy in flight or landed
+      uint32_t issued_par = 0;
+      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const TcTile tl = tiles[t];
+        const uint32_t lb = (uint32_t)tl.la * 1024u, rb = (uint32_t)tl.ra * 1024u;
+        for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
+          const TcSeg sg = segs[s];
+          for (int kc = 0; kc < sg.kchunks; ++kc) {
+            if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) goto producer_done;
+            char* st = ring + (size_t)stage * stage_bytes;
+            const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * 1024;
+            const char* rsrc = sg.r + ((int64_t)kc * sg.r_atoms + tl.n0 / 8) * 1024;
+            tc::mbar_arrive_expect_tx(&full[stage], PREC == DMRG_TF32 ? lb + rb : 2u * (lb + rb));
+            tc::bulk_g2s(st, lsrc, lb, &full[stage]);
+            tc::bulk_g2s(st + L_TILE_BYTES, rsrc, rb, &full[stage]);
+            if (PREC == DMRG_BF16X3) {
+              tc::bulk_g2s(st + L_TILE_BYTES + r_tile_bytes, lsrc + sg.l_lo, lb, &full[stage]);
+              tc::bulk_g2s(st + 2 * L_TILE_BYTES + r_tile_bytes, rsrc + sg.r_lo, rb, &full[stage]);
+            }
+            issued |= 1u << stage;
+            issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+    producer_done:
+      // never leave with a copy in flight: wait for the last copy of every stage
+      for (int s = 0; s < stages; ++s) {
+        if (!(issued >> s & 1u)) continue;
+        const uint64_t t0 = tc::globaltimer();
+        while (!tc::mbar_try_wait(&full[s], (issued_par >> s) & 1u)) {
+          if (tc::globaltimer() - t0 > tc::WAIT_LIMIT_NS) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      constexpr uint32_t fmt = PREC == DMRG_TF32 ? tc::FMT_TF32 : tc::FMT_BF16;
+      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const TcTile tl = tiles[t];
+        if (tl.seg_begin == tl.seg_end) continue;
+        if (!tc::mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag)) goto mma_done;
+        tc::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * acc_stride);
+        const uint32_t idesc = tc::idesc_f32acc(fmt, 128, (uint32_t)tl.ntile);
+        uint32_t accum = 0;
+        for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
+          const int kch = segs[s].kchunks;
+          for (int kc = 0; kc < kch; ++kc) {
+            if (!tc::mbar_wait(&full[stage], phase, abort_flag)) goto mma_done;
+            tc::tc_fence_after();
+            char* st = ring + (size_t)stage * stage_bytes;
+            const uint64_t ah = tc::sw128_desc(tc::smem_u32(st));
+            const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + L_TILE_BYTES));
+            if (PREC == DMRG_TF32) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                tc::mma_tf32(d_tmem, ah + 2 * k, bh + 2 * k, idesc, accum);
+                accum = 1;
+              }
+            } else {
+              const uint64_t al = tc::sw128_desc(tc::smem_u32(st + L_TILE_BYTES + r_tile_bytes));
+              const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + 2 * L_TILE_BYTES + r_tile_bytes));
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                tc::mma_bf16(d_tmem, ah + 2 * k, bh + 2 * k, idesc, accum);
+                accum = 1;
+                tc::mma_bf16(d_tmem, ah + 2 * k, bl + 2 * k, idesc, 1);
+                tc::mma_bf16(d_tmem, al + 2 * k, bh + 2 * k, idesc, 1);
+              }
+            }
+            tc::mma_commit(&empty[stage]);
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+        tc::mma_commit(&acc_full[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+    mma_done:
+      // every MMA this thread issued completes before the TMEM is released
+      tc::mma_commit(drain);
+      const uint64_t t0 = tc::globaltimer();
+      while (!tc::mbar_try_wait(drain, 0)) {
+        if (tc::globaltimer() - t0 > tc::WAIT_LIMIT_NS) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const TcTile tl = tiles[t];
+      const TcOut o = outs[tl.out];
+      const int m = tl.m0 + row;
+      const bool mv = m < o.M;
+      const int b = mv ? m / o.Rm : 0;
+      const int i = mv ? m - b * o.Rm : 0;
+      const int nend = min(tl.n0 + tl.ntile, o.N);
+      if (tl.seg_begin == tl.seg_end) {
+        if (mv && o.kind != OUT_PANEL && !(o.add || accumulate)) {
+          double* yb = y + (int64_t)b * D + o.y_off;
+          for (int n = tl.n0; n < nend; ++n)
+            yb[o.kind == OUT_Y_ROW ? (int64_t)i * o.ldy + n : (int64_t)n * o.ldy + i] = 0.0;
+        }
+        continue;
+      }
+      int ok = 1;
+      if (lane == 0) ok = tc::mbar_wait(&acc_full[acc], acc_phase, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const uint32_t tb = tmem_base + (uint32_t)(acc * acc_stride) + ((uint32_t)(32 * q) << 16);
+      const double sc = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? coef[(int64_t)b * n_terms + o.term] : 1.0;
+      const bool add = o.add || accumulate;
+      for (int c0 = 0; c0 < tl.ntile; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tb + (uint32_t)c0, v);
+        if (!mv) continue;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int n = tl.n0 + c0 + jj;
+          if (n >= nend) break;
+          if (o.kind == OUT_PANEL) {
+            store_panel<PREC>(o.p, o.p_lo, (int64_t)b * o.N + n, i, o.p_atoms, (float)(v[jj] * sc));
+          } else {
+            double* p = y + (int64_t)b * D + o.y_off +
+                        (o.kind == OUT_Y_ROW ? (int64_t)i * o.ldy + n : (int64_t)n * o.ldy + i);
+            *p = add ? *p + (double)v[jj] : (double)v[jj];
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 1) tc::tmem_dealloc(tmem_base, (uint32_t)tmem_cols);
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(err, 1);
+}
+
+// =================================================================== host
+namespace {
+
+struct CudaFail : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+#define TCK(x)                                                             \
+  do {                                                                     \
+    cudaError_t e_ = (x);                                                  \
+    if (e_ != cudaSuccess) throw CudaFail(std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+T* up(const std::vector<T>& h) {
+  void* p = nullptr;
+  const size_t n = std::max<size_t>(1, h.size());
+  TCK(cudaMalloc(&p, n * sizeof(T)));
+  if (!h.empty()) TCK(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return static_cast<T*>(p);
+}
+
+uint16_t f2bf(float f) {  // round to nearest even
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf2f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+float to_tf32(double x) {  // round to a 10-bit mantissa, nearest even
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0xfffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct Launch {  // one grouped GEMM launch
+  TcTile* tiles = nullptr;
+  TcSeg* segs = nullptr;
+  TcOut* outs = nullptr;
+  int n_tiles = 0;
+  int ntile_max = 16;
+};
+
+struct PairSet {  // the forward pairs or their transposes
+  StageJob* jobs = nullptr;
+  StageWork* work = nullptr;
+  int n_work = 0;
+  Launch ph1, grpE, grpS;
+};
+
+struct Fmt {
+  char* arena = nullptr;
+  size_t bytes = 0;   // per hi/lo half
+  PairSet fwd, bwd;
+};
+
+struct State {
+  int num_sms = 0;
+  bool ok = false;
+  Fmt f[2];  // 0: TF32, 1: BF16x3
+  double op_bytes_tf32 = 0;
+};
+
+void free_launch(Launch& l) {
+  for (void* p : {(void*)l.tiles, (void*)l.segs, (void*)l.outs})
+    if (p) cudaFree(p);
+  l = Launch{};
+}
+void free_set(PairSet& s) {
+  if (s.jobs) cudaFree(s.jobs);
+  if (s.work) cudaFree(s.work);
+  free_launch(s.ph1);
+  free_launch(s.grpE);
+  free_launch(s.grpS);
+  s = PairSet{};
+}
+
+// A pair as the product sees it (forward, or transposed for H^T)
+struct EPair {
+  int32_t term, s_out, s_in, flags, order;
+  const double* A;  // host, r_out x r_in (already transposed for H^T)
+  const double* B;  // host, c_out x c_in
+};
+
+struct Panel {
+  int64_t off = -1;  // byte offset in the half-arena
+  int64_t rows = 0, K = 0, atoms = 0;
+};
+
+// Pack a host float64 block (rows x K, element (row,k) at X[row*ld + k]) into a panel.
+void pack(std::vector<uint8_t>& hi, std::vector<uint8_t>& lo, const Panel& p, const double* X, int64_t ld,
+          int prec) {
+  const int es = prec == DMRG_TF32 ? 4 : 2;
+  for (int64_t r = 0; r < p.rows; ++r)
+    for (int64_t k = 0; k < p.K; ++k) {
+      const double x = X[r * ld + k];
+      const int64_t o = p.off + panel_off(r, k, p.atoms, es);
+      if (prec == DMRG_TF32) {
+        const float f = to_tf32(x);
+        memcpy(&hi[o], &f, 4);
+      } else {
+        const uint16_t h = f2bf((float)x);
+        const uint16_t l = f2bf((float)(x - (double)bf2f(h)));
+        memcpy(&hi[o], &h, 2);
+        memcpy(&lo[o], &l, 2);
+      }
+    }
+}
+
+}  // namespace
+
+// Build the panels and launches of one pair set in one format.  The caller's
+// half-arena layout starts at `base_off`; returns the bytes used.
+static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& P, int64_t base_off,
+                         std::vector<uint8_t>& hi, std::vector<uint8_t>& lo, char* d_hi, int64_t lo_delta,
+                         PairSet& out, bool dry) {
+  const int64_t nb = sb->batch;
+  const int es = prec == DMRG_TF32 ? 4 : 2;
+  const int64_t kce = 128 / es;
+  const auto& r = sb->r;
+  const auto& c = sb->c;
+  const int S = sb->S;
+  int64_t cur = base_off;
+  auto alloc = [&](int64_t rows, int64_t K) {
+    Panel p;
+    p.rows = rows;
+    p.K = K;
+    p.atoms = cdiv(rows, 8);
+    p.off = cur;
+    cur += p.atoms * cdiv(K, kce) * 1024;
+    return p;
+  };
+  const size_t np = P.size();
+  std::vector<Panel> pA(np), pB(np), pX(np), pS(np);  // operator A, B; intermediate; scaled psi copy
+  std::vector<Panel> psiP(S), psiPT(S);
+  std::vector<char> needP(S, 0), needPT(S, 0);
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    const int64_t ro = r[e.s_out], ri = r[e.s_in], co = c[e.s_out], ci = c[e.s_in];
+    if (!(e.flags & DMRG_ID_A)) pA[i] = alloc(ro, ri);
+    if (!(e.flags & DMRG_ID_B)) pB[i] = alloc(co, ci);
+    if (e.flags & DMRG_ID_A) pS[i] = alloc(nb * ri, ci);       // c Psi          (group E, L)
+    else if (e.flags & DMRG_ID_B) pS[i] = alloc(nb * ci, ri);  // (c Psi)^T      (group S, L)
+    else if (e.order == 1) { pX[i] = alloc(nb * co, ri); needP[e.s_in] = 1; }   // X^T stacked
+    else { pX[i] = alloc(nb * ro, ci); needPT[e.s_in] = 1; }                   // Z stacked
+  }
+  for (int s = 0; s < S; ++s) {
+    if (needP[s]) psiP[s] = alloc(nb * r[s], c[s]);
+    if (needPT[s]) psiPT[s] = alloc(nb * c[s], r[s]);
+  }
+  if (dry) return cur - base_off;
+  hi.resize(cur, 0);
+  if (prec == DMRG_BF16X3) lo.resize(cur, 0);
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (pA[i].off >= 0) pack(hi, lo, pA[i], e.A, r[e.s_in], prec);
+    if (pB[i].off >= 0) pack(hi, lo, pB[i], e.B, c[e.s_in], prec);
+  }
+  auto dptr = [&](const Panel& p) { return d_hi + p.off; };
+
+  // ---- staging jobs
+  std::vector<StageJob> jobs;
+  std::vector<StageWork> work;
+  auto add_job = [&](int s, int transpose, int term, const Panel& p) {
+    StageJob j{};
+    j.src_off = sb->off[s];
+    j.r = r[s];
+    j.c = c[s];
+    j.transpose = transpose;
+    j.term = term;
+    j.p = dptr(p);
+    j.p_lo = lo_delta;
+    j.atoms = (int32_t)p.atoms;
+    const int jid = (int)jobs.size();
+    jobs.push_back(j);
+    const int nt = (int)(cdiv(r[s], 32) * cdiv(c[s], 32));
+    for (int t = 0; t < nt; ++t) work.push_back({jid, t});
+  };
+  for (int s = 0; s < S; ++s) {
+    if (needP[s]) add_job(s, 0, -1, psiP[s]);
+    if (needPT[s]) add_job(s, 1, -1, psiPT[s]);
+  }
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (e.flags & DMRG_ID_A) add_job(e.s_in, 0, e.term, pS[i]);
+    else if (e.flags & DMRG_ID_B) add_job(e.s_in, 1, e.term, pS[i]);
+  }
+
+  // ---- grouped launches
+  struct Build {
+    std::vector<TcTile> tiles;
+    std::vector<TcSeg> segs;
+    std::vector<TcOut> outs;
+    std::vector<int64_t> weight;
+    int ntile_max = 16;
+  } L1, LE, LS;
+  // host-side bounds proof of every bulk copy the tiles will issue
+  auto check = [](bool ok, const char* what) {
+    if (!ok) throw std::logic_error(std::string("tensor-core task list: ") + what);
+  };
+  auto seg = [&](const Panel& Lp, const Panel& Rp) {
+    check(Lp.off >= 0 && Rp.off >= 0 && Lp.K == Rp.K, "segment operands");
+    TcSeg g{};
+    g.l = dptr(Lp);
+    g.r = dptr(Rp);
+    g.l_lo = lo_delta;
+    g.r_lo = lo_delta;
+    g.l_atoms = (int32_t)Lp.atoms;
+    g.r_atoms = (int32_t)Rp.atoms;
+    g.kchunks = (int32_t)cdiv(Lp.K, kce);
+    return g;
+  };
+  auto add_out = [&](Build& B, const TcOut& o, const std::vector<TcSeg>& sg) {
+    for (const TcSeg& g : sg) {
+      check(g.l_atoms == cdiv(o.M, 8) && g.r_atoms == cdiv(o.N, 8), "operand rows differ from the output");
+      check(g.kchunks >= 1, "empty K");
+    }
+    if (o.kind == OUT_PANEL) check(o.p_atoms == cdiv((int64_t)o.N * (o.M / o.Rm), 8), "panel rows");
+    else check(o.y_off + (int64_t)(o.kind == OUT_Y_ROW ? o.Rm : o.N) * o.ldy <= sb->D, "output block");
+    const int oid = (int)B.outs.size();
+    B.outs.push_back(o);
+    const int s0 = (int)B.segs.size();
+    B.segs.insert(B.segs.end(), sg.begin(), sg.end());
+    const int s1 = (int)B.segs.size();
+    int64_t kw = 0;
+    for (const TcSeg& g : sg) kw += g.kchunks;
+    for (int m0 = 0; m0 < o.M; m0 += 128)
+      for (int n0 = 0; n0 < o.N; n0 += 256) {
+        TcTile t{};
+        t.m0 = m0;
+        t.n0 = n0;
+        t.ntile = (int)std::min<int64_t>(256, cdiv(o.N - n0, 16) * 16);
+        t.la = (int)std::min<int64_t>(16, cdiv(o.M - m0, 8));
+        t.ra = (int)std::min<int64_t>(t.ntile / 8, cdiv(o.N - n0, 8));
+        t.seg_begin = s0;
+        t.seg_end = s1;
+        t.out = oid;
+        check(t.m0 % 8 == 0 && t.n0 % 8 == 0 && t.la >= 1 && t.ra >= 1, "tile origin");
+        check(t.m0 / 8 + t.la <= cdiv(o.M, 8) && t.n0 / 8 + t.ra <= cdiv(o.N, 8), "tile past its panels");
+        check(t.ntile % 16 == 0 && t.ntile >= 16 && t.ntile <= 256 && t.ra * 8 <= t.ntile, "MMA N");
+        B.ntile_max = std::max(B.ntile_max, t.ntile);
+        B.tiles.push_back(t);
+        B.weight.push_back(kw * (int64_t)t.ntile + 64);
+      }
+  };
+  // phase 1
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (e.flags & (DMRG_ID_A | DMRG_ID_B)) continue;
+    const int64_t ro = r[e.s_out], ri = r[e.s_in], co = c[e.s_out], ci = c[e.s_in];
+    TcOut o{};
+    o.kind = OUT_PANEL;
+    o.term = e.term;
+    o.p = dptr(pX[i]);
+    o.p_lo = lo_delta;
+    o.p_atoms = (int32_t)pX[i].atoms;
+    if (e.order == 1) {  // X_b = Psi_b B^T : rows (b, a'), cols beta; stored as X^T rows (b, beta), k = a'
+      o.Rm = (int32_t)ri;
+      o.M = (int32_t)(nb * ri);
+      o.N = (int32_t)co;
+      add_out(L1, o, {seg(psiP[e.s_in], pB[i])});
+    } else {  // Z_b^T = Psi_b^T A^T : rows (b, beta'), cols alpha; stored as Z rows (b, alpha), k = beta'
+      o.Rm = (int32_t)ci;
+      o.M = (int32_t)(nb * ci);
+      o.N = (int32_t)ro;
+      add_out(L1, o, {seg(psiPT[e.s_in], pA[i])});
+    }
+  }
+  // groups E and S per output sector
+  std::vector<std::vector<size_t>> by_out(S);
+  for (size_t i = 0; i < np; ++i) by_out[P[i].s_out].push_back(i);
+  for (int s = 0; s < S; ++s) {
+    if ((int64_t)r[s] * c[s] == 0) continue;
+    std::vector<TcSeg> sE, sS;
+    for (size_t i : by_out[s]) {
+      const EPair& e = P[i];
+      if (e.flags & DMRG_ID_A) sE.push_back(seg(pS[i], pB[i]));
+      else if (e.flags & DMRG_ID_B) sS.push_back(seg(pS[i], pA[i]));
+      else if (e.order == 0) sE.push_back(seg(pX[i], pB[i]));
+      else sS.push_back(seg(pX[i], pA[i]));
+    }
+    const bool hasE = !sE.empty(), hasS = !sS.empty();
+    if (hasE || !hasS) {
+      TcOut o{};
+      o.kind = OUT_Y_ROW;
+      o.Rm = r[s];
+      o.M = (int32_t)(nb * r[s]);
+      o.N = c[s];
+      o.ldy = c[s];
+      o.add = 0;
+      o.term = -1;
+      o.y_off = sb->off[s];
+      add_out(LE, o, sE);
+    }
+    if (hasS) {
+      TcOut o{};
+      o.kind = OUT_Y_COL;
+      o.Rm = c[s];
+      o.M = (int32_t)(nb * c[s]);
+      o.N = r[s];
+      o.ldy = c[s];
+      o.add = hasE ? 1 : 0;
+      o.term = -1;
+      o.y_off = sb->off[s];
+      add_out(LS, o, sS);
+    }
+  }
+  auto finish = [&](Build& B, Launch& L) {
+    // heaviest tiles first, dealt round-robin over the persistent CTAs
+    std::vector<size_t> perm(B.tiles.size());
+    for (size_t i = 0; i < perm.size(); ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return B.weight[a] > B.weight[b]; });
+    std::vector<TcTile> t(B.tiles.size());
+    for (size_t i = 0; i < perm.size(); ++i) t[i] = B.tiles[perm[i]];
+    L.tiles = up(t);
+    L.segs = up(B.segs);
+    L.outs = up(B.outs);
+    L.n_tiles = (int)t.size();
+    L.ntile_max = B.ntile_max;
+  };
+  finish(L1, out.ph1);
+  finish(LE, out.grpE);
+  finish(LS, out.grpS);
+  out.jobs = up(jobs);
+  out.work = up(work);
+  out.n_work = (int)work.size();
+  return cur - base_off;
+}
+
+static State* st_of(const dmrg_sb* sb) { return static_cast<State*>(sb->tc); }
+
+void tc_free(dmrg_sb* sb) {
+  State* s = st_of(sb);
+  if (!s) return;
+  for (Fmt& f : s->f) {
+    free_set(f.fwd);
+    free_set(f.bwd);
+    if (f.arena) cudaFree(f.arena);
+  }
+  delete s;
+  sb->tc = nullptr;
+}
+
+bool tc_available(const dmrg_sb* sb) {
+  const State* s = st_of(sb);
+  return s && s->ok;
+}
+
+double tc_operand_bytes(const dmrg_sb* sb) {
+  const State* s = st_of(sb);
+  return s ? s->op_bytes_tf32 : 0.0;
+}
+
+void tc_set_coeffs(dmrg_sb*) {}  // coefficients are read from the shared table at run time
+
+int tc_launches(const dmrg_sb* sb, int prec) {
+  const State* s = st_of(sb);
+  if (!s || !s->ok) return 0;
+  const PairSet& ps = s->f[prec == DMRG_TF32 ? 0 : 1].fwd;
+  return (ps.n_work > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
+}
+
+void tc_build(dmrg_sb* sb) {
+  int dev = 0;
+  TCK(cudaGetDevice(&dev));
+  cudaDeviceProp prop{};
+  TCK(cudaGetDeviceProperties(&prop, dev));
+  State* s = new State();
+  sb->tc = s;
+  s->num_sms = prop.multiProcessorCount;
+  if (prop.major != 10) return;  // tcgen05 is a Blackwell datacenter feature
+  // forward and transposed pair lists with host blocks
+  const double* H = sb->h_ops.data();
+  std::vector<EPair> fw, bw;
+  std::vector<std::vector<double>> trans;  // transposed host blocks for H^T
+  trans.reserve(sb->pairs.size() * 2);
+  for (const PairH& p : sb->pairs) {
+    EPair e{p.term, p.s_out, p.s_in, p.flags, p.order, p.a_off >= 0 ? H + p.a_off : nullptr,
+            p.b_off >= 0 ? H + p.b_off : nullptr};
+    fw.push_back(e);
+    const int64_t ro = sb->r[p.s_out], ri = sb->r[p.s_in], co = sb->c[p.s_out], ci = sb->c[p.s_in];
+    EPair t{p.term, p.s_in, p.s_out, p.flags, 0, nullptr, nullptr};
+    if (p.a_off >= 0) {
+      trans.emplace_back(ri * ro);
+      for (int64_t i = 0; i < ro; ++i)
+        for (int64_t j = 0; j < ri; ++j) trans.back()[j * ro + i] = H[p.a_off + i * ri + j];
+      t.A = trans.back().data();
+    }
+    if (p.b_off >= 0) {
+      trans.emplace_back(ci * co);
+      for (int64_t i = 0; i < co; ++i)
+        for (int64_t j = 0; j < ci; ++j) trans.back()[j * co + i] = H[p.b_off + i * ci + j];
+      t.B = trans.back().data();
+    }
+    if (!(p.flags & (DMRG_ID_A | DMRG_ID_B))) {
+      // transposed pair: r_out' = ri, r_in' = ro, c_out' = ci, c_in' = co
+      const double c0 = 2.0 * ri * ro * co + 2.0 * ri * co * ci;
+      const double c1 = 2.0 * ro * co * ci + 2.0 * ri * ro * ci;
+      t.order = c0 <= c1 ? 0 : 1;
+    }
+    bw.push_back(t);
+  }
+  for (int fi = 0; fi < 2; ++fi) {
+    const int prec = fi == 0 ? DMRG_TF32 : DMRG_BF16X3;
+    Fmt& F = s->f[fi];
+    // sizes depend only on shapes: a dry run lays the arena out first
+    std::vector<uint8_t> hi, lo;
+    {
+      PairSet none;
+      const int64_t a = build_set(sb, prec, fw, 0, hi, lo, nullptr, 0, none, true);
+      const int64_t b2 = build_set(sb, prec, bw, a, hi, lo, nullptr, 0, none, true);
+      F.bytes = (size_t)(a + b2);
+    }
+    const size_t total = F.bytes * (prec == DMRG_BF16X3 ? 2 : 1);
+    TCK(cudaMalloc(&F.arena, std::max<size_t>(total, 1024)));
+    TCK(cudaMemset(F.arena, 0, std::max<size_t>(total, 1024)));
+    const int64_t lo_delta = prec == DMRG_BF16X3 ? (int64_t)F.bytes : 0;
+    const int64_t a = build_set(sb, prec, fw, 0, hi, lo, F.arena, lo_delta, F.fwd, false);
+    build_set(sb, prec, bw, a, hi, lo, F.arena, lo_delta, F.bwd, false);
+    TCK(cudaMemcpy(F.arena, hi.data(), hi.size(), cudaMemcpyHostToDevice));
+    if (prec == DMRG_BF16X3) TCK(cudaMemcpy(F.arena + lo_delta, lo.data(), lo.size(), cudaMemcpyHostToDevice));
+    if (fi == 0) s->op_bytes_tf32 = (double)a;
+  }
+  TCK(cudaFuncSetAttribute(tc_gemm_kernel<DMRG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  TCK(cudaFuncSetAttribute(tc_gemm_kernel<DMRG_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  s->ok = true;
+}
+
+// ------------------------------------------------------------- launching
+template <int PREC>
+static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* sb, int accumulate,
+                     const int32_t* skip, cudaStream_t st) {
+  if (L.n_tiles == 0) return;
+  const int r_tile = L.ntile_max * 128;
+  const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
+  const int avail = 227 * 1024 - 2048;
+  const int stages = std::max(2, std::min(8, avail / stage_bytes));
+  const int smem = 2048 + stages * stage_bytes;
+  const int tmem_cols = L.ntile_max <= 128 ? 256 : 512;
+  const int grid = std::min(L.n_tiles, s->num_sms);
+  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
+                                                       sb->d_coeffs, sb->n_terms, accumulate, skip,
+                                                       sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols);
+}
+
+template <int PREC>
+static void run_set(const State* s, const PairSet& ps, const double* x, double* y, const dmrg_sb* sb,
+                    int accumulate, const int32_t* skip, cudaStream_t st) {
+  if (ps.n_work > 0)
+    tc_stage_kernel<PREC><<<dim3(ps.n_work, sb->batch), 256, 0, st>>>(ps.jobs, ps.work, x, sb->D, sb->d_coeffs,
+                                                                      sb->n_terms, skip);
+  run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
+  run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, st);
+  run_gemm<PREC>(s, ps.grpS, y, sb, accumulate, skip, st);
+}
+
+void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
+               cudaStream_t st) {
+  const State* s = st_of(sb);
+  if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
+  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st);
+  else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st);
+}
+
+void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st) {
+  const State* s = st_of(sb);
+  if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
+  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].bwd, g, dpsi, sb, 0, nullptr, st);
+  else run_set<DMRG_BF16X3>(s, s->f[1].bwd, g, dpsi, sb, 0, nullptr, st);
+}
+
 }  // namespace dmrg
