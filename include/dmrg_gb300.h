@@ -130,6 +130,21 @@ dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs);
 dmrg_status dmrg_apply_H(dmrg_sb* sb, const double* psi, double* y, int32_t accumulate,
                          int32_t prec, void* stream);
 
+/* The float64 product of dmrg_apply_H (FP64 precision) for callers that
+ * cannot allocate device memory when they apply H (code running under CUDA
+ * stream capture, processes whose device memory belongs to another
+ * framework's pool, allocation-free real-time loops).  Its intermediate
+ * workspace is one static buffer of 4 Mi float64 values (32 MiB) per GPU,
+ * part of the loaded library and held until the process exits; the call
+ * allocates nothing.  The first call on a device looks up the buffer's device
+ * address (cudaGetSymbolAddress) and must come before any stream capture.
+ * Calls share the buffer, which keeps the last call's contents: calls whose
+ * kernels overlap on the GPU race.  Returns DMRG_EINVAL, with a message, when
+ * the superblock needs more workspace than the buffer holds.  The paper has
+ * no counterpart to this call. */
+dmrg_status dmrg_apply_H_static_scratch(dmrg_sb* sb, const double* psi, double* y, int32_t accumulate,
+                                        void* stream);
+
 /* Reverse mode of y = H(c) psi for a cotangent g (device [batch][D]):
  * dpsi = H^T g (device [batch][D]) and dc[b][k] = <g_b, (A_k (x) B_k) psi_b>
  * (device [batch][n_terms]).  Either output may be NULL. */

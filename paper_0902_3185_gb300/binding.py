@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREA
 # exported symbols, as declared in include/dmrg_gb300.h
 SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error", "dmrg_query",
            "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
-           "dmrg_energy_grad"]
+           "dmrg_energy_grad", "dmrg_apply_H_static_scratch"]
 
 
 class DmrgError(RuntimeError):
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
     lib.dmrg_apply_H_backward.argtypes = [vp, dp, dp, dp, dp, i32, vp]
     lib.dmrg_lanczos_ground.argtypes = [vp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
     lib.dmrg_energy_grad.argtypes = [vp, dp, dp, i32, vp]
+    lib.dmrg_apply_H_static_scratch.argtypes = [vp, dp, dp, i32, vp]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -186,6 +187,16 @@ class GpuSuperblock:
             y = self.empty()
         self._check(self.lib.dmrg_apply_H(self.h, _ptr(psi), _ptr(y), int(accumulate), _prec(prec),
                                           _stream(stream)))
+        return y
+
+    def apply_H_static_scratch(self, psi, y=None, accumulate=False, stream=None):
+        """float64 product whose workspace is the library's static device
+        buffer: for callers that must not allocate device memory while they
+        apply H (the output tensor, when not given, is allocated here)."""
+        if y is None:
+            y = self.empty()
+        self._check(self.lib.dmrg_apply_H_static_scratch(self.h, _ptr(psi), _ptr(y), int(accumulate),
+                                                         _stream(stream)))
         return y
 
     def apply_H_backward(self, psi, g, want_dpsi=True, want_dc=True, prec="fp64", stream=None):
