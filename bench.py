@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=300)
+    ap.add_argument("--mixed-tol", type=float, default=1e-6)
+    ap.add_argument("--refine", default="newton", choices=["newton", "lanczos", "none"])
     return ap.parse_args()
 
 
@@ -213,8 +215,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(x):
-        e0, psi, infos, st = g.lanczos_ground(x, tol=args.tol, max_iter=args.max_iter, prec=prec,
-                                              refine=True, refine_tol=args.tol, graph_iters=8)
+        e0, psi, infos, st = g.lanczos_ground(x, tol=args.tol if prec == "fp64" else args.mixed_tol,
+                                              max_iter=args.max_iter, prec=prec, refine=args.refine,
+                                              refine_tol=args.tol, graph_iters=8)
         dEdc = g.energy_grad(psi)
         return e0, psi, infos, dEdc
 

@@ -90,10 +90,11 @@ typedef struct {
 
 typedef struct {
   double tol;          /* stop when beta_j |s_j| <= tol * max(1, |theta|) */
-  int32_t max_iter;    /* Krylov dimension cap (clamped to D) */
+  int32_t max_iter;    /* Krylov dimension cap (clamped to 768 and to D) */
   int32_t prec;        /* dmrg_prec of the products in the main solve */
-  int32_t refine;      /* 1: after a mixed-precision solve, restart FP64 Lanczos from its psi */
-  double refine_tol;   /* tolerance of the FP64 refinement */
+  int32_t refine;      /* after a mixed-precision solve: 0 none; 1 restart FP64 Lanczos from its psi;
+                          2 Newton steps: FP64 residual, correction equation by mixed-precision CG */
+  double refine_tol;   /* FP64 residual tolerance of the refinement, relative to max(1, |theta|) */
   int32_t check_every; /* run the tridiagonal test every this many iterations (>= 1) */
   int32_t graph_iters; /* iterations captured per CUDA graph launch (>= 1) */
 } dmrg_lanczos_opts;

@@ -211,13 +211,19 @@ class GpuSuperblock:
         self._check(self.lib.dmrg_energy_grad(self.h, _ptr(psi), _ptr(out), _prec(prec), _stream(stream)))
         return out
 
-    def lanczos_ground(self, psi0, tol=1e-12, max_iter=300, prec="fp64", refine=True, refine_tol=1e-10,
+    REFINE = {None: 0, False: 0, "none": 0, "lanczos": 1, True: 2, "newton": 2}
+
+    def lanczos_ground(self, psi0, tol=1e-12, max_iter=300, prec="fp64", refine="newton", refine_tol=1e-10,
                        check_every=1, graph_iters=8, psi_out=None, stream=None):
+        """Lowest eigenpair of every member.  With a mixed precision, refine =
+        "newton" (float64 residual + mixed CG correction steps, default),
+        "lanczos" (float64 Lanczos restarted from the mixed result) or "none"."""
         if psi_out is None:
             psi_out = self.empty()
         e0 = np.zeros(self.batch)
         info = (LanczosInfo * self.batch)()
-        opts = LanczosOpts(tol, max_iter, _prec(prec), int(refine), refine_tol, check_every, graph_iters)
+        mode = refine if isinstance(refine, int) and not isinstance(refine, bool) else self.REFINE[refine]
+        opts = LanczosOpts(tol, max_iter, _prec(prec), mode, refine_tol, check_every, graph_iters)
         st = self.lib.dmrg_lanczos_ground(self.h, _ptr(psi0), _ptr(psi_out), e0.ctypes.data, C.byref(opts),
                                           info, _stream(stream))
         infos = [{k: getattr(info[b], k) for k, _ in LanczosInfo._fields_} for b in range(self.batch)]

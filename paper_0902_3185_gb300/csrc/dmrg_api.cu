@@ -16,6 +16,7 @@
 
 #include "internal.h"
 #include "lanczos.h"
+#include "refine.h"
 #include "tc.h"
 
 using namespace dmrg;
@@ -327,9 +328,13 @@ void lz_free(dmrg_sb* sb) {
       sb->lz_graphs[i] = nullptr;
       sb->lz_graph_key[i] = 0;
     }
-  for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_ab, sb->lz_s, sb->lz_out})
+  for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_ab, sb->lz_s, sb->lz_out,
+                    sb->rf_res, sb->rf_p, sb->rf_q, sb->rf_t, sb->rf_sc})
     if (p) cudaFree(p);
   if (sb->lz_ctl) cudaFree(sb->lz_ctl);
+  if (sb->rf_ctl) cudaFree(sb->rf_ctl);
+  sb->rf_res = sb->rf_p = sb->rf_q = sb->rf_t = sb->rf_sc = nullptr;
+  sb->rf_ctl = nullptr;
   if (sb->h_ctl) cudaFreeHost(sb->h_ctl);
   sb->lz_V = sb->lz_w = sb->lz_vcur = sb->lz_partial = sb->lz_h = sb->lz_ab = sb->lz_s = sb->lz_out = nullptr;
   sb->lz_ctl = nullptr;
@@ -355,6 +360,12 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   CK(cudaMallocHost(&hp, sizeof(int32_t) * (LZ_CTL_MEMBER + 2 * B)));
   sb->h_ctl = static_cast<int32_t*>(hp);
   CK(cudaMemset(sb->lz_ab, 0, sizeof(double) * 2 * B * cap));
+  sb->rf_res = dalloc<double>((size_t)(B * D));
+  sb->rf_p = dalloc<double>((size_t)(B * D));
+  sb->rf_q = dalloc<double>((size_t)(B * D));
+  sb->rf_t = dalloc<double>((size_t)(B * D));
+  sb->rf_sc = dalloc<double>((size_t)(RF_NSC * B + 2));
+  sb->rf_ctl = dalloc<int32_t>((size_t)(2 * B + 2));
   sb->lz_cap = cap;
 }
 
@@ -368,10 +379,10 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   double* h2 = sb->lz_h + (size_t)B * cap;
   double* npart = sb->lz_partial;  // reused: the norm partials fit in the row partials
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, nch, st);
-  lz_launch_reduce_rows(sb->lz_partial, h1, ctl, nch, cap, B, st);
+  lz_launch_reduce_rows(sb->lz_partial, h1, ctl, lz_dot_nchunk(D), cap, B, st);
   lz_launch_multiaxpy(sb->lz_V, sb->lz_w, h1, nullptr, ctl, D, B, cap, nch, st);
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, nch, st);
-  lz_launch_reduce_rows(sb->lz_partial, h2, ctl, nch, cap, B, st);
+  lz_launch_reduce_rows(sb->lz_partial, h2, ctl, lz_dot_nchunk(D), cap, B, st);
   lz_launch_multiaxpy(sb->lz_V, sb->lz_w, h2, npart, ctl, D, B, cap, nch, st);
   lz_launch_finalize_ab(sb->lz_h, npart, sb->lz_ab, ctl, B, cap, nch, st);
   lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, ctl, sb->lz_out + 4 * B, B, cap, D, st);  // tol at out[4B]
@@ -428,7 +439,7 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
                int check_every, int graph_iters, cudaStream_t st) {
   const int64_t D = sb->D;
   const int B = sb->batch;
-  max_iter = (int)std::min<int64_t>(std::min(std::max(1, max_iter), 1024), D);
+  max_iter = (int)std::min<int64_t>(std::min(std::max(1, max_iter), 768), D);  // tridiagonal kernel keeps 60 B per Krylov vector in shared memory (48 KB)
   lz_alloc(sb, max_iter + 1);
   const int cap = sb->lz_cap, nch = sb->lz_nchunk;
   // v_0 = psi0 / |psi0|
@@ -473,6 +484,154 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
     r.theta.push_back(out[4 * b]);
     r.resid.push_back(out[4 * b + 1]);
   }
+  return r;
+}
+
+// ------------------------------------------------------------ refinement
+void rf_enqueue_inner(dmrg_sb* sb, int prec, cudaStream_t st) {
+  const int64_t D = sb->D;
+  const int B = sb->batch;
+  int32_t* ctl = sb->rf_ctl;
+  int32_t* stop = ctl + 2 * B;
+  double* sc = sb->rf_sc;
+  double* part = sb->lz_partial;
+  const double* psi = sb->lz_vcur;  // the current float64 iterate lives in lz_vcur during refinement
+  matvec(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st);
+  rf_launch_shift_dot(sb->rf_q, sb->rf_p, psi, sc, ctl, part, D, B, stop, st);
+  rf_launch_sum(part, sc, RF_S1, D, B, ctl, stop, st);
+  rf_launch_proj_dot(sb->rf_q, sb->rf_p, psi, sc, ctl, part, D, B, stop, st);
+  rf_launch_sum(part, sc, RF_PQ, D, B, ctl, stop, st);
+  rf_launch_alpha(sc, ctl, B, stop, st);
+  rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_q, sc, ctl, part, D, B, stop, st);
+  rf_launch_sum(part, sc, RF_RRNEW, D, B, ctl, stop, st);
+  rf_launch_beta(sc, ctl, sc + RF_NSC * B, B, stop, st);
+  rf_launch_dir(sb->rf_p, sb->rf_res, sc, ctl, D, B, stop, st);
+  CK(cudaGetLastError());
+}
+constexpr int RF_KERNELS_PER_ITER = 10;
+
+cudaGraphExec_t rf_graph(dmrg_sb* sb, int prec, int K) {
+  const int key = (1 << 20) + 1 + prec * 1024 + K;
+  for (int i = 0; i < 8; ++i)
+    if (sb->lz_graphs[i] && sb->lz_graph_key[i] == key) return (cudaGraphExec_t)sb->lz_graphs[i];
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  try {
+    for (int k = 0; k < K; ++k) rf_enqueue_inner(sb, prec, cs);
+  } catch (...) {
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    throw;
+  }
+  CK(cudaStreamEndCapture(cs, &g));
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  CK(e);
+  int slot = -1;
+  for (int i = 0; i < 8; ++i)
+    if (!sb->lz_graphs[i]) { slot = i; break; }
+  if (slot < 0) {
+    slot = 7;
+    cudaGraphExecDestroy((cudaGraphExec_t)sb->lz_graphs[slot]);
+  }
+  sb->lz_graphs[slot] = ge;
+  sb->lz_graph_key[slot] = key;
+  return ge;
+}
+
+struct RfRun {
+  std::vector<int32_t> code;  // LZ_CONVERGED or LZ_CAP
+  std::vector<double> theta, resid;
+  int outer = 0;              // float64 products spent
+  std::vector<int32_t> inner; // mixed CG iterations per member (all outer steps)
+  int64_t launches = 0;
+};
+
+// Newton refinement of psi (device [batch][D], normalised) in place.
+RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, int max_inner, double eps_in, int K,
+               cudaStream_t st) {
+  const int64_t D = sb->D;
+  const int B = sb->batch, nch = sb->lz_nchunk;
+  double* part = sb->lz_partial;
+  double* tmp = sb->d_scratch;
+  double* cur = sb->lz_vcur;
+  CK(cudaMemcpyAsync(cur, psi, sizeof(double) * B * D, cudaMemcpyDeviceToDevice, st));
+  RfRun r;
+  r.code.assign(B, LZ_CAP);
+  r.theta.assign(B, 0.0);
+  r.resid.assign(B, 0.0);
+  r.inner.assign(B, 0);
+  std::vector<double> hsc(RF_NSC * B);
+  std::vector<int32_t> hctl(2 * B + 2, 0), mask(B, 0);
+  std::vector<uint8_t> conv(B, 0);
+  const int Kg = std::max(1, K);
+  for (int o = 0; o < max_outer; ++o) {
+    // float64 residual of the current iterate
+    matvec(sb, DMRG_FP64, cur, sb->lz_w, 0, nullptr, st);
+    lz_launch_dot(cur, sb->lz_w, part, D, B, nch, st);
+    lz_launch_sum_chunks(part, tmp, nch, B, st);
+    rf_launch_set(sb->rf_sc, tmp, RF_THETA, B, 0, st);
+    rf_launch_start(sb->lz_w, cur, sb->rf_res, sb->rf_p, sb->rf_t, sb->rf_sc, part, D, B, st);
+    lz_launch_sum_chunks(part, tmp, nch, B, st);
+    rf_launch_set(sb->rf_sc, tmp, RF_RR, B, 1, st);
+    CK(cudaMemcpyAsync(hsc.data(), sb->rf_sc, sizeof(double) * RF_NSC * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    r.launches += 7 + matvec_launches(sb, DMRG_FP64);
+    ++r.outer;
+    bool all = true;
+    for (int b = 0; b < B; ++b) {
+      const double th = hsc[b * RF_NSC + RF_THETA], rn = hsc[b * RF_NSC + RF_BNORM];
+      r.theta[b] = th;
+      r.resid[b] = rn;
+      conv[b] = rn <= tol * std::max(1.0, std::fabs(th));
+      if (!std::isfinite(th) || !std::isfinite(rn)) throw Invalid{"refinement met a non-finite residual"};
+      r.code[b] = conv[b] ? LZ_CONVERGED : LZ_CAP;
+      all = all && conv[b];
+    }
+    if (all || o + 1 == max_outer) break;
+    // mixed-precision CG on the correction equation
+    for (int b = 0; b < B; ++b) {
+      hctl[b] = conv[b] ? 1 : 0;
+      hctl[B + b] = 0;
+      mask[b] = conv[b] ? 0 : 1;
+    }
+    hctl[2 * B] = 0;
+    hctl[2 * B + 1] = max_inner;
+    CK(cudaMemcpyAsync(sb->rf_ctl, hctl.data(), sizeof(int32_t) * (2 * B + 2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sb->rf_sc + RF_NSC * B, &eps_in, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    cudaGraphExec_t ge = rf_graph(sb, prec, Kg);
+    int launched = 0;
+    for (;;) {
+      CK(cudaGraphLaunch(ge, st));
+      launched += Kg;
+      r.launches += (int64_t)Kg * (RF_KERNELS_PER_ITER + matvec_launches(sb, prec));
+      int32_t stop = 0;
+      CK(cudaMemcpyAsync(&stop, sb->rf_ctl + 2 * B, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (stop) break;
+      if (launched > max_inner + Kg) throw Invalid{"refinement control did not terminate"};
+    }
+    CK(cudaMemcpyAsync(hctl.data(), sb->rf_ctl, sizeof(int32_t) * (2 * B + 2), cudaMemcpyDeviceToHost, st));
+    int32_t* dmask = reinterpret_cast<int32_t*>(sb->rf_ctl);  // reuse: done flags no longer needed
+    CK(cudaMemcpyAsync(dmask, mask.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < B; ++b) r.inner[b] += hctl[B + b];
+    // psi <- (psi + t) / |psi + t|
+    rf_launch_apply(cur, sb->rf_t, dmask, D, B, st);
+    lz_launch_sumsq(cur, part, D, B, nch, st);
+    lz_launch_sum_chunks(part, tmp, nch, B, st);
+    lz_launch_scale_unit(cur, tmp, cur, nullptr, D, B, st);
+    r.launches += 4;
+  }
+  CK(cudaMemcpyAsync(psi, cur, sizeof(double) * B * D, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
   return r;
 }
 
@@ -736,30 +895,35 @@ dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out
     const int B = sb->batch;
     const int ge = std::max(1, opts->graph_iters);
     LzRun r = lz_solve(sb, psi0, psi_out, opts->prec, opts->tol, opts->max_iter, opts->check_every, ge, st);
-    std::vector<int32_t> refine_iters(B, 0);
-    LzRun rr;
-    const bool refine = opts->prec != DMRG_FP64 && opts->refine;
-    if (refine) {
-      rr = lz_solve(sb, psi_out, psi_out, DMRG_FP64, opts->refine_tol > 0 ? opts->refine_tol : 1e-10,
-                    opts->max_iter, opts->check_every, ge, st);
-    }
+    const double rtol = opts->refine_tol > 0 ? opts->refine_tol : 1e-10;
+    const int mode = opts->prec == DMRG_FP64 ? 0 : opts->refine;
+    LzRun rr;   // mode 1: float64 Lanczos restarted from the mixed result
+    RfRun rn;   // mode 2: Newton steps, float64 residual + mixed CG correction
+    if (mode == 1)
+      rr = lz_solve(sb, psi_out, psi_out, DMRG_FP64, rtol, opts->max_iter, opts->check_every, ge, st);
+    else if (mode >= 2)
+      rn = rf_solve(sb, psi_out, opts->prec, rtol, 8, 400, 1e-3, ge, st);
     dmrg_status worst = DMRG_OK;
     for (int b = 0; b < B; ++b) {
-      const LzRun& fin = refine ? rr : r;
-      dmrg_status s = code_to_status(fin.code[b]);
+      int code = r.code[b];
+      double th = r.theta[b], res = r.resid[b];
+      if (mode == 1) { code = rr.code[b]; th = rr.theta[b]; res = rr.resid[b]; }
+      if (mode >= 2) { code = rn.code[b]; th = rn.theta[b]; res = rn.resid[b]; }
+      dmrg_status s = code_to_status(code);
       const dmrg_status report = s == DMRG_EBREAKDOWN ? DMRG_OK : s;
       if (report != DMRG_OK && worst == DMRG_OK) worst = report;
-      e0[b] = fin.theta[b];
+      e0[b] = th;
       if (info) {
-        info[b].e0 = fin.theta[b];
-        info[b].residual = fin.resid[b];
+        info[b].e0 = th;
+        info[b].residual = res;
         info[b].iters = r.iters[b];
-        info[b].refine_iters = refine ? rr.iters[b] : 0;
-        info[b].mixed_matvecs = opts->prec != DMRG_FP64 ? r.iters[b] : 0;
-        info[b].fp64_matvecs = opts->prec == DMRG_FP64 ? r.iters[b] : (refine ? rr.iters[b] : 0);
+        info[b].refine_iters = mode == 1 ? rr.iters[b] : (mode >= 2 ? rn.outer : 0);
+        const int mixed_lz = opts->prec != DMRG_FP64 ? r.iters[b] : 0;
+        info[b].mixed_matvecs = mixed_lz + (mode >= 2 ? rn.inner[b] : 0);
+        info[b].fp64_matvecs = opts->prec == DMRG_FP64 ? r.iters[b] : (mode == 1 ? rr.iters[b] : (mode >= 2 ? rn.outer : 0));
         info[b].status = s;
-        info[b].breakdown = fin.code[b] == LZ_BREAKDOWN;
-        info[b].kernel_launches = (int32_t)(r.launches + (refine ? rr.launches : 0));
+        info[b].breakdown = code == LZ_BREAKDOWN;
+        info[b].kernel_launches = (int32_t)(r.launches + (mode == 1 ? rr.launches : 0) + (mode >= 2 ? rn.launches : 0));
       }
     }
     return worst;

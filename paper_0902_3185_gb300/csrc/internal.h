@@ -102,6 +102,13 @@ struct dmrg_sb {
   int32_t* lz_ctl = nullptr;     // device control words
   int32_t* h_ctl = nullptr;      // pinned host mirror
   int32_t lz_nchunk = 0;
+  // float64 refinement (Newton step with mixed CG) buffers, allocated with Lanczos
+  double* rf_res = nullptr;      // [batch][D]
+  double* rf_p = nullptr;
+  double* rf_q = nullptr;
+  double* rf_t = nullptr;
+  double* rf_sc = nullptr;       // [batch][8] scalars, then eps
+  int32_t* rf_ctl = nullptr;     // [2 batch + 2]
   void* lz_graphs[8] = {};       // cached cudaGraphExec_t per (prec, K) slot
   int32_t lz_graph_key[8] = {};
 

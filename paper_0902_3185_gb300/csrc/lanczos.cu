@@ -36,63 +36,112 @@ __device__ __forceinline__ bool member_done(const int32_t* ctl, int b) {
   return ctl[LZ_CTL_ALLDONE] != 0 || ctl[LZ_CTL_MEMBER + b] != 0;
 }
 
-// partial[(b*nchunk + chunk)*cap + i] = sum_{d in chunk} V[i][b][d] * w[b][d], i <= j
+// partial[(b*nchunk + chunk)*cap + i] = sum_{d in chunk} V[i][b][d] * w[b][d], i <= j.
+// GB300 issues float64 at 1/64 of the float32 rate, so the reduction must not
+// cost more float64 work than the dot products: every thread keeps
+// LZ_DOT_EPT elements of w in registers, takes 8 rows at a time, and the 8
+// row sums are reduced across the warp by a butterfly that halves the values
+// per lane at each step (4+2+1+1+1 shuffle-adds for 8 rows, not 8 x 5).
 __global__ void __launch_bounds__(LZ_THREADS)
 k_multidot(const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ partial,
            const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk) {
-  __shared__ double red[LZ_THREADS / 32 * LZ_ROWS];
+  __shared__ double red[LZ_THREADS / 32][8];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (member_done(ctl, b)) return;
   const int j = ctl[LZ_CTL_J];
-  double wv[LZ_EPT];
-  int64_t dd[LZ_EPT];
-#pragma unroll
-  for (int e = 0; e < LZ_EPT; ++e) {
-    dd[e] = (int64_t)chunk * LZ_CHUNK + e * LZ_THREADS + threadIdx.x;
-    wv[e] = dd[e] < D ? w[(int64_t)b * D + dd[e]] : 0.0;
-  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i0 = 0; i0 <= j; i0 += LZ_ROWS) {
-    double p[LZ_ROWS];
+  double wv[LZ_DOT_EPT];
+  const int64_t base = (int64_t)chunk * LZ_DOT_CHUNK + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < LZ_ROWS; ++q) {
+  for (int e = 0; e < LZ_DOT_EPT; ++e) {
+    const int64_t d = base + e * LZ_THREADS;
+    wv[e] = d < D ? w[(int64_t)b * D + d] : 0.0;
+  }
+  const bool full = base + (LZ_DOT_EPT - 1) * LZ_THREADS < D;
+  for (int i0 = 0; i0 <= j; i0 += 8) {
+    double p[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
       p[q] = 0.0;
       const int i = i0 + q;
       if (i <= j) {
-        const double* v = V + ((int64_t)i * batch + b) * D;
+        const double* v = V + ((int64_t)i * batch + b) * D + base;
+        if (full) {
 #pragma unroll
-        for (int e = 0; e < LZ_EPT; ++e)
-          if (dd[e] < D) p[q] = fma(v[dd[e]], wv[e], p[q]);
+          for (int e = 0; e < LZ_DOT_EPT; ++e) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < LZ_DOT_EPT; ++e)
+            if (base + e * LZ_THREADS < D) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
+        }
       }
     }
+    // butterfly: after the step with offset 16 a lane holds 4 partial rows,
+    // after 8 two rows, after 4 one row; offsets 2 and 1 finish that row.
+    {
+      const bool up = lane & 16;
 #pragma unroll
-    for (int q = 0; q < LZ_ROWS; ++q) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) p[q] += __shfl_down_sync(0xffffffffu, p[q], o);
+      for (int q = 0; q < 4; ++q) {
+        const double send = up ? p[q] : p[q + 4];
+        const double keep = up ? p[q + 4] : p[q];
+        p[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
     }
-    __syncthreads();
-    if (lane == 0)
+    {
+      const bool up = lane & 8;
 #pragma unroll
-      for (int q = 0; q < LZ_ROWS; ++q) red[q * (LZ_THREADS / 32) + wid] = p[q];
+      for (int q = 0; q < 2; ++q) {
+        const double send = up ? p[q] : p[q + 2];
+        const double keep = up ? p[q + 2] : p[q];
+        p[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+    }
+    {
+      const bool up = lane & 4;
+      const double send = up ? p[0] : p[1];
+      const double keep = up ? p[1] : p[0];
+      p[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    p[0] += __shfl_xor_sync(0xffffffffu, p[0], 2);
+    p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
+    // lane holds row ((lane>>4)&1)*4 + ((lane>>3)&1)*2 + ((lane>>2)&1)
+    const int row = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     __syncthreads();
-    if (threadIdx.x < LZ_ROWS && i0 + (int)threadIdx.x <= j) {
+    if ((lane & 3) == 0) red[wid][row] = p[0];
+    __syncthreads();
+    if (threadIdx.x < 8 && i0 + (int)threadIdx.x <= j) {
       double t = 0.0;
-      for (int w2 = 0; w2 < LZ_THREADS / 32; ++w2) t += red[threadIdx.x * (LZ_THREADS / 32) + w2];
+#pragma unroll
+      for (int w2 = 0; w2 < LZ_THREADS / 32; ++w2) t += red[w2][threadIdx.x];
       partial[((int64_t)b * nchunk + chunk) * cap + i0 + threadIdx.x] = t;
     }
   }
 }
 
-// h[b*cap + i] = sum over chunks (in order) of the partials, i <= j
-__global__ void k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h,
-                              const int32_t* __restrict__ ctl, int nchunk, int cap) {
+// h[b*cap + i] = sum over chunks of the partials, i <= j.  Block (32 x 8):
+// lane x owns row i0 + x, warp y sums chunks y, y + 8, ...; the 8 warp sums
+// are then added in a fixed order (deterministic).
+__global__ void __launch_bounds__(256)
+k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h, const int32_t* __restrict__ ctl,
+              int nchunk, int cap) {
+  __shared__ double red[8][33];
   const int b = blockIdx.x;
   if (member_done(ctl, b)) return;
   const int j = ctl[LZ_CTL_J];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    double t = 0.0;
-    for (int ch = 0; ch < nchunk; ++ch) t += partial[((int64_t)b * nchunk + ch) * cap + i];
-    h[(int64_t)b * cap + i] = t;
+  const int i0 = blockIdx.y * 32;
+  if (i0 > j) return;
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int i = i0 + x;
+  double t = 0.0;
+  if (i <= j)
+    for (int ch = y; ch < nchunk; ch += 8) t += partial[((int64_t)b * nchunk + ch) * cap + i];
+  red[y][x] = t;
+  __syncthreads();
+  if (y == 0 && i <= j) {
+    double u = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u += red[k][x];
+    h[(int64_t)b * cap + i] = u;
   }
 }
 
@@ -138,131 +187,174 @@ __global__ void k_finalize_ab(const double* __restrict__ h, const double* __rest
   ab[((int64_t)batch + b) * cap + j] = sqrt(t);
 }
 
-// number of eigenvalues of T (diag a, off-diagonal e) below x: signs of the
-// LDL^T pivots (Sylvester), with a zero pivot nudged off zero
-__device__ int sturm_count(const double* a, const double* e, int n, double x) {
+// Number of eigenvalues of T (diagonal a, off-diagonal e) below x: the
+// negative pivots of T - x I = L D L^T (Sylvester's law of inertia); a zero
+// pivot is nudged off zero.
+template <class T>
+__device__ int sturm_count(const T* a, const T* e2, int n, T x, T tiny) {
   int cnt = 0;
-  double d = a[0] - x;
-  if (d < 0) ++cnt;
+  T d = a[0] - x;
+  if (d < T(0)) ++cnt;
   for (int i = 1; i < n; ++i) {
-    if (d == 0.0) d = DBL_MIN;
-    d = (a[i] - x) - e[i - 1] * e[i - 1] / d;
-    if (d < 0) ++cnt;
+    if (d == T(0)) d = tiny;
+    d = (a[i] - x) - e2[i - 1] / d;
+    if (d < T(0)) ++cnt;
   }
   return cnt;
 }
 
-// Lowest eigenpair of the (j+1) x (j+1) tridiagonal matrix of each member,
-// convergence test, and the Ritz coefficients s.  One block per member.
-//  - multisection: the LZ_TRI threads evaluate Sturm counts at evenly spaced
-//    points of the bracket [lo, hi] that holds the lowest eigenvalue, until
-//    the bracket is as narrow as float64 resolves;
-//  - inverse iteration with the shift lo < lambda_min: T - lo I is positive
-//    definite, so its LDL^T solve (one thread, O(n)) is stable, and two
-//    solves give the eigenvector to working precision.
-__global__ void __launch_bounds__(LZ_TRI)
+// Multisection by one warp: the 32 lanes evaluate Sturm counts at evenly
+// spaced points of [lo, hi] (count(lo) = 0 <= 1 <= count(hi) ... holds for
+// the lowest eigenvalue) and keep the sub-interval that holds it.
+template <class T>
+__device__ void multisection(const T* a, const T* e2, int n, T& lo, T& hi, T rel, int max_rounds, T tiny) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < max_rounds; ++round) {
+    const T w = hi - lo;
+    if (!(w > rel * fmax(fabs(lo), fabs(hi))) || !(w > T(0))) break;
+    const T step = w / T(33);
+    const T x = lo + step * T(lane + 1);
+    const int cnt = sturm_count<T>(a, e2, n, x, tiny);
+    const unsigned ball = __ballot_sync(0xffffffffu, cnt >= 1);
+    const int f = ball ? __ffs(ball) - 1 : 32;  // first point with an eigenvalue below it
+    const T nlo = lo + step * T(f);
+    const T nhi = f < 32 ? lo + step * T(f + 1) : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+}
+
+// Inverse iteration with a shift below lambda_min: T - sigma I is positive
+// definite, so its L D L^T factorisation needs no pivoting.  Lane 0 factors
+// once (reciprocal pivots) and solves `solves` times; returns in z the
+// normalised eigenvector estimate with z[0] >= 0.
+template <class T>
+__device__ void inverse_iteration(const T* a, const T* e, int n, T sigma, T* z, T* rpiv, int solves, T tiny) {
+  if ((threadIdx.x & 31) != 0) return;
+  T dp = a[0] - sigma;
+  rpiv[0] = T(1) / (dp == T(0) ? tiny : dp);
+  for (int i = 1; i < n; ++i) {
+    const T l = e[i - 1] * rpiv[i - 1];
+    dp = (a[i] - sigma) - l * e[i - 1];
+    rpiv[i] = T(1) / (dp == T(0) ? tiny : dp);
+  }
+  for (int i = 0; i < n; ++i) z[i] = T(1);
+  for (int it = 0; it < solves; ++it) {
+    for (int i = 1; i < n; ++i) z[i] -= (e[i - 1] * rpiv[i - 1]) * z[i - 1];
+    for (int i = 0; i < n; ++i) z[i] *= rpiv[i];
+    for (int i = n - 2; i >= 0; --i) z[i] -= (e[i] * rpiv[i]) * z[i + 1];
+    T nz = T(0);
+    for (int i = 0; i < n; ++i) nz = fma(z[i], z[i], nz);
+    const T inv = (z[0] < T(0) ? T(-1) : T(1)) / sqrt(nz);
+    for (int i = 0; i < n; ++i) z[i] *= inv;
+  }
+}
+
+// Lowest eigenpair of the (j+1) x (j+1) tridiagonal matrix of each member and
+// the convergence test.  One warp per member.
+//  - every check: float32 multisection and float32 inverse iteration give
+//    theta and the last Ritz-vector component to a few digits, enough for the
+//    test beta_j |s_j| <= tol max(1, |theta|);
+//  - when the test passes (or at breakdown / the cap) the eigenpair is
+//    recomputed in float64 (multisection from the float32 bracket, widened by
+//    its rounding bound, then inverse iteration), the test is repeated with
+//    the float64 values, and s is stored for the Ritz vector.
+// GB300 issues float64 at 1/64 of the float32 rate, which is why the per-
+// iteration test runs in float32.
+__global__ void __launch_bounds__(32)
 k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __restrict__ out,
           int32_t* __restrict__ ctl, const double* __restrict__ tolp, int batch, int cap, int64_t D) {
   extern __shared__ double sm[];
   double* a = sm;
   double* e = sm + cap;
-  double* z = sm + 2 * cap;
-  double* dpiv = sm + 3 * cap;
-  __shared__ double s_lo, s_hi, s_scale;
-  __shared__ int s_first;
-  __shared__ int s_do;
+  double* e2 = sm + 2 * cap;
+  double* z = sm + 3 * cap;
+  double* rp = sm + 4 * cap;
+  float* a32 = reinterpret_cast<float*>(sm + 5 * cap);
+  float* e32 = a32 + cap;
+  float* e232 = e32 + cap;
+  float* z32 = e232 + cap;
+  float* rp32 = z32 + cap;
   const int b = blockIdx.x;
+  const int lane = threadIdx.x;
   if (member_done(ctl, b)) return;
   const int j = ctl[LZ_CTL_J];
   const int n = j + 1;
   const int max_iter = ctl[LZ_CTL_MAXIT];
   const int check_every = ctl[LZ_CTL_CHECK];
   const double tol = *tolp;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    a[i] = ab[(int64_t)b * cap + i];
-    e[i] = ab[((int64_t)batch + b) * cap + i];  // e[n-1] = beta_j (the residual factor)
+  for (int i = lane; i < n; i += 32) {
+    const double ai = ab[(int64_t)b * cap + i], ei = ab[((int64_t)batch + b) * cap + i];
+    a[i] = ai;
+    e[i] = ei;  // e[n-1] = beta_j, the residual factor
+    e2[i] = ei * ei;
+    a32[i] = (float)ai;
+    e32[i] = (float)ei;
+    e232[i] = (float)(ei * ei);
   }
-  __syncthreads();
+  __syncwarp();
   const double beta = e[n - 1];
-  if (threadIdx.x == 0) {
-    double amax = 0.0;
-    for (int i = 0; i < n; ++i) amax = fmax(amax, fabs(a[i]));
-    s_scale = fmax(1.0, amax);
-    const bool bad = !isfinite(a[n - 1]) || !isfinite(beta);
-    const bool small_beta = beta < 1e-14 * s_scale;
-    s_do = bad ? 2 : ((n % check_every == 0) || n >= max_iter || (int64_t)n >= D || small_beta) ? 1 : 0;
+  // Gershgorin bounds (float64, lane-parallel), amax for the scales
+  double glo = 1e300, ghi = 1e300, amax = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double rad = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    glo = fmin(glo, a[i] - rad);
+    ghi = fmin(ghi, a[i]);
+    amax = fmax(amax, fabs(a[i]) + rad);
   }
-  __syncthreads();
-  if (s_do == 0) return;
-  if (s_do == 2) {
-    if (threadIdx.x == 0) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmin(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  }
+  const double scale_t = fmax(1.0, amax);
+  const bool bad = !isfinite(a[n - 1]) || !isfinite(beta);
+  const bool small_beta = beta < 1e-14 * scale_t;
+  const bool last = n >= max_iter || (int64_t)n >= D;
+  if (bad) {
+    if (lane == 0) {
       ctl[LZ_CTL_MEMBER + b] = LZ_NAN;
       ctl[LZ_CTL_MEMBER + batch + b] = n;
     }
     return;
   }
-  // Gershgorin bracket for the lowest eigenvalue, hi = min diagonal
-  if (threadIdx.x == 0) {
-    double lo = DBL_MAX, hi = DBL_MAX;
-    for (int i = 0; i < n; ++i) {
-      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-      lo = fmin(lo, a[i] - r);
-      hi = fmin(hi, a[i]);
+  if (!((n % check_every == 0) || last || small_beta)) return;
+
+  // ---- float32 estimate
+  const float eps32 = 1.2e-7f;
+  const float slack = (float)(8.0 * n * 6e-8 * scale_t);  // rounding of T to float32, Sturm backward error
+  float lo = (float)glo - slack, hi = (float)ghi + slack;
+  multisection<float>(a32, e232, n, lo, hi, 4.0f * eps32, 12, 1e-30f);
+  const float th32 = 0.5f * (lo + hi);
+  inverse_iteration<float>(a32, e32, n, lo - 2.0f * slack - 1e-6f * (float)scale_t, z32, rp32, 3, 1e-30f);
+  __syncwarp();
+  const double est = beta * fabs((double)z32[n - 1]);
+  const bool pass32 = est <= tol * fmax(1.0, fabs((double)th32));
+  if (!(pass32 || small_beta || last)) {
+    if (lane == 0) {
+      out[b * 4 + 0] = th32;
+      out[b * 4 + 1] = est;
+      out[b * 4 + 2] = beta;
     }
-    s_lo = lo - 1e-300;
-    s_hi = hi;
+    return;
   }
-  __syncthreads();
-  for (int round = 0; round < 64; ++round) {
-    const double lo = s_lo, hi = s_hi;
-    if (!(hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) || hi <= lo) break;
-    const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(blockDim.x + 1);
-    const int cnt = sturm_count(a, e, n, x);
-    if (threadIdx.x == 0) s_first = blockDim.x;
-    __syncthreads();
-    if (cnt >= 1) atomicMin(&s_first, (int)threadIdx.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int f = s_first;
-      const double step = (hi - lo) / (double)(blockDim.x + 1);
-      s_hi = (f < (int)blockDim.x) ? lo + step * (f + 1) : hi;
-      s_lo = lo + step * f;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    // shift strictly below lambda_min so that T - lo I is positive definite
-    const double lo = s_lo - 4.0 * DBL_EPSILON * s_scale;
-    const double theta = 0.5 * (s_lo + s_hi);
-    // inverse iteration with shift lo
-    for (int i = 0; i < n; ++i) z[i] = 1.0;
-    for (int it = 0; it < 3; ++it) {
-      // LDL^T: dpiv[i] pivots, forward then backward substitution
-      dpiv[0] = a[0] - lo;
-      for (int i = 1; i < n; ++i) {
-        double dp = dpiv[i - 1];
-        if (dp == 0.0) dp = DBL_MIN;
-        const double l = e[i - 1] / dp;
-        dpiv[i] = (a[i] - lo) - l * e[i - 1];
-        z[i] -= l * z[i - 1];
-      }
-      for (int i = 0; i < n; ++i) z[i] /= (dpiv[i] == 0.0 ? DBL_MIN : dpiv[i]);
-      for (int i = n - 2; i >= 0; --i) {
-        double dp = dpiv[i];
-        if (dp == 0.0) dp = DBL_MIN;
-        z[i] -= (e[i] / dp) * z[i + 1];
-      }
-      double nz = 0.0;
-      for (int i = 0; i < n; ++i) nz = fma(z[i], z[i], nz);
-      nz = sqrt(nz);
-      const double sg = z[0] < 0.0 ? -1.0 : 1.0;
-      for (int i = 0; i < n; ++i) z[i] = sg * z[i] / nz;
-    }
+
+  // ---- float64 eigenpair
+  double lo64 = (double)lo - 2.0 * slack, hi64 = (double)hi + 2.0 * slack;
+  lo64 = fmax(lo64, glo - 1e-300);
+  if (sturm_count<double>(a, e2, n, lo64, 1e-300) != 0) lo64 = glo - 1e-300;  // bracket must hold lambda_min
+  if (sturm_count<double>(a, e2, n, hi64, 1e-300) == 0) hi64 = ghi + 1e-12 * scale_t;
+  multisection<double>(a, e2, n, lo64, hi64, 4.0 * 2.2e-16, 64, 1e-300);
+  const double theta = 0.5 * (lo64 + hi64);
+  inverse_iteration<double>(a, e, n, lo64 - 4.0 * 2.2e-16 * scale_t, z, rp, 2, 1e-300);
+  __syncwarp();
+  if (lane == 0) {
     const double resid = beta * fabs(z[n - 1]);
     const double scale = fmax(1.0, fabs(theta));
     int code = 0;
     if (!isfinite(theta) || !isfinite(resid)) code = LZ_NAN;
-    else if (beta < 1e-14 * scale || (int64_t)n >= D) code = LZ_BREAKDOWN;
+    else if (small_beta || beta < 1e-14 * scale || (int64_t)n >= D) code = LZ_BREAKDOWN;
     else if (resid <= tol * scale) code = LZ_CONVERGED;
     else if (n >= max_iter) code = LZ_CAP;
     out[b * 4 + 0] = theta;
@@ -387,11 +479,12 @@ __global__ void k_reduce_terms(const double* __restrict__ part, const int32_t* _
 // ------------------------------------------------------------- launchers
 void lz_launch_multidot(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int nchunk, cudaStream_t st) {
-  k_multidot<<<dim3(nchunk, batch), LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, nchunk);
+  k_multidot<<<dim3(lz_dot_nchunk(D), batch), LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap,
+                                                                  lz_dot_nchunk(D));
 }
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, cudaStream_t st) {
-  k_reduce_rows<<<batch, 128, 0, st>>>(partial, h, ctl, nchunk, cap);
+  k_reduce_rows<<<dim3(batch, (cap + 31) / 32), 256, 0, st>>>(partial, h, ctl, nchunk, cap);
 }
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
                          const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, cudaStream_t st) {
@@ -404,7 +497,8 @@ void lz_launch_finalize_ab(const double* h, const double* norm_partial, double* 
 }
 void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
                        int cap, int64_t D, cudaStream_t st) {
-  k_tridiag<<<batch, LZ_TRI, 4 * cap * sizeof(double), st>>>(ab, s, out, ctl, tol, batch, cap, D);
+  k_tridiag<<<batch, 32, (5 * cap * sizeof(double) + 5 * cap * sizeof(float)), st>>>(ab, s, out, ctl, tol, batch,
+                                                                                   cap, D);
 }
 static int vec_blocks(int64_t D) {
   int64_t nb = (D + 255) / 256;

@@ -11,12 +11,15 @@ constexpr int LZ_THREADS = 256;   // threads of the vector kernels
 constexpr int LZ_EPT = 4;         // elements per thread
 constexpr int LZ_CHUNK = LZ_THREADS * LZ_EPT;
 constexpr int LZ_ROWS = 4;        // Krylov rows reduced together in k_multidot
-constexpr int LZ_TRI = 64;        // threads of the tridiagonal multisection
+constexpr int LZ_TRI = 32;        // threads of the tridiagonal multisection (one warp)
+constexpr int LZ_DOT_EPT = 16;    // elements per thread in the reorthogonalisation dots
+constexpr int LZ_DOT_CHUNK = LZ_THREADS * LZ_DOT_EPT;
 
 enum LzCtl : int { LZ_CTL_J = 0, LZ_CTL_MAXIT = 1, LZ_CTL_CHECK = 2, LZ_CTL_ALLDONE = 3, LZ_CTL_MEMBER = 4 };
 enum LzCode : int { LZ_RUNNING = 0, LZ_CONVERGED = 1, LZ_BREAKDOWN = 2, LZ_NAN = 3, LZ_CAP = 4 };
 
 inline int lz_nchunk(int64_t D) { return (int)((D + LZ_CHUNK - 1) / LZ_CHUNK); }
+inline int lz_dot_nchunk(int64_t D) { return (int)((D + LZ_DOT_CHUNK - 1) / LZ_DOT_CHUNK); }
 
 void lz_launch_multidot(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int nchunk, cudaStream_t st);

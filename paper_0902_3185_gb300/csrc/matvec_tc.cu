@@ -148,8 +148,12 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, const StageWork* __restrict__
 }
 
 // ------------------------------------------------------ grouped tile GEMM
-constexpr int TC_THREADS = 192;
-constexpr int L_TILE_BYTES = 128 * 128;  // 128 rows x 128 B
+constexpr int TC_EPI_WARPS = 8;                    // two per TMEM lane quadrant
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer, MMA, epilogue
+constexpr int L_TILE_BYTES = 128 * 128;             // 128 rows x 128 B
+constexpr int EPI_LD = 17;                          // staging row stride (doubles)
+constexpr int EPI_BYTES = TC_EPI_WARPS * 32 * EPI_LD * 8;
+constexpr int TC_CTRL_BYTES = 256;
 
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -167,8 +171,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* epi_stage = reinterpret_cast<double*>(smem_raw + TC_CTRL_BYTES);
   const uint32_t base_u32 = tc::smem_u32(smem_raw);
-  char* ring = smem_raw + (((base_u32 + 256 + 1023) & ~1023u) - base_u32);
+  char* ring = smem_raw + (((base_u32 + TC_CTRL_BYTES + EPI_BYTES + 1023) & ~1023u) - base_u32);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -178,7 +183,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(&acc_full[a], 1);
-      tc::mbar_init(&acc_empty[a], 4);
+      tc::mbar_init(&acc_empty[a], TC_EPI_WARPS);
     }
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -307,8 +312,12 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (the hardware's quadrant
+    // rule) and every other 16-column chunk: half = (w - 2) / 4.
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = 32 * q + lane;
+    double* stg = epi_stage + (warp - 2) * 32 * EPI_LD;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -319,8 +328,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       const int b = mv ? m / o.Rm : 0;
       const int i = mv ? m - b * o.Rm : 0;
       const int nend = min(tl.n0 + tl.ntile, o.N);
+      const bool add = o.add || accumulate;
       if (tl.seg_begin == tl.seg_end) {
-        if (mv && o.kind != OUT_PANEL && !(o.add || accumulate)) {
+        if (half == 0 && mv && o.kind != OUT_PANEL && !add) {
           double* yb = y + (int64_t)b * D + o.y_off;
           for (int n = tl.n0; n < nend; ++n)
             yb[o.kind == OUT_Y_ROW ? (int64_t)i * o.ldy + n : (int64_t)n * o.ldy + i] = 0.0;
@@ -334,10 +344,32 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       tc::tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(acc * acc_stride) + ((uint32_t)(32 * q) << 16);
       const double sc = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? coef[(int64_t)b * n_terms + o.term] : 1.0;
-      const bool add = o.add || accumulate;
-      for (int c0 = 0; c0 < tl.ntile; c0 += 16) {
+      // row-major output: element offset of this lane's row (-1 = row not stored)
+      const int64_t rbase = (o.kind == OUT_Y_ROW && mv) ? (int64_t)b * D + o.y_off + (int64_t)i * o.ldy : -1;
+      for (int c0 = 16 * half; c0 < tl.ntile; c0 += 32) {
         float v[16];
         tc::tmem_ld16(tb + (uint32_t)c0, v);
+        if (o.kind == OUT_Y_ROW) {
+          // stage 32 rows x 16 columns, then write each row's 16 values as one
+          // contiguous 128-byte segment (16 lanes per row, two rows per store)
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) stg[lane * EPI_LD + jj] = (double)v[jj];
+          __syncwarp();
+          const int jj = lane & 15;
+          const int n = tl.n0 + c0 + jj;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; rr += 2) {
+            const int r2 = rr + (lane >> 4);
+            const int64_t rb = __shfl_sync(0xffffffffu, rbase, r2);
+            if (rb >= 0 && n < nend) {
+              double* p = y + rb + n;
+              const double val = stg[r2 * EPI_LD + jj];
+              *p = add ? *p + val : val;
+            }
+          }
+          __syncwarp();
+          continue;
+        }
         if (!mv) continue;
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
@@ -346,8 +378,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           if (o.kind == OUT_PANEL) {
             store_panel<PREC>(o.p, o.p_lo, (int64_t)b * o.N + n, i, o.p_atoms, (float)(v[jj] * sc));
           } else {
-            double* p = y + (int64_t)b * D + o.y_off +
-                        (o.kind == OUT_Y_ROW ? (int64_t)i * o.ldy + n : (int64_t)n * o.ldy + i);
+            double* p = y + (int64_t)b * D + o.y_off + (int64_t)n * o.ldy + i;
             *p = add ? *p + (double)v[jj] : (double)v[jj];
           }
         }
@@ -817,9 +848,10 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   if (L.n_tiles == 0) return;
   const int r_tile = L.ntile_max * 128;
   const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
-  const int avail = 227 * 1024 - 2048;
+  const int fixed = TC_CTRL_BYTES + EPI_BYTES + 1024;  // control, epilogue staging, ring alignment
+  const int avail = 227 * 1024 - fixed;
   const int stages = std::max(2, std::min(8, avail / stage_bytes));
-  const int smem = 2048 + stages * stage_bytes;
+  const int smem = fixed + stages * stage_bytes;
   const int tmem_cols = L.ntile_max <= 128 ? 256 : 512;
   const int grid = std::min(L.n_tiles, s->num_sms);
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,

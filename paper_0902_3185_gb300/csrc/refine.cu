@@ -1,0 +1,244 @@
+// Float64 refinement of a mixed-precision ground state (batched, on device).
+//
+// Given psi from the mixed-precision Lanczos, each outer step computes the
+// float64 residual r = H psi - theta psi (theta = <psi, H psi>, psi
+// normalised) with one float64 product, then solves the projected correction
+// equation
+//     P (H - theta) P t = -r,   P = 1 - psi psi^T,   t orthogonal to psi,
+// by conjugate gradients whose products are the tensor-core (mixed) ones, and
+// updates psi <- (psi + t) / |psi + t|.  For theta below the second
+// eigenvalue, P (H - theta) P is positive definite on the complement of psi,
+// so CG applies.  Each outer step shrinks the eigenvector error by about
+// (mixed product error) * |H| / gap, so a few float64 products replace a
+// float64 Lanczos run.  All vectors and scalars are float64; reductions are
+// two-stage and fixed-order (deterministic).
+//
+// Per-member scalars (float64, device): [0] theta, [1] |b|, [2] rr, [3] pq,
+// [4] s1 = <psi, q>, [5] alpha, [6] beta, [7] rr_new; control (int32):
+// [b] done flag of the inner solve, [B + b] inner iterations, [2B] all
+// done, [2B + 1] inner iteration cap.
+
+#include "internal.h"
+#include "lanczos.h"
+#include "refine.h"
+
+namespace dmrg {
+
+__device__ __forceinline__ double rf_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+#define RF_LOOP(body)                                                                  \
+  _Pragma("unroll") for (int e = 0; e < LZ_EPT; ++e) {                               \
+    const int64_t d = (int64_t)chunk * LZ_CHUNK + e * LZ_THREADS + threadIdx.x;      \
+    if (d >= D) continue;                                                            \
+    const int64_t i = (int64_t)b * D + d;                                            \
+    body                                                                             \
+  }
+
+// q -= theta p ; part = <psi, q>
+__global__ void __launch_bounds__(LZ_THREADS)
+k_rf_shift_dot(double* __restrict__ q, const double* __restrict__ p, const double* __restrict__ psi,
+               const double* __restrict__ sc, const int32_t* __restrict__ ctl, double* __restrict__ part,
+               int64_t D, int nchunk, const int32_t* __restrict__ stop) {
+  __shared__ double red[LZ_THREADS / 32];
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if ((stop && *stop) || ctl[b]) return;
+  const double th = sc[b * RF_NSC + RF_THETA];
+  double acc = 0.0;
+  RF_LOOP({
+    const double v = q[i] - th * p[i];
+    q[i] = v;
+    acc = fma(psi[i], v, acc);
+  })
+  acc = rf_block_sum(acc, red);
+  if (threadIdx.x == 0) part[(int64_t)b * nchunk + chunk] = acc;
+}
+
+// q -= s1 psi ; part = <p, q>
+__global__ void __launch_bounds__(LZ_THREADS)
+k_rf_proj_dot(double* __restrict__ q, const double* __restrict__ p, const double* __restrict__ psi,
+              const double* __restrict__ sc, const int32_t* __restrict__ ctl, double* __restrict__ part,
+              int64_t D, int nchunk, const int32_t* __restrict__ stop) {
+  __shared__ double red[LZ_THREADS / 32];
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if ((stop && *stop) || ctl[b]) return;
+  const double s1 = sc[b * RF_NSC + RF_S1];
+  double acc = 0.0;
+  RF_LOOP({
+    const double v = q[i] - s1 * psi[i];
+    q[i] = v;
+    acc = fma(p[i], v, acc);
+  })
+  acc = rf_block_sum(acc, red);
+  if (threadIdx.x == 0) part[(int64_t)b * nchunk + chunk] = acc;
+}
+
+// t += alpha p ; res -= alpha q ; part = <res, res>
+__global__ void __launch_bounds__(LZ_THREADS)
+k_rf_update(double* __restrict__ t, double* __restrict__ res, const double* __restrict__ p,
+            const double* __restrict__ q, const double* __restrict__ sc, const int32_t* __restrict__ ctl,
+            double* __restrict__ part, int64_t D, int nchunk, const int32_t* __restrict__ stop) {
+  __shared__ double red[LZ_THREADS / 32];
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if ((stop && *stop) || ctl[b]) return;
+  const double al = sc[b * RF_NSC + RF_ALPHA];
+  double acc = 0.0;
+  RF_LOOP({
+    t[i] = fma(al, p[i], t[i]);
+    const double v = fma(-al, q[i], res[i]);
+    res[i] = v;
+    acc = fma(v, v, acc);
+  })
+  acc = rf_block_sum(acc, red);
+  if (threadIdx.x == 0) part[(int64_t)b * nchunk + chunk] = acc;
+}
+
+// p = res + beta p
+__global__ void __launch_bounds__(LZ_THREADS)
+k_rf_dir(double* __restrict__ p, const double* __restrict__ res, const double* __restrict__ sc,
+         const int32_t* __restrict__ ctl, int64_t D, const int32_t* __restrict__ stop) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if ((stop && *stop) || ctl[b]) return;
+  const double be = sc[b * RF_NSC + RF_BETA];
+  RF_LOOP({ p[i] = fma(be, p[i], res[i]); })
+}
+
+// sc[b][slot] = sum of the chunk partials (fixed order)
+__global__ void k_rf_sum(const double* __restrict__ part, double* __restrict__ sc, int slot, int nchunk, int batch,
+                         const int32_t* __restrict__ ctl, const int32_t* __restrict__ stop) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch || (stop && *stop) || (ctl && ctl[b])) return;
+  double t = 0.0;
+  for (int ch = 0; ch < nchunk; ++ch) t += part[(int64_t)b * nchunk + ch];
+  sc[b * RF_NSC + slot] = t;
+}
+
+// alpha = rr / pq; a non-positive pq ends the member's solve
+__global__ void k_rf_alpha(double* __restrict__ sc, int32_t* __restrict__ ctl, int batch,
+                           const int32_t* __restrict__ stop) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch || (stop && *stop) || ctl[b]) return;
+  double* s = sc + b * RF_NSC;
+  if (!(s[RF_PQ] > 0.0) || !isfinite(s[RF_PQ])) {
+    ctl[b] = 2;
+    s[RF_ALPHA] = 0.0;
+    return;
+  }
+  s[RF_ALPHA] = s[RF_RR] / s[RF_PQ];
+}
+
+// beta = rr_new / rr, rr = rr_new; stop a member at |res| <= eps |b| or the
+// cap; one thread walks the (few) members so the "all done" test is exact
+__global__ void k_rf_beta(double* __restrict__ sc, int32_t* __restrict__ ctl, const double* __restrict__ eps,
+                          int batch, int32_t* __restrict__ stop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || *stop) return;
+  const int max_inner = ctl[2 * batch + 1];
+  int all = 1;
+  for (int b = 0; b < batch; ++b) {
+    if (!ctl[b]) {
+      double* s = sc + b * RF_NSC;
+      const double rn = s[RF_RRNEW];
+      s[RF_BETA] = rn / s[RF_RR];
+      s[RF_RR] = rn;
+      const int it = ++ctl[batch + b];
+      if (sqrt(rn) <= (*eps) * s[RF_BNORM] || it >= max_inner || !isfinite(rn)) ctl[b] = 1;
+    }
+    all &= ctl[b] != 0;
+  }
+  if (all) *stop = 1;
+}
+
+// outer step: r = w - theta psi into res (negated: the CG right-hand side is
+// -r), p = res, t = 0; part = <res, res>
+__global__ void __launch_bounds__(LZ_THREADS)
+k_rf_start(const double* __restrict__ w, const double* __restrict__ psi, double* __restrict__ res,
+           double* __restrict__ p, double* __restrict__ t, const double* __restrict__ sc, double* __restrict__ part,
+           int64_t D, int nchunk) {
+  __shared__ double red[LZ_THREADS / 32];
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  const double th = sc[b * RF_NSC + RF_THETA];
+  double acc = 0.0;
+  RF_LOOP({
+    const double v = th * psi[i] - w[i];
+    res[i] = v;
+    p[i] = v;
+    t[i] = 0.0;
+    acc = fma(v, v, acc);
+  })
+  acc = rf_block_sum(acc, red);
+  if (threadIdx.x == 0) part[(int64_t)b * nchunk + chunk] = acc;
+}
+
+// per member: theta from <psi, w>; sets |b| and rr from |res|^2 afterwards
+__global__ void k_rf_set(double* __restrict__ sc, const double* __restrict__ src, int slot, int batch, int sqrt_too) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  sc[b * RF_NSC + slot] = src[b];
+  if (sqrt_too) {
+    sc[b * RF_NSC + RF_RR] = src[b];
+    sc[b * RF_NSC + RF_BNORM] = sqrt(src[b]);
+  }
+}
+
+// psi += t for members flagged active (mask[b] != 0)
+__global__ void k_rf_apply(double* __restrict__ psi, const double* __restrict__ t, const int32_t* __restrict__ mask,
+                           int64_t D) {
+  const int b = blockIdx.y;
+  if (!mask[b]) return;
+  for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x)
+    psi[(int64_t)b * D + d] += t[(int64_t)b * D + d];
+}
+
+// ------------------------------------------------------------- launchers
+static dim3 vgrid(int64_t D, int batch) { return dim3(lz_nchunk(D), batch); }
+
+void rf_launch_shift_dot(double* q, const double* p, const double* psi, const double* sc, const int32_t* ctl,
+                         double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st) {
+  k_rf_shift_dot<<<vgrid(D, B), LZ_THREADS, 0, st>>>(q, p, psi, sc, ctl, part, D, lz_nchunk(D), stop);
+}
+void rf_launch_proj_dot(double* q, const double* p, const double* psi, const double* sc, const int32_t* ctl,
+                        double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st) {
+  k_rf_proj_dot<<<vgrid(D, B), LZ_THREADS, 0, st>>>(q, p, psi, sc, ctl, part, D, lz_nchunk(D), stop);
+}
+void rf_launch_update(double* t, double* res, const double* p, const double* q, const double* sc,
+                      const int32_t* ctl, double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st) {
+  k_rf_update<<<vgrid(D, B), LZ_THREADS, 0, st>>>(t, res, p, q, sc, ctl, part, D, lz_nchunk(D), stop);
+}
+void rf_launch_dir(double* p, const double* res, const double* sc, const int32_t* ctl, int64_t D, int B,
+                   const int32_t* stop, cudaStream_t st) {
+  k_rf_dir<<<vgrid(D, B), LZ_THREADS, 0, st>>>(p, res, sc, ctl, D, stop);
+}
+void rf_launch_sum(const double* part, double* sc, int slot, int64_t D, int B, const int32_t* ctl,
+                   const int32_t* stop, cudaStream_t st) {
+  k_rf_sum<<<(B + 63) / 64, 64, 0, st>>>(part, sc, slot, lz_nchunk(D), B, ctl, stop);
+}
+void rf_launch_alpha(double* sc, int32_t* ctl, int B, const int32_t* stop, cudaStream_t st) {
+  k_rf_alpha<<<(B + 63) / 64, 64, 0, st>>>(sc, ctl, B, stop);
+}
+void rf_launch_beta(double* sc, int32_t* ctl, const double* eps, int B, int32_t* stop, cudaStream_t st) {
+  k_rf_beta<<<1, 32, 0, st>>>(sc, ctl, eps, B, stop);
+}
+void rf_launch_start(const double* w, const double* psi, double* res, double* p, double* t, const double* sc,
+                     double* part, int64_t D, int B, cudaStream_t st) {
+  k_rf_start<<<vgrid(D, B), LZ_THREADS, 0, st>>>(w, psi, res, p, t, sc, part, D, lz_nchunk(D));
+}
+void rf_launch_set(double* sc, const double* src, int slot, int B, int sqrt_too, cudaStream_t st) {
+  k_rf_set<<<(B + 63) / 64, 64, 0, st>>>(sc, src, slot, B, sqrt_too);
+}
+void rf_launch_apply(double* psi, const double* t, const int32_t* mask, int64_t D, int B, cudaStream_t st) {
+  int64_t nb = (D + 255) / 256;
+  if (nb > 2048) nb = 2048;
+  k_rf_apply<<<dim3((unsigned)nb, B), 256, 0, st>>>(psi, t, mask, D);
+}
+
+}  // namespace dmrg

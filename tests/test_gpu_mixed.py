@@ -109,12 +109,13 @@ def test_uncoupled_sector_zero_mixed(dev):
         assert np.all(y[off[6]:off[7]] == 0.0)
 
 
+@pytest.mark.parametrize("refine", ["newton", "lanczos"])
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
-def test_mixed_lanczos_refined_matches_fp64(dev, prec):
+def test_mixed_lanczos_refined_matches_fp64(dev, prec, refine):
     sb = CASES["chain_grown_b5"]()
     g = gpu_sb(sb)
     P0 = np.stack([seeded_normal(b, sb.dim) for b in range(sb.batch)])
-    e0, psi, infos, st = g.lanczos_ground(to_dev(P0), tol=1e-6, max_iter=300, prec=prec, refine=True,
+    e0, psi, infos, st = g.lanczos_ground(to_dev(P0), tol=1e-6, max_iter=300, prec=prec, refine=refine,
                                           refine_tol=1e-10)
     assert st == 0, infos
     psi = psi.cpu().numpy()
@@ -124,6 +125,9 @@ def test_mixed_lanczos_refined_matches_fp64(dev, prec):
         d = min(np.linalg.norm(psi[b] - ref.psi), np.linalg.norm(psi[b] + ref.psi))
         assert d < 1e-5
         assert infos[b]["mixed_matvecs"] > 0 and infos[b]["fp64_matvecs"] > 0
+        assert infos[b]["residual"] <= 1e-10 * max(1.0, abs(e0[b]))
+        if refine == "newton":
+            assert infos[b]["fp64_matvecs"] <= 8
 
 
 @pytest.mark.slow
