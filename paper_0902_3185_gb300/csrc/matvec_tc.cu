@@ -535,6 +535,9 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   const auto& r = sb->r;
   const auto& c = sb->c;
   const int S = sb->S;
+  // widest MMA N per tile: BF16x3 stages hold four operand tiles, so cap N at
+  // 128 to keep at least two pipeline stages in shared memory
+  const int max_ntile = prec == DMRG_BF16X3 ? 128 : 256;
   int64_t cur = base_off;
   auto alloc = [&](int64_t rows, int64_t K) {
     Panel p;
@@ -640,11 +643,11 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     int64_t kw = 0;
     for (const TcSeg& g : sg) kw += g.kchunks;
     for (int m0 = 0; m0 < o.M; m0 += 128)
-      for (int n0 = 0; n0 < o.N; n0 += 256) {
+      for (int n0 = 0; n0 < o.N; n0 += max_ntile) {
         TcTile t{};
         t.m0 = m0;
         t.n0 = n0;
-        t.ntile = (int)std::min<int64_t>(256, cdiv(o.N - n0, 16) * 16);
+        t.ntile = (int)std::min<int64_t>(max_ntile, cdiv(o.N - n0, 16) * 16);
         t.la = (int)std::min<int64_t>(16, cdiv(o.M - m0, 8));
         t.ra = (int)std::min<int64_t>(t.ntile / 8, cdiv(o.N - n0, 8));
         t.seg_begin = s0;
@@ -850,8 +853,9 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
   const int fixed = TC_CTRL_BYTES + EPI_BYTES + 1024;  // control, epilogue staging, ring alignment
   const int avail = 227 * 1024 - fixed;
-  const int stages = std::max(2, std::min(8, avail / stage_bytes));
+  const int stages = std::max(1, std::min(8, avail / stage_bytes));
   const int smem = fixed + stages * stage_bytes;
+  if (smem > 227 * 1024) throw CudaFail("tensor-core tile does not fit in shared memory");
   const int tmem_cols = L.ntile_max <= 128 ? 256 : 512;
   const int grid = std::min(L.n_tiles, s->num_sms);
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
