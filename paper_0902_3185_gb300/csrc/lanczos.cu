@@ -174,17 +174,22 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
   }
 }
 
-// alpha_j = h1[j] + h2[j], beta_j = sqrt(sum of norm partials)
+// alpha_j = h1[j] + h2[j], beta_j = sqrt(sum of norm partials); one warp per
+// member, lane-strided partial sums then a fixed shuffle tree (deterministic)
 __global__ void k_finalize_ab(const double* __restrict__ h, const double* __restrict__ norm_partial,
                               double* __restrict__ ab, const int32_t* __restrict__ ctl, int batch,
                               int cap, int nchunk) {
   const int b = blockIdx.x;
-  if (threadIdx.x != 0 || member_done(ctl, b)) return;
+  if (member_done(ctl, b)) return;
   const int j = ctl[LZ_CTL_J];
   double t = 0.0;
-  for (int ch = 0; ch < nchunk; ++ch) t += norm_partial[(int64_t)b * nchunk + ch];
-  ab[(int64_t)b * cap + j] = h[(int64_t)b * cap + j] + h[((int64_t)batch + b) * cap + j];
-  ab[((int64_t)batch + b) * cap + j] = sqrt(t);
+  for (int ch = threadIdx.x; ch < nchunk; ch += 32) t += norm_partial[(int64_t)b * nchunk + ch];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (threadIdx.x == 0) {
+    ab[(int64_t)b * cap + j] = h[(int64_t)b * cap + j] + h[((int64_t)batch + b) * cap + j];
+    ab[((int64_t)batch + b) * cap + j] = sqrt(t);
+  }
 }
 
 // Number of eigenvalues of T (diagonal a, off-diagonal e) below x: the
@@ -372,10 +377,14 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
 __global__ void k_next_vector(const double* __restrict__ w, const double* __restrict__ ab,
                               double* __restrict__ V, double* __restrict__ vcur,
                               const int32_t* __restrict__ ctl, int64_t D, int batch, int cap) {
+  __shared__ double s_inv;
   const int b = blockIdx.y;
   if (member_done(ctl, b)) return;
   const int j = ctl[LZ_CTL_J];
-  const double inv = 1.0 / ab[((int64_t)batch + b) * cap + j];
+  // one float64 division per block, not per element (GB300's float64 pipe is narrow)
+  if (threadIdx.x == 0) s_inv = 1.0 / ab[((int64_t)batch + b) * cap + j];
+  __syncthreads();
+  const double inv = s_inv;
   double* vn = V + ((int64_t)(j + 1) * batch + b) * D;
   for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
     const double v = w[(int64_t)b * D + d] * inv;
@@ -437,8 +446,11 @@ __global__ void k_sum_chunks(const double* __restrict__ part, double* __restrict
 // y[b] = x[b] / sqrt(nrm2[b]); also into y2 if given
 __global__ void k_scale_unit(const double* __restrict__ x, const double* __restrict__ nrm2,
                              double* __restrict__ y, double* __restrict__ y2, int64_t D) {
+  __shared__ double s_inv;
   const int b = blockIdx.y;
-  const double inv = 1.0 / sqrt(nrm2[b]);
+  if (threadIdx.x == 0) s_inv = 1.0 / sqrt(nrm2[b]);
+  __syncthreads();
+  const double inv = s_inv;
   for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
     const double v = x[(int64_t)b * D + d] * inv;
     y[(int64_t)b * D + d] = v;

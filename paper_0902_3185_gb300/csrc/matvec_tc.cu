@@ -76,15 +76,13 @@ struct TcOut {
 };
 
 struct StageJob {
-  int64_t src_off;  // sector block offset inside a member
-  int32_t r, c;     // source block dims
-  int32_t transpose, term;
+  int64_t src_off;    // sector block offset inside a member
+  int64_t first;      // first element of this job in the flattened stream
   char* p;
   int64_t p_lo;
+  int32_t r, c;       // source block dims
+  int32_t transpose, term;
   int32_t atoms, pad;
-};
-struct StageWork {
-  int32_t job, tile;  // tile = 32 x 32 block of the source, row-major over the source tiles
 };
 
 // byte offset of element (row, k) inside a panel
@@ -112,39 +110,50 @@ __device__ __forceinline__ void store_panel(char* p, int64_t p_lo, int64_t row, 
 
 // ---------------------------------------------------------------- staging
 // float64 psi blocks -> operand panels (optionally transposed and scaled by
-// the member's coefficient).  One block = one 32 x 32 tile of one job.
+// the member's coefficient).  The jobs' elements form one flat stream (jobs
+// back to back, `first` = prefix); consecutive threads take consecutive
+// elements: row-major for a plain job, column-major for a transposed one, so
+// that both the panel writes (along K) and, for plain jobs, the reads are
+// contiguous.  Each thread finds its job by binary search once, then walks.
 template <int PREC>
 __global__ void __launch_bounds__(256)
-tc_stage_kernel(const StageJob* __restrict__ jobs, const StageWork* __restrict__ work, const double* __restrict__ x,
+tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, const double* __restrict__ x,
                 int64_t D, const double* __restrict__ coef, int n_terms, const int32_t* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ double t[32][33];
-  const StageWork w = work[blockIdx.x];
-  const StageJob j = jobs[w.job];
   const int b = blockIdx.y;
-  const int tc_ = (j.c + 31) / 32;
-  const int a0 = (w.tile / tc_) * 32, b0 = (w.tile % tc_) * 32;
-  const double sc = j.term >= 0 ? coef[(int64_t)b * n_terms + j.term] : 1.0;
-  const double* src = x + (int64_t)b * D + j.src_off;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int e = ty; e < 32; e += 8) {
-    const int a = a0 + e, c = b0 + tx;
-    t[e][tx] = (a < j.r && c < j.c) ? src[(int64_t)a * j.c + c] * sc : 0.0;
+  const int64_t e0 = (int64_t)blockIdx.x * (256 * 8) + threadIdx.x;
+  if (e0 >= total) return;
+  int lo = 0, hi = n_jobs - 1;  // last job with first <= e0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].first <= e0) lo = mid;
+    else hi = mid - 1;
   }
-  __syncthreads();
-  constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
-  for (int e = ty; e < 32; e += 8) {
+  int jid = lo;
+  StageJob j = jobs[jid];
+  int64_t jend = j.first + (int64_t)j.r * j.c;
+  double sc = j.term >= 0 ? coef[(int64_t)b * n_terms + j.term] : 1.0;
+  const double* xb = x + (int64_t)b * D;
+#pragma unroll 1
+  for (int u = 0; u < 8; ++u) {
+    const int64_t e = e0 + (int64_t)u * 256;
+    if (e >= total) break;
+    while (e >= jend) {
+      j = jobs[++jid];
+      jend = j.first + (int64_t)j.r * j.c;
+      sc = j.term >= 0 ? coef[(int64_t)b * n_terms + j.term] : 1.0;
+    }
+    const int64_t loc = e - j.first;
     if (!j.transpose) {  // row = b*r + a, k = c
-      const int a = a0 + e, c = b0 + tx;
-      if (a < j.r && c < j.c)
-        store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, c, j.atoms, (float)t[e][tx]);
-    } else {  // row = b*c + c', k = a
-      const int c = b0 + e, a = a0 + tx;
-      if (a < j.r && c < j.c)
-        store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + c, a, j.atoms, (float)t[tx][e]);
+      const int64_t a = loc / j.c, cc = loc - a * j.c;
+      const double v = xb[j.src_off + a * j.c + cc] * sc;
+      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, cc, j.atoms, (float)v);
+    } else {  // row = b*c + c', k = a (column-major walk)
+      const int64_t cc = loc / j.r, a = loc - cc * j.r;
+      const double v = xb[j.src_off + a * j.c + cc] * sc;
+      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + cc, a, j.atoms, (float)v);
     }
   }
-  (void)es;
 }
 
 // ------------------------------------------------------ grouped tile GEMM
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
                const TcOut* __restrict__ outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
                int n_terms, int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
-               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols) {
+               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes) {
   if (skip && *skip) return;
   extern __shared__ __align__(1024) char smem_raw[];
   // control block, then 1024-aligned stage ring
@@ -173,7 +182,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* epi_stage = reinterpret_cast<double*>(smem_raw + TC_CTRL_BYTES);
   const uint32_t base_u32 = tc::smem_u32(smem_raw);
-  char* ring = smem_raw + (((base_u32 + TC_CTRL_BYTES + EPI_BYTES + 1023) & ~1023u) - base_u32);
+  char* ring = smem_raw + (((base_u32 + TC_CTRL_BYTES + (uint32_t)epi_bytes + 1023) & ~1023u) - base_u32);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -454,12 +463,13 @@ struct Launch {  // one grouped GEMM launch
   TcOut* outs = nullptr;
   int n_tiles = 0;
   int ntile_max = 16;
+  bool has_row_out = false;  // some output is row-major float64 (needs epilogue staging)
 };
 
 struct PairSet {  // the forward pairs or their transposes
   StageJob* jobs = nullptr;
-  StageWork* work = nullptr;
-  int n_work = 0;
+  int n_jobs = 0;
+  int64_t n_elems = 0;  // per member
   Launch ph1, grpE, grpS;
 };
 
@@ -483,7 +493,6 @@ void free_launch(Launch& l) {
 }
 void free_set(PairSet& s) {
   if (s.jobs) cudaFree(s.jobs);
-  if (s.work) cudaFree(s.work);
   free_launch(s.ph1);
   free_launch(s.grpE);
   free_launch(s.grpS);
@@ -576,12 +585,14 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   }
   auto dptr = [&](const Panel& p) { return d_hi + p.off; };
 
-  // ---- staging jobs
+  // ---- staging jobs (one flat element stream)
   std::vector<StageJob> jobs;
-  std::vector<StageWork> work;
+  int64_t n_elems = 0;
   auto add_job = [&](int s, int transpose, int term, const Panel& p) {
+    if ((int64_t)r[s] * c[s] == 0) return;
     StageJob j{};
     j.src_off = sb->off[s];
+    j.first = n_elems;
     j.r = r[s];
     j.c = c[s];
     j.transpose = transpose;
@@ -589,21 +600,9 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     j.p = dptr(p);
     j.p_lo = lo_delta;
     j.atoms = (int32_t)p.atoms;
-    const int jid = (int)jobs.size();
     jobs.push_back(j);
-    const int nt = (int)(cdiv(r[s], 32) * cdiv(c[s], 32));
-    for (int t = 0; t < nt; ++t) work.push_back({jid, t});
+    n_elems += (int64_t)r[s] * c[s];
   };
-  for (int s = 0; s < S; ++s) {
-    if (needP[s]) add_job(s, 0, -1, psiP[s]);
-    if (needPT[s]) add_job(s, 1, -1, psiPT[s]);
-  }
-  for (size_t i = 0; i < np; ++i) {
-    const EPair& e = P[i];
-    if (e.flags & DMRG_ID_A) add_job(e.s_in, 0, e.term, pS[i]);
-    else if (e.flags & DMRG_ID_B) add_job(e.s_in, 1, e.term, pS[i]);
-  }
-
   // ---- grouped launches
   struct Build {
     std::vector<TcTile> tiles;
@@ -735,13 +734,15 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     L.outs = up(B.outs);
     L.n_tiles = (int)t.size();
     L.ntile_max = B.ntile_max;
+    L.has_row_out = false;
+    for (const TcOut& o : B.outs) L.has_row_out = L.has_row_out || o.kind == OUT_Y_ROW;
   };
   finish(L1, out.ph1);
   finish(LE, out.grpE);
   finish(LS, out.grpS);
   out.jobs = up(jobs);
-  out.work = up(work);
-  out.n_work = (int)work.size();
+  out.n_jobs = (int)jobs.size();
+  out.n_elems = n_elems;
   return cur - base_off;
 }
 
@@ -775,7 +776,7 @@ int tc_launches(const dmrg_sb* sb, int prec) {
   const State* s = st_of(sb);
   if (!s || !s->ok) return 0;
   const PairSet& ps = s->f[prec == DMRG_TF32 ? 0 : 1].fwd;
-  return (ps.n_work > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
+  return (ps.n_elems > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
 }
 
 void tc_build(dmrg_sb* sb) {
@@ -851,7 +852,8 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   if (L.n_tiles == 0) return;
   const int r_tile = L.ntile_max * 128;
   const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
-  const int fixed = TC_CTRL_BYTES + EPI_BYTES + 1024;  // control, epilogue staging, ring alignment
+  const int epi = L.has_row_out ? EPI_BYTES : 0;       // row-major output staging
+  const int fixed = TC_CTRL_BYTES + epi + 1024;        // control, epilogue staging, ring alignment
   const int avail = 227 * 1024 - fixed;
   const int stages = std::max(1, std::min(8, avail / stage_bytes));
   const int smem = fixed + stages * stage_bytes;
@@ -860,15 +862,17 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   const int grid = std::min(L.n_tiles, s->num_sms);
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, accumulate, skip,
-                                                       sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols);
+                                                       sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi);
 }
 
 template <int PREC>
 static void run_set(const State* s, const PairSet& ps, const double* x, double* y, const dmrg_sb* sb,
                     int accumulate, const int32_t* skip, cudaStream_t st) {
-  if (ps.n_work > 0)
-    tc_stage_kernel<PREC><<<dim3(ps.n_work, sb->batch), 256, 0, st>>>(ps.jobs, ps.work, x, sb->D, sb->d_coeffs,
-                                                                      sb->n_terms, skip);
+  if (ps.n_elems > 0) {
+    const int64_t blocks = (ps.n_elems + 256 * 8 - 1) / (256 * 8);
+    tc_stage_kernel<PREC><<<dim3((unsigned)blocks, sb->batch), 256, 0, st>>>(ps.jobs, ps.n_jobs, ps.n_elems, x, sb->D,
+                                                                            sb->d_coeffs, sb->n_terms, skip);
+  }
   run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
   run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, st);
   run_gemm<PREC>(s, ps.grpS, y, sb, accumulate, skip, st);
