@@ -603,6 +603,15 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     jobs.push_back(j);
     n_elems += (int64_t)r[s] * c[s];
   };
+  for (int s = 0; s < S; ++s) {
+    if (needP[s]) add_job(s, 0, -1, psiP[s]);
+    if (needPT[s]) add_job(s, 1, -1, psiPT[s]);
+  }
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (e.flags & DMRG_ID_A) add_job(e.s_in, 0, e.term, pS[i]);
+    else if (e.flags & DMRG_ID_B) add_job(e.s_in, 1, e.term, pS[i]);
+  }
   // ---- grouped launches
   struct Build {
     std::vector<TcTile> tiles;
