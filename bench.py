@@ -258,6 +258,27 @@ def main():
     ms_per_step = ms / args.steps
     value = world * mv_count * flops_mv / (ms / 1e3) / 1e12
 
+    # where the step goes: the mixed Lanczos alone, then the refinement
+    def timed(fn):
+        a_ = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        r_ = fn()
+        b_.record(stream)
+        torch.cuda.synchronize(dev)
+        return a_.elapsed_time(b_), r_
+    t_lz, (_, _, info_lz, _) = timed(lambda: g.lanczos_ground(
+        x0, tol=args.tol if prec == "fp64" else args.mixed_tol, max_iter=args.max_iter, prec=prec,
+        refine="none", graph_iters=8))
+    t_full, (_, _, info_full, _) = timed(lambda: g.lanczos_ground(
+        x0, tol=args.tol if prec == "fp64" else args.mixed_tol, max_iter=args.max_iter, prec=prec,
+        refine=args.refine, refine_tol=args.tol, graph_iters=8))
+    breakdown = {"lanczos_ms": t_lz, "refine_ms": t_full - t_lz,
+                 "lanczos_iters": max(i["iters"] for i in info_full),
+                 "fp64_products": max(i["fp64_matvecs"] for i in info_full),
+                 "mixed_products": max(i["mixed_matvecs"] for i in info_full),
+                 "residual_max": max(i["residual"] for i in info_full)}
+
     # kernel-only product timing (events on the launching stream)
     y = g.empty()
     reps = 20
@@ -323,6 +344,7 @@ def main():
            "matvec_fp64_tflops": flops_mv / (mv64_ms / 1e3) / 1e12,
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
+           "breakdown": breakdown,
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline_sample(sb)

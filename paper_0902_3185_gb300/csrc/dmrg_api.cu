@@ -82,55 +82,69 @@ dmrg_status guard(dmrg_sb* sb, F&& fn) {
 }
 
 // ----------------------------------------------------------- task building
-struct SegSpec {
-  int32_t l_buf;
-  int64_t l_off;
-  int32_t ldl, l_trans;
-  int32_t r_buf;
-  int64_t r_off;
-  int32_t ldr, r_trans;
-  int32_t K, coef;
+// An operator block as seen by one product: element (i, j) lives at
+// ops[off + (trans ? j*ld + i : i*ld + j)] (trans = 1 reads A^T / B^T).
+struct OpAcc {
+  int64_t off;
+  int32_t ld, trans;
 };
 
-SegF64 mkseg(const SegSpec& s) {
+// A (term, sector pair) in the direction of one product: forward pairs, or
+// the transposed pairs of H^T.  A is r[s_out] x r[s_in], B is c[s_out] x c[s_in].
+struct GPair {
+  int32_t term, s_out, s_in, flags, order;
+  OpAcc A, B;
+};
+
+SegF64 seg_base() {
   SegF64 g{};
-  g.l_off = s.l_off;
-  g.r_off = s.r_off;
-  g.l_buf = s.l_buf;
-  g.r_buf = s.r_buf;
-  g.ldl = s.ldl;
-  g.ldr = s.ldr;
-  g.K = s.K;
-  g.l_trans = s.l_trans;
-  g.r_trans = s.r_trans;
-  g.coef = s.coef;
+  g.coef = -1;
   return g;
 }
 
+// L = a block operand (no members)
+void set_L_op(SegF64& g, const OpAcc& o) {
+  g.l_buf = BUF_OPS;
+  g.l_off = o.off;
+  g.ldl = o.ld;
+  g.l_trans = o.trans;
+}
+// R(k, n) = B(n, k): the transposed block as the right operand
+void set_R_opT(SegF64& g, const OpAcc& o) {
+  g.r_buf = BUF_OPS;
+  g.r_off = o.off;
+  g.ldr = o.ld;
+  g.r_trans = o.trans ? 0 : 1;
+}
+
 // Append the tiles of one M x N output and its segment list; returns the
-// positions (before sorting) of the new tiles.
-void add_output(TaskListF64& tl, int32_t c_buf, int64_t c_off, int32_t ldc, int32_t M, int32_t N, int32_t mode,
-                const std::vector<SegF64>& segs, std::vector<int64_t>* ids) {
-  if (M <= 0 || N <= 0) return;
+// positions (before sorting) of the new tiles in *ids.
+void add_output(TaskListF64& tl, const TileF64& proto, const std::vector<SegF64>& segs, std::vector<int64_t>* ids) {
+  if (proto.M <= 0 || proto.N <= 0) return;
   const int32_t sb = (int32_t)tl.h_segs.size();
   tl.h_segs.insert(tl.h_segs.end(), segs.begin(), segs.end());
   const int32_t se = (int32_t)tl.h_segs.size();
-  for (int32_t m0 = 0; m0 < M; m0 += 64)
-    for (int32_t n0 = 0; n0 < N; n0 += 64) {
-      TileF64 t{};
-      t.c_off = c_off;
-      t.c_buf = c_buf;
-      t.ldc = ldc;
-      t.M = M;
-      t.N = N;
+  for (int32_t m0 = 0; m0 < proto.M; m0 += 64)
+    for (int32_t n0 = 0; n0 < proto.N; n0 += 64) {
+      TileF64 t = proto;
       t.m0 = m0;
       t.n0 = n0;
       t.seg_begin = sb;
       t.seg_end = se;
-      t.mode = mode;
       if (ids) ids->push_back((int64_t)tl.h_tiles.size());
       tl.h_tiles.push_back(t);
     }
+}
+
+TileF64 out_tile(int32_t buf, int64_t off, int32_t ldc, int32_t M, int32_t N, int32_t mode) {
+  TileF64 t{};
+  t.c_buf = buf;
+  t.c_off = off;
+  t.ldc = ldc;
+  t.M = M;
+  t.N = N;
+  t.mode = mode;
+  return t;
 }
 
 // Heaviest tiles first (one CTA per tile); returns new position of each old tile.
@@ -166,125 +180,162 @@ void free_tl(TaskListF64& tl) {
   tl.d_segs = nullptr;
 }
 
-bool is_gemm_pair(const PairH& p) { return (p.flags & (DMRG_ID_A | DMRG_ID_B)) == 0; }
+bool is_gemm_pair(int flags) { return (flags & (DMRG_ID_A | DMRG_ID_B)) == 0; }
+
+// One product over a pair set with the batch members stacked:
+//   phase 1 (two-GEMM pairs): order 1  X_b = c Psi_b B^T  (members along M)
+//                              order 0  T_b = c A Psi_b    (members along N)
+//   group M (members along M): Y_b += c Psi_b B^T (A = 1), Y_b += T_b B^T
+//   group N (members along N): Y_b += c A Psi_b (B = 1),   Y_b += A X_b
+// Intermediates: member b, pair i at T + b*Tm + toff[i], row-major (order 1:
+// r_in x c_out, order 0: r_out x c_in).  scaled = false drops every
+// coefficient (for the per-term dot products).
+void build_stacked(const dmrg_sb* sb, const std::vector<GPair>& P, const std::vector<int64_t>& toff, int64_t Tm,
+                   bool scaled, TaskListF64& ph1, TaskListF64* gM, TaskListF64* gN) {
+  const int nb = sb->batch;
+  const int64_t D = sb->D;
+  const auto& r = sb->r;
+  const auto& c = sb->c;
+  for (size_t i = 0; i < P.size(); ++i) {
+    const GPair& p = P[i];
+    if (!is_gemm_pair(p.flags)) continue;
+    const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
+    SegF64 g = seg_base();
+    g.K = p.order == 1 ? ci : ri;
+    if (scaled) { g.coef = p.term; g.coef_mode = p.order == 1 ? 1 : 2; }
+    if (p.order == 1) {  // X_b = Psi_b B^T : M = (b, a'), N = beta, K = c_in
+      g.l_buf = BUF_X; g.l_off = sb->off[p.s_in]; g.ldl = ci; g.l_rm = ri; g.l_bs = D;
+      set_R_opT(g, p.B);
+      TileF64 t = out_tile(BUF_T, toff[i], co, nb * ri, co, TM_STORE);
+      t.c_rm = ri; t.c_axis = 0; t.c_bs = Tm;
+      add_output(ph1, t, {g}, nullptr);
+    } else {  // T_b = A Psi_b : M = alpha, N = (b, beta'), K = r_in
+      set_L_op(g, p.A);
+      g.r_buf = BUF_X; g.r_off = sb->off[p.s_in]; g.ldr = ci; g.r_trans = 0; g.r_rm = ci; g.r_bs = D;
+      TileF64 t = out_tile(BUF_T, toff[i], ci, ro, nb * ci, TM_STORE);
+      t.c_rm = ci; t.c_axis = 1; t.c_bs = Tm;
+      add_output(ph1, t, {g}, nullptr);
+    }
+  }
+  if (!gM) return;
+  std::vector<std::vector<size_t>> by_out(sb->S);
+  for (size_t i = 0; i < P.size(); ++i) by_out[P[i].s_out].push_back(i);
+  for (int s = 0; s < sb->S; ++s) {
+    if ((int64_t)r[s] * c[s] == 0) continue;
+    std::vector<SegF64> sM, sN;
+    for (size_t i : by_out[s]) {
+      const GPair& p = P[i];
+      const int32_t ri = r[p.s_in], ci = c[p.s_in], co = c[p.s_out];
+      SegF64 g = seg_base();
+      if (p.flags & DMRG_ID_A) {  // Y_b += c Psi_b B^T
+        g.K = ci;
+        g.l_buf = BUF_X; g.l_off = sb->off[p.s_in]; g.ldl = ci; g.l_rm = ri; g.l_bs = D;
+        set_R_opT(g, p.B);
+        if (scaled) { g.coef = p.term; g.coef_mode = 1; }
+        sM.push_back(g);
+      } else if (p.flags & DMRG_ID_B) {  // Y_b += c A Psi_b
+        g.K = ri;
+        set_L_op(g, p.A);
+        g.r_buf = BUF_X; g.r_off = sb->off[p.s_in]; g.ldr = ci; g.r_trans = 0; g.r_rm = ci; g.r_bs = D;
+        if (scaled) { g.coef = p.term; g.coef_mode = 2; }
+        sN.push_back(g);
+      } else if (p.order == 0) {  // Y_b += T_b B^T
+        g.K = ci;
+        g.l_buf = BUF_T; g.l_off = toff[i]; g.ldl = ci; g.l_rm = r[p.s_out]; g.l_bs = Tm;
+        set_R_opT(g, p.B);
+        sM.push_back(g);
+      } else {  // Y_b += A X_b
+        g.K = ri;
+        set_L_op(g, p.A);
+        g.r_buf = BUF_T; g.r_off = toff[i]; g.ldr = co; g.r_trans = 0; g.r_rm = co; g.r_bs = Tm;
+        sN.push_back(g);
+      }
+    }
+    const bool hasM = !sM.empty(), hasN = !sN.empty();
+    if (hasM || !hasN) {
+      TileF64 t = out_tile(BUF_Y, sb->off[s], c[s], nb * r[s], c[s], TM_STORE);
+      t.c_rm = r[s]; t.c_axis = 0; t.c_bs = D;
+      add_output(*gM, t, sM, nullptr);
+    }
+    if (hasN) {
+      TileF64 t = out_tile(BUF_Y, sb->off[s], c[s], r[s], nb * c[s], TM_STORE);
+      t.c_rm = c[s]; t.c_axis = 1; t.c_bs = D; t.add = hasM ? 1 : 0;
+      add_output(*gN, t, sN, nullptr);
+    }
+  }
+}
+
+// intermediate layout of a pair set: offsets per pair inside one member's T
+int64_t layout_T(const dmrg_sb* sb, const std::vector<GPair>& P, std::vector<int64_t>& toff) {
+  toff.assign(P.size(), -1);
+  int64_t T = 0;
+  for (size_t i = 0; i < P.size(); ++i) {
+    const GPair& p = P[i];
+    if (!is_gemm_pair(p.flags)) continue;
+    const int64_t ro = sb->r[p.s_out], ri = sb->r[p.s_in], co = sb->c[p.s_out], ci = sb->c[p.s_in];
+    toff[i] = T;
+    T += p.order == 0 ? ro * ci : ri * co;
+  }
+  return T;
+}
 
 void build_f64_tasks(dmrg_sb* sb) {
   const int nt = sb->n_terms;
   const auto& r = sb->r;
   const auto& c = sb->c;
-  // intermediate offsets (per member), forward and transposed orders
-  std::vector<int64_t> toff_f(sb->pairs.size(), -1), toff_b(sb->pairs.size(), -1);
-  std::vector<int32_t> border(sb->pairs.size(), 0);
-  int64_t Tf = 0, Tb = 0;
-  for (size_t i = 0; i < sb->pairs.size(); ++i) {
-    const PairH& p = sb->pairs[i];
-    if (!is_gemm_pair(p)) continue;
-    const int64_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
-    toff_f[i] = Tf;
-    Tf += p.order == 0 ? ro * ci : ri * co;
-    const double c0 = 2.0 * ri * ro * co + 2.0 * ri * co * ci;  // (A^T G) B first
-    const double c1 = 2.0 * ro * co * ci + 2.0 * ri * ro * ci;  // A^T (G B) first
-    border[i] = c0 <= c1 ? 0 : 1;
-    toff_b[i] = Tb;
-    Tb += border[i] == 0 ? ri * co : ro * ci;
+  std::vector<GPair> fw, bw;
+  for (const PairH& p : sb->pairs) {
+    const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
+    GPair f{p.term, p.s_out, p.s_in, p.flags, p.order, {p.a_off, ri, 0}, {p.b_off, ci, 0}};
+    fw.push_back(f);
+    // transposed pair: s_in <- s_out, A^T (r_in x r_out), B^T (c_in x c_out)
+    GPair t{p.term, p.s_in, p.s_out, p.flags, 0, {p.a_off, ri, 1}, {p.b_off, ci, 1}};
+    if (is_gemm_pair(p.flags)) {
+      const double c0 = 2.0 * ri * ro * co + 2.0 * ri * co * ci;  // (A^T G) B first
+      const double c1 = 2.0 * ro * co * ci + 2.0 * ri * ro * ci;  // A^T (G B) first
+      t.order = c0 <= c1 ? 0 : 1;
+    }
+    bw.push_back(t);
   }
+  std::vector<int64_t> toff_f, toff_b;
+  const int64_t Tf = layout_T(sb, fw, toff_f), Tb = layout_T(sb, bw, toff_b);
   const int64_t Tm = std::max(Tf, Tb);
   sb->T_elems = Tm * sb->batch;
   if (sb->d_T) cudaFree(sb->d_T);
   sb->d_T = dalloc<double>((size_t)sb->T_elems);
 
-  std::vector<std::vector<size_t>> by_out(sb->S), by_in(sb->S);
-  for (size_t i = 0; i < sb->pairs.size(); ++i) {
-    by_out[sb->pairs[i].s_out].push_back(i);
-    by_in[sb->pairs[i].s_in].push_back(i);
-  }
-  std::vector<int64_t> dot_ids;                 // tile id (pre-sort) per recorded entry
-  std::vector<std::vector<int64_t>> dot_list((size_t)sb->batch * nt);
+  build_stacked(sb, fw, toff_f, Tm, true, sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3);
+  build_stacked(sb, bw, toff_b, Tm, true, sb->f64_bwd1, &sb->f64_bwd2, &sb->f64_bwd3);
+  build_stacked(sb, fw, toff_f, Tm, false, sb->f64_dot1, nullptr, nullptr);
 
+  // per-term dots: one unstacked output per (member, pair), dotted with G
+  std::vector<std::vector<int64_t>> dot_list((size_t)sb->batch * nt);
   for (int b = 0; b < sb->batch; ++b) {
-    const int64_t xb = (int64_t)b * sb->D;
-    const int64_t tb = (int64_t)b * Tm;
-    auto coef = [&](const PairH& p) { return b * nt + p.term; };
-    auto X = [&](int s) { return xb + sb->off[s]; };
-    // ---------------- forward and dot phase 1
-    for (size_t i = 0; i < sb->pairs.size(); ++i) {
-      const PairH& p = sb->pairs[i];
-      if (!is_gemm_pair(p)) continue;
-      const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
-      for (int pass = 0; pass < 2; ++pass) {
-        TaskListF64& tl = pass == 0 ? sb->f64_fwd1 : sb->f64_dot1;
-        const int32_t cf = pass == 0 ? coef(p) : -1;
-        if (p.order == 0) {  // T = A Psi_in  (r_out x c_in)
-          add_output(tl, BUF_T, tb + toff_f[i], ci, ro, ci, TM_STORE,
-                     {mkseg({BUF_OPS, p.a_off, ri, 0, BUF_X, X(p.s_in), ci, 0, ri, cf})}, nullptr);
-        } else {  // T = Psi_in B^T  (r_in x c_out)
-          add_output(tl, BUF_T, tb + toff_f[i], co, ri, co, TM_STORE,
-                     {mkseg({BUF_X, X(p.s_in), ci, 0, BUF_OPS, p.b_off, ci, 1, ci, cf})}, nullptr);
-        }
-      }
-    }
-    // forward phase-2 segments of one pair (coefficient cf for identity pairs)
-    auto fwd_seg = [&](size_t i, int32_t cf) {
-      const PairH& p = sb->pairs[i];
+    const int64_t xb = (int64_t)b * sb->D, tb = (int64_t)b * Tm;
+    for (size_t i = 0; i < fw.size(); ++i) {
+      const GPair& p = fw[i];
       const int32_t ri = r[p.s_in], ci = c[p.s_in], co = c[p.s_out];
-      if (p.flags & DMRG_ID_B)
-        return mkseg({BUF_OPS, p.a_off, ri, 0, BUF_X, X(p.s_in), ci, 0, ri, cf});
-      if (p.flags & DMRG_ID_A)
-        return mkseg({BUF_X, X(p.s_in), ci, 0, BUF_OPS, p.b_off, ci, 1, ci, cf});
-      if (p.order == 0)
-        return mkseg({BUF_T, tb + toff_f[i], ci, 0, BUF_OPS, p.b_off, ci, 1, ci, -1});
-      return mkseg({BUF_OPS, p.a_off, ri, 0, BUF_T, tb + toff_f[i], co, 0, ri, -1});
-    };
-    // ---------------- forward phase 2: one output per sector
-    for (int s = 0; s < sb->S; ++s) {
-      if ((int64_t)r[s] * c[s] == 0) continue;
-      std::vector<SegF64> segs;
-      for (size_t i : by_out[s]) segs.push_back(fwd_seg(i, coef(sb->pairs[i])));
-      add_output(sb->f64_fwd2, BUF_Y, X(s), c[s], r[s], c[s], TM_STORE, segs, nullptr);
-    }
-    // ---------------- dot phase 2: one output per pair, dotted with G
-    for (size_t i = 0; i < sb->pairs.size(); ++i) {
-      const PairH& p = sb->pairs[i];
+      SegF64 g = seg_base();
+      if (p.flags & DMRG_ID_B) {
+        g.K = ri; set_L_op(g, p.A);
+        g.r_buf = BUF_X; g.r_off = xb + sb->off[p.s_in]; g.ldr = ci; g.r_trans = 0;
+      } else if (p.flags & DMRG_ID_A) {
+        g.K = ci; g.l_buf = BUF_X; g.l_off = xb + sb->off[p.s_in]; g.ldl = ci; set_R_opT(g, p.B);
+      } else if (p.order == 0) {
+        g.K = ci; g.l_buf = BUF_T; g.l_off = tb + toff_f[i]; g.ldl = ci; set_R_opT(g, p.B);
+      } else {
+        g.K = ri; set_L_op(g, p.A);
+        g.r_buf = BUF_T; g.r_off = tb + toff_f[i]; g.ldr = co; g.r_trans = 0;
+      }
       std::vector<int64_t> ids;
-      add_output(sb->f64_dot2, BUF_G, X(p.s_out), c[p.s_out], r[p.s_out], c[p.s_out], TM_DOT, {fwd_seg(i, -1)},
-                 &ids);
+      add_output(sb->f64_dot2, out_tile(BUF_G, xb + sb->off[p.s_out], c[p.s_out], r[p.s_out], c[p.s_out], TM_DOT),
+                 {g}, &ids);
       for (int64_t id : ids) dot_list[(size_t)b * nt + p.term].push_back(id);
     }
-    // ---------------- transposed product: dpsi[s_in] += c A^T G[s_out] B
-    for (size_t i = 0; i < sb->pairs.size(); ++i) {
-      const PairH& p = sb->pairs[i];
-      if (!is_gemm_pair(p)) continue;
-      const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
-      if (border[i] == 0)  // T = c A^T G  (r_in x c_out)
-        add_output(sb->f64_bwd1, BUF_T, tb + toff_b[i], co, ri, co, TM_STORE,
-                   {mkseg({BUF_OPS, p.a_off, ri, 1, BUF_X, X(p.s_out), co, 0, ro, coef(p)})}, nullptr);
-      else  // T = c G B  (r_out x c_in)
-        add_output(sb->f64_bwd1, BUF_T, tb + toff_b[i], ci, ro, ci, TM_STORE,
-                   {mkseg({BUF_X, X(p.s_out), co, 0, BUF_OPS, p.b_off, ci, 0, co, coef(p)})}, nullptr);
-    }
-    for (int s = 0; s < sb->S; ++s) {
-      if ((int64_t)r[s] * c[s] == 0) continue;
-      std::vector<SegF64> segs;
-      for (size_t i : by_in[s]) {
-        const PairH& p = sb->pairs[i];
-        const int32_t ro = r[p.s_out], ri = r[p.s_in], co = c[p.s_out], ci = c[p.s_in];
-        if (p.flags & DMRG_ID_B)
-          segs.push_back(mkseg({BUF_OPS, p.a_off, ri, 1, BUF_X, X(p.s_out), co, 0, ro, coef(p)}));
-        else if (p.flags & DMRG_ID_A)
-          segs.push_back(mkseg({BUF_X, X(p.s_out), co, 0, BUF_OPS, p.b_off, ci, 0, co, coef(p)}));
-        else if (border[i] == 0)
-          segs.push_back(mkseg({BUF_T, tb + toff_b[i], co, 0, BUF_OPS, p.b_off, ci, 0, co, -1}));
-        else
-          segs.push_back(mkseg({BUF_OPS, p.a_off, ri, 1, BUF_T, tb + toff_b[i], ci, 0, ro, -1}));
-      }
-      add_output(sb->f64_bwd2, BUF_Y, X(s), c[s], r[s], c[s], TM_STORE, segs, nullptr);
-    }
   }
-  sort_tiles(sb->f64_fwd1);
-  sort_tiles(sb->f64_fwd2);
-  sort_tiles(sb->f64_dot1);
-  sort_tiles(sb->f64_bwd1);
-  sort_tiles(sb->f64_bwd2);
+  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_bwd1, &sb->f64_bwd2, &sb->f64_bwd3,
+                          &sb->f64_dot1})
+    sort_tiles(*tl);
   const std::vector<int64_t> where = sort_tiles(sb->f64_dot2);
   std::vector<int32_t> ptr(1, 0), idx;
   for (auto& lst : dot_list) {
@@ -295,7 +346,8 @@ void build_f64_tasks(dmrg_sb* sb) {
   upload(sb->d_dot_red_idx, idx);
   if (sb->d_dot_partial) cudaFree(sb->d_dot_partial);
   sb->d_dot_partial = dalloc<double>((size_t)std::max<int64_t>(1, (int64_t)sb->f64_dot2.h_tiles.size()));
-  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1, &sb->f64_bwd2})
+  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
+                          &sb->f64_bwd2, &sb->f64_bwd3})
     finish(*tl);
 }
 
@@ -304,8 +356,9 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
             cudaStream_t st) {
   if (prec == DMRG_FP64) {
     Bufs bufs{{const_cast<double*>(x), y, sb->d_T, sb->d_ops, nullptr}};
-    launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, 0, nullptr, skip, st);
-    launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, accumulate, nullptr, skip, st);
+    launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, skip, st);
+    launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
+    launch_seg_gemm_f64(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
   } else {
     tc_matvec(sb, prec, x, y, accumulate, skip, st);
   }
@@ -314,8 +367,8 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
 
 void term_dots(dmrg_sb* sb, const double* psi, const double* g, double* dc, cudaStream_t st) {
   Bufs bufs{{const_cast<double*>(psi), nullptr, sb->d_T, sb->d_ops, const_cast<double*>(g)}};
-  launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
-  launch_seg_gemm_f64(sb->f64_dot2, bufs, sb->d_coeffs, 0, sb->d_dot_partial, nullptr, st);
+  launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+  launch_seg_gemm_f64(sb->f64_dot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_dot_partial, nullptr, st);
   lz_launch_reduce_terms(sb->d_dot_partial, sb->d_dot_red_ptr, sb->d_dot_red_idx, dc, sb->batch * sb->n_terms, st);
   CK(cudaGetLastError());
 }
@@ -429,7 +482,8 @@ struct LzRun {
 };
 
 int matvec_launches(const dmrg_sb* sb, int prec) {
-  if (prec == DMRG_FP64) return (sb->f64_fwd1.n_tiles > 0) + (sb->f64_fwd2.n_tiles > 0);
+  if (prec == DMRG_FP64)
+    return (sb->f64_fwd1.n_tiles > 0) + (sb->f64_fwd2.n_tiles > 0) + (sb->f64_fwd3.n_tiles > 0);
   return tc_launches(sb, prec);
 }
 constexpr int LZ_KERNELS_PER_ITER = 10;  // everything in lz_enqueue_iteration besides the product
@@ -751,7 +805,8 @@ void destroy(dmrg_sb* sb) {
   if (!sb) return;
   lz_free(sb);
   tc_free(sb);
-  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1, &sb->f64_bwd2})
+  for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
+                          &sb->f64_bwd2, &sb->f64_bwd3})
     free_tl(*tl);
   for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red})
     if (p) cudaFree(p);
@@ -852,8 +907,9 @@ dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* 
     if (dpsi) {
       if (prec == DMRG_FP64 || !tc_available(sb)) {
         Bufs bufs{{const_cast<double*>(g), dpsi, sb->d_T, sb->d_ops, nullptr}};
-        launch_seg_gemm_f64(sb->f64_bwd1, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
-        launch_seg_gemm_f64(sb->f64_bwd2, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
+        launch_seg_gemm_f64(sb->f64_bwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+        launch_seg_gemm_f64(sb->f64_bwd2, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+        launch_seg_gemm_f64(sb->f64_bwd3, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
       } else {
         tc_matvec_T(sb, prec, g, dpsi, st);
       }

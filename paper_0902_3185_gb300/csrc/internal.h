@@ -20,25 +20,38 @@ struct Bufs {
   double* p[NBUF];
 };
 
-// One product L (M x K) * R (K x N) scaled by `scale`, added into the tile.
+// One product L (M x K) * R (K x N) added into the tile.  Either operand may
+// stack the batch members along its outer dimension (rows of L, columns of
+// R): element index -> (member, index within the member) with `*_rm` rows
+// per member and `*_bs` elements between members.  The coefficient is a
+// table index (coef_mode 0, -1 = none) or a term whose member is taken from
+// the stacked side (coef_mode 1: rows of L, 2: columns of R).
 struct SegF64 {
   int64_t l_off, r_off;
+  int64_t l_bs, r_bs;
   int32_t l_buf, r_buf;
   int32_t ldl, ldr;
   int32_t K;
   int32_t l_trans;  // 0: L(m,k) = X[m*ldl + k]; 1: L(m,k) = X[k*ldl + m]
   int32_t r_trans;  // 0: R(k,n) = X[k*ldr + n]; 1: R(k,n) = X[n*ldr + k]
-  int32_t coef;     // index into the coefficient table, -1 = 1.0
+  int32_t l_rm, r_rm;
+  int32_t coef;
+  int32_t coef_mode;
+  int32_t pad;
 };
 
-// One output tile C[m0:m0+64, n0:n0+64] of an M x N matrix.
+// One output tile C[m0:m0+64, n0:n0+64] of an M x N matrix; the members may
+// be stacked along M (c_axis 0) or N (c_axis 1), c_rm rows per member.
 enum TileMode : int32_t { TM_STORE = 0, TM_DOT = 2 };
 struct TileF64 {
-  int64_t c_off;
+  int64_t c_off, c_bs;
   int32_t c_buf, ldc;
   int32_t M, N, m0, n0;
   int32_t seg_begin, seg_end;
-  int32_t mode;  // TM_STORE: C = acc (or C += acc when the launch accumulates); TM_DOT: sum(acc .* C)
+  int32_t mode;     // TM_STORE: C = acc (C += acc when the launch accumulates or `add`); TM_DOT: sum(acc .* C)
+  int32_t c_rm, c_axis;
+  int32_t c_trans;  // 0: C(mm, nn) at [mm*ldc + nn]; 1: at [nn*ldc + mm]
+  int32_t add;      // second writer of an output block: always accumulate
   int32_t pad;
 };
 
@@ -51,7 +64,7 @@ struct TaskListF64 {
 };
 
 // skip: optional device flag; when *skip != 0 the launch does nothing
-void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef,
+void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
                          int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
 
 // ------------------------------------------------------------ host pair info
@@ -77,8 +90,8 @@ struct dmrg_sb {
   double flops = 0;            // algorithmic flops of one product, one member
 
   // FP64 task lists
-  dmrg::TaskListF64 f64_fwd1, f64_fwd2;   // forward: phase 1 (intermediates), phase 2 (outputs)
-  dmrg::TaskListF64 f64_bwd1, f64_bwd2;   // H^T g
+  dmrg::TaskListF64 f64_fwd1, f64_fwd2, f64_fwd3;  // forward: intermediates, outputs (members along M, along N)
+  dmrg::TaskListF64 f64_bwd1, f64_bwd2, f64_bwd3;  // H^T g
   dmrg::TaskListF64 f64_dot1, f64_dot2;   // per-pair <g, A psi B^T>
   double* d_T = nullptr;                  // FP64 intermediate workspace
   int64_t T_elems = 0;

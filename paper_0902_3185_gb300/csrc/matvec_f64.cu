@@ -9,8 +9,10 @@
 // output element exactly once, so results do not depend on scheduling.
 //
 // Tile 64 x 64, K step 16, 256 threads with a 4 x 4 register block each
-// (rows ty + 16 i, cols tx + 16 j).  GB300 runs float64 at a small fraction
-// of its FP32 rate, so this kernel is bound by DFMA issue, not by memory.
+// (rows ty + 16 i, cols tx + 16 j).  GB300 runs float64 at 1/64 of its FP32
+// rate, so this kernel is bound by DFMA issue, not by memory; batch members
+// that share operator blocks are stacked along M or N so that the small
+// sector blocks of a DMRG superblock fill the 64 x 64 tiles.
 
 #include "internal.h"
 
@@ -20,7 +22,7 @@ constexpr int F64_BM = 64, F64_BN = 64, F64_BK = 16, F64_THREADS = 256;
 
 __global__ void __launch_bounds__(F64_THREADS)
 seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs,
-                    Bufs bufs, const double* __restrict__ coef, int accumulate,
+                    Bufs bufs, const double* __restrict__ coef, int n_terms, int accumulate,
                     double* __restrict__ dot_out, const int32_t* __restrict__ skip) {
   __shared__ double Ls[F64_BK][F64_BM + 1];
   __shared__ double Rs[F64_BK][F64_BN + 1];
@@ -40,7 +42,7 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
     const SegF64 s = segs[sg];
     const double* L = bufs.p[s.l_buf] + s.l_off;
     const double* R = bufs.p[s.r_buf] + s.r_off;
-    const double scale = s.coef >= 0 ? coef[s.coef] : 1.0;
+    const double uscale = (s.coef_mode == 0 && s.coef >= 0) ? coef[s.coef] : 1.0;
     for (int k0 = 0; k0 < s.K; k0 += F64_BK) {
 #pragma unroll
       for (int e = 0; e < (F64_BM * F64_BK) / F64_THREADS; ++e) {
@@ -50,9 +52,14 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
         else { m = idx / F64_BK; k = idx % F64_BK; }
         const int gm = t.m0 + m, gk = k0 + k;
         double v = 0.0;
-        if (gm < t.M && gk < s.K)
-          v = s.l_trans ? L[(int64_t)gk * s.ldl + gm] : L[(int64_t)gm * s.ldl + gk];
-        Ls[k][m] = v * scale;
+        if (gm < t.M && gk < s.K) {
+          int bl = 0, mm = gm;
+          if (s.l_rm) { bl = gm / s.l_rm; mm = gm - bl * s.l_rm; }
+          const double* Lb = L + (int64_t)bl * s.l_bs;
+          v = s.l_trans ? Lb[(int64_t)gk * s.ldl + mm] : Lb[(int64_t)mm * s.ldl + gk];
+          v *= s.coef_mode == 1 ? coef[bl * n_terms + s.coef] : uscale;
+        }
+        Ls[k][m] = v;
       }
 #pragma unroll
       for (int e = 0; e < (F64_BN * F64_BK) / F64_THREADS; ++e) {
@@ -62,8 +69,13 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
         else { k = idx / F64_BN; n = idx % F64_BN; }
         const int gn = t.n0 + n, gk = k0 + k;
         double v = 0.0;
-        if (gn < t.N && gk < s.K)
-          v = s.r_trans ? R[(int64_t)gn * s.ldr + gk] : R[(int64_t)gk * s.ldr + gn];
+        if (gn < t.N && gk < s.K) {
+          int br = 0, nn = gn;
+          if (s.r_rm) { br = gn / s.r_rm; nn = gn - br * s.r_rm; }
+          const double* Rb = R + (int64_t)br * s.r_bs;
+          v = s.r_trans ? Rb[(int64_t)nn * s.ldr + gk] : Rb[(int64_t)gk * s.ldr + nn];
+          if (s.coef_mode == 2) v *= coef[br * n_terms + s.coef];
+        }
         Rs[k][n] = v;
       }
       __syncthreads();
@@ -84,7 +96,17 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
   }
 
   double* C = bufs.p[t.c_buf] + t.c_off;
+  // element offset of C(m, n) with the members stacked along M or N
+  auto coff = [&](int m, int n) -> int64_t {
+    int b = 0;
+    if (t.c_rm) {
+      if (t.c_axis == 0) { b = m / t.c_rm; m -= b * t.c_rm; }
+      else { b = n / t.c_rm; n -= b * t.c_rm; }
+    }
+    return (int64_t)b * t.c_bs + (t.c_trans ? (int64_t)n * t.ldc + m : (int64_t)m * t.ldc + n);
+  };
   if (t.mode == TM_STORE) {
+    const bool add = accumulate || t.add;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int m = t.m0 + ty + 16 * i;
@@ -93,8 +115,8 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
       for (int j = 0; j < 4; ++j) {
         const int n = t.n0 + tx + 16 * j;
         if (n >= t.N) continue;
-        double* p = C + (int64_t)m * t.ldc + n;
-        *p = accumulate ? *p + acc[i][j] : acc[i][j];
+        double* p = C + coff(m, n);
+        *p = add ? *p + acc[i][j] : acc[i][j];
       }
     }
   } else {  // TM_DOT: sum over the tile of acc .* C, fixed-order block reduction
@@ -107,7 +129,7 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
       for (int j = 0; j < 4; ++j) {
         const int n = t.n0 + tx + 16 * j;
         if (n >= t.N) continue;
-        part = fma(acc[i][j], C[(int64_t)m * t.ldc + n], part);
+        part = fma(acc[i][j], C[coff(m, n)], part);
       }
     }
 #pragma unroll
@@ -122,11 +144,11 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
   }
 }
 
-void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef,
+void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
                          int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st) {
   if (tl.n_tiles == 0) return;
   seg_gemm_f64_kernel<<<(unsigned)tl.n_tiles, F64_THREADS, 0, st>>>(
-      tl.d_tiles, tl.d_segs, bufs, coef, accumulate, dot_out, skip);
+      tl.d_tiles, tl.d_segs, bufs, coef, n_terms, accumulate, dot_out, skip);
 }
 
 }  // namespace dmrg

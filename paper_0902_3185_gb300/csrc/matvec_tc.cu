@@ -132,7 +132,7 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
   int jid = lo;
   StageJob j = jobs[jid];
   int64_t jend = j.first + (int64_t)j.r * j.c;
-  double sc = j.term >= 0 ? coef[(int64_t)b * n_terms + j.term] : 1.0;
+  float scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
   const double* xb = x + (int64_t)b * D;
 #pragma unroll 1
   for (int u = 0; u < 8; ++u) {
@@ -141,17 +141,17 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
     while (e >= jend) {
       j = jobs[++jid];
       jend = j.first + (int64_t)j.r * j.c;
-      sc = j.term >= 0 ? coef[(int64_t)b * n_terms + j.term] : 1.0;
+      scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
     }
     const int64_t loc = e - j.first;
     if (!j.transpose) {  // row = b*r + a, k = c
       const int64_t a = loc / j.c, cc = loc - a * j.c;
-      const double v = xb[j.src_off + a * j.c + cc] * sc;
-      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, cc, j.atoms, (float)v);
+      const float v = tc::d2f_rn(xb[j.src_off + a * j.c + cc]) * scf;
+      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, cc, j.atoms, v);
     } else {  // row = b*c + c', k = a (column-major walk)
       const int64_t cc = loc / j.r, a = loc - cc * j.r;
-      const double v = xb[j.src_off + a * j.c + cc] * sc;
-      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + cc, a, j.atoms, (float)v);
+      const float v = tc::d2f_rn(xb[j.src_off + a * j.c + cc]) * scf;
+      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + cc, a, j.atoms, v);
     }
   }
 }
@@ -352,7 +352,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       if (!ok) break;
       tc::tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(acc * acc_stride) + ((uint32_t)(32 * q) << 16);
-      const double sc = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? coef[(int64_t)b * n_terms + o.term] : 1.0;
+      // the coefficient is applied in float32 (its rounding, 2^-24, is far below the operand precision)
+      const float scf = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? tc::d2f_rn(coef[(int64_t)b * n_terms + o.term]) : 1.0f;
       // row-major output: element offset of this lane's row (-1 = row not stored)
       const int64_t rbase = (o.kind == OUT_Y_ROW && mv) ? (int64_t)b * D + o.y_off + (int64_t)i * o.ldy : -1;
       for (int c0 = 16 * half; c0 < tl.ntile; c0 += 32) {
@@ -362,7 +363,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           // stage 32 rows x 16 columns, then write each row's 16 values as one
           // contiguous 128-byte segment (16 lanes per row, two rows per store)
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) stg[lane * EPI_LD + jj] = (double)v[jj];
+          for (int jj = 0; jj < 16; ++jj) stg[lane * EPI_LD + jj] = tc::f2d_exact(v[jj]);
           __syncwarp();
           const int jj = lane & 15;
           const int n = tl.n0 + c0 + jj;
@@ -385,10 +386,11 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           const int n = tl.n0 + c0 + jj;
           if (n >= nend) break;
           if (o.kind == OUT_PANEL) {
-            store_panel<PREC>(o.p, o.p_lo, (int64_t)b * o.N + n, i, o.p_atoms, (float)(v[jj] * sc));
+            store_panel<PREC>(o.p, o.p_lo, (int64_t)b * o.N + n, i, o.p_atoms, v[jj] * scf);
           } else {
             double* p = y + (int64_t)b * D + o.y_off + (int64_t)n * o.ldy + i;
-            *p = add ? *p + (double)v[jj] : (double)v[jj];
+            const double val = tc::f2d_exact(v[jj]);
+            *p = add ? *p + val : val;
           }
         }
       }

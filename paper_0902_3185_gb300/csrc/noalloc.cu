@@ -77,8 +77,10 @@ extern "C" dmrg_status dmrg_apply_H_static_scratch(dmrg_sb* sb, const double* ps
   }
   cudaStream_t st = (cudaStream_t)stream;
   dmrg::Bufs bufs{{const_cast<double*>(psi), y, scratch, sb->d_ops, nullptr}};
-  dmrg::launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, 0, nullptr, nullptr, st);
-  dmrg::launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, accumulate ? 1 : 0, nullptr, nullptr, st);
+  const int acc = accumulate ? 1 : 0;
+  dmrg::launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+  dmrg::launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, acc, nullptr, nullptr, st);
+  dmrg::launch_seg_gemm_f64(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, acc, nullptr, nullptr, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     sb->err = std::string("apply_H_static_scratch: launch: ") + cudaGetErrorString(e);

@@ -157,6 +157,64 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// float64 <-> float32 conversions with integer instructions.  GB300 issues
+// float64 work (conversions included) at 1/64 of the float32 rate, so the
+// staging and epilogue paths, which convert every element, do it on the
+// integer pipes instead.
+//
+// double -> float, round to nearest even; results below the float normal
+// range are rounded into float subnormals, overflow gives +-inf.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned long long m = u & 0xfffffffffffffull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  if (e == 0) return __uint_as_float(sign);  // float64 subnormals are far below float range
+  int e32 = e - 1023 + 127;
+  unsigned long long sig = m | (1ull << 52);  // 53-bit significand
+  int shift = 29;                              // keep 24 bits
+  if (e32 <= 0) {                              // float subnormal: shift further
+    shift += 1 - e32;
+    e32 = 0;
+    if (shift > 63) return __uint_as_float(sign);
+  }
+  unsigned long long kept = sig >> shift;
+  const unsigned long long rem = sig & ((1ull << shift) - 1);
+  const unsigned long long half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (kept & 1ull))) ++kept;
+  uint32_t bits;
+  if (e32 == 0) {
+    bits = (uint32_t)kept;  // subnormal (a carry into bit 23 makes it the smallest normal)
+  } else {
+    if (kept >> 24) {  // rounding carried out of the significand
+      kept >>= 1;
+      ++e32;
+    }
+    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+    bits = ((uint32_t)e32 << 23) | ((uint32_t)kept & 0x7fffffu);
+  }
+  return __uint_as_float(sign | bits);
+}
+
+// float -> double, exact
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const uint32_t e = (u >> 23) & 0xff;
+  uint32_t m = u & 0x7fffffu;
+  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((unsigned long long)m << 29)));
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    const int lz = __clz(m) - 8;  // leading bit at 23 - lz: normalise, value = 2^(p - 149)
+    m = (m << lz) & 0x7fffffu;
+    const unsigned long long ed = (unsigned long long)(1023 - 126 - lz);
+    return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)m << 29)));
+  }
+  const unsigned long long ed = (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)m << 29)));
+}
+
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
