@@ -52,12 +52,15 @@ struct TcSeg {
   int64_t l_lo, r_lo; // byte offset hi -> lo panel (BF16x3)
   int32_t l_atoms, r_atoms;  // atoms per K chunk in each panel
   int32_t kchunks;
-  int32_t pad;
+  int32_t slot;       // accumulator slot (0: coefficients already applied)
 };
 
+constexpr int TC_MAX_SLOTS = 4;
 struct TcTile {
   int32_t m0, n0, ntile, la, ra;  // la / ra: atoms to load from L / R
   int32_t seg_begin, seg_end, out;
+  int32_t slot_used;              // bit k: slot k receives at least one product
+  int32_t slot_term[TC_MAX_SLOTS];  // slot k >= 1: its coefficient column (member from the row)
 };
 
 enum OutKind : int32_t { OUT_Y_ROW = 0, OUT_Y_COL = 1, OUT_PANEL = 2 };
@@ -143,14 +146,14 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
       jend = j.first + (int64_t)j.r * j.c;
       scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
     }
-    const int64_t loc = e - j.first;
+    const int loc = (int)(e - j.first);  // < r * c: 32-bit division (64-bit is a long sequence)
     if (!j.transpose) {  // row = b*r + a, k = c
-      const int64_t a = loc / j.c, cc = loc - a * j.c;
-      const float v = tc::d2f_rn(xb[j.src_off + a * j.c + cc]) * scf;
+      const int a = loc / j.c, cc = loc - a * j.c;
+      const float v = tc::d2f_rn(xb[j.src_off + (int64_t)a * j.c + cc]) * scf;
       store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, cc, j.atoms, v);
     } else {  // row = b*c + c', k = a (column-major walk)
-      const int64_t cc = loc / j.r, a = loc - cc * j.r;
-      const float v = tc::d2f_rn(xb[j.src_off + a * j.c + cc]) * scf;
+      const int cc = loc / j.r, a = loc - cc * j.r;
+      const float v = tc::d2f_rn(xb[j.src_off + (int64_t)a * j.c + cc]) * scf;
       store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + cc, a, j.atoms, v);
     }
   }
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
                const TcOut* __restrict__ outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
                int n_terms, int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
-               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes) {
+               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride) {
   if (skip && *skip) return;
   extern __shared__ __align__(1024) char smem_raw[];
   // control block, then 1024-aligned stage ring
@@ -206,7 +209,6 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int acc_stride = tmem_cols / 2;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -267,11 +269,15 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         if (tl.seg_begin == tl.seg_end) continue;
         if (!tc::mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag)) goto mma_done;
         tc::tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * acc_stride);
+        const uint32_t d_acc = tmem_base + (uint32_t)(acc * acc_stride);
         const uint32_t idesc = tc::idesc_f32acc(fmt, 128, (uint32_t)tl.ntile);
-        uint32_t accum = 0;
+        uint32_t started = 0;  // slots that already hold a partial sum
         for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
           const int kch = segs[s].kchunks;
+          const int slot = segs[s].slot;
+          const uint32_t d_tmem = d_acc + (uint32_t)(slot * tl.ntile);
+          uint32_t accum = (started >> slot) & 1u;
+          started |= 1u << slot;
           for (int kc = 0; kc < kch; ++kc) {
             if (!tc::mbar_wait(&full[stage], phase, abort_flag)) goto mma_done;
             tc::tc_fence_after();
@@ -356,9 +362,29 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       const float scf = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? tc::d2f_rn(coef[(int64_t)b * n_terms + o.term]) : 1.0f;
       // row-major output: element offset of this lane's row (-1 = row not stored)
       const int64_t rbase = (o.kind == OUT_Y_ROW && mv) ? (int64_t)b * D + o.y_off + (int64_t)i * o.ldy : -1;
+      float slot_sc[TC_MAX_SLOTS];
+#pragma unroll
+      for (int k = 1; k < TC_MAX_SLOTS; ++k)
+        slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? tc::d2f_rn(coef[(int64_t)b * n_terms + tl.slot_term[k]]) : 0.0f;
       for (int c0 = 16 * half; c0 < tl.ntile; c0 += 32) {
         float v[16];
-        tc::tmem_ld16(tb + (uint32_t)c0, v);
+        if (tl.slot_used == 1) {
+          tc::tmem_ld16(tb + (uint32_t)c0, v);
+        } else {
+          // products of the identity terms were accumulated per coefficient:
+          // y = slot 0 + sum_k c_k(member) * slot k
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) v[jj] = 0.0f;
+#pragma unroll
+          for (int k = 0; k < TC_MAX_SLOTS; ++k) {
+            if (!((tl.slot_used >> k) & 1)) continue;
+            float u[16];
+            tc::tmem_ld16(tb + (uint32_t)(k * tl.ntile + c0), u);
+            const float w = k == 0 ? 1.0f : slot_sc[k];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = fmaf(w, u[jj], v[jj]);
+          }
+        }
         if (o.kind == OUT_Y_ROW) {
           // stage 32 rows x 16 columns, then write each row's 16 values as one
           // contiguous 128-byte segment (16 lanes per row, two rows per store)
@@ -465,6 +491,7 @@ struct Launch {  // one grouped GEMM launch
   TcOut* outs = nullptr;
   int n_tiles = 0;
   int ntile_max = 16;
+  int acc_cols = 16;         // TMEM columns per accumulator buffer (all slots)
   bool has_row_out = false;  // some output is row-major float64 (needs epilogue staging)
 };
 
@@ -560,6 +587,31 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     return p;
   };
   const size_t np = P.size();
+  std::vector<std::vector<size_t>> by_out(S);
+  for (size_t i = 0; i < np; ++i) by_out[P[i].s_out].push_back(i);
+  // Identity-term coefficients differ per member.  Where the accumulator has
+  // room, each such term accumulates into its own TMEM slot (weighted by the
+  // member's coefficient in the epilogue) and reads the shared unscaled
+  // wavefunction panel; otherwise the term gets a coefficient-scaled copy.
+  // slot_of[i]: slot of identity pair i (0 = scaled copy or not an identity pair)
+  std::vector<int> slot_of(np, 0);
+  for (int s = 0; s < S; ++s) {
+    for (int grp = 0; grp < 2; ++grp) {  // 0: 1 (x) B terms (group E), 1: A (x) 1 terms (group S)
+      const int flag = grp == 0 ? DMRG_ID_A : DMRG_ID_B;
+      std::vector<int> terms;
+      for (size_t i : by_out[s])
+        if ((P[i].flags & flag) && std::find(terms.begin(), terms.end(), P[i].term) == terms.end())
+          terms.push_back(P[i].term);
+      if (terms.empty()) continue;
+      const int64_t Nout = grp == 0 ? c[s] : r[s];
+      const int64_t ntile = std::min<int64_t>(max_ntile, cdiv(Nout, 16) * 16);
+      const int nslot = 1 + (int)terms.size();
+      if (nslot > TC_MAX_SLOTS || nslot * ntile > 256) continue;
+      for (size_t i : by_out[s])
+        if (P[i].flags & flag)
+          slot_of[i] = 1 + (int)(std::find(terms.begin(), terms.end(), P[i].term) - terms.begin());
+    }
+  }
   std::vector<Panel> pA(np), pB(np), pX(np), pS(np);  // operator A, B; intermediate; scaled psi copy
   std::vector<Panel> psiP(S), psiPT(S);
   std::vector<char> needP(S, 0), needPT(S, 0);
@@ -568,9 +620,13 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     const int64_t ro = r[e.s_out], ri = r[e.s_in], co = c[e.s_out], ci = c[e.s_in];
     if (!(e.flags & DMRG_ID_A)) pA[i] = alloc(ro, ri);
     if (!(e.flags & DMRG_ID_B)) pB[i] = alloc(co, ci);
-    if (e.flags & DMRG_ID_A) pS[i] = alloc(nb * ri, ci);       // c Psi          (group E, L)
-    else if (e.flags & DMRG_ID_B) pS[i] = alloc(nb * ci, ri);  // (c Psi)^T      (group S, L)
-    else if (e.order == 1) { pX[i] = alloc(nb * co, ri); needP[e.s_in] = 1; }   // X^T stacked
+    if (e.flags & DMRG_ID_A) {                                  // c Psi       (group E, L)
+      if (slot_of[i]) needP[e.s_in] = 1;
+      else pS[i] = alloc(nb * ri, ci);
+    } else if (e.flags & DMRG_ID_B) {                           // (c Psi)^T   (group S, L)
+      if (slot_of[i]) needPT[e.s_in] = 1;
+      else pS[i] = alloc(nb * ci, ri);
+    } else if (e.order == 1) { pX[i] = alloc(nb * co, ri); needP[e.s_in] = 1; }   // X^T stacked
     else { pX[i] = alloc(nb * ro, ci); needPT[e.s_in] = 1; }                   // Z stacked
   }
   for (int s = 0; s < S; ++s) {
@@ -611,6 +667,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   }
   for (size_t i = 0; i < np; ++i) {
     const EPair& e = P[i];
+    if (slot_of[i]) continue;
     if (e.flags & DMRG_ID_A) add_job(e.s_in, 0, e.term, pS[i]);
     else if (e.flags & DMRG_ID_B) add_job(e.s_in, 1, e.term, pS[i]);
   }
@@ -621,6 +678,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     std::vector<TcOut> outs;
     std::vector<int64_t> weight;
     int ntile_max = 16;
+    int acc_cols = 16;  // TMEM columns of one accumulator buffer (slots x N)
   } L1, LE, LS;
   // host-side bounds proof of every bulk copy the tiles will issue
   auto check = [](bool ok, const char* what) {
@@ -638,7 +696,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     g.kchunks = (int32_t)cdiv(Lp.K, kce);
     return g;
   };
-  auto add_out = [&](Build& B, const TcOut& o, const std::vector<TcSeg>& sg) {
+  auto add_out = [&](Build& B, const TcOut& o, const std::vector<TcSeg>& sg, const std::vector<int>& slot_terms) {
     for (const TcSeg& g : sg) {
       check(g.l_atoms == cdiv(o.M, 8) && g.r_atoms == cdiv(o.N, 8), "operand rows differ from the output");
       check(g.kchunks >= 1, "empty K");
@@ -663,6 +721,15 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
         t.seg_begin = s0;
         t.seg_end = s1;
         t.out = oid;
+        for (const TcSeg& g : sg) t.slot_used |= 1 << g.slot;
+        if (sg.empty()) t.slot_used = 1;
+        for (size_t k = 0; k < slot_terms.size(); ++k) t.slot_term[k + 1] = slot_terms[k];
+        check(t.slot_used < (1 << TC_MAX_SLOTS), "accumulator slots");
+        int top = 0;
+        for (int k = 0; k < TC_MAX_SLOTS; ++k)
+          if (t.slot_used >> k & 1) top = k;
+        B.acc_cols = std::max(B.acc_cols, (top + 1) * t.ntile);
+        check(B.acc_cols <= 256, "accumulator columns");
         check(t.m0 % 8 == 0 && t.n0 % 8 == 0 && t.la >= 1 && t.ra >= 1, "tile origin");
         check(t.m0 / 8 + t.la <= cdiv(o.M, 8) && t.n0 / 8 + t.ra <= cdiv(o.N, 8), "tile past its panels");
         check(t.ntile % 16 == 0 && t.ntile >= 16 && t.ntile <= 256 && t.ra * 8 <= t.ntile, "MMA N");
@@ -686,26 +753,38 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       o.Rm = (int32_t)ri;
       o.M = (int32_t)(nb * ri);
       o.N = (int32_t)co;
-      add_out(L1, o, {seg(psiP[e.s_in], pB[i])});
+      add_out(L1, o, {seg(psiP[e.s_in], pB[i])}, {});
     } else {  // Z_b^T = Psi_b^T A^T : rows (b, beta'), cols alpha; stored as Z rows (b, alpha), k = beta'
       o.Rm = (int32_t)ci;
       o.M = (int32_t)(nb * ci);
       o.N = (int32_t)ro;
-      add_out(L1, o, {seg(psiPT[e.s_in], pA[i])});
+      add_out(L1, o, {seg(psiPT[e.s_in], pA[i])}, {});
     }
   }
   // groups E and S per output sector
-  std::vector<std::vector<size_t>> by_out(S);
-  for (size_t i = 0; i < np; ++i) by_out[P[i].s_out].push_back(i);
   for (int s = 0; s < S; ++s) {
     if ((int64_t)r[s] * c[s] == 0) continue;
     std::vector<TcSeg> sE, sS;
+    std::vector<int> tE, tS;  // terms of slots 1, 2, ...
     for (size_t i : by_out[s]) {
       const EPair& e = P[i];
-      if (e.flags & DMRG_ID_A) sE.push_back(seg(pS[i], pB[i]));
-      else if (e.flags & DMRG_ID_B) sS.push_back(seg(pS[i], pA[i]));
-      else if (e.order == 0) sE.push_back(seg(pX[i], pB[i]));
-      else sS.push_back(seg(pX[i], pA[i]));
+      if (e.flags & DMRG_ID_A) {
+        TcSeg g = slot_of[i] ? seg(psiP[e.s_in], pB[i]) : seg(pS[i], pB[i]);
+        g.slot = slot_of[i];
+        if (g.slot && (int)tE.size() < g.slot) tE.resize(g.slot, -1);
+        if (g.slot) tE[g.slot - 1] = e.term;
+        sE.push_back(g);
+      } else if (e.flags & DMRG_ID_B) {
+        TcSeg g = slot_of[i] ? seg(psiPT[e.s_in], pA[i]) : seg(pS[i], pA[i]);
+        g.slot = slot_of[i];
+        if (g.slot && (int)tS.size() < g.slot) tS.resize(g.slot, -1);
+        if (g.slot) tS[g.slot - 1] = e.term;
+        sS.push_back(g);
+      } else if (e.order == 0) {
+        sE.push_back(seg(pX[i], pB[i]));
+      } else {
+        sS.push_back(seg(pX[i], pA[i]));
+      }
     }
     const bool hasE = !sE.empty(), hasS = !sS.empty();
     if (hasE || !hasS) {
@@ -718,7 +797,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       o.add = 0;
       o.term = -1;
       o.y_off = sb->off[s];
-      add_out(LE, o, sE);
+      add_out(LE, o, sE, tE);
     }
     if (hasS) {
       TcOut o{};
@@ -730,7 +809,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       o.add = hasE ? 1 : 0;
       o.term = -1;
       o.y_off = sb->off[s];
-      add_out(LS, o, sS);
+      add_out(LS, o, sS, tS);
     }
   }
   auto finish = [&](Build& B, Launch& L) {
@@ -745,6 +824,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     L.outs = up(B.outs);
     L.n_tiles = (int)t.size();
     L.ntile_max = B.ntile_max;
+    L.acc_cols = B.acc_cols;
     L.has_row_out = false;
     for (const TcOut& o : B.outs) L.has_row_out = L.has_row_out || o.kind == OUT_Y_ROW;
   };
@@ -869,11 +949,13 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   const int stages = std::max(1, std::min(8, avail / stage_bytes));
   const int smem = fixed + stages * stage_bytes;
   if (smem > 227 * 1024) throw CudaFail("tensor-core tile does not fit in shared memory");
-  const int tmem_cols = L.ntile_max <= 128 ? 256 : 512;
+  int tmem_cols = 32;  // power of two holding both accumulator buffers
+  while (tmem_cols < 2 * L.acc_cols) tmem_cols *= 2;
   const int grid = std::min(L.n_tiles, s->num_sms);
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, accumulate, skip,
-                                                       sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi);
+                                                       sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
+                                                       L.acc_cols);
 }
 
 template <int PREC>
