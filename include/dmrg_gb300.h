@@ -162,6 +162,24 @@ dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out
                                 const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info,
                                 void* stream);
 
+/* Autotuner of the tensor-core product (no paper counterpart; the paper's
+ * block loop has no tuning): times the product of this superblock, `reps`
+ * launches per candidate after a warm-up, for every tile width (64, 128,
+ * and 256 for TF32) and tile order (heaviest first, or as built), keeps the
+ * fastest, and also times the baseline that launches one kernel per output
+ * block.  Rebuilds task lists and operand panels (allocates); invalidates
+ * captured Lanczos graphs.  Synchronises the stream. */
+typedef struct {
+  double best_ms;        /* median product time with the chosen tuning */
+  double default_ms;     /* median product time with the build-time default */
+  double per_block_ms;   /* median product time, one launch per output block */
+  int32_t best_tile_n;   /* chosen widest MMA N */
+  int32_t heavy_first;   /* chosen tile order */
+  int32_t candidates;
+  int32_t pad;
+} dmrg_tune_info;
+dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream, dmrg_tune_info* info);
+
 /* Hellmann-Feynman: dE0/dc_k = <psi, (A_k (x) B_k) psi> / <psi, psi> for
  * every batch member.  psi: device [batch][D]; dE_dc: device [batch][n_terms]. */
 dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int32_t prec,

@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREA
 # exported symbols, as declared in include/dmrg_gb300.h
 SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error", "dmrg_query",
            "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
-           "dmrg_energy_grad", "dmrg_apply_H_static_scratch"]
+           "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune"]
 
 
 class DmrgError(RuntimeError):
@@ -50,6 +50,12 @@ class _Info(C.Structure):
     _fields_ = [("dim", C.c_int64), ("batch", C.c_int32), ("n_sectors", C.c_int32), ("n_terms", C.c_int32),
                 ("n_pairs", C.c_int32), ("flops_per_matvec", C.c_double), ("op_bytes_f64", C.c_double),
                 ("op_bytes_mixed", C.c_double)]
+
+
+class TuneInfo(C.Structure):
+    _fields_ = [("best_ms", C.c_double), ("default_ms", C.c_double), ("per_block_ms", C.c_double),
+                ("best_tile_n", C.c_int32), ("heavy_first", C.c_int32), ("candidates", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class LanczosOpts(C.Structure):
@@ -95,6 +101,7 @@ def load(build_if_missing: bool = True):
     lib.dmrg_lanczos_ground.argtypes = [vp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
     lib.dmrg_energy_grad.argtypes = [vp, dp, dp, i32, vp]
     lib.dmrg_apply_H_static_scratch.argtypes = [vp, dp, dp, i32, vp]
+    lib.dmrg_autotune.argtypes = [vp, i32, i32, vp, C.POINTER(TuneInfo)]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -188,6 +195,12 @@ class GpuSuperblock:
         self._check(self.lib.dmrg_apply_H(self.h, _ptr(psi), _ptr(y), int(accumulate), _prec(prec),
                                           _stream(stream)))
         return y
+
+    def autotune(self, prec="bf16x3", reps=5, stream=None):
+        """Pick the tensor-core tiling for this superblock by timing; returns the report."""
+        info = TuneInfo()
+        self._check(self.lib.dmrg_autotune(self.h, _prec(prec), reps, _stream(stream), C.byref(info)))
+        return {k: getattr(info, k) for k, _ in TuneInfo._fields_ if k != "pad"}
 
     def apply_H_static_scratch(self, psi, y=None, accumulate=False, stream=None):
         """float64 product whose workspace is the library's static device

@@ -920,6 +920,34 @@ dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* 
   });
 }
 
+dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream, dmrg_tune_info* info) {
+  if (!sb || (prec != DMRG_TF32 && prec != DMRG_BF16X3)) return DMRG_EINVAL;
+  if (!tc_available(sb)) {
+    sb->err = "autotune: tensor-core path not available on this device";
+    return DMRG_EUNSUPPORTED;
+  }
+  return guard(sb, [&] {
+    double out[6] = {};
+    tc_autotune(sb, prec, reps, (cudaStream_t)stream, out);
+    // captured graphs hold the old task lists
+    for (int i = 0; i < 8; ++i)
+      if (sb->lz_graphs[i]) {
+        cudaGraphExecDestroy((cudaGraphExec_t)sb->lz_graphs[i]);
+        sb->lz_graphs[i] = nullptr;
+        sb->lz_graph_key[i] = 0;
+      }
+    if (info) {
+      info->best_ms = out[0];
+      info->default_ms = out[1];
+      info->per_block_ms = out[2];
+      info->best_tile_n = (int32_t)out[3];
+      info->heavy_first = (int32_t)out[4];
+      info->candidates = (int32_t)out[5];
+    }
+    return DMRG_OK;
+  });
+}
+
 dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int32_t prec, void* stream) {
   if (!sb || !psi || !dE_dc) return DMRG_EINVAL;
   (void)prec;

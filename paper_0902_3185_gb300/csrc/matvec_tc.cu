@@ -407,16 +407,28 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           continue;
         }
         if (!mv) continue;
+        if (o.kind == OUT_PANEL) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int n = tl.n0 + c0 + jj;
-          if (n >= nend) break;
-          if (o.kind == OUT_PANEL) {
+          for (int jj = 0; jj < 16; ++jj) {
+            const int n = tl.n0 + c0 + jj;
+            if (n >= nend) break;
             store_panel<PREC>(o.p, o.p_lo, (int64_t)b * o.N + n, i, o.p_atoms, v[jj] * scf);
+          }
+        } else {  // column-major float64 output: lanes write consecutive i
+          double* yb = y + (int64_t)b * D + o.y_off + i;
+          const int nn = min(16, nend - (tl.n0 + c0));
+          if (add) {
+            double old[16];  // issue every load before the first add
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+              if (jj < nn) old[jj] = yb[(int64_t)(tl.n0 + c0 + jj) * o.ldy];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+              if (jj < nn) yb[(int64_t)(tl.n0 + c0 + jj) * o.ldy] = old[jj] + tc::f2d_exact(v[jj]);
           } else {
-            double* p = y + (int64_t)b * D + o.y_off + (int64_t)n * o.ldy + i;
-            const double val = tc::f2d_exact(v[jj]);
-            *p = add ? *p + val : val;
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+              if (jj < nn) yb[(int64_t)(tl.n0 + c0 + jj) * o.ldy] = tc::f2d_exact(v[jj]);
           }
         }
       }
@@ -487,6 +499,8 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 struct Launch {  // one grouped GEMM launch
   TcTile* tiles = nullptr;
+  TcTile* tiles_by_out = nullptr;   // the same tiles grouped by output block
+  std::vector<int> out_begin;       // per output: first tile in tiles_by_out (+ end)
   TcSeg* segs = nullptr;
   TcOut* outs = nullptr;
   int n_tiles = 0;
@@ -508,15 +522,32 @@ struct Fmt {
   PairSet fwd, bwd;
 };
 
+// A pair as the product sees it (forward, or transposed for H^T)
+struct EPair {
+  int32_t term, s_out, s_in, flags, order;
+  const double* A;  // host, r_out x r_in (already transposed for H^T)
+  const double* B;  // host, c_out x c_in
+};
+
+struct Tune {         // picked by dmrg_autotune
+  int max_ntile = 0;  // widest MMA N of a tile (0: default per precision)
+  int heavy_first = 1;  // deal the heaviest tiles first (else build order)
+  int per_block = 0;  // baseline: one launch per output block instead of one persistent launch
+};
+
 struct State {
   int num_sms = 0;
   bool ok = false;
   Fmt f[2];  // 0: TF32, 1: BF16x3
+  Tune tune[2];
   double op_bytes_tf32 = 0;
+  std::vector<double> host_ops;               // float64 blocks (forward)
+  std::vector<std::vector<double>> trans;     // transposed blocks (H^T)
+  std::vector<EPair> fw, bw;
 };
 
 void free_launch(Launch& l) {
-  for (void* p : {(void*)l.tiles, (void*)l.segs, (void*)l.outs})
+  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs, (void*)l.outs})
     if (p) cudaFree(p);
   l = Launch{};
 }
@@ -527,13 +558,6 @@ void free_set(PairSet& s) {
   free_launch(s.grpS);
   s = PairSet{};
 }
-
-// A pair as the product sees it (forward, or transposed for H^T)
-struct EPair {
-  int32_t term, s_out, s_in, flags, order;
-  const double* A;  // host, r_out x r_in (already transposed for H^T)
-  const double* B;  // host, c_out x c_in
-};
 
 struct Panel {
   int64_t off = -1;  // byte offset in the half-arena
@@ -566,7 +590,7 @@ void pack(std::vector<uint8_t>& hi, std::vector<uint8_t>& lo, const Panel& p, co
 // half-arena layout starts at `base_off`; returns the bytes used.
 static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& P, int64_t base_off,
                          std::vector<uint8_t>& hi, std::vector<uint8_t>& lo, char* d_hi, int64_t lo_delta,
-                         PairSet& out, bool dry) {
+                         PairSet& out, bool dry, const Tune& tune) {
   const int64_t nb = sb->batch;
   const int es = prec == DMRG_TF32 ? 4 : 2;
   const int64_t kce = 128 / es;
@@ -575,7 +599,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   const int S = sb->S;
   // widest MMA N per tile: BF16x3 stages hold four operand tiles, so cap N at
   // 128 to keep at least two pipeline stages in shared memory
-  const int max_ntile = prec == DMRG_BF16X3 ? 128 : 256;
+  const int max_ntile = tune.max_ntile > 0 ? tune.max_ntile : (prec == DMRG_BF16X3 ? 128 : 256);
   int64_t cur = base_off;
   auto alloc = [&](int64_t rows, int64_t K) {
     Panel p;
@@ -816,10 +840,17 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     // heaviest tiles first, dealt round-robin over the persistent CTAs
     std::vector<size_t> perm(B.tiles.size());
     for (size_t i = 0; i < perm.size(); ++i) perm[i] = i;
-    std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return B.weight[a] > B.weight[b]; });
+    if (tune.heavy_first)
+      std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return B.weight[a] > B.weight[b]; });
     std::vector<TcTile> t(B.tiles.size());
     for (size_t i = 0; i < perm.size(); ++i) t[i] = B.tiles[perm[i]];
     L.tiles = up(t);
+    // tiles are built output by output: record where each output starts
+    L.tiles_by_out = up(B.tiles);
+    L.out_begin.assign(1, 0);
+    for (size_t i = 1; i < B.tiles.size(); ++i)
+      if (B.tiles[i].out != B.tiles[i - 1].out) L.out_begin.push_back((int)i);
+    L.out_begin.push_back((int)B.tiles.size());
     L.segs = up(B.segs);
     L.outs = up(B.outs);
     L.n_tiles = (int)t.size();
@@ -870,6 +901,33 @@ int tc_launches(const dmrg_sb* sb, int prec) {
   return (ps.n_elems > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
 }
 
+// (Re)build the panels and task lists of one precision with its tuning.
+static void build_fmt(dmrg_sb* sb, State* s, int fi) {
+  const int prec = fi == 0 ? DMRG_TF32 : DMRG_BF16X3;
+  Fmt& F = s->f[fi];
+  free_set(F.fwd);
+  free_set(F.bwd);
+  if (F.arena) cudaFree(F.arena);
+  F = Fmt{};
+  // sizes depend only on shapes: a dry run lays the arena out first
+  std::vector<uint8_t> hi, lo;
+  {
+    PairSet none;
+    const int64_t a = build_set(sb, prec, s->fw, 0, hi, lo, nullptr, 0, none, true, s->tune[fi]);
+    const int64_t b2 = build_set(sb, prec, s->bw, a, hi, lo, nullptr, 0, none, true, s->tune[fi]);
+    F.bytes = (size_t)(a + b2);
+  }
+  const size_t total = F.bytes * (prec == DMRG_BF16X3 ? 2 : 1);
+  TCK(cudaMalloc(&F.arena, std::max<size_t>(total, 1024)));
+  TCK(cudaMemset(F.arena, 0, std::max<size_t>(total, 1024)));
+  const int64_t lo_delta = prec == DMRG_BF16X3 ? (int64_t)F.bytes : 0;
+  const int64_t a = build_set(sb, prec, s->fw, 0, hi, lo, F.arena, lo_delta, F.fwd, false, s->tune[fi]);
+  build_set(sb, prec, s->bw, a, hi, lo, F.arena, lo_delta, F.bwd, false, s->tune[fi]);
+  TCK(cudaMemcpy(F.arena, hi.data(), hi.size(), cudaMemcpyHostToDevice));
+  if (prec == DMRG_BF16X3) TCK(cudaMemcpy(F.arena + lo_delta, lo.data(), lo.size(), cudaMemcpyHostToDevice));
+  if (fi == 0) s->op_bytes_tf32 = (double)a;
+}
+
 void tc_build(dmrg_sb* sb) {
   int dev = 0;
   TCK(cudaGetDevice(&dev));
@@ -879,28 +937,27 @@ void tc_build(dmrg_sb* sb) {
   sb->tc = s;
   s->num_sms = prop.multiProcessorCount;
   if (prop.major != 10) return;  // tcgen05 is a Blackwell datacenter feature
-  // forward and transposed pair lists with host blocks
-  const double* H = sb->h_ops.data();
-  std::vector<EPair> fw, bw;
-  std::vector<std::vector<double>> trans;  // transposed host blocks for H^T
-  trans.reserve(sb->pairs.size() * 2);
+  // forward and transposed pair lists with host blocks (kept for re-tuning)
+  s->host_ops = sb->h_ops;
+  const double* H = s->host_ops.data();
+  s->trans.reserve(sb->pairs.size() * 2);
   for (const PairH& p : sb->pairs) {
     EPair e{p.term, p.s_out, p.s_in, p.flags, p.order, p.a_off >= 0 ? H + p.a_off : nullptr,
             p.b_off >= 0 ? H + p.b_off : nullptr};
-    fw.push_back(e);
+    s->fw.push_back(e);
     const int64_t ro = sb->r[p.s_out], ri = sb->r[p.s_in], co = sb->c[p.s_out], ci = sb->c[p.s_in];
     EPair t{p.term, p.s_in, p.s_out, p.flags, 0, nullptr, nullptr};
     if (p.a_off >= 0) {
-      trans.emplace_back(ri * ro);
+      s->trans.emplace_back(ri * ro);
       for (int64_t i = 0; i < ro; ++i)
-        for (int64_t j = 0; j < ri; ++j) trans.back()[j * ro + i] = H[p.a_off + i * ri + j];
-      t.A = trans.back().data();
+        for (int64_t j = 0; j < ri; ++j) s->trans.back()[j * ro + i] = H[p.a_off + i * ri + j];
+      t.A = s->trans.back().data();
     }
     if (p.b_off >= 0) {
-      trans.emplace_back(ci * co);
+      s->trans.emplace_back(ci * co);
       for (int64_t i = 0; i < co; ++i)
-        for (int64_t j = 0; j < ci; ++j) trans.back()[j * co + i] = H[p.b_off + i * ci + j];
-      t.B = trans.back().data();
+        for (int64_t j = 0; j < ci; ++j) s->trans.back()[j * co + i] = H[p.b_off + i * ci + j];
+      t.B = s->trans.back().data();
     }
     if (!(p.flags & (DMRG_ID_A | DMRG_ID_B))) {
       // transposed pair: r_out' = ri, r_in' = ro, c_out' = ci, c_in' = co
@@ -908,29 +965,9 @@ void tc_build(dmrg_sb* sb) {
       const double c1 = 2.0 * ro * co * ci + 2.0 * ri * ro * ci;
       t.order = c0 <= c1 ? 0 : 1;
     }
-    bw.push_back(t);
+    s->bw.push_back(t);
   }
-  for (int fi = 0; fi < 2; ++fi) {
-    const int prec = fi == 0 ? DMRG_TF32 : DMRG_BF16X3;
-    Fmt& F = s->f[fi];
-    // sizes depend only on shapes: a dry run lays the arena out first
-    std::vector<uint8_t> hi, lo;
-    {
-      PairSet none;
-      const int64_t a = build_set(sb, prec, fw, 0, hi, lo, nullptr, 0, none, true);
-      const int64_t b2 = build_set(sb, prec, bw, a, hi, lo, nullptr, 0, none, true);
-      F.bytes = (size_t)(a + b2);
-    }
-    const size_t total = F.bytes * (prec == DMRG_BF16X3 ? 2 : 1);
-    TCK(cudaMalloc(&F.arena, std::max<size_t>(total, 1024)));
-    TCK(cudaMemset(F.arena, 0, std::max<size_t>(total, 1024)));
-    const int64_t lo_delta = prec == DMRG_BF16X3 ? (int64_t)F.bytes : 0;
-    const int64_t a = build_set(sb, prec, fw, 0, hi, lo, F.arena, lo_delta, F.fwd, false);
-    build_set(sb, prec, bw, a, hi, lo, F.arena, lo_delta, F.bwd, false);
-    TCK(cudaMemcpy(F.arena, hi.data(), hi.size(), cudaMemcpyHostToDevice));
-    if (prec == DMRG_BF16X3) TCK(cudaMemcpy(F.arena + lo_delta, lo.data(), lo.size(), cudaMemcpyHostToDevice));
-    if (fi == 0) s->op_bytes_tf32 = (double)a;
-  }
+  for (int fi = 0; fi < 2; ++fi) build_fmt(sb, s, fi);
   TCK(cudaFuncSetAttribute(tc_gemm_kernel<DMRG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   TCK(cudaFuncSetAttribute(tc_gemm_kernel<DMRG_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   s->ok = true;
@@ -951,6 +988,16 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   if (smem > 227 * 1024) throw CudaFail("tensor-core tile does not fit in shared memory");
   int tmem_cols = 32;  // power of two holding both accumulator buffers
   while (tmem_cols < 2 * L.acc_cols) tmem_cols *= 2;
+  if (s->tune[PREC == DMRG_TF32 ? 0 : 1].per_block) {
+    // baseline for the autotuner's report: one launch per output block
+    for (size_t o = 0; o + 1 < L.out_begin.size(); ++o) {
+      const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
+      tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
+          L.tiles_by_out + b0, n, L.segs, L.outs, y, sb->D, sb->d_coeffs, sb->n_terms, accumulate, skip,
+          sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols);
+    }
+    return;
+  }
   const int grid = std::min(L.n_tiles, s->num_sms);
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, accumulate, skip,
@@ -969,6 +1016,70 @@ static void run_set(const State* s, const PairSet& ps, const double* x, double* 
   run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
   run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, st);
   run_gemm<PREC>(s, ps.grpS, y, sb, accumulate, skip, st);
+}
+
+// Time the product under each candidate tuning on this superblock and keep
+// the fastest (median of `reps` launches after a warm-up, CUDA events on the
+// caller's stream).  Also times the per-block launch baseline.
+void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out) {
+  State* s = st_of(sb);
+  if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
+  const int fi = prec == DMRG_TF32 ? 0 : 1;
+  const int64_t n = sb->D * sb->batch;
+  double *x = nullptr, *y = nullptr;
+  TCK(cudaMalloc(&x, n * sizeof(double)));
+  TCK(cudaMalloc(&y, n * sizeof(double)));
+  TCK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+  cudaEvent_t e0, e1;
+  TCK(cudaEventCreate(&e0));
+  TCK(cudaEventCreate(&e1));
+  auto time_it = [&]() {
+    std::vector<float> ms;
+    for (int w = 0; w < 2; ++w) tc_matvec(sb, prec, x, y, 0, nullptr, st);
+    for (int r = 0; r < std::max(1, reps); ++r) {
+      TCK(cudaEventRecord(e0, st));
+      tc_matvec(sb, prec, x, y, 0, nullptr, st);
+      TCK(cudaEventRecord(e1, st));
+      TCK(cudaEventSynchronize(e1));
+      float t = 0;
+      TCK(cudaEventElapsedTime(&t, e0, e1));
+      ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    return (double)ms[ms.size() / 2];
+  };
+  std::vector<int> widths = {64, 128};
+  if (prec == DMRG_TF32) widths.push_back(256);
+  const Tune start = s->tune[fi];
+  Tune best = start;
+  double best_ms = 1e30, default_ms = 0;
+  int tried = 0;
+  for (int w : widths)
+    for (int hf : {1, 0}) {
+      s->tune[fi] = Tune{w, hf, 0};
+      build_fmt(sb, s, fi);
+      const double t = time_it();
+      ++tried;
+      if (w == (prec == DMRG_TF32 ? 256 : 128) && hf == 1) default_ms = t;
+      if (t < best_ms) { best_ms = t; best = s->tune[fi]; }
+    }
+  s->tune[fi] = best;
+  s->tune[fi].per_block = 1;
+  build_fmt(sb, s, fi);
+  const double per_block_ms = time_it();
+  s->tune[fi].per_block = 0;
+  TCK(cudaStreamSynchronize(st));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  out[0] = best_ms;
+  out[1] = default_ms;
+  out[2] = per_block_ms;
+  out[3] = best.max_ntile;
+  out[4] = best.heavy_first;
+  out[5] = tried;
+  (void)start;
 }
 
 void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,

@@ -18,5 +18,7 @@ int tc_launches(const dmrg_sb* sb, int prec);  // kernels one product launches
 void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
                cudaStream_t st);
 void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st);
+// out: best ms, default ms, per-block baseline ms, best tile N, heavy-first flag, candidates
+void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out);
 
 }  // namespace dmrg

@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--lanczos-iters", type=int, default=0, help="also run a fixed-length Lanczos")
+    ap.add_argument("--autotune", action="store_true", help="autotune, then time eager and graph-captured products")
     a = ap.parse_args()
     import torch
     from paper_0902_3185_gb300.binding import GpuSuperblock
@@ -37,6 +38,37 @@ def main():
     y = g.empty()
     for _ in range(a.reps):
         g.apply_H(x, y, prec=a.prec)
+    if a.autotune and a.prec != "fp64":
+        import json
+        rep = g.autotune(prec=a.prec, reps=7)
+        # products replayed from a CUDA graph (the library launches on the capturing stream)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                g.apply_H(x, y, prec=a.prec)
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        n_rep = 10
+        with torch.cuda.graph(graph):
+            for _ in range(n_rep):
+                g.apply_H(x, y, prec=a.prec)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        rep["graph_ms"] = e0.elapsed_time(e1) / (5 * n_rep)
+        rep["flops"] = g.info["flops_per_matvec"]
+        rep["tflops_best"] = rep["flops"] / (rep["best_ms"] * 1e-3) / 1e12
+        rep["tflops_per_block"] = rep["flops"] / (rep["per_block_ms"] * 1e-3) / 1e12
+        rep["workload"] = a.workload
+        rep["prec"] = a.prec
+        print(json.dumps(rep))
     if a.lanczos_iters:
         g.lanczos_ground(x, tol=1e-300, max_iter=a.lanczos_iters, prec=a.prec, refine=False)
     torch.cuda.synchronize()
