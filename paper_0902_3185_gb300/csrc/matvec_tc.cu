@@ -827,28 +827,6 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       const int order = keys[gi].first, s_in = keys[gi].second;
       const int64_t ri = r[s_in], ci = c[s_in];
       const Panel& Lp = order == 1 ? psiP[s_in] : psiPT[s_in];
-      // pairs wider than one tile keep their own output, tiled along N
-      std::vector<size_t> narrow;
-      for (size_t i : groups[gi]) {
-        const EPair& e = P[i];
-        const Panel& Rp = order == 1 ? pB[i] : pA[i];
-        if (Rp.atoms * 8 <= cap) {
-          narrow.push_back(i);
-          continue;
-        }
-        const int64_t ro = r[e.s_out], co = c[e.s_out];
-        TcOut o{};
-        o.kind = OUT_PANEL;
-        o.term = e.term;
-        o.p = dptr(pX[i]);
-        o.p_lo = lo_delta;
-        o.p_atoms = (int32_t)pX[i].atoms;
-        o.Rm = (int32_t)(order == 1 ? ri : ci);
-        o.M = (int32_t)(nb * o.Rm);
-        o.N = (int32_t)(order == 1 ? co : ro);
-        add_out(L1, o, {seg(Lp, Rp)}, {});
-      }
-      groups[gi].swap(narrow);
       size_t a = 0;
       while (a < groups[gi].size()) {
         // one chunk of pieces
