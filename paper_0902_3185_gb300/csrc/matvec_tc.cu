@@ -61,22 +61,6 @@ struct TcTile {
   int32_t seg_begin, seg_end, out;
   int32_t slot_used;              // bit k: slot k receives at least one product
   int32_t slot_term[TC_MAX_SLOTS];  // slot k >= 1: its coefficient column (member from the row)
-  int32_t piece_begin, piece_end;   // phase-1 tiles: several R panels side by side along N
-};
-
-// Phase 1: pairs that share the left operand (same input sector and order)
-// are computed in one tile, their right operands side by side along N; each
-// piece writes its own intermediate panel with its own coefficient.
-constexpr int TC_MAX_PIECES = 16;
-struct TcPiece {
-  const char* r;      // R panel (hi) of this pair
-  char* p;            // its intermediate panel (hi)
-  int32_t r_atoms;    // atoms per K chunk of the R panel
-  int32_t ra;         // atoms loaded (all rows of the panel)
-  int32_t n_off;      // first column of the piece in the tile (multiple of 8)
-  int32_t n_valid;    // columns of the piece (rows of its R panel)
-  int32_t term;       // coefficient column
-  int32_t p_atoms;    // atoms per K chunk of the intermediate panel
 };
 
 enum OutKind : int32_t { OUT_Y_ROW = 0, OUT_Y_COL = 1, OUT_PANEL = 2 };
@@ -186,7 +170,7 @@ constexpr int TC_CTRL_BYTES = 256;
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
-               const TcOut* __restrict__ outs, const TcPiece* __restrict__ pieces, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
+               const TcOut* __restrict__ outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
                int n_terms, int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
                int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride) {
   if (skip && *skip) return;
@@ -242,23 +226,13 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
             if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) goto producer_done;
             char* st = ring + (size_t)stage * stage_bytes;
             const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * 1024;
+            const char* rsrc = sg.r + ((int64_t)kc * sg.r_atoms + tl.n0 / 8) * 1024;
             tc::mbar_arrive_expect_tx(&full[stage], PREC == DMRG_TF32 ? lb + rb : 2u * (lb + rb));
             tc::bulk_g2s(st, lsrc, lb, &full[stage]);
-            if (PREC == DMRG_BF16X3) tc::bulk_g2s(st + L_TILE_BYTES + r_tile_bytes, lsrc + sg.l_lo, lb, &full[stage]);
-            if (tl.piece_end > tl.piece_begin) {
-              for (int q = tl.piece_begin; q < tl.piece_end; ++q) {
-                const TcPiece pc = pieces[q];
-                const char* rsrc = pc.r + (int64_t)kc * pc.r_atoms * 1024;
-                const uint32_t pb = (uint32_t)pc.ra * 1024u;
-                tc::bulk_g2s(st + L_TILE_BYTES + pc.n_off * 128, rsrc, pb, &full[stage]);
-                if (PREC == DMRG_BF16X3)
-                  tc::bulk_g2s(st + 2 * L_TILE_BYTES + r_tile_bytes + pc.n_off * 128, rsrc + sg.r_lo, pb, &full[stage]);
-              }
-            } else {
-              const char* rsrc = sg.r + ((int64_t)kc * sg.r_atoms + tl.n0 / 8) * 1024;
-              tc::bulk_g2s(st + L_TILE_BYTES, rsrc, rb, &full[stage]);
-              if (PREC == DMRG_BF16X3)
-                tc::bulk_g2s(st + 2 * L_TILE_BYTES + r_tile_bytes, rsrc + sg.r_lo, rb, &full[stage]);
+            tc::bulk_g2s(st + L_TILE_BYTES, rsrc, rb, &full[stage]);
+            if (PREC == DMRG_BF16X3) {
+              tc::bulk_g2s(st + L_TILE_BYTES + r_tile_bytes, lsrc + sg.l_lo, lb, &full[stage]);
+              tc::bulk_g2s(st + 2 * L_TILE_BYTES + r_tile_bytes, rsrc + sg.r_lo, rb, &full[stage]);
             }
             issued |= 1u << stage;
             issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
@@ -433,22 +407,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           continue;
         }
         if (!mv) continue;
-        if (tl.piece_end > tl.piece_begin) {
-          int q = tl.piece_begin;
-          while (q + 1 < tl.piece_end && c0 >= pieces[q + 1].n_off) ++q;
-          TcPiece pc = pieces[q];
-          float w = tc::d2f_rn(coef[(int64_t)b * n_terms + pc.term]);
-          for (int jj = 0; jj < 16; ++jj) {
-            const int n = c0 + jj;
-            if (q + 1 < tl.piece_end && n >= pieces[q + 1].n_off) {
-              pc = pieces[++q];
-              w = tc::d2f_rn(coef[(int64_t)b * n_terms + pc.term]);
-            }
-            const int local = n - pc.n_off;
-            if (local >= pc.n_valid) continue;
-            store_panel<PREC>(pc.p, o.p_lo, (int64_t)b * pc.n_valid + local, i, pc.p_atoms, v[jj] * w);
-          }
-        } else if (o.kind == OUT_PANEL) {
+        if (o.kind == OUT_PANEL) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int n = tl.n0 + c0 + jj;
@@ -544,7 +503,6 @@ struct Launch {  // one grouped GEMM launch
   std::vector<int> out_begin;       // per output: first tile in tiles_by_out (+ end)
   TcSeg* segs = nullptr;
   TcOut* outs = nullptr;
-  TcPiece* pieces = nullptr;
   int n_tiles = 0;
   int ntile_max = 16;
   int acc_cols = 16;         // TMEM columns per accumulator buffer (all slots)
@@ -589,7 +547,7 @@ struct State {
 };
 
 void free_launch(Launch& l) {
-  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs, (void*)l.outs, (void*)l.pieces})
+  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs, (void*)l.outs})
     if (p) cudaFree(p);
   l = Launch{};
 }
@@ -745,7 +703,6 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     std::vector<int64_t> weight;
     int ntile_max = 16;
     int acc_cols = 16;  // TMEM columns of one accumulator buffer (slots x N)
-    std::vector<TcPiece> pieces;
   } L1, LE, LS;
   // host-side bounds proof of every bulk copy the tiles will issue
   auto check = [](bool ok, const char* what) {
@@ -805,94 +762,27 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
         B.weight.push_back(kw * (int64_t)t.ntile + 64);
       }
   };
-  // phase 1: pairs sharing (order, input sector) share the left operand; pack
-  // them side by side along N (up to 256 columns per tile)
-  {
-    std::vector<std::vector<size_t>> groups;
-    std::vector<std::pair<int, int>> keys;
-    for (size_t i = 0; i < np; ++i) {
-      const EPair& e = P[i];
-      if (e.flags & (DMRG_ID_A | DMRG_ID_B)) continue;
-      const std::pair<int, int> key(e.order, e.s_in);
-      size_t gi = 0;
-      while (gi < keys.size() && keys[gi] != key) ++gi;
-      if (gi == keys.size()) {
-        keys.push_back(key);
-        groups.emplace_back();
-      }
-      groups[gi].push_back(i);
-    }
-    const int cap = 256;
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-      const int order = keys[gi].first, s_in = keys[gi].second;
-      const int64_t ri = r[s_in], ci = c[s_in];
-      const Panel& Lp = order == 1 ? psiP[s_in] : psiPT[s_in];
-      size_t a = 0;
-      while (a < groups[gi].size()) {
-        // one chunk of pieces
-        std::vector<TcPiece> pcs;
-        int rows = 0;
-        size_t bnd = a;
-        while (bnd < groups[gi].size() && (int)pcs.size() < TC_MAX_PIECES) {
-          const size_t i = groups[gi][bnd];
-          const EPair& e = P[i];
-          const Panel& Rp = order == 1 ? pB[i] : pA[i];
-          const int prow = (int)Rp.atoms * 8;
-          if (!pcs.empty() && rows + prow > cap) break;
-          check(Rp.K == Lp.K, "piece operands");
-          TcPiece pc{};
-          pc.r = dptr(Rp);
-          pc.p = dptr(pX[i]);
-          pc.r_atoms = (int32_t)Rp.atoms;
-          pc.ra = (int32_t)Rp.atoms;
-          pc.n_off = rows;
-          pc.n_valid = (int32_t)Rp.rows;
-          pc.term = e.term;
-          pc.p_atoms = (int32_t)pX[i].atoms;
-          check(pc.p_atoms == cdiv(nb * Rp.rows, 8), "intermediate panel rows");
-          pcs.push_back(pc);
-          rows += prow;
-          ++bnd;
-        }
-        check(rows <= cap || pcs.size() == 1, "piece columns");
-        TcOut o{};
-        o.kind = OUT_PANEL;
-        o.term = -1;
-        o.p_lo = lo_delta;
-        o.Rm = (int32_t)(order == 1 ? ri : ci);
-        o.M = (int32_t)(nb * o.Rm);
-        o.N = rows;
-        const int oid = (int)L1.outs.size();
-        L1.outs.push_back(o);
-        TcSeg g = seg(Lp, Lp);  // R is given by the pieces; kchunks and L from here
-        g.r = nullptr;
-        const int s0 = (int)L1.segs.size();
-        L1.segs.push_back(g);
-        const int p0 = (int)L1.pieces.size();
-        L1.pieces.insert(L1.pieces.end(), pcs.begin(), pcs.end());
-        const int p1 = (int)L1.pieces.size();
-        for (int m0 = 0; m0 < o.M; m0 += 128) {
-          TcTile t{};
-          t.m0 = m0;
-          t.n0 = 0;
-          t.ntile = (int)(cdiv(rows, 16) * 16);
-          t.la = (int)std::min<int64_t>(16, cdiv(o.M - m0, 8));
-          t.ra = rows / 8;
-          t.seg_begin = s0;
-          t.seg_end = s0 + 1;
-          t.out = oid;
-          t.slot_used = 1;
-          t.piece_begin = p0;
-          t.piece_end = p1;
-          check(t.ntile >= 16 && t.ntile <= 256 && t.ra * 8 <= t.ntile, "MMA N (pieces)");
-          check(t.m0 / 8 + t.la <= cdiv(o.M, 8) && g.l_atoms == cdiv(o.M, 8), "tile past its panels");
-          L1.ntile_max = std::max(L1.ntile_max, t.ntile);
-          L1.acc_cols = std::max(L1.acc_cols, t.ntile);
-          L1.tiles.push_back(t);
-          L1.weight.push_back((int64_t)g.kchunks * t.ntile + 64);
-        }
-        a = bnd;
-      }
+  // phase 1
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (e.flags & (DMRG_ID_A | DMRG_ID_B)) continue;
+    const int64_t ro = r[e.s_out], ri = r[e.s_in], co = c[e.s_out], ci = c[e.s_in];
+    TcOut o{};
+    o.kind = OUT_PANEL;
+    o.term = e.term;
+    o.p = dptr(pX[i]);
+    o.p_lo = lo_delta;
+    o.p_atoms = (int32_t)pX[i].atoms;
+    if (e.order == 1) {  // X_b = Psi_b B^T : rows (b, a'), cols beta; stored as X^T rows (b, beta), k = a'
+      o.Rm = (int32_t)ri;
+      o.M = (int32_t)(nb * ri);
+      o.N = (int32_t)co;
+      add_out(L1, o, {seg(psiP[e.s_in], pB[i])}, {});
+    } else {  // Z_b^T = Psi_b^T A^T : rows (b, beta'), cols alpha; stored as Z rows (b, alpha), k = beta'
+      o.Rm = (int32_t)ci;
+      o.M = (int32_t)(nb * ci);
+      o.N = (int32_t)ro;
+      add_out(L1, o, {seg(psiPT[e.s_in], pA[i])}, {});
     }
   }
   // groups E and S per output sector
@@ -963,7 +853,6 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     L.out_begin.push_back((int)B.tiles.size());
     L.segs = up(B.segs);
     L.outs = up(B.outs);
-    L.pieces = up(B.pieces);
     L.n_tiles = (int)t.size();
     L.ntile_max = B.ntile_max;
     L.acc_cols = B.acc_cols;
@@ -1104,13 +993,13 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
     for (size_t o = 0; o + 1 < L.out_begin.size(); ++o) {
       const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
       tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
-          L.tiles_by_out + b0, n, L.segs, L.outs, L.pieces, y, sb->D, sb->d_coeffs, sb->n_terms, accumulate, skip,
+          L.tiles_by_out + b0, n, L.segs, L.outs, y, sb->D, sb->d_coeffs, sb->n_terms, accumulate, skip,
           sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols);
     }
     return;
   }
   const int grid = std::min(L.n_tiles, s->num_sms);
-  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, L.pieces, y, sb->D,
+  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, accumulate, skip,
                                                        sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
                                                        L.acc_cols);
