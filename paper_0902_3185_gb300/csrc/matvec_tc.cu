@@ -98,6 +98,38 @@ __host__ __device__ inline int64_t panel_off(int64_t row, int64_t k, int64_t ato
   return (kc * atoms + atom) * 1024 + r8 * 128 + (chunk << 4) + (byte & 15);
 }
 
+// Writes of one epilogue thread: fixed K index k, varying panel row.  The
+// byte offset splits into a per-thread part (K chunk, byte inside the row)
+// and a per-row part (atom, row in atom, swizzled 16-byte chunk), in 32-bit.
+template <int PREC>
+struct PanelColumnWriter {
+  char* hi;
+  int64_t lo_delta;
+  int32_t kbase;  // kc * atoms * 1024 + (byte & 15)
+  int32_t chunk;  // 16-byte chunk of k before the swizzle
+  __device__ __forceinline__ PanelColumnWriter(char* p, int64_t p_lo, int k, int atoms) {
+    constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
+    constexpr int kce = 128 / es;
+    const int kc = k / kce, byte = (k - kc * kce) * es;
+    hi = p;
+    lo_delta = p_lo;
+    kbase = kc * atoms * 1024 + (byte & 15);
+    chunk = byte >> 4;
+  }
+  __device__ __forceinline__ void put(int row, float v) const {
+    const int r8 = row & 7;
+    const int off = kbase + ((row >> 3) << 10) + (r8 << 7) + ((chunk ^ r8) << 4);
+    if (PREC == DMRG_TF32) {
+      *reinterpret_cast<float*>(hi + off) = tc::round_tf32(v);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+      *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+      *reinterpret_cast<__nv_bfloat16*>(hi + lo_delta + off) = l;
+    }
+  }
+};
+
 template <int PREC>
 __device__ __forceinline__ void store_panel(char* p, int64_t p_lo, int64_t row, int64_t k, int atoms, float v) {
   if (PREC == DMRG_TF32) {
@@ -160,7 +192,8 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
 }
 
 // ------------------------------------------------------ grouped tile GEMM
-constexpr int TC_EPI_WARPS = 8;                    // two per TMEM lane quadrant
+constexpr int TC_EPI_WARPS = 12;                   // three per TMEM lane quadrant
+constexpr int TC_EPI_PARTS = TC_EPI_WARPS / 4;      // column interleave between warps of a quadrant
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer, MMA, epilogue
 constexpr int L_TILE_BYTES = 128 * 128;             // 128 rows x 128 B
 constexpr int EPI_LD = 17;                          // staging row stride (doubles)
@@ -328,7 +361,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
   } else {
     // ------------------------------------------------------------ epilogue
     // warp w reads TMEM lanes 32 (w % 4) .. +31 (the hardware's quadrant
-    // rule) and every other 16-column chunk: half = (w - 2) / 4.
+    // rule) and every TC_EPI_PARTS-th 16-column chunk, starting at part = (w - 2) / 4.
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const int row = 32 * q + lane;
@@ -366,7 +399,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
 #pragma unroll
       for (int k = 1; k < TC_MAX_SLOTS; ++k)
         slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? tc::d2f_rn(coef[(int64_t)b * n_terms + tl.slot_term[k]]) : 0.0f;
-      for (int c0 = 16 * half; c0 < tl.ntile; c0 += 32) {
+      for (int c0 = 16 * half; c0 < tl.ntile; c0 += 16 * TC_EPI_PARTS) {
         float v[16];
         if (tl.slot_used == 1) {
           tc::tmem_ld16(tb + (uint32_t)c0, v);
@@ -408,11 +441,12 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         }
         if (!mv) continue;
         if (o.kind == OUT_PANEL) {
+          const PanelColumnWriter<PREC> wr(o.p, o.p_lo, i, o.p_atoms);
+          const int row0 = b * o.N + tl.n0 + c0;
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            const int n = tl.n0 + c0 + jj;
-            if (n >= nend) break;
-            store_panel<PREC>(o.p, o.p_lo, (int64_t)b * o.N + n, i, o.p_atoms, v[jj] * scf);
+            if (tl.n0 + c0 + jj >= nend) break;
+            wr.put(row0 + jj, v[jj] * scf);
           }
         } else {  // column-major float64 output: lanes write consecutive i
           double* yb = y + (int64_t)b * D + o.y_off + i;
