@@ -111,6 +111,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist, device):
+    """Timed milliseconds of the slowest rank (the step ends when every rank is done)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, products, flops, ms_total):
+    """Whole-job algorithmic TFLOP/s: every rank ran `products` products of
+    `flops` flops within the max-over-ranks time."""
+    return world * products * flops / (ms_total / 1e3) / 1e12
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -250,13 +266,9 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist if world > 1 else None, dev)
     ms_per_step = ms / args.steps
-    value = world * mv_count * flops_mv / (ms / 1e3) / 1e12
+    value = job_value(world, mv_count, flops_mv, ms)
 
     # where the step goes: the mixed Lanczos alone, then the refinement
     def timed(fn):

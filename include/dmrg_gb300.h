@@ -180,6 +180,18 @@ typedef struct {
 } dmrg_tune_info;
 dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream, dmrg_tune_info* info);
 
+/* Synchronise `stream` and report device-side failures of earlier calls on
+ * this superblock: DMRG_ETIMEOUT if a bounded wait inside a tensor-core
+ * kernel gave up (the kernel then skipped its output and released its
+ * resources; the context stays usable).  Clears the flag. */
+dmrg_status dmrg_sync_status(dmrg_sb* sb, void* stream);
+
+/* Testing hook (no paper counterpart): what = 1 makes the next tensor-core
+ * product's copy warp issue no copies, so that its bounded waits run out and
+ * report DMRG_ETIMEOUT through dmrg_sync_status; what = 0 clears it.  No
+ * memory is touched out of bounds and every wait ends after its limit. */
+dmrg_status dmrg_test_inject(dmrg_sb* sb, int32_t what);
+
 /* Hellmann-Feynman: dE0/dc_k = <psi, (A_k (x) B_k) psi> / <psi, psi> for
  * every batch member.  psi: device [batch][D]; dE_dc: device [batch][n_terms]. */
 dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int32_t prec,

@@ -26,7 +26,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREA
 # exported symbols, as declared in include/dmrg_gb300.h
 SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error", "dmrg_query",
            "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
-           "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune"]
+           "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune", "dmrg_sync_status",
+           "dmrg_test_inject"]
 
 
 class DmrgError(RuntimeError):
@@ -102,6 +103,8 @@ def load(build_if_missing: bool = True):
     lib.dmrg_energy_grad.argtypes = [vp, dp, dp, i32, vp]
     lib.dmrg_apply_H_static_scratch.argtypes = [vp, dp, dp, i32, vp]
     lib.dmrg_autotune.argtypes = [vp, i32, i32, vp, C.POINTER(TuneInfo)]
+    lib.dmrg_sync_status.argtypes = [vp, vp]
+    lib.dmrg_test_inject.argtypes = [vp, i32]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -195,6 +198,10 @@ class GpuSuperblock:
         self._check(self.lib.dmrg_apply_H(self.h, _ptr(psi), _ptr(y), int(accumulate), _prec(prec),
                                           _stream(stream)))
         return y
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise DmrgError(ETIMEOUT) if a device-side wait gave up."""
+        self._check(self.lib.dmrg_sync_status(self.h, _stream(stream)))
 
     def autotune(self, prec="bf16x3", reps=5, stream=None):
         """Pick the tensor-core tiling for this superblock by timing; returns the report."""

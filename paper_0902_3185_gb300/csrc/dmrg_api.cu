@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -41,10 +42,22 @@ struct Timeout {
   std::string msg;
 };
 
+// Testing hook: DMRG_TEST_FAIL_ALLOC=n makes the n-th device allocation of
+// the process report out-of-memory (host-side fault injection).
+long g_alloc_count = 0;
+long fail_alloc_at() {
+  static const long at = [] {
+    const char* e = getenv("DMRG_TEST_FAIL_ALLOC");
+    return e ? atol(e) : 0L;
+  }();
+  return at;
+}
+
 template <class T>
 T* dalloc(size_t n) {
   if (n == 0) n = 1;
   void* p = nullptr;
+  if (fail_alloc_at() > 0 && ++g_alloc_count == fail_alloc_at()) throw CudaError{cudaErrorMemoryAllocation, "cudaMalloc (injected)"};
   CK(cudaMalloc(&p, n * sizeof(T)));
   return static_cast<T*>(p);
 }
@@ -955,6 +968,29 @@ dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream,
     }
     return DMRG_OK;
   });
+}
+
+dmrg_status dmrg_sync_status(dmrg_sb* sb, void* stream) {
+  if (!sb) return DMRG_EINVAL;
+  return guard(sb, [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t flag = 0;
+    CK(cudaMemcpyAsync(&flag, sb->d_tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) {
+      CK(cudaMemsetAsync(sb->d_tc_err, 0, sizeof(int32_t), st));
+      CK(cudaStreamSynchronize(st));
+      sb->err = "a tensor-core kernel gave up a bounded wait; its output was not written";
+      return DMRG_ETIMEOUT;
+    }
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_test_inject(dmrg_sb* sb, int32_t what) {
+  if (!sb || what < 0 || what > 1) return DMRG_EINVAL;
+  sb->test_stall = what;
+  return DMRG_OK;
 }
 
 dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int32_t prec, void* stream) {

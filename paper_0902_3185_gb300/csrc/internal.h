@@ -127,6 +127,7 @@ struct dmrg_sb {
 
   void* tc = nullptr;            // tensor-core path state (matvec_tc.cu)
   int32_t* d_tc_err = nullptr;   // set by a tensor-core kernel whose bounded wait gave up
+  int32_t test_stall = 0;        // testing hook: the next tensor-core product issues no copies
   std::vector<double> h_ops;     // host copy of the float64 arena during creation only
 
   std::string err;

@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
                const TcOut* __restrict__ outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
                int n_terms, int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
-               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride) {
+               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride,
+               int stall) {
   if (skip && *skip) return;
   extern __shared__ __align__(1024) char smem_raw[];
   // control block, then 1024-aligned stage ring
@@ -245,7 +246,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
+    if (lane == 0 && !stall) {  // stall: testing hook, the consumers' bounded waits run out
       int stage = 0;
       uint32_t phase = 0;
       uint32_t issued = 0;  // bit s: stage s has a copy in flight or landed
@@ -1028,7 +1029,7 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
       const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
       tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
           L.tiles_by_out + b0, n, L.segs, L.outs, y, sb->D, sb->d_coeffs, sb->n_terms, accumulate, skip,
-          sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols);
+          sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, sb->test_stall);
     }
     return;
   }
@@ -1036,7 +1037,7 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, accumulate, skip,
                                                        sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
-                                                       L.acc_cols);
+                                                       L.acc_cols, sb->test_stall);
 }
 
 template <int PREC>
@@ -1122,6 +1123,7 @@ void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate
   if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
   if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st);
   else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st);
+  sb->test_stall = 0;  // the hook applies to one product
 }
 
 void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st) {
