@@ -130,6 +130,25 @@ void set_R_opT(SegF64& g, const OpAcc& o) {
   g.r_trans = o.trans ? 0 : 1;
 }
 
+// Tile shape of an M x N output: the 16*ni x 16*nj tiling (ni, nj in 1..4)
+// with the least padded area; among equals the largest tile (fewer operand
+// reloads).  Returns ni | nj << 8.
+int32_t f64_shape(int32_t M, int32_t N) {
+  int64_t best = -1;
+  int32_t shape = 4 | (4 << 8);
+  for (int32_t ni = 1; ni <= 4; ++ni)
+    for (int32_t nj = 1; nj <= 4; ++nj) {
+      const int64_t bm = 16 * ni, bn = 16 * nj;
+      const int64_t area = ((M + bm - 1) / bm * bm) * ((N + bn - 1) / bn * bn);
+      const int64_t bs = (int64_t)(shape & 0xff) * (shape >> 8);
+      if (best < 0 || area < best || (area == best && ni * nj > bs)) {
+        best = area;
+        shape = ni | (nj << 8);
+      }
+    }
+  return shape;
+}
+
 // Append the tiles of one M x N output and its segment list; returns the
 // positions (before sorting) of the new tiles in *ids.
 void add_output(TaskListF64& tl, const TileF64& proto, const std::vector<SegF64>& segs, std::vector<int64_t>* ids) {
@@ -137,13 +156,16 @@ void add_output(TaskListF64& tl, const TileF64& proto, const std::vector<SegF64>
   const int32_t sb = (int32_t)tl.h_segs.size();
   tl.h_segs.insert(tl.h_segs.end(), segs.begin(), segs.end());
   const int32_t se = (int32_t)tl.h_segs.size();
-  for (int32_t m0 = 0; m0 < proto.M; m0 += 64)
-    for (int32_t n0 = 0; n0 < proto.N; n0 += 64) {
+  const int32_t shape = f64_shape(proto.M, proto.N);
+  const int32_t bm = 16 * (shape & 0xff), bn = 16 * (shape >> 8);
+  for (int32_t m0 = 0; m0 < proto.M; m0 += bm)
+    for (int32_t n0 = 0; n0 < proto.N; n0 += bn) {
       TileF64 t = proto;
       t.m0 = m0;
       t.n0 = n0;
       t.seg_begin = sb;
       t.seg_end = se;
+      t.shape = shape;
       if (ids) ids->push_back((int64_t)tl.h_tiles.size());
       tl.h_tiles.push_back(t);
     }
@@ -167,7 +189,7 @@ std::vector<int64_t> sort_tiles(TaskListF64& tl) {
   for (size_t i = 0; i < n; ++i) {
     int64_t k = 0;
     for (int32_t s = tl.h_tiles[i].seg_begin; s < tl.h_tiles[i].seg_end; ++s) k += tl.h_segs[s].K;
-    w[i] = k;
+    w[i] = k * (tl.h_tiles[i].shape & 0xff) * (tl.h_tiles[i].shape >> 8);  // FMAs per thread
   }
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return w[a] > w[b]; });

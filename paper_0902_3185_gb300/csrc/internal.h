@@ -40,8 +40,9 @@ struct SegF64 {
   int32_t pad;
 };
 
-// One output tile C[m0:m0+64, n0:n0+64] of an M x N matrix; the members may
-// be stacked along M (c_axis 0) or N (c_axis 1), c_rm rows per member.
+// One output tile C[m0:m0+16*ni, n0:n0+16*nj] of an M x N matrix (ni, nj in
+// 1..4, chosen per output to fit its shape); the members may be stacked along
+// M (c_axis 0) or N (c_axis 1), c_rm rows per member.
 enum TileMode : int32_t { TM_STORE = 0, TM_DOT = 2 };
 struct TileF64 {
   int64_t c_off, c_bs;
@@ -52,7 +53,7 @@ struct TileF64 {
   int32_t c_rm, c_axis;
   int32_t c_trans;  // 0: C(mm, nn) at [mm*ldc + nn]; 1: at [nn*ldc + mm]
   int32_t add;      // second writer of an output block: always accumulate
-  int32_t pad;
+  int32_t shape;    // ni | nj << 8
 };
 
 struct TaskListF64 {

@@ -8,35 +8,38 @@
 // and coefficient, and accumulates them in registers.  One tile writes each
 // output element exactly once, so results do not depend on scheduling.
 //
-// Tile 64 x 64, K step 16, 256 threads with a 4 x 4 register block each
-// (rows ty + 16 i, cols tx + 16 j).  GB300 runs float64 at 1/64 of its FP32
-// rate, so this kernel is bound by DFMA issue, not by memory; batch members
-// that share operator blocks are stacked along M or N so that the small
-// sector blocks of a DMRG superblock fill the 64 x 64 tiles.
+// Tiles of 16*ni x 16*nj (ni, nj in 1..4, chosen per output so that the
+// sector blocks -- 1..80 wide in a DMRG superblock -- fill them), K step 16
+// with the last step cut to the true K, 256 threads with an ni x nj register
+// block each (rows ty + 16 i, cols tx + 16 j).  GB300 runs float64 at 1/64 of
+// its FP32 rate (2 DFMA per clock per SM), so this kernel is bound by DFMA
+// issue, not by memory, and the FMAs it spends on padding are the loss to
+// avoid; batch members that share operator blocks are stacked along M or N.
 
 #include "internal.h"
 
 namespace dmrg {
 
-constexpr int F64_BM = 64, F64_BN = 64, F64_BK = 16, F64_THREADS = 256;
+constexpr int F64_BMAX = 64, F64_BK = 16, F64_THREADS = 256;
 
-__global__ void __launch_bounds__(F64_THREADS)
-seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs,
-                    Bufs bufs, const double* __restrict__ coef, int n_terms, int accumulate,
-                    double* __restrict__ dot_out, const int32_t* __restrict__ skip) {
-  __shared__ double Ls[F64_BK][F64_BM + 1];
-  __shared__ double Rs[F64_BK][F64_BN + 1];
-  __shared__ double red[F64_THREADS / 32];
+struct F64Smem {
+  double L[F64_BK][F64_BMAX + 1];
+  double R[F64_BK][F64_BMAX + 1];
+  double red[F64_THREADS / 32];
+};
 
-  if (skip && *skip) return;
-  const TileF64 t = tiles[blockIdx.x];
+template <int NI, int NJ>
+__device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restrict__ segs, const Bufs& bufs,
+                                         const double* __restrict__ coef, int n_terms, int accumulate,
+                                         double* __restrict__ dot_out, F64Smem& sm) {
+  constexpr int BM = 16 * NI, BN = 16 * NJ;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  double acc[4][4];
+  double acc[NI][NJ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < NI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
 
   for (int sg = t.seg_begin; sg < t.seg_end; ++sg) {
     const SegF64 s = segs[sg];
@@ -45,10 +48,10 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
     const double uscale = (s.coef_mode == 0 && s.coef >= 0) ? coef[s.coef] : 1.0;
     for (int k0 = 0; k0 < s.K; k0 += F64_BK) {
 #pragma unroll
-      for (int e = 0; e < (F64_BM * F64_BK) / F64_THREADS; ++e) {
+      for (int e = 0; e < NI; ++e) {  // BM x BK elements, 256 per pass
         const int idx = tid + e * F64_THREADS;
         int m, k;
-        if (s.l_trans) { k = idx / F64_BM; m = idx % F64_BM; }
+        if (s.l_trans) { k = idx / BM; m = idx % BM; }
         else { m = idx / F64_BK; k = idx % F64_BK; }
         const int gm = t.m0 + m, gk = k0 + k;
         double v = 0.0;
@@ -59,14 +62,14 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
           v = s.l_trans ? Lb[(int64_t)gk * s.ldl + mm] : Lb[(int64_t)mm * s.ldl + gk];
           v *= s.coef_mode == 1 ? coef[bl * n_terms + s.coef] : uscale;
         }
-        Ls[k][m] = v;
+        sm.L[k][m] = v;
       }
 #pragma unroll
-      for (int e = 0; e < (F64_BN * F64_BK) / F64_THREADS; ++e) {
+      for (int e = 0; e < NJ; ++e) {  // BN x BK elements
         const int idx = tid + e * F64_THREADS;
         int n, k;
         if (s.r_trans) { n = idx / F64_BK; k = idx % F64_BK; }
-        else { k = idx / F64_BN; n = idx % F64_BN; }
+        else { k = idx / BN; n = idx % BN; }
         const int gn = t.n0 + n, gk = k0 + k;
         double v = 0.0;
         if (gn < t.N && gk < s.K) {
@@ -76,20 +79,26 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
           v = s.r_trans ? Rb[(int64_t)nn * s.ldr + gk] : Rb[(int64_t)gk * s.ldr + nn];
           if (s.coef_mode == 2) v *= coef[br * n_terms + s.coef];
         }
-        Rs[k][n] = v;
+        sm.R[k][n] = v;
       }
       __syncthreads();
+      const int kmax = min(F64_BK, s.K - k0);
+      auto step = [&](int k) {
+        double a[NI], b[NJ];
 #pragma unroll
-      for (int k = 0; k < F64_BK; ++k) {
-        double a[4], b[4];
+        for (int i = 0; i < NI; ++i) a[i] = sm.L[k][ty + 16 * i];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = Ls[k][ty + 16 * i];
+        for (int j = 0; j < NJ; ++j) b[j] = sm.R[k][tx + 16 * j];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Rs[k][tx + 16 * j];
+        for (int i = 0; i < NI; ++i)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      };
+      if (kmax == F64_BK) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int k = 0; k < F64_BK; ++k) step(k);
+      } else {
+        for (int k = 0; k < kmax; ++k) step(k);  // no FMAs on the zero padding of K
       }
       __syncthreads();
     }
@@ -108,11 +117,11 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
   if (t.mode == TM_STORE) {
     const bool add = accumulate || t.add;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NI; ++i) {
       const int m = t.m0 + ty + 16 * i;
       if (m >= t.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < NJ; ++j) {
         const int n = t.n0 + tx + 16 * j;
         if (n >= t.N) continue;
         double* p = C + coff(m, n);
@@ -122,11 +131,11 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
   } else {  // TM_DOT: sum over the tile of acc .* C, fixed-order block reduction
     double part = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NI; ++i) {
       const int m = t.m0 + ty + 16 * i;
       if (m >= t.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < NJ; ++j) {
         const int n = t.n0 + tx + 16 * j;
         if (n >= t.N) continue;
         part = fma(acc[i][j], C[coff(m, n)], part);
@@ -134,14 +143,33 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
+    if ((tid & 31) == 0) sm.red[tid >> 5] = part;
     __syncthreads();
     if (tid == 0) {
       double tot = 0.0;
-      for (int w = 0; w < F64_THREADS / 32; ++w) tot += red[w];
+      for (int w = 0; w < F64_THREADS / 32; ++w) tot += sm.red[w];
       dot_out[blockIdx.x] = tot;
     }
   }
+}
+
+__global__ void __launch_bounds__(F64_THREADS, 3)
+seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs,
+                    Bufs bufs, const double* __restrict__ coef, int n_terms, int accumulate,
+                    double* __restrict__ dot_out, const int32_t* __restrict__ skip) {
+  __shared__ F64Smem sm;
+  if (skip && *skip) return;
+  const TileF64 t = tiles[blockIdx.x];
+#define F64_CASE(I, J) \
+  case (I) | ((J) << 8): f64_tile<I, J>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm); break;
+  switch (t.shape) {
+    F64_CASE(1, 1) F64_CASE(1, 2) F64_CASE(1, 3) F64_CASE(1, 4)
+    F64_CASE(2, 1) F64_CASE(2, 2) F64_CASE(2, 3) F64_CASE(2, 4)
+    F64_CASE(3, 1) F64_CASE(3, 2) F64_CASE(3, 3) F64_CASE(3, 4)
+    F64_CASE(4, 1) F64_CASE(4, 2) F64_CASE(4, 3) F64_CASE(4, 4)
+    default: break;  // the host builds only the shapes above
+  }
+#undef F64_CASE
 }
 
 void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
