@@ -416,16 +416,18 @@ void lz_free(dmrg_sb* sb) {
       sb->lz_graphs[i] = nullptr;
       sb->lz_graph_key[i] = 0;
     }
-  for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_ab, sb->lz_s, sb->lz_out,
-                    sb->rf_res, sb->rf_p, sb->rf_q, sb->rf_t, sb->rf_sc})
+  for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_npart, sb->lz_ab, sb->lz_s,
+                    sb->lz_out, sb->rf_res, sb->rf_p, sb->rf_q, sb->rf_t, sb->rf_sc})
     if (p) cudaFree(p);
   if (sb->lz_ctl) cudaFree(sb->lz_ctl);
+  if (sb->lz_gate) cudaFree(sb->lz_gate);
   if (sb->rf_ctl) cudaFree(sb->rf_ctl);
   sb->rf_res = sb->rf_p = sb->rf_q = sb->rf_t = sb->rf_sc = nullptr;
   sb->rf_ctl = nullptr;
   if (sb->h_ctl) cudaFreeHost(sb->h_ctl);
-  sb->lz_V = sb->lz_w = sb->lz_vcur = sb->lz_partial = sb->lz_h = sb->lz_ab = sb->lz_s = sb->lz_out = nullptr;
-  sb->lz_ctl = nullptr;
+  sb->lz_V = sb->lz_w = sb->lz_vcur = sb->lz_partial = sb->lz_h = sb->lz_npart = sb->lz_ab = sb->lz_s =
+      sb->lz_out = nullptr;
+  sb->lz_ctl = sb->lz_gate = nullptr;
   sb->h_ctl = nullptr;
   sb->lz_cap = 0;
 }
@@ -439,7 +441,9 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   sb->lz_w = dalloc<double>((size_t)(B * D));
   sb->lz_vcur = dalloc<double>((size_t)(B * D));
   sb->lz_partial = dalloc<double>((size_t)(B * sb->lz_nchunk * cap));
-  sb->lz_h = dalloc<double>((size_t)(2 * B * cap));
+  sb->lz_h = dalloc<double>((size_t)(3 * B * cap));
+  sb->lz_npart = dalloc<double>((size_t)(3 * B * sb->lz_nchunk));
+  sb->lz_gate = dalloc<int32_t>((size_t)B);
   sb->lz_ab = dalloc<double>((size_t)(2 * B * cap));
   sb->lz_s = dalloc<double>((size_t)(B * cap));
   sb->lz_out = dalloc<double>((size_t)(4 * B + 1));
@@ -463,16 +467,26 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   const int B = sb->batch, cap = sb->lz_cap, nch = sb->lz_nchunk;
   int32_t* ctl = sb->lz_ctl;
   matvec(sb, prec, sb->lz_vcur, sb->lz_w, 0, ctl + LZ_CTL_ALLDONE, st);
-  double* h1 = sb->lz_h;
-  double* h2 = sb->lz_h + (size_t)B * cap;
-  double* npart = sb->lz_partial;  // reused: the norm partials fit in the row partials
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, nch, st);
-  lz_launch_reduce_rows(sb->lz_partial, h1, ctl, lz_dot_nchunk(D), cap, B, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, h1, nullptr, ctl, D, B, cap, nch, st);
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, nch, st);
-  lz_launch_reduce_rows(sb->lz_partial, h2, ctl, lz_dot_nchunk(D), cap, B, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, h2, npart, ctl, D, B, cap, nch, st);
-  lz_launch_finalize_ab(sb->lz_h, npart, sb->lz_ab, ctl, B, cap, nch, st);
+  // reorthogonalisation: (A) three-term step, (B) full pass, (C) second full
+  // pass where the DGKS test asks for it (see lanczos.cu)
+  double* hA = sb->lz_h;
+  double* hB = sb->lz_h + (size_t)B * cap;
+  double* hC = sb->lz_h + (size_t)2 * B * cap;
+  double* nA = sb->lz_npart;
+  double* nB = sb->lz_npart + (size_t)B * nch;
+  double* nC = sb->lz_npart + (size_t)2 * B * nch;
+  const int ndot = lz_dot_nchunk(D);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st);
+  lz_launch_reduce_rows(sb->lz_partial, hA, ctl, ndot, cap, B, 2, nullptr, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hA, nA, ctl, D, B, cap, nch, 2, nullptr, st);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st);
+  lz_launch_reduce_rows(sb->lz_partial, hB, ctl, ndot, cap, B, 0, nullptr, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st);
+  lz_launch_dgks(nA, nB, sb->lz_gate, ctl, B, nch, st);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st);
+  lz_launch_reduce_rows(sb->lz_partial, hC, ctl, ndot, cap, B, 0, sb->lz_gate, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st);
+  lz_launch_finalize_ab(sb->lz_h, nB, nC, sb->lz_gate, sb->lz_ab, ctl, B, cap, nch, st);
   lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, ctl, sb->lz_out + 4 * B, B, cap, D, st);  // tol at out[4B]
   lz_launch_next_vector(sb->lz_w, sb->lz_ab, sb->lz_V, sb->lz_vcur, ctl, D, B, cap, st);
   lz_launch_advance(ctl, B, st);
@@ -521,7 +535,7 @@ int matvec_launches(const dmrg_sb* sb, int prec) {
     return (sb->f64_fwd1.n_tiles > 0) + (sb->f64_fwd2.n_tiles > 0) + (sb->f64_fwd3.n_tiles > 0);
   return tc_launches(sb, prec);
 }
-constexpr int LZ_KERNELS_PER_ITER = 10;  // everything in lz_enqueue_iteration besides the product
+constexpr int LZ_KERNELS_PER_ITER = 14;  // everything in lz_enqueue_iteration besides the product
 
 // Lanczos from psi0 (device [batch][D]) to psi_out; returns per-member results.
 LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double tol, int max_iter,

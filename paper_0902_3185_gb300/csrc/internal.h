@@ -109,7 +109,9 @@ struct dmrg_sb {
   double* lz_w = nullptr;        // [batch][D]
   double* lz_vcur = nullptr;     // [batch][D]
   double* lz_partial = nullptr;  // [batch][nchunk][lz_cap]
-  double* lz_h = nullptr;        // [2][batch][lz_cap]
+  double* lz_h = nullptr;        // Gram-Schmidt coefficients of passes A, B, C: [3][batch][lz_cap]
+  double* lz_npart = nullptr;    // |w|^2 chunk partials after passes A, B, C: [3][batch][nchunk]
+  int32_t* lz_gate = nullptr;    // [batch] 1: run the second full pass (C)
   double* lz_ab = nullptr;       // alpha [batch][lz_cap], beta [batch][lz_cap]
   double* lz_s = nullptr;        // Ritz vector [batch][lz_cap]
   double* lz_out = nullptr;      // per member: theta, resid

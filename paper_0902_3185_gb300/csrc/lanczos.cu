@@ -1,5 +1,14 @@
-// Float64 Lanczos kernels: Krylov scalars, full reorthogonalisation (classical
-// Gram-Schmidt applied twice), the tridiagonal eigenproblem and the Ritz vector.
+// Float64 Lanczos kernels: Krylov scalars, full reorthogonalisation, the
+// tridiagonal eigenproblem and the Ritz vector.
+//
+// Reorthogonalisation of w = H v_j, every iteration against every Krylov
+// vector, in three classical Gram-Schmidt passes: (A) the three-term step
+// against v_{j-1}, v_j (alpha_j is its v_j coefficient); (B) one pass against
+// v_0..v_j; (C) a second full pass for the members whose norm fell below
+// 1/sqrt(2) of its value before pass B (the Daniel-Gragg-Kaufman-Stewart
+// test).  After the three-term step the remaining components along the basis
+// are small, so pass B rarely shrinks w and pass C is rarely run; each full
+// pass costs 2 (j+1) D float64 FMAs per member.
 //
 // Paper Sec. 3.3: each targeted symmetry block is diagonalised with Lanczos,
 // which needs only x += H y.  Everything here runs on the device for all batch
@@ -36,7 +45,16 @@ __device__ __forceinline__ bool member_done(const int32_t* ctl, int b) {
   return ctl[LZ_CTL_ALLDONE] != 0 || ctl[LZ_CTL_MEMBER + b] != 0;
 }
 
-// partial[(b*nchunk + chunk)*cap + i] = sum_{d in chunk} V[i][b][d] * w[b][d], i <= j.
+// skip a member: finished, or gated off (gate != NULL and gate[b] == 0)
+__device__ __forceinline__ bool member_skip(const int32_t* ctl, const int32_t* gate, int b) {
+  return member_done(ctl, b) || (gate && gate[b] == 0);
+}
+
+// first Krylov row of a pass: the last `win` rows, or all (win = 0)
+__device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j - win + 1) : 0; }
+
+// partial[(b*nchunk + chunk)*cap + i] = sum_{d in chunk} V[i][b][d] * w[b][d], i0 <= i <= j
+// (i0 = first_row(j, win)).
 // GB300 issues float64 at 1/64 of the float32 rate, so the reduction must not
 // cost more float64 work than the dot products: every thread keeps
 // LZ_DOT_EPT elements of w in registers, takes 8 rows at a time, and the 8
@@ -44,10 +62,11 @@ __device__ __forceinline__ bool member_done(const int32_t* ctl, int b) {
 // per lane at each step (4+2+1+1+1 shuffle-adds for 8 rows, not 8 x 5).
 __global__ void __launch_bounds__(LZ_THREADS)
 k_multidot(const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ partial,
-           const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk) {
+           const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk, int win,
+           const int32_t* __restrict__ gate) {
   __shared__ double red[LZ_THREADS / 32][8];
   const int b = blockIdx.y, chunk = blockIdx.x;
-  if (member_done(ctl, b)) return;
+  if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double wv[LZ_DOT_EPT];
@@ -58,7 +77,7 @@ k_multidot(const double* __restrict__ V, const double* __restrict__ w, double* _
     wv[e] = d < D ? w[(int64_t)b * D + d] : 0.0;
   }
   const bool full = base + (LZ_DOT_EPT - 1) * LZ_THREADS < D;
-  for (int i0 = 0; i0 <= j; i0 += 8) {
+  for (int i0 = first_row(j, win); i0 <= j; i0 += 8) {
     double p[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -118,17 +137,17 @@ k_multidot(const double* __restrict__ V, const double* __restrict__ w, double* _
   }
 }
 
-// h[b*cap + i] = sum over chunks of the partials, i <= j.  Block (32 x 8):
+// h[b*cap + i] = sum over chunks of the partials, first_row(j, win) <= i <= j.  Block (32 x 8):
 // lane x owns row i0 + x, warp y sums chunks y, y + 8, ...; the 8 warp sums
 // are then added in a fixed order (deterministic).
 __global__ void __launch_bounds__(256)
 k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h, const int32_t* __restrict__ ctl,
-              int nchunk, int cap) {
+              int nchunk, int cap, int win, const int32_t* __restrict__ gate) {
   __shared__ double red[8][33];
   const int b = blockIdx.x;
-  if (member_done(ctl, b)) return;
+  if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
-  const int i0 = blockIdx.y * 32;
+  const int i0 = first_row(j, win) + blockIdx.y * 32;
   if (i0 > j) return;
   const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
   const int i = i0 + x;
@@ -145,18 +164,19 @@ k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h, const 
   }
 }
 
-// w[b] -= sum_{i<=j} V[i][b] h[b][i]; with norm_partial != NULL also the
-// per-chunk sum of squares of the new w.
+// w[b] -= sum_{i0<=i<=j} V[i][b] h[b][i] (i0 = first_row(j, win)); with
+// norm_partial != NULL also the per-chunk sum of squares of the new w.
 __global__ void __launch_bounds__(LZ_THREADS)
 k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* __restrict__ h,
             double* __restrict__ norm_partial, const int32_t* __restrict__ ctl, int64_t D, int batch,
-            int cap, int nchunk) {
+            int cap, int nchunk, int win, const int32_t* __restrict__ gate) {
   extern __shared__ double sh[];
   __shared__ double red[LZ_THREADS / 32];
   const int b = blockIdx.y, chunk = blockIdx.x;
-  if (member_done(ctl, b)) return;
+  if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) sh[i] = h[(int64_t)b * cap + i];
+  const int i0 = first_row(j, win);
+  for (int i = i0 + threadIdx.x; i <= j; i += blockDim.x) sh[i] = h[(int64_t)b * cap + i];
   __syncthreads();
   double nrm = 0.0;
 #pragma unroll
@@ -164,7 +184,7 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
     const int64_t d = (int64_t)chunk * LZ_CHUNK + e * LZ_THREADS + threadIdx.x;
     if (d >= D) continue;
     double acc = w[(int64_t)b * D + d];
-    for (int i = 0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
+    for (int i = i0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
     w[(int64_t)b * D + d] = acc;
     nrm = fma(acc, acc, nrm);
   }
@@ -174,20 +194,41 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
   }
 }
 
-// alpha_j = h1[j] + h2[j], beta_j = sqrt(sum of norm partials); one warp per
-// member, lane-strided partial sums then a fixed shuffle tree (deterministic)
-__global__ void k_finalize_ab(const double* __restrict__ h, const double* __restrict__ norm_partial,
-                              double* __restrict__ ab, const int32_t* __restrict__ ctl, int batch,
-                              int cap, int nchunk) {
+// sum of a member's norm partials: lane-strided sums, then a fixed shuffle tree
+__device__ __forceinline__ double warp_sum_chunks(const double* __restrict__ part, int nchunk) {
+  double t = 0.0;
+  for (int ch = threadIdx.x; ch < nchunk; ch += 32) t += part[ch];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// Daniel-Gragg-Kaufman-Stewart test after pass B: gate[b] = 1 (run pass C)
+// unless |w_B|^2 >= |w_A|^2 / 2.  One warp per member.
+__global__ void k_dgks(const double* __restrict__ npart_a, const double* __restrict__ npart_b,
+                       int32_t* __restrict__ gate, const int32_t* __restrict__ ctl, int nchunk) {
+  const int b = blockIdx.x;
+  if (member_done(ctl, b)) return;
+  const double na = warp_sum_chunks(npart_a + (int64_t)b * nchunk, nchunk);
+  const double nb = warp_sum_chunks(npart_b + (int64_t)b * nchunk, nchunk);
+  if (threadIdx.x == 0) gate[b] = (nb >= 0.5 * na) ? 0 : 1;  // NaN: run pass C, then the NaN check stops it
+}
+
+// alpha_j = sum of the v_j coefficients of the passes that ran, beta_j = |w|
+// after the last pass.  One warp per member (deterministic).
+__global__ void k_finalize_ab(const double* __restrict__ h, const double* __restrict__ npart_b,
+                              const double* __restrict__ npart_c, const int32_t* __restrict__ gate,
+                              double* __restrict__ ab, const int32_t* __restrict__ ctl, int batch, int cap,
+                              int nchunk) {
   const int b = blockIdx.x;
   if (member_done(ctl, b)) return;
   const int j = ctl[LZ_CTL_J];
-  double t = 0.0;
-  for (int ch = threadIdx.x; ch < nchunk; ch += 32) t += norm_partial[(int64_t)b * nchunk + ch];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const bool c = gate[b] != 0;
+  const double t = warp_sum_chunks((c ? npart_c : npart_b) + (int64_t)b * nchunk, nchunk);
   if (threadIdx.x == 0) {
-    ab[(int64_t)b * cap + j] = h[(int64_t)b * cap + j] + h[((int64_t)batch + b) * cap + j];
+    double a = h[(int64_t)b * cap + j] + h[((int64_t)batch + b) * cap + j];
+    if (c) a += h[(2 * (int64_t)batch + b) * cap + j];
+    ab[(int64_t)b * cap + j] = a;
     ab[((int64_t)batch + b) * cap + j] = sqrt(t);
   }
 }
@@ -490,22 +531,28 @@ __global__ void k_reduce_terms(const double* __restrict__ part, const int32_t* _
 
 // ------------------------------------------------------------- launchers
 void lz_launch_multidot(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
-                        int batch, int cap, int nchunk, cudaStream_t st) {
+                        int batch, int cap, int win, const int32_t* gate, cudaStream_t st) {
   k_multidot<<<dim3(lz_dot_nchunk(D), batch), LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap,
-                                                                  lz_dot_nchunk(D));
+                                                                  lz_dot_nchunk(D), win, gate);
 }
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
-                           int batch, cudaStream_t st) {
-  k_reduce_rows<<<dim3(batch, (cap + 31) / 32), 256, 0, st>>>(partial, h, ctl, nchunk, cap);
+                           int batch, int win, const int32_t* gate, cudaStream_t st) {
+  const int rows = win ? win : cap;
+  k_reduce_rows<<<dim3(batch, (rows + 31) / 32), 256, 0, st>>>(partial, h, ctl, nchunk, cap, win, gate);
 }
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
-                         const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, cudaStream_t st) {
+                         const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, int win,
+                         const int32_t* gate, cudaStream_t st) {
   k_multiaxpy<<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl, D,
-                                                                            batch, cap, nchunk);
+                                                                            batch, cap, nchunk, win, gate);
 }
-void lz_launch_finalize_ab(const double* h, const double* norm_partial, double* ab, const int32_t* ctl,
-                           int batch, int cap, int nchunk, cudaStream_t st) {
-  k_finalize_ab<<<batch, 32, 0, st>>>(h, norm_partial, ab, ctl, batch, cap, nchunk);
+void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate, const int32_t* ctl, int batch,
+                    int nchunk, cudaStream_t st) {
+  k_dgks<<<batch, 32, 0, st>>>(npart_a, npart_b, gate, ctl, nchunk);
+}
+void lz_launch_finalize_ab(const double* h, const double* npart_b, const double* npart_c, const int32_t* gate,
+                           double* ab, const int32_t* ctl, int batch, int cap, int nchunk, cudaStream_t st) {
+  k_finalize_ab<<<batch, 32, 0, st>>>(h, npart_b, npart_c, gate, ab, ctl, batch, cap, nchunk);
 }
 void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
                        int cap, int64_t D, cudaStream_t st) {

@@ -80,12 +80,13 @@ struct TcOut {
 
 struct StageJob {
   int64_t src_off;    // sector block offset inside a member
-  int64_t first;      // first element of this job in the flattened stream
+  int64_t first;      // first granule of this job in the flattened stream
   char* p;
   int64_t p_lo;
   int32_t r, c;       // source block dims
   int32_t transpose, term;
-  int32_t atoms, pad;
+  int32_t atoms;
+  int32_t nkg;        // granules per panel row: ceil(K / values per granule)
 };
 
 // byte offset of element (row, k) inside a panel
@@ -130,33 +131,28 @@ struct PanelColumnWriter {
   }
 };
 
-template <int PREC>
-__device__ __forceinline__ void store_panel(char* p, int64_t p_lo, int64_t row, int64_t k, int atoms, float v) {
-  if (PREC == DMRG_TF32) {
-    *reinterpret_cast<float*>(p + panel_off(row, k, atoms, 4)) = tc::round_tf32(v);
-  } else {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    const int64_t o = panel_off(row, k, atoms, 2);
-    *reinterpret_cast<__nv_bfloat16*>(p + o) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(p + p_lo + o) = lo;
-  }
-}
-
 // ---------------------------------------------------------------- staging
 // float64 psi blocks -> operand panels (optionally transposed and scaled by
-// the member's coefficient).  The jobs' elements form one flat stream (jobs
-// back to back, `first` = prefix); consecutive threads take consecutive
-// elements: row-major for a plain job, column-major for a transposed one, so
-// that both the panel writes (along K) and, for plain jobs, the reads are
-// contiguous.  Each thread finds its job by binary search once, then walks.
+// the member's coefficient), in 16-byte granules: 8 BF16 (hi and lo) or 4
+// TF32 consecutive K values of one panel row, converted once and written
+// with one vector store per half.  The jobs' granules form one flat stream
+// (jobs back to back, `first` = prefix).  Consecutive threads take
+// consecutive granules along the row for a plain job (each thread reads a
+// contiguous run of its row) and consecutive panel rows for a transposed job
+// (each of a thread's loads is coalesced across the warp).  Granules reaching
+// into the K padding write zeros there.  Each thread finds its job by binary
+// search once, then walks.
+constexpr int STAGE_GRANULES_PER_THREAD = 2;
+
 template <int PREC>
 __global__ void __launch_bounds__(256)
 tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, const double* __restrict__ x,
                 int64_t D, const double* __restrict__ coef, int n_terms, const int32_t* __restrict__ skip) {
+  constexpr int G = PREC == DMRG_TF32 ? 4 : 8;  // values per 16-byte granule
+  constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
   if (skip && *skip) return;
   const int b = blockIdx.y;
-  const int64_t e0 = (int64_t)blockIdx.x * (256 * 8) + threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * (256 * STAGE_GRANULES_PER_THREAD) + threadIdx.x;
   if (e0 >= total) return;
   int lo = 0, hi = n_jobs - 1;  // last job with first <= e0
   while (lo < hi) {
@@ -166,27 +162,50 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
   }
   int jid = lo;
   StageJob j = jobs[jid];
-  int64_t jend = j.first + (int64_t)j.r * j.c;
+  int rows = j.transpose ? j.c : j.r;
+  int64_t jend = j.first + (int64_t)rows * j.nkg;
   float scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
   const double* xb = x + (int64_t)b * D;
 #pragma unroll 1
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < STAGE_GRANULES_PER_THREAD; ++u) {
     const int64_t e = e0 + (int64_t)u * 256;
     if (e >= total) break;
     while (e >= jend) {
       j = jobs[++jid];
-      jend = j.first + (int64_t)j.r * j.c;
+      rows = j.transpose ? j.c : j.r;
+      jend = j.first + (int64_t)rows * j.nkg;
       scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
     }
-    const int loc = (int)(e - j.first);  // < r * c: 32-bit division (64-bit is a long sequence)
-    if (!j.transpose) {  // row = b*r + a, k = c
-      const int a = loc / j.c, cc = loc - a * j.c;
-      const float v = tc::d2f_rn(xb[j.src_off + (int64_t)a * j.c + cc]) * scf;
-      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.r + a, cc, j.atoms, v);
-    } else {  // row = b*c + c', k = a (column-major walk)
-      const int cc = loc / j.r, a = loc - cc * j.r;
-      const float v = tc::d2f_rn(xb[j.src_off + (int64_t)a * j.c + cc]) * scf;
-      store_panel<PREC>(j.p, j.p_lo, (int64_t)b * j.c + cc, a, j.atoms, v);
+    const int loc = (int)(e - j.first);  // < rows * nkg: 32-bit division
+    int row, kg;
+    if (!j.transpose) { row = loc / j.nkg; kg = loc - row * j.nkg; }  // panel row a, K = c
+    else { kg = loc / rows; row = loc - kg * rows; }                  // panel row c', K = a
+    const int K = j.transpose ? j.r : j.c;
+    const double* src = xb + j.src_off;
+    float v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int k = kg * G + i;
+      v[i] = 0.0f;
+      if (k < K) v[i] = tc::d2f_rn(j.transpose ? src[(int64_t)k * j.c + row] : src[(int64_t)row * j.c + k]) * scf;
+    }
+    const int64_t o = panel_off((int64_t)b * rows + row, (int64_t)kg * G, j.atoms, es);
+    if (PREC == DMRG_TF32) {
+      const uint4 w = make_uint4(__float_as_uint(tc::round_tf32(v[0])), __float_as_uint(tc::round_tf32(v[1])),
+                                 __float_as_uint(tc::round_tf32(v[2])), __float_as_uint(tc::round_tf32(v[3])));
+      *reinterpret_cast<uint4*>(j.p + o) = w;
+    } else {
+      uint32_t wh[4], wl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
+        wh[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        wl[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      *reinterpret_cast<uint4*>(j.p + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+      *reinterpret_cast<uint4*>(j.p + j.p_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
   }
 }
@@ -547,7 +566,7 @@ struct Launch {  // one grouped GEMM launch
 struct PairSet {  // the forward pairs or their transposes
   StageJob* jobs = nullptr;
   int n_jobs = 0;
-  int64_t n_elems = 0;  // per member
+  int64_t n_gran = 0;  // staging granules per member
   Launch ph1, grpE, grpS;
 };
 
@@ -704,12 +723,12 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
 
   // ---- staging jobs (one flat element stream)
   std::vector<StageJob> jobs;
-  int64_t n_elems = 0;
+  int64_t n_gran = 0;
   auto add_job = [&](int s, int transpose, int term, const Panel& p) {
     if ((int64_t)r[s] * c[s] == 0) return;
     StageJob j{};
     j.src_off = sb->off[s];
-    j.first = n_elems;
+    j.first = n_gran;
     j.r = r[s];
     j.c = c[s];
     j.transpose = transpose;
@@ -717,8 +736,9 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     j.p = dptr(p);
     j.p_lo = lo_delta;
     j.atoms = (int32_t)p.atoms;
+    j.nkg = (int32_t)cdiv(transpose ? r[s] : c[s], 16 / es);  // 16-byte granules per panel row
     jobs.push_back(j);
-    n_elems += (int64_t)r[s] * c[s];
+    n_gran += (int64_t)(transpose ? c[s] : r[s]) * j.nkg;
   };
   for (int s = 0; s < S; ++s) {
     if (needP[s]) add_job(s, 0, -1, psiP[s]);
@@ -899,7 +919,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   finish(LS, out.grpS);
   out.jobs = up(jobs);
   out.n_jobs = (int)jobs.size();
-  out.n_elems = n_elems;
+  out.n_gran = n_gran;
   return cur - base_off;
 }
 
@@ -933,7 +953,7 @@ int tc_launches(const dmrg_sb* sb, int prec) {
   const State* s = st_of(sb);
   if (!s || !s->ok) return 0;
   const PairSet& ps = s->f[prec == DMRG_TF32 ? 0 : 1].fwd;
-  return (ps.n_elems > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
+  return (ps.n_gran > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
 }
 
 // (Re)build the panels and task lists of one precision with its tuning.
@@ -1043,9 +1063,9 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
 template <int PREC>
 static void run_set(const State* s, const PairSet& ps, const double* x, double* y, const dmrg_sb* sb,
                     int accumulate, const int32_t* skip, cudaStream_t st) {
-  if (ps.n_elems > 0) {
-    const int64_t blocks = (ps.n_elems + 256 * 8 - 1) / (256 * 8);
-    tc_stage_kernel<PREC><<<dim3((unsigned)blocks, sb->batch), 256, 0, st>>>(ps.jobs, ps.n_jobs, ps.n_elems, x, sb->D,
+  if (ps.n_gran > 0) {
+    const int64_t blocks = cdiv(ps.n_gran, 256 * STAGE_GRANULES_PER_THREAD);
+    tc_stage_kernel<PREC><<<dim3((unsigned)blocks, sb->batch), 256, 0, st>>>(ps.jobs, ps.n_jobs, ps.n_gran, x, sb->D,
                                                                             sb->d_coeffs, sb->n_terms, skip);
   }
   run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
