@@ -3,8 +3,9 @@
 // Paper Sec. 3.3: x += H y as system, environment and connection tasks, each
 // a product of sector blocks, formed on the fly.  With batch members that
 // share every operator block (coupling sweeps), the member wavefunctions are
-// stacked along the M dimension of every product, so that the small, uneven
-// sector blocks of a DMRG superblock become GEMMs with M = batch x dim:
+// stacked along the M dimension of every product (member stride = dim rounded
+// up to 8 rows, the padding rows zero), so that the small, uneven sector
+// blocks of a DMRG superblock become GEMMs with M = batch x dim:
 //
 //   order R pairs (A last):  X_b = Psi_b[s_in] B^T         (phase 1)
 //                            Y_b^T += X_b^T A^T              (group S)
@@ -24,9 +25,10 @@
 // One persistent kernel runs a list of output tiles (128 x up to 256) per
 // launch: warp 0 streams operand tiles through a multi-stage shared-memory
 // ring, warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator,
-// warps 2-5 drain the accumulator (tcgen05.ld) and either write the float64
+// warps 2-13 drain the accumulator (tcgen05.ld) and either write the float64
 // output block or the next phase's operand panel (scaled by the member's
-// coefficient, rounded to TF32 or split into BF16 hi + lo).
+// coefficient, rounded to TF32 or split into BF16 hi + lo, written in 16-byte
+// granules after a transpose across lanes).
 //
 // Precisions: TF32 (kind::tf32), and BF16x3: x = hi + lo, products
 // hi*hi + hi*lo + lo*hi in kind::f16 with an FP32 accumulator.
@@ -55,20 +57,14 @@ struct TcSeg {
   int32_t slot;       // accumulator slot (0: coefficients already applied)
 };
 
-constexpr int TC_MAX_SLOTS = 4;
-struct TcTile {
-  int32_t m0, n0, ntile, la, ra;  // la / ra: atoms to load from L / R
-  int32_t seg_begin, seg_end, out;
-  int32_t slot_used;              // bit k: slot k receives at least one product
-  int32_t slot_term[TC_MAX_SLOTS];  // slot k >= 1: its coefficient column (member from the row)
-};
-
 enum OutKind : int32_t { OUT_Y_ROW = 0, OUT_Y_COL = 1, OUT_PANEL = 2 };
 
 struct TcOut {
   int32_t kind;
-  int32_t Rm;      // accumulator rows per batch member
-  int32_t M, N;    // valid accumulator rows / columns
+  int32_t Rm;      // accumulator rows per batch member (a multiple of 8)
+  int32_t Rv;      // of which hold data (the rest is padding of the member stride)
+  int32_t Np;      // panel: panel rows per member (N rounded up to 8)
+  int32_t M, N;    // accumulator rows (batch x Rm) / valid columns
   int32_t ldy;     // Y: row length of the output block
   int32_t add;     // Y: accumulate into y (second group of a sector)
   int32_t term;    // panel: coefficient column, -1 = 1
@@ -76,6 +72,15 @@ struct TcOut {
   int64_t y_off;   // Y: element offset of the sector block in a member
   char* p;         // panel (hi)
   int64_t p_lo;
+};
+
+constexpr int TC_MAX_SLOTS = 4;
+struct TcTile {
+  int32_t m0, n0, ntile, la, ra;  // la / ra: atoms to load from L / R
+  int32_t seg_begin, seg_end, out;
+  int32_t slot_used;              // bit k: slot k receives at least one product
+  int32_t slot_term[TC_MAX_SLOTS];  // slot k >= 1: its coefficient column (member from the row)
+  TcOut o;                        // the output this tile belongs to (a copy: one load per tile)
 };
 
 struct StageJob {
@@ -98,38 +103,6 @@ __host__ __device__ inline int64_t panel_off(int64_t row, int64_t k, int64_t ato
   const int64_t chunk = (byte >> 4) ^ r8;
   return (kc * atoms + atom) * 1024 + r8 * 128 + (chunk << 4) + (byte & 15);
 }
-
-// Writes of one epilogue thread: fixed K index k, varying panel row.  The
-// byte offset splits into a per-thread part (K chunk, byte inside the row)
-// and a per-row part (atom, row in atom, swizzled 16-byte chunk), in 32-bit.
-template <int PREC>
-struct PanelColumnWriter {
-  char* hi;
-  int64_t lo_delta;
-  int32_t kbase;  // kc * atoms * 1024 + (byte & 15)
-  int32_t chunk;  // 16-byte chunk of k before the swizzle
-  __device__ __forceinline__ PanelColumnWriter(char* p, int64_t p_lo, int k, int atoms) {
-    constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
-    constexpr int kce = 128 / es;
-    const int kc = k / kce, byte = (k - kc * kce) * es;
-    hi = p;
-    lo_delta = p_lo;
-    kbase = kc * atoms * 1024 + (byte & 15);
-    chunk = byte >> 4;
-  }
-  __device__ __forceinline__ void put(int row, float v) const {
-    const int r8 = row & 7;
-    const int off = kbase + ((row >> 3) << 10) + (r8 << 7) + ((chunk ^ r8) << 4);
-    if (PREC == DMRG_TF32) {
-      *reinterpret_cast<float*>(hi + off) = tc::round_tf32(v);
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-      *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
-      *reinterpret_cast<__nv_bfloat16*>(hi + lo_delta + off) = l;
-    }
-  }
-};
 
 // ---------------------------------------------------------------- staging
 // float64 psi blocks -> operand panels (optionally transposed and scaled by
@@ -189,7 +162,7 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
       v[i] = 0.0f;
       if (k < K) v[i] = tc::d2f_rn(j.transpose ? src[(int64_t)k * j.c + row] : src[(int64_t)row * j.c + k]) * scf;
     }
-    const int64_t o = panel_off((int64_t)b * rows + row, (int64_t)kg * G, j.atoms, es);
+    const int64_t o = panel_off((int64_t)b * ((rows + 7) & ~7) + row, (int64_t)kg * G, j.atoms, es);
     if (PREC == DMRG_TF32) {
       const uint4 w = make_uint4(__float_as_uint(tc::round_tf32(v[0])), __float_as_uint(tc::round_tf32(v[1])),
                                  __float_as_uint(tc::round_tf32(v[2])), __float_as_uint(tc::round_tf32(v[3])));
@@ -217,13 +190,14 @@ constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer, MMA, epilogue
 constexpr int L_TILE_BYTES = 128 * 128;             // 128 rows x 128 B
 constexpr int EPI_LD = 17;                          // staging row stride (doubles)
 constexpr int EPI_BYTES = TC_EPI_WARPS * 32 * EPI_LD * 8;
-constexpr int TC_CTRL_BYTES = 256;
+constexpr int TC_COEF_MAX = 512;                    // coefficients cached in shared memory (float)
+constexpr int TC_CTRL_BYTES = 256 + 4 * TC_COEF_MAX;  // barriers etc., then the coefficient cache
 
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
-               const TcOut* __restrict__ outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef,
-               int n_terms, int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
+               double* __restrict__ y, int64_t D, const double* __restrict__ coef, int n_terms, int n_coef,
+               int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
                int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride,
                int stall) {
   if (skip && *skip) return;
@@ -236,6 +210,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* coef_s = reinterpret_cast<float*>(smem_raw + 256);  // member coefficients as float
   double* epi_stage = reinterpret_cast<double*>(smem_raw + TC_CTRL_BYTES);
   const uint32_t base_u32 = tc::smem_u32(smem_raw);
   char* ring = smem_raw + (((base_u32 + TC_CTRL_BYTES + (uint32_t)epi_bytes + 1023) & ~1023u) - base_u32);
@@ -258,6 +233,12 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
     tc::tmem_alloc(tmem_slot, (uint32_t)tmem_cols);
     tc::tmem_relinquish();
   }
+  // the coefficients are applied in float32 (their rounding, 2^-24, is far
+  // below the operand precision); cached here so that no tile waits on them
+  const bool coef_cached = n_coef <= TC_COEF_MAX;
+  if (coef_cached)
+    for (int k = threadIdx.x; k < n_coef; k += blockDim.x) coef_s[k] = tc::d2f_rn(coef[k]);
+  auto coef_f = [&](int k) { return coef_cached ? coef_s[k] : tc::d2f_rn(coef[k]); };
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -270,11 +251,27 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       uint32_t phase = 0;
       uint32_t issued = 0;  // bit s: stage s has a copy in flight or landed
       uint32_t issued_par = 0;
-      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const TcTile tl = tiles[t];
+      // descriptors are fetched one segment (and one tile) ahead, so that
+      // their load latency overlaps the copies of the current segment
+      int t = blockIdx.x;
+      TcTile tl{}, tl_n{};
+      if (t < n_tiles) tl_n = tiles[t];
+      TcSeg sg_n{};
+      int sg_n_idx = -1;
+      for (; t < n_tiles; t += gridDim.x) {
+        tl = tl_n;
+        const int tn = t + gridDim.x;
+        if (tn < n_tiles) tl_n = tiles[tn];
         const uint32_t lb = (uint32_t)tl.la * 1024u, rb = (uint32_t)tl.ra * 1024u;
         for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
-          const TcSeg sg = segs[s];
+          const TcSeg sg = sg_n_idx == s ? sg_n : segs[s];
+          if (s + 1 < tl.seg_end) {
+            sg_n = segs[s + 1];
+            sg_n_idx = s + 1;
+          } else if (tn < n_tiles && tl_n.seg_begin < tl_n.seg_end) {
+            sg_n = segs[tl_n.seg_begin];
+            sg_n_idx = tl_n.seg_begin;
+          }
           for (int kc = 0; kc < sg.kchunks; ++kc) {
             if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) goto producer_done;
             char* st = ring + (size_t)stage * stage_bytes;
@@ -317,17 +314,25 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       int acc = 0;
       uint32_t acc_phase = 0;
       constexpr uint32_t fmt = PREC == DMRG_TF32 ? tc::FMT_TF32 : tc::FMT_BF16;
+      TcTile tl_n{};
+      if (blockIdx.x < n_tiles) tl_n = tiles[blockIdx.x];
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const TcTile tl = tiles[t];
+        const TcTile tl = tl_n;
+        if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
         if (tl.seg_begin == tl.seg_end) continue;
+        int kch_n = segs[tl.seg_begin].kchunks, slot_n = segs[tl.seg_begin].slot;  // in flight during the wait
         if (!tc::mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag)) goto mma_done;
         tc::tc_fence_after();
         const uint32_t d_acc = tmem_base + (uint32_t)(acc * acc_stride);
         const uint32_t idesc = tc::idesc_f32acc(fmt, 128, (uint32_t)tl.ntile);
         uint32_t started = 0;  // slots that already hold a partial sum
         for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
-          const int kch = segs[s].kchunks;
-          const int slot = segs[s].slot;
+          const int kch = kch_n;
+          const int slot = slot_n;
+          if (s + 1 < tl.seg_end) {  // one segment ahead
+            kch_n = segs[s + 1].kchunks;
+            slot_n = segs[s + 1].slot;
+          }
           const uint32_t d_tmem = d_acc + (uint32_t)(slot * tl.ntile);
           uint32_t accum = (started >> slot) & 1u;
           started |= 1u << slot;
@@ -388,13 +393,16 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
     double* stg = epi_stage + (warp - 2) * 32 * EPI_LD;
     int acc = 0;
     uint32_t acc_phase = 0;
+    TcTile tl_n{};
+    if (blockIdx.x < n_tiles) tl_n = tiles[blockIdx.x];
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-      const TcTile tl = tiles[t];
-      const TcOut o = outs[tl.out];
+      const TcTile tl = tl_n;
+      if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
+      const TcOut& o = tl.o;
       const int m = tl.m0 + row;
-      const bool mv = m < o.M;
-      const int b = mv ? m / o.Rm : 0;
-      const int i = mv ? m - b * o.Rm : 0;
+      const int b = m < o.M ? m / o.Rm : 0;
+      const int i = m < o.M ? m - b * o.Rm : 0;
+      const bool mv = m < o.M && i < o.Rv;  // this lane's row holds data (not stride padding)
       const int nend = min(tl.n0 + tl.ntile, o.N);
       const bool add = o.add || accumulate;
       if (tl.seg_begin == tl.seg_end) {
@@ -411,14 +419,13 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       if (!ok) break;
       tc::tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(acc * acc_stride) + ((uint32_t)(32 * q) << 16);
-      // the coefficient is applied in float32 (its rounding, 2^-24, is far below the operand precision)
-      const float scf = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? tc::d2f_rn(coef[(int64_t)b * n_terms + o.term]) : 1.0f;
+      const float scf = (o.kind == OUT_PANEL && o.term >= 0 && mv) ? coef_f(b * n_terms + o.term) : 1.0f;
       // row-major output: element offset of this lane's row (-1 = row not stored)
       const int64_t rbase = (o.kind == OUT_Y_ROW && mv) ? (int64_t)b * D + o.y_off + (int64_t)i * o.ldy : -1;
       float slot_sc[TC_MAX_SLOTS];
 #pragma unroll
       for (int k = 1; k < TC_MAX_SLOTS; ++k)
-        slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? tc::d2f_rn(coef[(int64_t)b * n_terms + tl.slot_term[k]]) : 0.0f;
+        slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? coef_f(b * n_terms + tl.slot_term[k]) : 0.0f;
       for (int c0 = 16 * half; c0 < tl.ntile; c0 += 16 * TC_EPI_PARTS) {
         float v[16];
         if (tl.slot_used == 1) {
@@ -459,16 +466,67 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           __syncwarp();
           continue;
         }
-        if (!mv) continue;
         if (o.kind == OUT_PANEL) {
-          const PanelColumnWriter<PREC> wr(o.p, o.p_lo, i, o.p_atoms);
-          const int row0 = b * o.N + tl.n0 + c0;
+          // Lanes G g .. G g + G-1 hold G consecutive accumulator rows, i.e. G
+          // consecutive K values of one member (the member stride is a
+          // multiple of 8).  Transpose each G x G block of (row, column) across
+          // those lanes so that a lane holds G rows of one column, and write
+          // them as one 16-byte granule of the panel (per half for BF16).
+          constexpr int G = PREC == DMRG_TF32 ? 4 : 8;
+          uint32_t w[16];
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            if (tl.n0 + c0 + jj >= nend) break;
-            wr.put(row0 + jj, v[jj] * scf);
+            const float x = v[jj] * scf;
+            if (PREC == DMRG_TF32) {
+              w[jj] = __float_as_uint(tc::round_tf32(x));
+            } else {
+              const __nv_bfloat16 h = __float2bfloat16_rn(x);
+              const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+              w[jj] = (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+            }
           }
-        } else {  // column-major float64 output: lanes write consecutive i
+          // block transpose: swap the off-diagonal half blocks between lanes
+          // differing in `bit`, then recurse into the halves
+#pragma unroll
+          for (int bit = G / 2; bit >= 1; bit >>= 1) {
+            const bool upper = (lane & bit) != 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              if (k & bit) continue;
+              const uint32_t send = upper ? w[k] : w[k + bit];
+              const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, bit);
+              if (upper) w[k] = recv;
+              else w[k + bit] = recv;
+            }
+          }
+          const int cg = lane & (G - 1);
+          const bool gv = tl.m0 + 32 * q + (lane & ~(G - 1)) < o.M;  // the group's rows exist
+          constexpr int es = PREC == DMRG_TF32 ? 4 : 2, kce = 128 / es;
+          const int kfirst = i - cg;  // a multiple of G
+          const int kc = kfirst / kce;
+          const int chunk = ((kfirst - kc * kce) * es) >> 4;
+#pragma unroll
+          for (int blk = 0; blk < 16; blk += G) {
+            const int n = tl.n0 + c0 + blk + cg;
+            if (!gv || n >= nend) continue;
+            const int prow = b * o.Np + n;
+            const int r8 = prow & 7;
+            const int off = (kc * o.p_atoms + (prow >> 3)) * 1024 + r8 * 128 + ((chunk ^ r8) << 4);
+            if (PREC == DMRG_TF32) {
+              *reinterpret_cast<uint4*>(o.p + off) = make_uint4(w[blk], w[blk + 1], w[blk + 2], w[blk + 3]);
+            } else {
+              const uint4 hi4 = make_uint4(__byte_perm(w[blk], w[blk + 1], 0x5410), __byte_perm(w[blk + 2], w[blk + 3], 0x5410),
+                                           __byte_perm(w[blk + 4], w[blk + 5], 0x5410), __byte_perm(w[blk + 6], w[blk + 7], 0x5410));
+              const uint4 lo4 = make_uint4(__byte_perm(w[blk], w[blk + 1], 0x7632), __byte_perm(w[blk + 2], w[blk + 3], 0x7632),
+                                           __byte_perm(w[blk + 4], w[blk + 5], 0x7632), __byte_perm(w[blk + 6], w[blk + 7], 0x7632));
+              *reinterpret_cast<uint4*>(o.p + off) = hi4;
+              *reinterpret_cast<uint4*>(o.p + o.p_lo + off) = lo4;
+            }
+          }
+          continue;
+        }
+        if (!mv) continue;
+        {  // column-major float64 output: lanes write consecutive i
           double* yb = y + (int64_t)b * D + o.y_off + i;
           const int nn = min(16, nend - (tl.n0 + c0));
           if (add) {
@@ -550,13 +608,13 @@ float to_tf32(double x) {  // round to a 10-bit mantissa, nearest even
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t pad8(int64_t a) { return cdiv(a, 8) * 8; }  // member stride of stacked panels and accumulators
 
 struct Launch {  // one grouped GEMM launch
   TcTile* tiles = nullptr;
   TcTile* tiles_by_out = nullptr;   // the same tiles grouped by output block
   std::vector<int> out_begin;       // per output: first tile in tiles_by_out (+ end)
   TcSeg* segs = nullptr;
-  TcOut* outs = nullptr;
   int n_tiles = 0;
   int ntile_max = 16;
   int acc_cols = 16;         // TMEM columns per accumulator buffer (all slots)
@@ -601,7 +659,7 @@ struct State {
 };
 
 void free_launch(Launch& l) {
-  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs, (void*)l.outs})
+  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs})
     if (p) cudaFree(p);
   l = Launch{};
 }
@@ -700,16 +758,16 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     if (!(e.flags & DMRG_ID_B)) pB[i] = alloc(co, ci);
     if (e.flags & DMRG_ID_A) {                                  // c Psi       (group E, L)
       if (slot_of[i]) needP[e.s_in] = 1;
-      else pS[i] = alloc(nb * ri, ci);
+      else pS[i] = alloc(nb * pad8(ri), ci);
     } else if (e.flags & DMRG_ID_B) {                           // (c Psi)^T   (group S, L)
       if (slot_of[i]) needPT[e.s_in] = 1;
-      else pS[i] = alloc(nb * ci, ri);
-    } else if (e.order == 1) { pX[i] = alloc(nb * co, ri); needP[e.s_in] = 1; }   // X^T stacked
-    else { pX[i] = alloc(nb * ro, ci); needPT[e.s_in] = 1; }                   // Z stacked
+      else pS[i] = alloc(nb * pad8(ci), ri);
+    } else if (e.order == 1) { pX[i] = alloc(nb * pad8(co), ri); needP[e.s_in] = 1; }   // X^T stacked
+    else { pX[i] = alloc(nb * pad8(ro), ci); needPT[e.s_in] = 1; }                   // Z stacked
   }
   for (int s = 0; s < S; ++s) {
-    if (needP[s]) psiP[s] = alloc(nb * r[s], c[s]);
-    if (needPT[s]) psiPT[s] = alloc(nb * c[s], r[s]);
+    if (needP[s]) psiP[s] = alloc(nb * pad8(r[s]), c[s]);
+    if (needPT[s]) psiPT[s] = alloc(nb * pad8(c[s]), r[s]);
   }
   if (dry) return cur - base_off;
   hi.resize(cur, 0);
@@ -780,8 +838,10 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       check(g.l_atoms == cdiv(o.M, 8) && g.r_atoms == cdiv(o.N, 8), "operand rows differ from the output");
       check(g.kchunks >= 1, "empty K");
     }
-    if (o.kind == OUT_PANEL) check(o.p_atoms == cdiv((int64_t)o.N * (o.M / o.Rm), 8), "panel rows");
-    else check(o.y_off + (int64_t)(o.kind == OUT_Y_ROW ? o.Rm : o.N) * o.ldy <= sb->D, "output block");
+    check(o.Rm % 8 == 0 && o.Rv <= o.Rm && o.M % o.Rm == 0, "member stride");
+    if (o.kind == OUT_PANEL)
+      check(o.Np == pad8(o.N) && o.p_atoms == (int64_t)o.Np * (o.M / o.Rm) / 8, "panel rows");
+    else check(o.y_off + (int64_t)(o.kind == OUT_Y_ROW ? o.Rv : o.N) * o.ldy <= sb->D, "output block");
     const int oid = (int)B.outs.size();
     B.outs.push_back(o);
     const int s0 = (int)B.segs.size();
@@ -800,6 +860,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
         t.seg_begin = s0;
         t.seg_end = s1;
         t.out = oid;
+        t.o = o;
         for (const TcSeg& g : sg) t.slot_used |= 1 << g.slot;
         if (sg.empty()) t.slot_used = 1;
         for (size_t k = 0; k < slot_terms.size(); ++k) t.slot_term[k + 1] = slot_terms[k];
@@ -829,14 +890,18 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     o.p_lo = lo_delta;
     o.p_atoms = (int32_t)pX[i].atoms;
     if (e.order == 1) {  // X_b = Psi_b B^T : rows (b, a'), cols beta; stored as X^T rows (b, beta), k = a'
-      o.Rm = (int32_t)ri;
-      o.M = (int32_t)(nb * ri);
+      o.Rm = (int32_t)pad8(ri);
+      o.Rv = (int32_t)ri;
+      o.M = (int32_t)(nb * o.Rm);
       o.N = (int32_t)co;
+      o.Np = (int32_t)pad8(co);
       add_out(L1, o, {seg(psiP[e.s_in], pB[i])}, {});
     } else {  // Z_b^T = Psi_b^T A^T : rows (b, beta'), cols alpha; stored as Z rows (b, alpha), k = beta'
-      o.Rm = (int32_t)ci;
-      o.M = (int32_t)(nb * ci);
+      o.Rm = (int32_t)pad8(ci);
+      o.Rv = (int32_t)ci;
+      o.M = (int32_t)(nb * o.Rm);
       o.N = (int32_t)ro;
+      o.Np = (int32_t)pad8(ro);
       add_out(L1, o, {seg(psiPT[e.s_in], pA[i])}, {});
     }
   }
@@ -869,8 +934,9 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     if (hasE || !hasS) {
       TcOut o{};
       o.kind = OUT_Y_ROW;
-      o.Rm = r[s];
-      o.M = (int32_t)(nb * r[s]);
+      o.Rm = (int32_t)pad8(r[s]);
+      o.Rv = r[s];
+      o.M = (int32_t)(nb * o.Rm);
       o.N = c[s];
       o.ldy = c[s];
       o.add = 0;
@@ -881,8 +947,9 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     if (hasS) {
       TcOut o{};
       o.kind = OUT_Y_COL;
-      o.Rm = c[s];
-      o.M = (int32_t)(nb * c[s]);
+      o.Rm = (int32_t)pad8(c[s]);
+      o.Rv = c[s];
+      o.M = (int32_t)(nb * o.Rm);
       o.N = r[s];
       o.ldy = c[s];
       o.add = hasE ? 1 : 0;
@@ -907,7 +974,6 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       if (B.tiles[i].out != B.tiles[i - 1].out) L.out_begin.push_back((int)i);
     L.out_begin.push_back((int)B.tiles.size());
     L.segs = up(B.segs);
-    L.outs = up(B.outs);
     L.n_tiles = (int)t.size();
     L.ntile_max = B.ntile_max;
     L.acc_cols = B.acc_cols;
@@ -1048,14 +1114,15 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
     for (size_t o = 0; o + 1 < L.out_begin.size(); ++o) {
       const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
       tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
-          L.tiles_by_out + b0, n, L.segs, L.outs, y, sb->D, sb->d_coeffs, sb->n_terms, accumulate, skip,
+          L.tiles_by_out + b0, n, L.segs, y, sb->D, sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms, accumulate, skip,
           sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, sb->test_stall);
     }
     return;
   }
   const int grid = std::min(L.n_tiles, s->num_sms);
-  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.outs, y, sb->D,
-                                                       sb->d_coeffs, sb->n_terms, accumulate, skip,
+  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, y, sb->D,
+                                                       sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms,
+                                                       accumulate, skip,
                                                        sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
                                                        L.acc_cols, sb->test_stall);
 }
