@@ -168,14 +168,11 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
                                  __float_as_uint(tc::round_tf32(v[2])), __float_as_uint(tc::round_tf32(v[3])));
       *reinterpret_cast<uint4*>(j.p + o) = w;
     } else {
-      uint32_t wh[4], wl[4];
+      uint32_t wh[4], wl[4];  // hi = bf16(x), lo = bf16(x - hi), two K values per word
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
-        wh[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        wl[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        wh[i] = tc::bf16x2_rn(v[2 * i], v[2 * i + 1]);
+        wl[i] = tc::bf16x2_rn(v[2 * i] - __uint_as_float(wh[i] << 16), v[2 * i + 1] - __uint_as_float(wh[i] & 0xffff0000u));
       }
       *reinterpret_cast<uint4*>(j.p + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
       *reinterpret_cast<uint4*>(j.p + j.p_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
@@ -185,11 +182,17 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
 
 // ------------------------------------------------------ grouped tile GEMM
 constexpr int TC_EPI_WARPS = 12;                   // three per TMEM lane quadrant
-constexpr int TC_EPI_PARTS = TC_EPI_WARPS / 4;      // column interleave between warps of a quadrant
+constexpr int TC_EPI_PARTS = TC_EPI_WARPS / 4;      // warps per TMEM lane quadrant
+constexpr int TC_MAX_ACC = 4;                        // accumulator buffers in TMEM
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer, MMA, epilogue
 constexpr int L_TILE_BYTES = 128 * 128;             // 128 rows x 128 B
 constexpr int EPI_LD = 17;                          // staging row stride (doubles)
 constexpr int EPI_BYTES = TC_EPI_WARPS * 32 * EPI_LD * 8;
+// panel outputs: a warp's 16 x 32 block of packed words, column stride chosen
+// so that the transposed 16-byte reads hit distinct banks
+template <int PREC>
+constexpr int panel_ld() { return PREC == DMRG_TF32 ? 40 : 36; }
+constexpr int PANEL_EPI_BYTES = TC_EPI_WARPS * 16 * 40 * 4;
 constexpr int TC_COEF_MAX = 512;                    // coefficients cached in shared memory (float)
 constexpr int TC_CTRL_BYTES = 256 + 4 * TC_COEF_MAX;  // barriers etc., then the coefficient cache
 
@@ -199,15 +202,15 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
                double* __restrict__ y, int64_t D, const double* __restrict__ coef, int n_terms, int n_coef,
                int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
                int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride,
-               int stall) {
+               int n_acc, int tile_split, int stall) {
   if (skip && *skip) return;
   extern __shared__ __align__(1024) char smem_raw[];
   // control block, then 1024-aligned stage ring
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + 8;
   uint64_t* acc_full = empty + 8;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* drain = acc_empty + 2;
+  uint64_t* acc_empty = acc_full + TC_MAX_ACC;
+  uint64_t* drain = acc_empty + TC_MAX_ACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* coef_s = reinterpret_cast<float*>(smem_raw + 256);  // member coefficients as float
@@ -221,9 +224,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < n_acc; ++a) {
       tc::mbar_init(&acc_full[a], 1);
-      tc::mbar_init(&acc_empty[a], TC_EPI_WARPS);
+      tc::mbar_init(&acc_empty[a], tile_split ? 4 : TC_EPI_WARPS);  // the warps that drain one tile
     }
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -311,8 +314,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int acc = 0;
-      uint32_t acc_phase = 0;
+      int kk = 0;  // tiles with products so far: tile kk uses accumulator buffer kk % n_acc
       constexpr uint32_t fmt = PREC == DMRG_TF32 ? tc::FMT_TF32 : tc::FMT_BF16;
       TcTile tl_n{};
       if (blockIdx.x < n_tiles) tl_n = tiles[blockIdx.x];
@@ -321,6 +323,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
         if (tl.seg_begin == tl.seg_end) continue;
         int kch_n = segs[tl.seg_begin].kchunks, slot_n = segs[tl.seg_begin].slot;  // in flight during the wait
+        const int acc = kk % n_acc;
+        const uint32_t acc_phase = (uint32_t)(kk / n_acc) & 1u;
+        ++kk;
         if (!tc::mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag)) goto mma_done;
         tc::tc_fence_after();
         const uint32_t d_acc = tmem_base + (uint32_t)(acc * acc_stride);
@@ -367,10 +372,6 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           }
         }
         tc::mma_commit(&acc_full[acc]);
-        if (++acc == 2) {
-          acc = 0;
-          acc_phase ^= 1u;
-        }
       }
     mma_done:
       // every MMA this thread issued completes before the TMEM is released
@@ -386,13 +387,16 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
   } else {
     // ------------------------------------------------------------ epilogue
     // warp w reads TMEM lanes 32 (w % 4) .. +31 (the hardware's quadrant
-    // rule) and every TC_EPI_PARTS-th 16-column chunk, starting at part = (w - 2) / 4.
+    // rule); its part = (w - 2) / 4 in 0..TC_EPI_PARTS-1 takes either every
+    // TC_EPI_PARTS-th 16-column chunk of every tile (column split: many
+    // columns per tile), or every column of every TC_EPI_PARTS-th tile (tile
+    // split: many small tiles, whose epilogues then run concurrently from
+    // different accumulator buffers).
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const int row = 32 * q + lane;
-    double* stg = epi_stage + (warp - 2) * 32 * EPI_LD;
-    int acc = 0;
-    uint32_t acc_phase = 0;
+    double* stg = epi_stage + (warp - 2) * (epi_bytes / (8 * TC_EPI_WARPS));  // this warp's staging
+    int kk = 0;  // tiles with products so far (same count as the MMA warp's)
     TcTile tl_n{};
     if (blockIdx.x < n_tiles) tl_n = tiles[blockIdx.x];
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -413,6 +417,11 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         }
         continue;
       }
+      const int acc = kk % n_acc;
+      const uint32_t acc_phase = (uint32_t)(kk / n_acc) & 1u;
+      const bool mine = !tile_split || kk % TC_EPI_PARTS == half;
+      ++kk;
+      if (!mine) continue;
       int ok = 1;
       if (lane == 0) ok = tc::mbar_wait(&acc_full[acc], acc_phase, abort_flag) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -426,7 +435,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
 #pragma unroll
       for (int k = 1; k < TC_MAX_SLOTS; ++k)
         slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? coef_f(b * n_terms + tl.slot_term[k]) : 0.0f;
-      for (int c0 = 16 * half; c0 < tl.ntile; c0 += 16 * TC_EPI_PARTS) {
+      const int c_first = tile_split ? 0 : 16 * half, c_step = tile_split ? 16 : 16 * TC_EPI_PARTS;
+      for (int c0 = c_first; c0 < tl.ntile; c0 += c_step) {
         float v[16];
         if (tl.slot_used == 1) {
           tc::tmem_ld16(tb + (uint32_t)c0, v);
@@ -469,60 +479,55 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         if (o.kind == OUT_PANEL) {
           // Lanes G g .. G g + G-1 hold G consecutive accumulator rows, i.e. G
           // consecutive K values of one member (the member stride is a
-          // multiple of 8).  Transpose each G x G block of (row, column) across
-          // those lanes so that a lane holds G rows of one column, and write
-          // them as one 16-byte granule of the panel (per half for BF16).
+          // multiple of 8).  Transpose the warp's 32 x 16 block through shared
+          // memory so that a lane holds G rows of one column, and write them
+          // as one 16-byte granule of the panel (per half for BF16).
           constexpr int G = PREC == DMRG_TF32 ? 4 : 8;
-          uint32_t w[16];
+          constexpr int LD = panel_ld<PREC>();
+          uint32_t* pstg = reinterpret_cast<uint32_t*>(stg);
+          if (PREC == DMRG_TF32) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const float x = v[jj] * scf;
-            if (PREC == DMRG_TF32) {
-              w[jj] = __float_as_uint(tc::round_tf32(x));
-            } else {
-              const __nv_bfloat16 h = __float2bfloat16_rn(x);
-              const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-              w[jj] = (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+            for (int jj = 0; jj < 16; ++jj) pstg[jj * LD + lane] = __float_as_uint(tc::round_tf32(v[jj] * scf));
+          } else {
+            // two columns per conversion instruction: hi = bf16(x), lo = bf16(x - hi)
+#pragma unroll
+            for (int jj = 0; jj < 16; jj += 2) {
+              const float x0 = v[jj] * scf, x1 = v[jj + 1] * scf;
+              const uint32_t hp = tc::bf16x2_rn(x0, x1);
+              const uint32_t lp = tc::bf16x2_rn(x0 - __uint_as_float(hp << 16), x1 - __uint_as_float(hp & 0xffff0000u));
+              pstg[jj * LD + lane] = __byte_perm(hp, lp, 0x5410);        // hi | lo << 16 of column jj
+              pstg[(jj + 1) * LD + lane] = __byte_perm(hp, lp, 0x7632);  // of column jj + 1
             }
           }
-          // block transpose: swap the off-diagonal half blocks between lanes
-          // differing in `bit`, then recurse into the halves
-#pragma unroll
-          for (int bit = G / 2; bit >= 1; bit >>= 1) {
-            const bool upper = (lane & bit) != 0;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              if (k & bit) continue;
-              const uint32_t send = upper ? w[k] : w[k + bit];
-              const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, bit);
-              if (upper) w[k] = recv;
-              else w[k + bit] = recv;
-            }
-          }
-          const int cg = lane & (G - 1);
-          const bool gv = tl.m0 + 32 * q + (lane & ~(G - 1)) < o.M;  // the group's rows exist
+          __syncwarp();
+          const int cg = lane & (G - 1), g0 = lane & ~(G - 1);
+          const bool gv = tl.m0 + 32 * q + g0 < o.M;  // the group's rows exist
           constexpr int es = PREC == DMRG_TF32 ? 4 : 2, kce = 128 / es;
-          const int kfirst = i - cg;  // a multiple of G
+          const int kfirst = i - cg;  // K index of row g0: a multiple of G
           const int kc = kfirst / kce;
           const int chunk = ((kfirst - kc * kce) * es) >> 4;
 #pragma unroll
           for (int blk = 0; blk < 16; blk += G) {
             const int n = tl.n0 + c0 + blk + cg;
             if (!gv || n >= nend) continue;
+            const uint32_t* src = pstg + (blk + cg) * LD + g0;
             const int prow = b * o.Np + n;
             const int r8 = prow & 7;
             const int off = (kc * o.p_atoms + (prow >> 3)) * 1024 + r8 * 128 + ((chunk ^ r8) << 4);
             if (PREC == DMRG_TF32) {
-              *reinterpret_cast<uint4*>(o.p + off) = make_uint4(w[blk], w[blk + 1], w[blk + 2], w[blk + 3]);
+              *reinterpret_cast<uint4*>(o.p + off) = *reinterpret_cast<const uint4*>(src);
             } else {
-              const uint4 hi4 = make_uint4(__byte_perm(w[blk], w[blk + 1], 0x5410), __byte_perm(w[blk + 2], w[blk + 3], 0x5410),
-                                           __byte_perm(w[blk + 4], w[blk + 5], 0x5410), __byte_perm(w[blk + 6], w[blk + 7], 0x5410));
-              const uint4 lo4 = make_uint4(__byte_perm(w[blk], w[blk + 1], 0x7632), __byte_perm(w[blk + 2], w[blk + 3], 0x7632),
-                                           __byte_perm(w[blk + 4], w[blk + 5], 0x7632), __byte_perm(w[blk + 6], w[blk + 7], 0x7632));
-              *reinterpret_cast<uint4*>(o.p + off) = hi4;
-              *reinterpret_cast<uint4*>(o.p + o.p_lo + off) = lo4;
+              const uint4 a = *reinterpret_cast<const uint4*>(src);
+              const uint4 c4 = *reinterpret_cast<const uint4*>(src + 4);
+              *reinterpret_cast<uint4*>(o.p + off) =
+                  make_uint4(__byte_perm(a.x, a.y, 0x5410), __byte_perm(a.z, a.w, 0x5410),
+                             __byte_perm(c4.x, c4.y, 0x5410), __byte_perm(c4.z, c4.w, 0x5410));
+              *reinterpret_cast<uint4*>(o.p + o.p_lo + off) =
+                  make_uint4(__byte_perm(a.x, a.y, 0x7632), __byte_perm(a.z, a.w, 0x7632),
+                             __byte_perm(c4.x, c4.y, 0x7632), __byte_perm(c4.z, c4.w, 0x7632));
             }
           }
+          __syncwarp();
           continue;
         }
         if (!mv) continue;
@@ -547,10 +552,6 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
-      if (++acc == 2) {
-        acc = 0;
-        acc_phase ^= 1u;
-      }
     }
   }
 
@@ -619,6 +620,7 @@ struct Launch {  // one grouped GEMM launch
   int ntile_max = 16;
   int acc_cols = 16;         // TMEM columns per accumulator buffer (all slots)
   bool has_row_out = false;  // some output is row-major float64 (needs epilogue staging)
+  bool has_panel_out = false;  // some output is a panel (transposed through shared memory)
 };
 
 struct PairSet {  // the forward pairs or their transposes
@@ -978,7 +980,11 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     L.ntile_max = B.ntile_max;
     L.acc_cols = B.acc_cols;
     L.has_row_out = false;
-    for (const TcOut& o : B.outs) L.has_row_out = L.has_row_out || o.kind == OUT_Y_ROW;
+    L.has_panel_out = false;
+    for (const TcOut& o : B.outs) {
+      L.has_row_out = L.has_row_out || o.kind == OUT_Y_ROW;
+      L.has_panel_out = L.has_panel_out || o.kind == OUT_PANEL;
+    }
   };
   finish(L1, out.ph1);
   finish(LE, out.grpE);
@@ -1101,21 +1107,27 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
   if (L.n_tiles == 0) return;
   const int r_tile = L.ntile_max * 128;
   const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
-  const int epi = L.has_row_out ? EPI_BYTES : 0;       // row-major output staging
+  // epilogue staging: row-major float64 outputs, panel transposes
+  const int epi = L.has_row_out ? EPI_BYTES : L.has_panel_out ? PANEL_EPI_BYTES : 0;
   const int fixed = TC_CTRL_BYTES + epi + 1024;        // control, epilogue staging, ring alignment
   const int avail = 227 * 1024 - fixed;
   const int stages = std::max(1, std::min(8, avail / stage_bytes));
   const int smem = fixed + stages * stage_bytes;
   if (smem > 227 * 1024) throw CudaFail("tensor-core tile does not fit in shared memory");
-  int tmem_cols = 32;  // power of two holding both accumulator buffers
-  while (tmem_cols < 2 * L.acc_cols) tmem_cols *= 2;
+  // accumulator buffers: three where they fit in the 512 TMEM columns (so
+  // that three tiles' epilogues can run at once), else two; launches of many
+  // small tiles split the epilogue warps by tile, the others by column
+  const int n_acc = 3 * L.acc_cols <= 512 ? 3 : 2;
+  const int tile_split = (L.n_tiles >= 6 * s->num_sms && n_acc == 3) ? 1 : 0;
+  int tmem_cols = 32;  // power of two holding the accumulator buffers
+  while (tmem_cols < n_acc * L.acc_cols) tmem_cols *= 2;
   if (s->tune[PREC == DMRG_TF32 ? 0 : 1].per_block) {
     // baseline for the autotuner's report: one launch per output block
     for (size_t o = 0; o + 1 < L.out_begin.size(); ++o) {
       const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
       tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
           L.tiles_by_out + b0, n, L.segs, y, sb->D, sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms, accumulate, skip,
-          sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, sb->test_stall);
+          sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, n_acc, 0, sb->test_stall);
     }
     return;
   }
@@ -1124,7 +1136,7 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
                                                        sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms,
                                                        accumulate, skip,
                                                        sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
-                                                       L.acc_cols, sb->test_stall);
+                                                       L.acc_cols, n_acc, tile_split, sb->test_stall);
 }
 
 template <int PREC>

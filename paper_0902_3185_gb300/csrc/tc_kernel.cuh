@@ -215,6 +215,13 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)m << 29)));
 }
 
+// two floats -> packed bfloat16 pair (x0 in the low half), round to nearest even
+__device__ __forceinline__ uint32_t bf16x2_rn(float x0, float x1) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
