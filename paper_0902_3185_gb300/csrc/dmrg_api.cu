@@ -417,12 +417,13 @@ void lz_free(dmrg_sb* sb) {
       sb->lz_graph_key[i] = 0;
     }
   for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_npart, sb->lz_ab, sb->lz_s,
-                    sb->lz_out, sb->rf_res, sb->rf_p, sb->rf_q, sb->rf_t, sb->rf_sc})
+                    sb->lz_out, sb->rf_res, sb->rf_p, sb->rf_q, sb->rf_t, sb->rf_sc, sb->rf_diag, sb->rf_minv,
+                    sb->rf_part})
     if (p) cudaFree(p);
   if (sb->lz_ctl) cudaFree(sb->lz_ctl);
   if (sb->lz_gate) cudaFree(sb->lz_gate);
   if (sb->rf_ctl) cudaFree(sb->rf_ctl);
-  sb->rf_res = sb->rf_p = sb->rf_q = sb->rf_t = sb->rf_sc = nullptr;
+  sb->rf_res = sb->rf_p = sb->rf_q = sb->rf_t = sb->rf_sc = sb->rf_diag = sb->rf_minv = sb->rf_part = nullptr;
   sb->rf_ctl = nullptr;
   if (sb->h_ctl) cudaFreeHost(sb->h_ctl);
   sb->lz_V = sb->lz_w = sb->lz_vcur = sb->lz_partial = sb->lz_h = sb->lz_npart = sb->lz_ab = sb->lz_s =
@@ -458,6 +459,9 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   sb->rf_t = dalloc<double>((size_t)(B * D));
   sb->rf_sc = dalloc<double>((size_t)(RF_NSC * B + 2));
   sb->rf_ctl = dalloc<int32_t>((size_t)(2 * B + 2));
+  sb->rf_diag = dalloc<double>((size_t)(B * D));
+  sb->rf_minv = dalloc<double>((size_t)(B * D));
+  sb->rf_part = dalloc<double>((size_t)(5 * B * sb->lz_nchunk));
   sb->lz_cap = cap;
 }
 
@@ -605,10 +609,11 @@ void rf_enqueue_inner(dmrg_sb* sb, int prec, cudaStream_t st) {
   rf_launch_proj_dot(sb->rf_q, sb->rf_p, psi, sc, ctl, part, D, B, stop, st);
   rf_launch_sum(part, sc, RF_PQ, D, B, ctl, stop, st);
   rf_launch_alpha(sc, ctl, B, stop, st);
-  rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_q, sc, ctl, part, D, B, stop, st);
-  rf_launch_sum(part, sc, RF_RRNEW, D, B, ctl, stop, st);
+  rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_q, psi, sb->rf_minv, sc, ctl, sb->rf_part, D, B, stop,
+                   st);
+  rf_launch_sum4(sb->rf_part, sc, D, B, ctl, stop, st);
   rf_launch_beta(sc, ctl, sc + RF_NSC * B, B, stop, st);
-  rf_launch_dir(sb->rf_p, sb->rf_res, sc, ctl, D, B, stop, st);
+  rf_launch_dir(sb->rf_p, sb->rf_res, psi, sb->rf_minv, sc, ctl, D, B, 0, stop, st);
   CK(cudaGetLastError());
 }
 constexpr int RF_KERNELS_PER_ITER = 10;
@@ -673,18 +678,25 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
   std::vector<int32_t> hctl(2 * B + 2, 0), mask(B, 0);
   std::vector<uint8_t> conv(B, 0);
   const int Kg = std::max(1, K);
+  rf_launch_diag(sb->d_dg, sb->d_dg_terms, (int)sb->dg_terms.size(), sb->d_coeffs, sb->n_terms, sb->rf_diag, D, B,
+                 st);
+  ++r.launches;
   for (int o = 0; o < max_outer; ++o) {
     // float64 residual of the current iterate
     matvec(sb, DMRG_FP64, cur, sb->lz_w, 0, nullptr, st);
     lz_launch_dot(cur, sb->lz_w, part, D, B, nch, st);
     lz_launch_sum_chunks(part, tmp, nch, B, st);
     rf_launch_set(sb->rf_sc, tmp, RF_THETA, B, 0, st);
-    rf_launch_start(sb->lz_w, cur, sb->rf_res, sb->rf_p, sb->rf_t, sb->rf_sc, part, D, B, st);
-    lz_launch_sum_chunks(part, tmp, nch, B, st);
-    rf_launch_set(sb->rf_sc, tmp, RF_RR, B, 1, st);
+    // preconditioner, right-hand side -r, first direction p = K (-r)
+    rf_launch_minv(sb->rf_diag, sb->rf_sc, sb->rf_minv, D, B, st);
+    rf_launch_start(sb->lz_w, cur, sb->rf_minv, sb->rf_res, sb->rf_t, sb->rf_sc, sb->rf_part, D, B, st);
+    rf_launch_sum4(sb->rf_part, sb->rf_sc, D, B, nullptr, nullptr, st);
+    rf_launch_sum(sb->rf_part + (size_t)4 * B * nch, sb->rf_sc, RF_MU, D, B, nullptr, nullptr, st);
+    rf_launch_rho0(sb->rf_sc, B, st);
+    rf_launch_dir(sb->rf_p, sb->rf_res, cur, sb->rf_minv, sb->rf_sc, nullptr, D, B, 1, nullptr, st);
     CK(cudaMemcpyAsync(hsc.data(), sb->rf_sc, sizeof(double) * RF_NSC * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    r.launches += 7 + matvec_launches(sb, DMRG_FP64);
+    r.launches += 10 + matvec_launches(sb, DMRG_FP64);
     ++r.outer;
     bool all = true;
     for (int b = 0; b < B; ++b) {
@@ -851,6 +863,33 @@ void validate_and_copy(dmrg_sb* sb, const dmrg_sb_desc* d, int32_t batch) {
   }
   sb->d_ops = dalloc<double>((size_t)std::max<int64_t>(ops, 1));
   if (ops) CK(cudaMemcpy(sb->d_ops, host.data(), ops * sizeof(double), cudaMemcpyHostToDevice));
+  // diagonal of every term with diagonal blocks (s_out == s_in): the
+  // refinement's preconditioner sums them with the member's coefficients
+  {
+    std::vector<int32_t> slot(sb->n_terms, -1);
+    std::vector<double> dg;
+    for (const PairH& h : sb->pairs) {
+      if (h.s_out != h.s_in) continue;
+      if (slot[h.term] < 0) {
+        slot[h.term] = (int32_t)sb->dg_terms.size();
+        sb->dg_terms.push_back(h.term);
+        dg.resize(dg.size() + (size_t)sb->D, 0.0);
+      }
+      const int64_t r = sb->r[h.s_in], c = sb->c[h.s_in];
+      double* out = dg.data() + (size_t)slot[h.term] * sb->D + sb->off[h.s_in];
+      for (int64_t a = 0; a < r; ++a) {
+        const double aa = (h.flags & DMRG_ID_A) ? 1.0 : host[h.a_off + a * r + a];
+        for (int64_t bb = 0; bb < c; ++bb) {
+          const double bv = (h.flags & DMRG_ID_B) ? 1.0 : host[h.b_off + bb * c + bb];
+          out[a * c + bb] += aa * bv;
+        }
+      }
+    }
+    if (!sb->dg_terms.empty()) {
+      upload(sb->d_dg, dg);
+      upload(sb->d_dg_terms, sb->dg_terms);
+    }
+  }
   sb->h_ops = std::move(host);
   sb->d_tc_err = dalloc<int32_t>(1);
   CK(cudaMemset(sb->d_tc_err, 0, sizeof(int32_t)));
@@ -866,8 +905,9 @@ void destroy(dmrg_sb* sb) {
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
                           &sb->f64_bwd2, &sb->f64_bwd3})
     free_tl(*tl);
-  for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red})
+  for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red, sb->d_dg})
     if (p) cudaFree(p);
+  if (sb->d_dg_terms) cudaFree(sb->d_dg_terms);
   if (sb->d_tc_err) cudaFree(sb->d_tc_err);
   if (sb->d_dot_red_ptr) cudaFree(sb->d_dot_red_ptr);
   if (sb->d_dot_red_idx) cudaFree(sb->d_dot_red_idx);

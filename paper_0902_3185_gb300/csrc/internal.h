@@ -125,6 +125,13 @@ struct dmrg_sb {
   double* rf_t = nullptr;
   double* rf_sc = nullptr;       // [batch][8] scalars, then eps
   int32_t* rf_ctl = nullptr;     // [2 batch + 2]
+  double* rf_diag = nullptr;     // [batch][D] diag(H) per member (preconditioner)
+  double* rf_minv = nullptr;     // [batch][D] 1 / max(diag - theta, delta)
+  double* rf_part = nullptr;     // [5][batch][nchunk] reduction partials
+  // terms with diagonal blocks (s_out == s_in): their diagonals, [n][D]
+  std::vector<int32_t> dg_terms;
+  int32_t* d_dg_terms = nullptr;
+  double* d_dg = nullptr;
   void* lz_graphs[8] = {};       // cached cudaGraphExec_t per (prec, K) slot
   int32_t lz_graph_key[8] = {};
 

@@ -403,25 +403,26 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       const TcTile tl = tl_n;
       if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
       const TcOut& o = tl.o;
+      const bool empty_tile = tl.seg_begin == tl.seg_end;
+      const int acc = kk % n_acc;
+      const uint32_t acc_phase = (uint32_t)(kk / n_acc) & 1u;
+      const bool mine = empty_tile ? half == 0 : !tile_split || kk % TC_EPI_PARTS == half;
+      if (!empty_tile) ++kk;
+      if (!mine) continue;
       const int m = tl.m0 + row;
       const int b = m < o.M ? m / o.Rm : 0;
       const int i = m < o.M ? m - b * o.Rm : 0;
       const bool mv = m < o.M && i < o.Rv;  // this lane's row holds data (not stride padding)
       const int nend = min(tl.n0 + tl.ntile, o.N);
       const bool add = o.add || accumulate;
-      if (tl.seg_begin == tl.seg_end) {
-        if (half == 0 && mv && o.kind != OUT_PANEL && !add) {
+      if (empty_tile) {
+        if (mv && o.kind != OUT_PANEL && !add) {
           double* yb = y + (int64_t)b * D + o.y_off;
           for (int n = tl.n0; n < nend; ++n)
             yb[o.kind == OUT_Y_ROW ? (int64_t)i * o.ldy + n : (int64_t)n * o.ldy + i] = 0.0;
         }
         continue;
       }
-      const int acc = kk % n_acc;
-      const uint32_t acc_phase = (uint32_t)(kk / n_acc) & 1u;
-      const bool mine = !tile_split || kk % TC_EPI_PARTS == half;
-      ++kk;
-      if (!mine) continue;
       int ok = 1;
       if (lane == 0) ok = tc::mbar_wait(&acc_full[acc], acc_phase, abort_flag) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -436,7 +437,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       for (int k = 1; k < TC_MAX_SLOTS; ++k)
         slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? coef_f(b * n_terms + tl.slot_term[k]) : 0.0f;
       const int c_first = tile_split ? 0 : 16 * half, c_step = tile_split ? 16 : 16 * TC_EPI_PARTS;
-      for (int c0 = c_first; c0 < tl.ntile; c0 += c_step) {
+      const int c_end = tl.m0 + 32 * q < o.M ? tl.ntile : 0;  // no rows of this quadrant: nothing to drain
+      for (int c0 = c_first; c0 < c_end; c0 += c_step) {
         float v[16];
         if (tl.slot_used == 1) {
           tc::tmem_ld16(tb + (uint32_t)c0, v);
