@@ -5,11 +5,17 @@ N_up = N_dn = 28 (1/8 hole doping), 16 superblocks with U = 4 .. 12 that
 share every operator block (isometry-grown, seeded; see workloads/grown.py).
 
 One timed step = the whole hot path for the 16-member batch: a ground-state
-solve (dmrg_lanczos_ground: products, float64 Lanczos scalars, CGS2 full
+solve (dmrg_lanczos_ground: products, float64 Lanczos scalars, full
 reorthogonalisation, tridiagonal test, CUDA graphs; mixed precision followed
 by float64 refinement when a tensor-core precision is selected) plus the
 Hellmann-Feynman gradient (dmrg_energy_grad).  value = algorithmic H*psi
 flops executed in the step / step time.
+
+roofline: the product kernel with the larger share of the step (tensor-core
+or float64), its algorithmic flops per product / its event-timed duration,
+against its peak; roofline_kernels lists both.  traffic: DRAM bytes per
+product from the committed ncu record (profiles/traffic.json), reported only
+while the kernel sources still hash to the recorded value.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own batch (weak scaling, no collective on
@@ -134,6 +140,32 @@ def measured_peaks():
             d = json.load(f)
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# float64 FMA issue rate of the chip (ncu: 304 DFMA thread-instructions per cycle, 2 per SM x 152)
+FP64_FMA_PER_CLK = 304
+
+
+def source_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name):
+    """DRAM bytes per product from profiles/traffic.json, or None if the
+    kernel's sources changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f).get(name)
+    if not rec or source_sha(rec["sources"]) != rec["source_sha"]:
+        return None
+    return rec["dram_bytes_per_product"]
 
 
 def make_workload(batch, rank):
@@ -335,20 +367,48 @@ def main():
     e2e = {"value": world * mv_count / args.steps * flops_mv / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(X0.nbytes), "d2h_bytes_per_step": int(X0.nbytes + dh.numel() * 8)}
 
+    # Hellmann-Feynman gradient alone (float64 per-term dots)
+    t_grad, _ = timed(lambda: g.energy_grad(psi))
+    # Lanczos iteration rate at fixed Krylov length j (no early stop)
+    fixed_j = {}
+    for pj in ([prec, "fp64"] if prec != "fp64" else ["fp64"]):
+        for j in (20, 100):
+            t_j, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=j, prec=pj, refine="none",
+                                                    graph_iters=10))
+            fixed_j[f"{pj}_j{j}_steps_per_s"] = j / (t_j / 1e3)
+    # one full Gram-Schmidt pass reads the Krylov basis twice (dots, then update)
+    for j in (20, 100):
+        fixed_j[f"reorth_bytes_per_step_j{j}"] = 2 * (j + 1) * sb.batch * sb.dim * 8
+
     peaks, kind = measured_peaks()
-    if prec == "fp64":
-        peak = peaks["bf16_tflops"] * 1.25 / 2250.0
-        bound, pk_note = "alu", f"float64 = {kind} bf16 peak x nominal 1.25/2250"
-    elif prec == "tf32":
-        peak = peaks["bf16_tflops"] * 1100.0 / 2250.0
-        bound, pk_note = "tensor", f"tf32 = {kind} bf16 peak x nominal 1100/2250"
-    else:
-        peak = peaks["bf16_tflops"] / 3.0
-        bound, pk_note = "tensor", f"{kind} bf16 peak / 3 (three bf16 products per algorithmic product)"
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_mixed = mv_count / args.steps - max(i["fp64_matvecs"] for i in infos) if prec != "fp64" else 0
+    n_f64 = max(i["fp64_matvecs"] for i in infos) if prec != "fp64" else mv_count / args.steps
+    kernels = {}
+    if prec != "fp64":
+        pk = peaks["bf16_tflops"] / 3.0 if prec == "bf16x3" else peaks["bf16_tflops"] * 1100.0 / 2250.0
+        a_t = flops_mv / (mv_ms / 1e3) / 1e12
+        kernels["tensor_product"] = {
+            "bound": "tensor", "achieved": a_t, "peak": pk, "unit": "TFLOP/s", "frac": a_t / pk,
+            "traffic": recorded_traffic(f"tensor_product_{prec}"),
+            "kernel": f"tcgen05 product, {prec} (staging + 3 grouped launches per dmrg_apply_H)",
+            "peak_source": (f"{kind} bf16 peak / 3 (three bf16 MMAs per algorithmic product)" if prec == "bf16x3"
+                            else f"{kind} bf16 peak x nominal 1100/2250"),
+            "ms_per_step": n_mixed * mv_ms}
+    pk64 = FP64_FMA_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
+    a_64 = flops_mv / (mv64_ms / 1e3) / 1e12
+    kernels["fp64_product"] = {
+        "bound": "alu", "achieved": a_64, "peak": pk64, "unit": "TFLOP/s", "frac": a_64 / pk64,
+        "traffic": recorded_traffic("fp64_product"),
+        "kernel": "grouped float64 product (3 launches per dmrg_apply_H; the gradient's dot pass is the same kernel)",
+        "peak_source": f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz (median SM clock of the timed region)",
+        "ms_per_step": n_f64 * mv64_ms + t_grad}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    roof = dict(kernels[dom])
+    roof["share_of_step"] = roof["ms_per_step"] / ms_per_step
+    for k in kernels:
+        kernels[k]["share_of_step"] = kernels[k]["ms_per_step"] / ms_per_step
     achieved = flops_mv / (mv_ms / 1e3) / 1e12
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "superblock product (all launches of one dmrg_apply_H)",
-            "peak_source": pk_note}
 
     out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -363,8 +423,8 @@ def main():
            "matvec_fp64_tflops": flops_mv / (mv64_ms / 1e3) / 1e12,
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
-           "breakdown": breakdown,
-           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+           "breakdown": dict(breakdown, energy_grad_ms=t_grad), "lanczos_fixed_j": fixed_j,
+           "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline_sample(sb)
         print(json.dumps(out), flush=True)

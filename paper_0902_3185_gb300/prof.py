@@ -1,6 +1,11 @@
 """Profiling driver: build a superblock and run a few products (for ncu).
 
 python -m paper_0902_3185_gb300.prof --workload ladder_m1000 --prec bf16x3 --reps 3
+
+Recording the DRAM traffic of one product from an ncu capture of exactly its
+launches (``ncu -i <rep> --page raw --csv > raw.csv``) for bench.py:
+
+python -m paper_0902_3185_gb300.prof --record-traffic tensor_product_bf16x3 raw.csv
 """
 from __future__ import annotations
 
@@ -15,7 +20,43 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+# kernel sources whose hash keys each traffic record (a change voids the record)
+TRAFFIC_SOURCES = {
+    "tensor_product_bf16x3": ["paper_0902_3185_gb300/csrc/matvec_tc.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
+    "tensor_product_tf32": ["paper_0902_3185_gb300/csrc/matvec_tc.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
+    "fp64_product": ["paper_0902_3185_gb300/csrc/matvec_f64.cu"],
+}
+
+
+def record_traffic(name, csv_path, note=""):
+    import csv
+    import hashlib
+    import json
+    rows = list(csv.reader(open(csv_path)))
+    hdr, units = rows[0], rows[1]
+    total, launches = 0.0, 0
+    for r in rows[2:]:
+        d = dict(zip(hdr, r))
+        for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            u = units[hdr.index(k)].lower()
+            scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}[u]
+            total += float(d[k]) * scale
+        launches += 1
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[name]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    out_path = os.path.join(ROOT, "profiles", "traffic.json")
+    data = json.load(open(out_path)) if os.path.exists(out_path) else {}
+    data[name] = {"dram_bytes_per_product": total, "launches": launches, "sources": TRAFFIC_SOURCES[name],
+                  "source_sha": h.hexdigest()[:16], "capture": note}
+    with open(out_path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    print(name, total, "bytes over", launches, "launches")
+
+
 def main():
+    if len(sys.argv) >= 4 and sys.argv[1] == "--record-traffic":
+        return record_traffic(sys.argv[2], sys.argv[3], " ".join(sys.argv[4:]))
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder_m1000", choices=["ladder_m1000", "random64"])
     ap.add_argument("--batch", type=int, default=16)
