@@ -93,7 +93,8 @@ typedef struct {
   int32_t max_iter;    /* Krylov dimension cap (clamped to 768 and to D) */
   int32_t prec;        /* dmrg_prec of the products in the main solve */
   int32_t refine;      /* after a mixed-precision solve: 0 none; 1 restart FP64 Lanczos from its psi;
-                          2 Newton steps: FP64 residual, correction equation by mixed-precision CG */
+                          2 Newton steps: FP64 residual, correction equation by mixed-precision CG
+                          preconditioned with diag(H) */
   double refine_tol;   /* FP64 residual tolerance of the refinement, relative to max(1, |theta|) */
   int32_t check_every; /* run the tridiagonal test every this many iterations (>= 1) */
   int32_t graph_iters; /* iterations captured per CUDA graph launch (>= 1) */
@@ -153,8 +154,10 @@ dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* 
                                   double* dpsi, double* dc, int32_t prec, void* stream);
 
 /* Sec. 3.3 (diagonalize / Lanczos): lowest eigenpair of every batch member,
- * Lanczos with float64 scalars and full reorthogonalisation (CGS2), the
- * iteration captured in CUDA graphs.  psi0: device [batch][D] start vectors;
+ * Lanczos with float64 scalars and full reorthogonalisation (every step
+ * against every Krylov vector: the three-term step, one classical
+ * Gram-Schmidt pass, and a second pass where the norm fell below 1/sqrt(2)),
+ * the iteration captured in CUDA graphs.  psi0: device [batch][D] start vectors;
  * psi_out: device [batch][D], normalised; e0: host [batch]; info: host
  * [batch] or NULL.  Returns the worst member status (DMRG_OK if all met the
  * tolerance; DMRG_EBREAKDOWN is reported in info only). */
