@@ -206,30 +206,57 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "2 members x 1 product per step"},
             "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} blocked float64 products of single members (NumPy), D={sb.dim}"},
+                             "sample": f"{n} blocked float64 products of single members (NumPy, default BLAS "
+                                       f"threading; blocks this small mostly run on one thread), D={sb.dim}"},
             "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline_sample(sb):
+def _oracle_products(sb, seconds, max_n=200):
+    """Time the oracle's blocked float64 product (one member per call)."""
     from oracle import superblock as osb
     from workloads.superblock import seeded_normal
-    flops = osb.matvec_flops(sb)
     x = seeded_normal(1, sb.dim)
     osb.apply_H(sb, x, 0)
     n = 0
     t0 = time.perf_counter()
-    while n < 3 or time.perf_counter() - t0 < 10.0:
+    while n < 3 or time.perf_counter() - t0 < seconds:
         x = osb.apply_H(sb, x, n % sb.batch)
         x /= np.linalg.norm(x)
         n += 1
-        if n >= 200:
+        if n >= max_n:
             break
-    sec = time.perf_counter() - t0
-    return {"value": n * flops / sec / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle", "sample": f"{n} blocked float64 products (one member each, NumPy) of the same "
-                                        f"workload, {sec:.1f} s"}
+    return n, time.perf_counter() - t0
+
+
+_ONE_THREAD = r"""
+import sys, time
+sys.path.insert(0, sys.argv[1])
+import bench
+sb = bench.make_workload(int(sys.argv[2]), 0)
+n, sec = bench._oracle_products(sb, float(sys.argv[3]), int(sys.argv[4]))
+print(n, sec)
+"""
+
+
+def cpu_baseline_sample(sb):
+    """The oracle's blocked product on one host thread (BLAS threads pinned
+    to 1 before NumPy loads, in a child process), and in this process with
+    NumPy's default BLAS threading over the host cores for comparison."""
+    from oracle import superblock as osb
+    flops = osb.matvec_flops(sb)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", _ONE_THREAD, ROOT, str(sb.batch), "10.0", "200"],
+                       env=env, capture_output=True, text=True, timeout=600)
+    n1, s1 = r.stdout.split()[-2:]
+    n1, s1 = int(n1), float(s1)
+    n, sec = _oracle_products(sb, 5.0)
+    return {"value": n1 * flops / s1 / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n1} blocked float64 products (one member each, NumPy, one thread) of the same "
+                      f"workload, {s1:.1f} s",
+            "value_all_cores": n * flops / sec / 1e12, "host_cores": len(os.sched_getaffinity(0)),
+            "sample_all_cores": f"{n} products with NumPy's default BLAS threading, {sec:.1f} s"}
 
 
 # ------------------------------------------------------------------- ours
