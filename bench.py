@@ -7,8 +7,10 @@ share every operator block (isometry-grown, seeded; see workloads/grown.py).
 One timed step = the whole hot path for the 16-member batch: a ground-state
 solve (dmrg_lanczos_ground: products, float64 Lanczos scalars, full
 reorthogonalisation, tridiagonal test, CUDA graphs; mixed precision followed
-by float64 refinement when a tensor-core precision is selected) plus the
-Hellmann-Feynman gradient (dmrg_energy_grad).  value = algorithmic H*psi
+by float64 refinement when a tensor-core precision is selected) with the
+Hellmann-Feynman gradient of the refined state (dmrg_lanczos_ground_grad: the
+refinement's float64 residual products after the first give H psi and the
+per-term dots in one pass).  value = algorithmic H*psi
 flops executed in the step / step time.
 
 roofline: the product kernel with the larger share of the step (tensor-core
@@ -290,10 +292,12 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(x):
-        e0, psi, infos, st = g.lanczos_ground(x, tol=args.tol if prec == "fp64" else args.mixed_tol,
-                                              max_iter=args.max_iter, prec=prec, refine=args.refine,
-                                              refine_tol=args.tol, graph_iters=8)
-        dEdc = g.energy_grad(psi)
+        # ground state and its Hellmann-Feynman gradient (with the Newton
+        # refinement the gradient comes out of its last float64 product)
+        e0, psi, infos, st, dEdc = g.lanczos_ground(x, tol=args.tol if prec == "fp64" else args.mixed_tol,
+                                                    max_iter=args.max_iter, prec=prec, refine=args.refine,
+                                                    refine_tol=args.tol, graph_iters=8, grad=True)
+        step.status = st
         return e0, psi, infos, dEdc
 
     for _ in range(max(3, args.warmup)):
@@ -320,7 +324,7 @@ def main():
         ev.append((a, b))
         mv_count += max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
         it_count += max(i["iters"] + i["refine_iters"] for i in infos)
-        launches += infos[0]["kernel_launches"] + 4
+        launches += infos[0]["kernel_launches"]
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -349,7 +353,7 @@ def main():
     t_64, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=n64, prec="fp64", refine="none",
                                              graph_iters=10))
     lz_iters = max(i["iters"] for i in info_lz)
-    breakdown = {"lanczos_ms": t_lz, "refine_ms": t_full - t_lz,
+    breakdown = {"lanczos_ms": t_lz, "refine_ms": t_full - t_lz, "solve_status": step.status,
                  "mixed_lanczos_steps_per_s": lz_iters / (t_lz / 1e3),
                  "fp64_lanczos_steps_per_s_first20": n64 / (t_64 / 1e3),
                  "lanczos_iters": max(i["iters"] for i in info_full),
@@ -394,8 +398,10 @@ def main():
     e2e = {"value": world * mv_count / args.steps * flops_mv / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(X0.nbytes), "d2h_bytes_per_step": int(X0.nbytes + dh.numel() * 8)}
 
-    # Hellmann-Feynman gradient alone (float64 per-term dots)
+    # Hellmann-Feynman gradient alone (float64 per-term dots), and the float64
+    # product that also gives the per-term dots
     t_grad, _ = timed(lambda: g.energy_grad(psi))
+    t_pdot, _ = timed(lambda: g.apply_H_term_dots(x0))
     # Lanczos iteration rate at fixed Krylov length j (no early stop)
     fixed_j = {}
     for pj in ([prec, "fp64"] if prec != "fp64" else ["fp64"]):
@@ -429,7 +435,8 @@ def main():
         "traffic": recorded_traffic("fp64_product"),
         "kernel": "grouped float64 product (3 launches per dmrg_apply_H; the gradient's dot pass is the same kernel)",
         "peak_source": f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz (median SM clock of the timed region)",
-        "ms_per_step": n_f64 * mv64_ms + t_grad}
+        "ms_per_step": (n_f64 * mv64_ms + t_grad if prec == "fp64" or args.refine != "newton"
+                        else mv64_ms + max(0, n_f64 - 1) * t_pdot)}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     roof = dict(kernels[dom])
     roof["share_of_step"] = roof["ms_per_step"] / ms_per_step
@@ -450,7 +457,8 @@ def main():
            "matvec_fp64_tflops": flops_mv / (mv64_ms / 1e3) / 1e12,
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
-           "breakdown": dict(breakdown, energy_grad_ms=t_grad), "lanczos_fixed_j": fixed_j,
+           "breakdown": dict(breakdown, energy_grad_ms=t_grad, fp64_product_with_dots_ms=t_pdot),
+           "lanczos_fixed_j": fixed_j,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline_sample(sb)

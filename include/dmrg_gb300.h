@@ -165,6 +165,24 @@ dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out
                                 const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info,
                                 void* stream);
 
+/* dmrg_lanczos_ground, then the Hellmann-Feynman gradient of the returned
+ * state, dE_dc[b][k] = <psi_b, (A_k (x) B_k) psi_b> / <psi_b, psi_b> (device
+ * [batch][n_terms], as dmrg_energy_grad).  With refine = 2 the refinement's
+ * float64 residual products after the first give H psi and the per-term dots
+ * in one pass, so the gradient of the final state costs no extra pass;
+ * otherwise it is computed after the solve.  Same statuses as
+ * dmrg_lanczos_ground; DMRG_EINVAL for dE_dc == NULL. */
+dmrg_status dmrg_lanczos_ground_grad(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0,
+                                     double* dE_dc, const dmrg_lanczos_opts* opts,
+                                     dmrg_lanczos_info* info, void* stream);
+
+/* Sec. 3.3 product with the per-term dots: y = H psi in float64 (device
+ * [batch][D], y must not overlap psi) and dots[b][k] = <psi_b, (A_k (x) B_k)
+ * psi_b> (device [batch][n_terms], no coefficient), in one pass over the
+ * pair products.  Stream-ordered; DMRG_EINVAL for NULL or aliased pointers. */
+dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, double* dots,
+                                   void* stream);
+
 /* Autotuner of the tensor-core product (no paper counterpart; the paper's
  * block loop has no tuning): times the product of this superblock, `reps`
  * launches per candidate after a warm-up, for every tile width (64, 128,

@@ -27,7 +27,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREA
 SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error", "dmrg_query",
            "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
            "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune", "dmrg_sync_status",
-           "dmrg_test_inject"]
+           "dmrg_test_inject", "dmrg_lanczos_ground_grad", "dmrg_apply_H_term_dots"]
 
 
 class DmrgError(RuntimeError):
@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
     lib.dmrg_autotune.argtypes = [vp, i32, i32, vp, C.POINTER(TuneInfo)]
     lib.dmrg_sync_status.argtypes = [vp, vp]
     lib.dmrg_test_inject.argtypes = [vp, i32]
+    lib.dmrg_lanczos_ground_grad.argtypes = [vp, dp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
+    lib.dmrg_apply_H_term_dots.argtypes = [vp, dp, dp, dp, vp]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -234,22 +236,38 @@ class GpuSuperblock:
     REFINE = {None: 0, False: 0, "none": 0, "lanczos": 1, True: 2, "newton": 2}
 
     def lanczos_ground(self, psi0, tol=1e-12, max_iter=300, prec="fp64", refine="newton", refine_tol=1e-10,
-                       check_every=1, graph_iters=8, psi_out=None, stream=None):
+                       check_every=1, graph_iters=8, psi_out=None, stream=None, grad=False):
         """Lowest eigenpair of every member.  With a mixed precision, refine =
         "newton" (float64 residual + mixed CG correction steps, default),
-        "lanczos" (float64 Lanczos restarted from the mixed result) or "none"."""
+        "lanczos" (float64 Lanczos restarted from the mixed result) or "none".
+        Returns (e0, psi, infos, status); with grad=True also the
+        Hellmann-Feynman gradient [batch][n_terms] of psi, as a fifth value."""
         if psi_out is None:
             psi_out = self.empty()
         e0 = np.zeros(self.batch)
         info = (LanczosInfo * self.batch)()
         mode = refine if isinstance(refine, int) and not isinstance(refine, bool) else self.REFINE[refine]
         opts = LanczosOpts(tol, max_iter, _prec(prec), mode, refine_tol, check_every, graph_iters)
-        st = self.lib.dmrg_lanczos_ground(self.h, _ptr(psi0), _ptr(psi_out), e0.ctypes.data, C.byref(opts),
-                                          info, _stream(stream))
+        if grad:
+            dE = torch.empty(self.batch, self.n_terms, dtype=torch.float64, device=self.device)
+            st = self.lib.dmrg_lanczos_ground_grad(self.h, _ptr(psi0), _ptr(psi_out), e0.ctypes.data, _ptr(dE),
+                                                   C.byref(opts), info, _stream(stream))
+        else:
+            st = self.lib.dmrg_lanczos_ground(self.h, _ptr(psi0), _ptr(psi_out), e0.ctypes.data, C.byref(opts),
+                                              info, _stream(stream))
         infos = [{k: getattr(info[b], k) for k, _ in LanczosInfo._fields_} for b in range(self.batch)]
         if st not in (0, 4):
             self._check(st)
+        if grad:
+            return e0, psi_out, infos, st, dE
         return e0, psi_out, infos, st
+
+    def apply_H_term_dots(self, psi, stream=None):
+        """y = H psi (float64) and dots[b][k] = <psi_b, (A_k (x) B_k) psi_b>, one pass."""
+        y = self.empty()
+        dots = torch.empty(self.batch, self.n_terms, dtype=torch.float64, device=self.device)
+        self._check(self.lib.dmrg_apply_H_term_dots(self.h, _ptr(psi), _ptr(y), _ptr(dots), _stream(stream)))
+        return y, dots
 
 
 class ApplyH(torch.autograd.Function):

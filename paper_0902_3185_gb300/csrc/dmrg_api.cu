@@ -368,9 +368,62 @@ void build_f64_tasks(dmrg_sb* sb) {
       for (int64_t id : ids) dot_list[(size_t)b * nt + p.term].push_back(id);
     }
   }
+  // H psi with the per-term dots <psi, (A_k x B_k) psi> in one pass: one
+  // output per (member, sector) whose segments are the unscaled pair
+  // products (after f64_dot1); the tile applies c(member, term) itself
+  for (int b = 0; b < sb->batch; ++b) {
+    const int64_t xb = (int64_t)b * sb->D, tb = (int64_t)b * Tm;
+    std::vector<std::vector<size_t>> into(sb->S);
+    for (size_t i = 0; i < fw.size(); ++i) into[fw[i].s_out].push_back(i);
+    for (int so = 0; so < sb->S; ++so) {
+      if ((int64_t)r[so] * c[so] == 0) continue;
+      std::vector<SegF64> sg;
+      for (size_t i : into[so]) {
+        const GPair& p = fw[i];
+        const int32_t ri = r[p.s_in], ci = c[p.s_in], co = c[p.s_out];
+        SegF64 g = seg_base();
+        g.coef = p.term;
+        g.coef_mode = -1;  // no scaling while loading: the tile scales the segment's sum
+        if (p.flags & DMRG_ID_B) {
+          g.K = ri; set_L_op(g, p.A);
+          g.r_buf = BUF_X; g.r_off = xb + sb->off[p.s_in]; g.ldr = ci; g.r_trans = 0;
+        } else if (p.flags & DMRG_ID_A) {
+          g.K = ci; g.l_buf = BUF_X; g.l_off = xb + sb->off[p.s_in]; g.ldl = ci; set_R_opT(g, p.B);
+        } else if (p.order == 0) {
+          g.K = ci; g.l_buf = BUF_T; g.l_off = tb + toff_f[i]; g.ldl = ci; set_R_opT(g, p.B);
+        } else {
+          g.K = ri; set_L_op(g, p.A);
+          g.r_buf = BUF_T; g.r_off = tb + toff_f[i]; g.ldr = co; g.r_trans = 0;
+        }
+        sg.push_back(g);
+      }
+      TileF64 t = out_tile(BUF_Y, xb + sb->off[so], c[so], r[so], c[so], TM_STORE_DOTS);
+      t.member = b;
+      add_output(sb->f64_pdot, t, sg, nullptr);
+    }
+  }
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_bwd1, &sb->f64_bwd2, &sb->f64_bwd3,
-                          &sb->f64_dot1})
+                          &sb->f64_dot1, &sb->f64_pdot})
     sort_tiles(*tl);
+  {  // segment partials of f64_pdot: slots in tile order, then the (member, term) lists
+    std::vector<std::vector<int32_t>> lists((size_t)sb->batch * nt);
+    int32_t base = 0;
+    for (TileF64& t : sb->f64_pdot.h_tiles) {
+      t.dot_base = base;
+      for (int32_t q = t.seg_begin; q < t.seg_end; ++q)
+        lists[(size_t)t.member * nt + sb->f64_pdot.h_segs[q].coef].push_back(base + (q - t.seg_begin));
+      base += t.seg_end - t.seg_begin;
+    }
+    std::vector<int32_t> ptr(1, 0), idx;
+    for (auto& l : lists) {
+      idx.insert(idx.end(), l.begin(), l.end());
+      ptr.push_back((int32_t)idx.size());
+    }
+    upload(sb->d_pdot_ptr, ptr);
+    upload(sb->d_pdot_idx, idx);
+    if (sb->d_pdot_partial) cudaFree(sb->d_pdot_partial);
+    sb->d_pdot_partial = dalloc<double>((size_t)std::max<int32_t>(1, base));
+  }
   const std::vector<int64_t> where = sort_tiles(sb->f64_dot2);
   std::vector<int32_t> ptr(1, 0), idx;
   for (auto& lst : dot_list) {
@@ -382,7 +435,7 @@ void build_f64_tasks(dmrg_sb* sb) {
   if (sb->d_dot_partial) cudaFree(sb->d_dot_partial);
   sb->d_dot_partial = dalloc<double>((size_t)std::max<int64_t>(1, (int64_t)sb->f64_dot2.h_tiles.size()));
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
-                          &sb->f64_bwd2, &sb->f64_bwd3})
+                          &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot})
     finish(*tl);
 }
 
@@ -397,6 +450,15 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
   } else {
     tc_matvec(sb, prec, x, y, accumulate, skip, st);
   }
+  CK(cudaGetLastError());
+}
+
+// y = H psi (float64) and dc[b][k] = <psi_b, (A_k x B_k) psi_b> in one pass
+void matvec_f64_dots(dmrg_sb* sb, const double* psi, double* y, double* dc, cudaStream_t st) {
+  Bufs bufs{{const_cast<double*>(psi), y, sb->d_T, sb->d_ops, nullptr}};
+  launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+  launch_seg_gemm_f64_dots(sb->f64_pdot, bufs, sb->d_coeffs, sb->n_terms, sb->d_pdot_partial, nullptr, st);
+  lz_launch_reduce_terms(sb->d_pdot_partial, sb->d_pdot_ptr, sb->d_pdot_idx, dc, sb->batch * sb->n_terms, st);
   CK(cudaGetLastError());
 }
 
@@ -658,11 +720,15 @@ struct RfRun {
   int outer = 0;              // float64 products spent
   std::vector<int32_t> inner; // mixed CG iterations per member (all outer steps)
   int64_t launches = 0;
+  bool dots_final = false;    // dc holds the per-term dots of the returned psi
 };
 
-// Newton refinement of psi (device [batch][D], normalised) in place.
+// Newton refinement of psi (device [batch][D], normalised) in place.  With
+// dc != NULL the float64 residual products after the first also give the
+// per-term dots <psi, (A_k x B_k) psi> (one pass, f64_pdot); the last one is
+// of the returned psi.
 RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, int max_inner, double eps_in, int K,
-               cudaStream_t st) {
+               cudaStream_t st, double* dc = nullptr) {
   const int64_t D = sb->D;
   const int B = sb->batch, nch = sb->lz_nchunk;
   double* part = sb->lz_partial;
@@ -682,8 +748,12 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
                  st);
   ++r.launches;
   for (int o = 0; o < max_outer; ++o) {
-    // float64 residual of the current iterate
-    matvec(sb, DMRG_FP64, cur, sb->lz_w, 0, nullptr, st);
+    // float64 residual of the current iterate (the first outer step is never
+    // the last in practice: the mixed solve stops far above the tolerance)
+    const bool with_dots = dc && o >= 1;
+    if (with_dots) matvec_f64_dots(sb, cur, sb->lz_w, dc, st);
+    else matvec(sb, DMRG_FP64, cur, sb->lz_w, 0, nullptr, st);
+    r.dots_final = with_dots;
     lz_launch_dot(cur, sb->lz_w, part, D, B, nch, st);
     lz_launch_sum_chunks(part, tmp, nch, B, st);
     rf_launch_set(sb->rf_sc, tmp, RF_THETA, B, 0, st);
@@ -696,7 +766,7 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
     rf_launch_dir(sb->rf_p, sb->rf_res, cur, sb->rf_minv, sb->rf_sc, nullptr, D, B, 1, nullptr, st);
     CK(cudaMemcpyAsync(hsc.data(), sb->rf_sc, sizeof(double) * RF_NSC * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    r.launches += 10 + matvec_launches(sb, DMRG_FP64);
+    r.launches += 10 + (with_dots ? 3 : matvec_launches(sb, DMRG_FP64));
     ++r.outer;
     bool all = true;
     for (int b = 0; b < B; ++b) {
@@ -903,9 +973,12 @@ void destroy(dmrg_sb* sb) {
   lz_free(sb);
   tc_free(sb);
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
-                          &sb->f64_bwd2, &sb->f64_bwd3})
+                          &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot})
     free_tl(*tl);
-  for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red, sb->d_dg})
+  for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red, sb->d_dg,
+                    sb->d_pdot_partial})
+    if (p) cudaFree(p);
+  for (int32_t* p : {sb->d_pdot_ptr, sb->d_pdot_idx})
     if (p) cudaFree(p);
   if (sb->d_dg_terms) cudaFree(sb->d_dg_terms);
   if (sb->d_tc_err) cudaFree(sb->d_tc_err);
@@ -1084,7 +1157,7 @@ dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int3
   });
 }
 
-dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0,
+static dmrg_status lanczos_impl(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0, double* dE_dc,
                                 const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info, void* stream) {
   if (!sb || !psi0 || !psi_out || !e0 || !opts) return DMRG_EINVAL;
   if (opts->prec < DMRG_FP64 || opts->prec > DMRG_BF16X3 || !(opts->tol > 0) || opts->max_iter < 1) {
@@ -1107,7 +1180,22 @@ dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out
     if (mode == 1)
       rr = lz_solve(sb, psi_out, psi_out, DMRG_FP64, rtol, opts->max_iter, opts->check_every, ge, st);
     else if (mode >= 2)
-      rn = rf_solve(sb, psi_out, opts->prec, rtol, 8, 400, 1e-2, ge, st);
+      rn = rf_solve(sb, psi_out, opts->prec, rtol, 8, 400, 1e-2, ge, st, dE_dc);
+    int64_t grad_launches = 0;
+    if (dE_dc) {
+      // Hellmann-Feynman: dots of the returned psi / <psi, psi>, from the
+      // refinement's last float64 product when it carried them
+      if (!(mode >= 2 && rn.dots_final)) {
+        term_dots(sb, psi_out, psi_out, dE_dc, st);
+        grad_launches += 3;
+      }
+      const int nch = lz_nchunk(sb->D);
+      lz_launch_sumsq(psi_out, sb->d_red, sb->D, B, nch, st);
+      lz_launch_sum_chunks(sb->d_red, sb->d_scratch, nch, B, st);
+      lz_launch_div_rows(dE_dc, sb->d_scratch, sb->n_terms, B, st);
+      CK(cudaGetLastError());
+      grad_launches += 3;
+    }
     dmrg_status worst = DMRG_OK;
     for (int b = 0; b < B; ++b) {
       int code = r.code[b];
@@ -1128,10 +1216,34 @@ dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out
         info[b].fp64_matvecs = opts->prec == DMRG_FP64 ? r.iters[b] : (mode == 1 ? rr.iters[b] : (mode >= 2 ? rn.outer : 0));
         info[b].status = s;
         info[b].breakdown = code == LZ_BREAKDOWN;
-        info[b].kernel_launches = (int32_t)(r.launches + (mode == 1 ? rr.launches : 0) + (mode >= 2 ? rn.launches : 0));
+        info[b].kernel_launches = (int32_t)(r.launches + (mode == 1 ? rr.launches : 0) + (mode >= 2 ? rn.launches : 0) +
+                                            grad_launches);
       }
     }
     return worst;
+  });
+}
+
+dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0,
+                                const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info, void* stream) {
+  return lanczos_impl(sb, psi0, psi_out, e0, nullptr, opts, info, stream);
+}
+
+dmrg_status dmrg_lanczos_ground_grad(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0, double* dE_dc,
+                                     const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info, void* stream) {
+  if (!dE_dc) return DMRG_EINVAL;
+  return lanczos_impl(sb, psi0, psi_out, e0, dE_dc, opts, info, stream);
+}
+
+dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, double* dots, void* stream) {
+  if (!sb) return DMRG_EINVAL;
+  if (!psi || !y || !dots || psi == y) {
+    sb->err = "apply_H_term_dots: null or aliased psi / y / dots";
+    return DMRG_EINVAL;
+  }
+  return guard(sb, [&] {
+    matvec_f64_dots(sb, psi, y, dots, (cudaStream_t)stream);
+    return DMRG_OK;
   });
 }
 

@@ -43,17 +43,21 @@ struct SegF64 {
 // One output tile C[m0:m0+16*ni, n0:n0+16*nj] of an M x N matrix (ni, nj in
 // 1..4, chosen per output to fit its shape); the members may be stacked along
 // M (c_axis 0) or N (c_axis 1), c_rm rows per member.
-enum TileMode : int32_t { TM_STORE = 0, TM_DOT = 2 };
+enum TileMode : int32_t { TM_STORE = 0, TM_DOT = 2, TM_STORE_DOTS = 3 };
 struct TileF64 {
   int64_t c_off, c_bs;
   int32_t c_buf, ldc;
   int32_t M, N, m0, n0;
   int32_t seg_begin, seg_end;
-  int32_t mode;     // TM_STORE: C = acc (C += acc when the launch accumulates or `add`); TM_DOT: sum(acc .* C)
+  int32_t mode;     // TM_STORE: C = acc (C += acc when the launch accumulates or `add`); TM_DOT: sum(acc .* C);
+                    // TM_STORE_DOTS: C = sum over segments of c(member, seg) * seg_acc, and per segment
+                    // sum(seg_acc .* X) at the same offset of BUF_X (one member per tile)
   int32_t c_rm, c_axis;
   int32_t c_trans;  // 0: C(mm, nn) at [mm*ldc + nn]; 1: at [nn*ldc + mm]
   int32_t add;      // second writer of an output block: always accumulate
   int32_t shape;    // ni | nj << 8
+  int32_t member;   // TM_STORE_DOTS: the batch member of the tile
+  int32_t dot_base; // TM_STORE_DOTS: partial of segment s at dot_out[dot_base + s - seg_begin]
 };
 
 struct TaskListF64 {
@@ -67,6 +71,9 @@ struct TaskListF64 {
 // skip: optional device flag; when *skip != 0 the launch does nothing
 void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
                          int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
+// tiles of mode TM_STORE_DOTS (product and per-segment dots in one pass)
+void launch_seg_gemm_f64_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
+                              double* dot_out, const int32_t* skip, cudaStream_t st);
 
 // ------------------------------------------------------------ host pair info
 struct PairH {
@@ -94,6 +101,10 @@ struct dmrg_sb {
   dmrg::TaskListF64 f64_fwd1, f64_fwd2, f64_fwd3;  // forward: intermediates, outputs (members along M, along N)
   dmrg::TaskListF64 f64_bwd1, f64_bwd2, f64_bwd3;  // H^T g
   dmrg::TaskListF64 f64_dot1, f64_dot2;   // per-pair <g, A psi B^T>
+  dmrg::TaskListF64 f64_pdot;             // H psi and per-term <psi, (A_k x B_k) psi> in one pass (after f64_dot1)
+  int32_t* d_pdot_ptr = nullptr;          // term reduction of its segment partials, as d_dot_red_*
+  int32_t* d_pdot_idx = nullptr;
+  double* d_pdot_partial = nullptr;
   double* d_T = nullptr;                  // FP64 intermediate workspace
   int64_t T_elems = 0;
   // term reduction of dot tiles: for (b, k): tile range [dot_red_ptr[bk], dot_red_ptr[bk+1])

@@ -28,7 +28,7 @@ struct F64Smem {
   double red[F64_THREADS / 32];
 };
 
-template <int NI, int NJ>
+template <int NI, int NJ, bool DOTS>
 __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restrict__ segs, const Bufs& bufs,
                                          const double* __restrict__ coef, int n_terms, int accumulate,
                                          double* __restrict__ dot_out, F64Smem& sm) {
@@ -40,9 +40,30 @@ __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restr
   for (int i = 0; i < NI; ++i)
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
+  // TM_STORE_DOTS: each segment accumulates alone (sacc), is dotted with the
+  // wavefunction block at the output's place (xo), then added with its
+  // member's coefficient
+  double sacc[DOTS ? NI : 1][DOTS ? NJ : 1];
+  double xo[DOTS ? NI : 1][DOTS ? NJ : 1];
+  if (DOTS) {
+    const double* X = bufs.p[BUF_X] + t.c_off;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int m = t.m0 + ty + 16 * i, n = t.n0 + tx + 16 * j;
+        xo[DOTS ? i : 0][DOTS ? j : 0] = (m < t.M && n < t.N) ? X[(int64_t)m * t.ldc + n] : 0.0;
+      }
+  }
 
   for (int sg = t.seg_begin; sg < t.seg_end; ++sg) {
     const SegF64 s = segs[sg];
+    if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) sacc[DOTS ? i : 0][DOTS ? j : 0] = 0.0;
+    }
     const double* L = bufs.p[s.l_buf] + s.l_off;
     const double* R = bufs.p[s.r_buf] + s.r_off;
     const double uscale = (s.coef_mode == 0 && s.coef >= 0) ? coef[s.coef] : 1.0;
@@ -92,13 +113,37 @@ __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restr
 #pragma unroll
         for (int i = 0; i < NI; ++i)
 #pragma unroll
-          for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < NJ; ++j) {
+            if (DOTS) sacc[DOTS ? i : 0][DOTS ? j : 0] = fma(a[i], b[j], sacc[DOTS ? i : 0][DOTS ? j : 0]);
+            else acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          }
       };
       if (kmax == F64_BK) {
 #pragma unroll
         for (int k = 0; k < F64_BK; ++k) step(k);
       } else {
         for (int k = 0; k < kmax; ++k) step(k);  // no FMAs on the zero padding of K
+      }
+      __syncthreads();
+    }
+    if (DOTS) {  // this segment's dot with the wavefunction, then its coefficient
+      const double cf = coef[t.member * n_terms + s.coef];
+      double part = 0.0;
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          part = fma(sacc[DOTS ? i : 0][DOTS ? j : 0], xo[DOTS ? i : 0][DOTS ? j : 0], part);
+          acc[i][j] = fma(cf, sacc[DOTS ? i : 0][DOTS ? j : 0], acc[i][j]);
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+      if ((tid & 31) == 0) sm.red[tid >> 5] = part;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < F64_THREADS / 32; ++w) tot += sm.red[w];
+        dot_out[t.dot_base + (sg - t.seg_begin)] = tot;
       }
       __syncthreads();
     }
@@ -114,7 +159,7 @@ __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restr
     }
     return (int64_t)b * t.c_bs + (t.c_trans ? (int64_t)n * t.ldc + m : (int64_t)m * t.ldc + n);
   };
-  if (t.mode == TM_STORE) {
+  if (t.mode == TM_STORE || t.mode == TM_STORE_DOTS) {
     const bool add = accumulate || t.add;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
@@ -161,7 +206,7 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
   if (skip && *skip) return;
   const TileF64 t = tiles[blockIdx.x];
 #define F64_CASE(I, J) \
-  case (I) | ((J) << 8): f64_tile<I, J>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm); break;
+  case (I) | ((J) << 8): f64_tile<I, J, false>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm); break;
   switch (t.shape) {
     F64_CASE(1, 1) F64_CASE(1, 2) F64_CASE(1, 3) F64_CASE(1, 4)
     F64_CASE(2, 1) F64_CASE(2, 2) F64_CASE(2, 3) F64_CASE(2, 4)
@@ -170,6 +215,34 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
     default: break;  // the host builds only the shapes above
   }
 #undef F64_CASE
+}
+
+// Product and per-segment dots in one pass (tiles of one member, mode
+// TM_STORE_DOTS); three accumulator sets per thread, so fewer blocks per SM.
+__global__ void __launch_bounds__(F64_THREADS, 2)
+seg_gemm_f64_dots_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs, Bufs bufs,
+                         const double* __restrict__ coef, int n_terms, double* __restrict__ dot_out,
+                         const int32_t* __restrict__ skip) {
+  __shared__ F64Smem sm;
+  if (skip && *skip) return;
+  const TileF64 t = tiles[blockIdx.x];
+#define F64_CASE(I, J) \
+  case (I) | ((J) << 8): f64_tile<I, J, true>(t, segs, bufs, coef, n_terms, 0, dot_out, sm); break;
+  switch (t.shape) {
+    F64_CASE(1, 1) F64_CASE(1, 2) F64_CASE(1, 3) F64_CASE(1, 4)
+    F64_CASE(2, 1) F64_CASE(2, 2) F64_CASE(2, 3) F64_CASE(2, 4)
+    F64_CASE(3, 1) F64_CASE(3, 2) F64_CASE(3, 3) F64_CASE(3, 4)
+    F64_CASE(4, 1) F64_CASE(4, 2) F64_CASE(4, 3) F64_CASE(4, 4)
+    default: break;
+  }
+#undef F64_CASE
+}
+
+void launch_seg_gemm_f64_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
+                              double* dot_out, const int32_t* skip, cudaStream_t st) {
+  if (tl.n_tiles == 0) return;
+  seg_gemm_f64_dots_kernel<<<(unsigned)tl.n_tiles, F64_THREADS, 0, st>>>(tl.d_tiles, tl.d_segs, bufs, coef, n_terms,
+                                                                        dot_out, skip);
 }
 
 void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,

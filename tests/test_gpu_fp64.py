@@ -174,3 +174,42 @@ def test_full_size_ladder_m1000_sampled(dev):
     y = g.apply_H(to_dev(X)).cpu().numpy()
     for b in (0, 15):
         assert close(y[b], osb.apply_H(sb, X[b], b))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_H_term_dots(dev, name):
+    """One pass gives H psi (as the float64 product) and the per-term dots
+    <psi, (A_k x B_k) psi> (as the oracle's term products)."""
+    sb = CASES[name]()
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(30 + b, sb.dim) for b in range(sb.batch)])
+    y, dots = g.apply_H_term_dots(to_dev(X))
+    y, dots = y.cpu().numpy(), dots.cpu().numpy()
+    for b in range(sb.batch):
+        assert close(y[b], osb.apply_H(sb, X[b], b))
+        assert close(dots[b], osb.term_products(sb, X[b], X[b]))
+        # and H psi = sum_k c_k (A_k x B_k) psi, dotted with psi
+        assert float(X[b] @ y[b]) == pytest.approx(float(sb.coeffs[b] @ dots[b]), rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("prec,refine", [("bf16x3", "newton"), ("tf32", "newton"), ("fp64", "none"),
+                                         ("bf16x3", "lanczos")])
+def test_lanczos_ground_grad(dev, prec, refine):
+    """The gradient returned with the solve (from the refinement's last float64
+    product, or computed after it) equals dmrg_energy_grad of the returned
+    state and the oracle's Hellmann-Feynman gradient."""
+    sb = grown_hubbard_superblock(12, "ladder", 5, 5, m=60, cut=6, U_values=[4.0, 8.0])
+    g = gpu_sb(sb)
+    x0 = to_dev(np.stack([seeded_normal(3 + b, sb.dim) for b in range(sb.batch)]))
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    e0, psi, infos, st, dE = g.lanczos_ground(x0, tol=tol, max_iter=400, prec=prec, refine=refine,
+                                              refine_tol=1e-11, grad=True)
+    assert st == 0, infos
+    ref = g.energy_grad(psi).cpu().numpy()
+    dE = dE.cpu().numpy()
+    assert close(dE, ref, rel=1e-12)
+    P = psi.cpu().numpy()
+    for b in range(sb.batch):
+        assert close(dE[b], ograd.hf_grad(sb, P[b]), rel=1e-11)
+        # E0 = sum_k c_k dE0/dc_k (H is linear in the coefficients)
+        assert float(sb.coeffs[b] @ dE[b]) == pytest.approx(e0[b], rel=1e-10)
