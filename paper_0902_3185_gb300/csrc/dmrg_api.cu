@@ -225,8 +225,10 @@ bool is_gemm_pair(int flags) { return (flags & (DMRG_ID_A | DMRG_ID_B)) == 0; }
 // Intermediates: member b, pair i at T + b*Tm + toff[i], row-major (order 1:
 // r_in x c_out, order 0: r_out x c_in).  scaled = false drops every
 // coefficient (for the per-term dot products).
+// dots = true (with scaled = false): the output tiles are TM_STORE_DOTS and
+// each segment carries its term (coef) for the tile to apply per member.
 void build_stacked(const dmrg_sb* sb, const std::vector<GPair>& P, const std::vector<int64_t>& toff, int64_t Tm,
-                   bool scaled, TaskListF64& ph1, TaskListF64* gM, TaskListF64* gN) {
+                   bool scaled, TaskListF64& ph1, TaskListF64* gM, TaskListF64* gN, bool dots = false) {
   const int nb = sb->batch;
   const int64_t D = sb->D;
   const auto& r = sb->r;
@@ -262,6 +264,10 @@ void build_stacked(const dmrg_sb* sb, const std::vector<GPair>& P, const std::ve
       const GPair& p = P[i];
       const int32_t ri = r[p.s_in], ci = c[p.s_in], co = c[p.s_out];
       SegF64 g = seg_base();
+      if (dots) {
+        g.coef = p.term;
+        g.coef_mode = -1;  // no scaling while loading: the tile scales the segment's sum
+      }
       if (p.flags & DMRG_ID_A) {  // Y_b += c Psi_b B^T
         g.K = ci;
         g.l_buf = BUF_X; g.l_off = sb->off[p.s_in]; g.ldl = ci; g.l_rm = ri; g.l_bs = D;
@@ -287,13 +293,14 @@ void build_stacked(const dmrg_sb* sb, const std::vector<GPair>& P, const std::ve
       }
     }
     const bool hasM = !sM.empty(), hasN = !sN.empty();
+    const int32_t mode = dots ? TM_STORE_DOTS : TM_STORE;
     if (hasM || !hasN) {
-      TileF64 t = out_tile(BUF_Y, sb->off[s], c[s], nb * r[s], c[s], TM_STORE);
+      TileF64 t = out_tile(BUF_Y, sb->off[s], c[s], nb * r[s], c[s], mode);
       t.c_rm = r[s]; t.c_axis = 0; t.c_bs = D;
       add_output(*gM, t, sM, nullptr);
     }
     if (hasN) {
-      TileF64 t = out_tile(BUF_Y, sb->off[s], c[s], r[s], nb * c[s], TM_STORE);
+      TileF64 t = out_tile(BUF_Y, sb->off[s], c[s], r[s], nb * c[s], mode);
       t.c_rm = c[s]; t.c_axis = 1; t.c_bs = D; t.add = hasM ? 1 : 0;
       add_output(*gN, t, sN, nullptr);
     }
@@ -368,52 +375,37 @@ void build_f64_tasks(dmrg_sb* sb) {
       for (int64_t id : ids) dot_list[(size_t)b * nt + p.term].push_back(id);
     }
   }
-  // H psi with the per-term dots <psi, (A_k x B_k) psi> in one pass: one
-  // output per (member, sector) whose segments are the unscaled pair
-  // products (after f64_dot1); the tile applies c(member, term) itself
-  for (int b = 0; b < sb->batch; ++b) {
-    const int64_t xb = (int64_t)b * sb->D, tb = (int64_t)b * Tm;
-    std::vector<std::vector<size_t>> into(sb->S);
-    for (size_t i = 0; i < fw.size(); ++i) into[fw[i].s_out].push_back(i);
-    for (int so = 0; so < sb->S; ++so) {
-      if ((int64_t)r[so] * c[so] == 0) continue;
-      std::vector<SegF64> sg;
-      for (size_t i : into[so]) {
-        const GPair& p = fw[i];
-        const int32_t ri = r[p.s_in], ci = c[p.s_in], co = c[p.s_out];
-        SegF64 g = seg_base();
-        g.coef = p.term;
-        g.coef_mode = -1;  // no scaling while loading: the tile scales the segment's sum
-        if (p.flags & DMRG_ID_B) {
-          g.K = ri; set_L_op(g, p.A);
-          g.r_buf = BUF_X; g.r_off = xb + sb->off[p.s_in]; g.ldr = ci; g.r_trans = 0;
-        } else if (p.flags & DMRG_ID_A) {
-          g.K = ci; g.l_buf = BUF_X; g.l_off = xb + sb->off[p.s_in]; g.ldl = ci; set_R_opT(g, p.B);
-        } else if (p.order == 0) {
-          g.K = ci; g.l_buf = BUF_T; g.l_off = tb + toff_f[i]; g.ldl = ci; set_R_opT(g, p.B);
-        } else {
-          g.K = ri; set_L_op(g, p.A);
-          g.r_buf = BUF_T; g.r_off = tb + toff_f[i]; g.ldr = co; g.r_trans = 0;
-        }
-        sg.push_back(g);
-      }
-      TileF64 t = out_tile(BUF_Y, xb + sb->off[so], c[so], r[so], c[so], TM_STORE_DOTS);
-      t.member = b;
-      add_output(sb->f64_pdot, t, sg, nullptr);
-    }
+  // H psi with the per-term dots <psi, (A_k x B_k) psi> in one pass: the
+  // output launches of the product with unscaled segments (after f64_dot1's
+  // unscaled intermediates); the tiles apply c(member, term) themselves
+  {
+    TaskListF64 unused;
+    build_stacked(sb, fw, toff_f, Tm, false, unused, &sb->f64_pdot2, &sb->f64_pdot3, true);
   }
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_bwd1, &sb->f64_bwd2, &sb->f64_bwd3,
-                          &sb->f64_dot1, &sb->f64_pdot})
+                          &sb->f64_dot1, &sb->f64_pdot2, &sb->f64_pdot3})
     sort_tiles(*tl);
-  {  // segment partials of f64_pdot: slots in tile order, then the (member, term) lists
+  {  // partials of f64_pdot2/3: 64 per (tile, segment) in tile order, then the (member, term) lists
     std::vector<std::vector<int32_t>> lists((size_t)sb->batch * nt);
     int32_t base = 0;
-    for (TileF64& t : sb->f64_pdot.h_tiles) {
-      t.dot_base = base;
-      for (int32_t q = t.seg_begin; q < t.seg_end; ++q)
-        lists[(size_t)t.member * nt + sb->f64_pdot.h_segs[q].coef].push_back(base + (q - t.seg_begin));
-      base += t.seg_end - t.seg_begin;
-    }
+    for (TaskListF64* tl : {&sb->f64_pdot2, &sb->f64_pdot3})
+      for (TileF64& t : tl->h_tiles) {
+        t.dot_base = base;
+        const bool by_col = t.c_rm && t.c_axis == 1;
+        const int32_t bm = 16 * (t.shape & 0xff), bn = 16 * (t.shape >> 8);
+        for (int32_t q = t.seg_begin; q < t.seg_end; ++q) {
+          const int32_t term = tl->h_segs[q].coef;
+          const int64_t slot = (int64_t)(base + (q - t.seg_begin)) * 64;
+          for (int32_t e = 0; e < (by_col ? bn : bm); ++e) {
+            const int32_t g = (by_col ? t.n0 : t.m0) + e;
+            if (g >= (by_col ? t.N : t.M)) break;
+            const int32_t member = t.c_rm ? g / t.c_rm : t.member;
+            lists[(size_t)member * nt + term].push_back((int32_t)(slot + e));
+          }
+        }
+        base += t.seg_end - t.seg_begin;
+      }
+    if ((int64_t)base * 64 > INT32_MAX) throw Invalid{"too many product segments for the per-term dots"};
     std::vector<int32_t> ptr(1, 0), idx;
     for (auto& l : lists) {
       idx.insert(idx.end(), l.begin(), l.end());
@@ -422,7 +414,7 @@ void build_f64_tasks(dmrg_sb* sb) {
     upload(sb->d_pdot_ptr, ptr);
     upload(sb->d_pdot_idx, idx);
     if (sb->d_pdot_partial) cudaFree(sb->d_pdot_partial);
-    sb->d_pdot_partial = dalloc<double>((size_t)std::max<int32_t>(1, base));
+    sb->d_pdot_partial = dalloc<double>((size_t)std::max<int64_t>(1, (int64_t)base * 64));
   }
   const std::vector<int64_t> where = sort_tiles(sb->f64_dot2);
   std::vector<int32_t> ptr(1, 0), idx;
@@ -435,7 +427,7 @@ void build_f64_tasks(dmrg_sb* sb) {
   if (sb->d_dot_partial) cudaFree(sb->d_dot_partial);
   sb->d_dot_partial = dalloc<double>((size_t)std::max<int64_t>(1, (int64_t)sb->f64_dot2.h_tiles.size()));
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
-                          &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot})
+                          &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot2, &sb->f64_pdot3})
     finish(*tl);
 }
 
@@ -457,7 +449,8 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
 void matvec_f64_dots(dmrg_sb* sb, const double* psi, double* y, double* dc, cudaStream_t st) {
   Bufs bufs{{const_cast<double*>(psi), y, sb->d_T, sb->d_ops, nullptr}};
   launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
-  launch_seg_gemm_f64_dots(sb->f64_pdot, bufs, sb->d_coeffs, sb->n_terms, sb->d_pdot_partial, nullptr, st);
+  launch_seg_gemm_f64_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+  launch_seg_gemm_f64_dots(sb->f64_pdot3, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
   lz_launch_reduce_terms(sb->d_pdot_partial, sb->d_pdot_ptr, sb->d_pdot_idx, dc, sb->batch * sb->n_terms, st);
   CK(cudaGetLastError());
 }
@@ -523,7 +516,7 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   sb->rf_ctl = dalloc<int32_t>((size_t)(2 * B + 2));
   sb->rf_diag = dalloc<double>((size_t)(B * D));
   sb->rf_minv = dalloc<double>((size_t)(B * D));
-  sb->rf_part = dalloc<double>((size_t)(5 * B * sb->lz_nchunk));
+  sb->rf_part = dalloc<double>((size_t)(4 * B * sb->lz_nchunk));
   sb->lz_cap = cap;
 }
 
@@ -663,22 +656,18 @@ void rf_enqueue_inner(dmrg_sb* sb, int prec, cudaStream_t st) {
   int32_t* ctl = sb->rf_ctl;
   int32_t* stop = ctl + 2 * B;
   double* sc = sb->rf_sc;
-  double* part = sb->lz_partial;
   const double* psi = sb->lz_vcur;  // the current float64 iterate lives in lz_vcur during refinement
-  matvec(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st);
-  rf_launch_shift_dot(sb->rf_q, sb->rf_p, psi, sc, ctl, part, D, B, stop, st);
-  rf_launch_sum(part, sc, RF_S1, D, B, ctl, stop, st);
-  rf_launch_proj_dot(sb->rf_q, sb->rf_p, psi, sc, ctl, part, D, B, stop, st);
-  rf_launch_sum(part, sc, RF_PQ, D, B, ctl, stop, st);
-  rf_launch_alpha(sc, ctl, B, stop, st);
+  matvec(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st);  // q = H p (mixed)
+  rf_launch_dots4(sb->rf_q, sb->rf_p, psi, ctl, sb->rf_part, D, B, stop, st);
+  rf_launch_alpha4(sb->rf_part, sc, ctl, D, B, stop, st);
   rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_q, psi, sb->rf_minv, sc, ctl, sb->rf_part, D, B, stop,
                    st);
-  rf_launch_sum4(sb->rf_part, sc, D, B, ctl, stop, st);
+  rf_launch_sum4(sb->rf_part, sc, D, B, 0, ctl, stop, st);
   rf_launch_beta(sc, ctl, sc + RF_NSC * B, B, stop, st);
   rf_launch_dir(sb->rf_p, sb->rf_res, psi, sb->rf_minv, sc, ctl, D, B, 0, stop, st);
   CK(cudaGetLastError());
 }
-constexpr int RF_KERNELS_PER_ITER = 10;
+constexpr int RF_KERNELS_PER_ITER = 6;
 
 cudaGraphExec_t rf_graph(dmrg_sb* sb, int prec, int K) {
   const int key = (1 << 20) + 1 + prec * 1024 + K;
@@ -725,7 +714,7 @@ struct RfRun {
 
 // Newton refinement of psi (device [batch][D], normalised) in place.  With
 // dc != NULL the float64 residual products after the first also give the
-// per-term dots <psi, (A_k x B_k) psi> (one pass, f64_pdot); the last one is
+// per-term dots <psi, (A_k x B_k) psi> (one pass, f64_pdot2/3); the last one is
 // of the returned psi.
 RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, int max_inner, double eps_in, int K,
                cudaStream_t st, double* dc = nullptr) {
@@ -760,13 +749,12 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
     // preconditioner, right-hand side -r, first direction p = K (-r)
     rf_launch_minv(sb->rf_diag, sb->rf_sc, sb->rf_minv, D, B, st);
     rf_launch_start(sb->lz_w, cur, sb->rf_minv, sb->rf_res, sb->rf_t, sb->rf_sc, sb->rf_part, D, B, st);
-    rf_launch_sum4(sb->rf_part, sb->rf_sc, D, B, nullptr, nullptr, st);
-    rf_launch_sum(sb->rf_part + (size_t)4 * B * nch, sb->rf_sc, RF_MU, D, B, nullptr, nullptr, st);
+    rf_launch_sum4(sb->rf_part, sb->rf_sc, D, B, 1, nullptr, nullptr, st);
     rf_launch_rho0(sb->rf_sc, B, st);
     rf_launch_dir(sb->rf_p, sb->rf_res, cur, sb->rf_minv, sb->rf_sc, nullptr, D, B, 1, nullptr, st);
     CK(cudaMemcpyAsync(hsc.data(), sb->rf_sc, sizeof(double) * RF_NSC * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    r.launches += 10 + (with_dots ? 3 : matvec_launches(sb, DMRG_FP64));
+    r.launches += 9 + (with_dots ? 4 : matvec_launches(sb, DMRG_FP64));
     ++r.outer;
     bool all = true;
     for (int b = 0; b < B; ++b) {
@@ -973,7 +961,7 @@ void destroy(dmrg_sb* sb) {
   lz_free(sb);
   tc_free(sb);
   for (TaskListF64* tl : {&sb->f64_fwd1, &sb->f64_fwd2, &sb->f64_fwd3, &sb->f64_dot1, &sb->f64_dot2, &sb->f64_bwd1,
-                          &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot})
+                          &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot2, &sb->f64_pdot3})
     free_tl(*tl);
   for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red, sb->d_dg,
                     sb->d_pdot_partial})

@@ -57,7 +57,7 @@ struct TileF64 {
   int32_t add;      // second writer of an output block: always accumulate
   int32_t shape;    // ni | nj << 8
   int32_t member;   // TM_STORE_DOTS: the batch member of the tile
-  int32_t dot_base; // TM_STORE_DOTS: partial of segment s at dot_out[dot_base + s - seg_begin]
+  int32_t dot_base; // TM_STORE_DOTS: partials of segment s at dot_out[(dot_base + s - seg_begin) * 64 + row/col]
 };
 
 struct TaskListF64 {
@@ -73,7 +73,7 @@ void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* 
                          int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
 // tiles of mode TM_STORE_DOTS (product and per-segment dots in one pass)
 void launch_seg_gemm_f64_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
-                              double* dot_out, const int32_t* skip, cudaStream_t st);
+                              int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
 
 // ------------------------------------------------------------ host pair info
 struct PairH {
@@ -101,7 +101,7 @@ struct dmrg_sb {
   dmrg::TaskListF64 f64_fwd1, f64_fwd2, f64_fwd3;  // forward: intermediates, outputs (members along M, along N)
   dmrg::TaskListF64 f64_bwd1, f64_bwd2, f64_bwd3;  // H^T g
   dmrg::TaskListF64 f64_dot1, f64_dot2;   // per-pair <g, A psi B^T>
-  dmrg::TaskListF64 f64_pdot;             // H psi and per-term <psi, (A_k x B_k) psi> in one pass (after f64_dot1)
+  dmrg::TaskListF64 f64_pdot2, f64_pdot3; // H psi and per-term <psi, (A_k x B_k) psi> in one pass (after f64_dot1)
   int32_t* d_pdot_ptr = nullptr;          // term reduction of its segment partials, as d_dot_red_*
   int32_t* d_pdot_idx = nullptr;
   double* d_pdot_partial = nullptr;
@@ -138,7 +138,7 @@ struct dmrg_sb {
   int32_t* rf_ctl = nullptr;     // [2 batch + 2]
   double* rf_diag = nullptr;     // [batch][D] diag(H) per member (preconditioner)
   double* rf_minv = nullptr;     // [batch][D] 1 / max(diag - theta, delta)
-  double* rf_part = nullptr;     // [5][batch][nchunk] reduction partials
+  double* rf_part = nullptr;     // [4][batch][nchunk] reduction partials
   // terms with diagonal blocks (s_out == s_in): their diagonals, [n][D]
   std::vector<int32_t> dg_terms;
   int32_t* d_dg_terms = nullptr;

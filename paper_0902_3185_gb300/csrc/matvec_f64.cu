@@ -27,11 +27,14 @@ struct F64Smem {
   double R[F64_BK][F64_BMAX + 1];
   double red[F64_THREADS / 32];
 };
+struct F64DotSmem {  // column partials of TM_STORE_DOTS tiles with members along N
+  double col[16][F64_BMAX + 1];
+};
 
 template <int NI, int NJ, bool DOTS>
 __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restrict__ segs, const Bufs& bufs,
                                          const double* __restrict__ coef, int n_terms, int accumulate,
-                                         double* __restrict__ dot_out, F64Smem& sm) {
+                                         double* __restrict__ dot_out, F64Smem& sm, F64DotSmem* dsm) {
   constexpr int BM = 16 * NI, BN = 16 * NJ;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
@@ -40,21 +43,47 @@ __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restr
   for (int i = 0; i < NI; ++i)
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
+  // element offset of C(m, n) with the members stacked along M or N
+  auto coff = [&](int m, int n) -> int64_t {
+    int b = 0;
+    if (t.c_rm) {
+      if (t.c_axis == 0) { b = m / t.c_rm; m -= b * t.c_rm; }
+      else { b = n / t.c_rm; n -= b * t.c_rm; }
+    }
+    return (int64_t)b * t.c_bs + (t.c_trans ? (int64_t)n * t.ldc + m : (int64_t)m * t.ldc + n);
+  };
   // TM_STORE_DOTS: each segment accumulates alone (sacc), is dotted with the
-  // wavefunction block at the output's place (xo), then added with its
-  // member's coefficient
+  // wavefunction at the output's place (xo) -- per tile row, or per tile
+  // column when the members are stacked along N -- and is then added with
+  // the coefficient of each element's member
+  const bool by_col = t.c_rm && t.c_axis == 1;
   double sacc[DOTS ? NI : 1][DOTS ? NJ : 1];
-  double xo[DOTS ? NI : 1][DOTS ? NJ : 1];
+  // member of each of this thread's rows / columns, and the offsets of its
+  // output elements split as roff[i] + coffj[j] (-1: outside the output)
+  int mrow[DOTS ? NI : 1], mcol[DOTS ? NJ : 1];
+  int64_t roff[DOTS ? NI : 1], coffj[DOTS ? NJ : 1];
+  const double* X = bufs.p[BUF_X] + t.c_off;
   if (DOTS) {
-    const double* X = bufs.p[BUF_X] + t.c_off;
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
+    for (int i = 0; i < NI; ++i) {
+      const int m = t.m0 + ty + 16 * i;
+      const int b = (t.c_rm && t.c_axis == 0) ? m / t.c_rm : 0;
+      mrow[DOTS ? i : 0] = t.c_rm ? b : t.member;
+      roff[DOTS ? i : 0] = m < t.M ? (int64_t)b * t.c_bs + (int64_t)(m - b * t.c_rm) * t.ldc : -1;
+    }
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const int m = t.m0 + ty + 16 * i, n = t.n0 + tx + 16 * j;
-        xo[DOTS ? i : 0][DOTS ? j : 0] = (m < t.M && n < t.N) ? X[(int64_t)m * t.ldc + n] : 0.0;
-      }
+    for (int j = 0; j < NJ; ++j) {
+      const int n = t.n0 + tx + 16 * j;
+      const int b = by_col ? n / t.c_rm : 0;
+      mcol[DOTS ? j : 0] = b;
+      coffj[DOTS ? j : 0] = n < t.N ? (int64_t)b * t.c_bs + (n - b * t.c_rm) : -1;
+    }
   }
+  // the wavefunction at this thread's output element (i, j), 0 outside
+  auto xo = [&](int i, int j) -> double {
+    const int64_t r = roff[DOTS ? i : 0], c = coffj[DOTS ? j : 0];
+    return (r >= 0 && c >= 0) ? X[r + c] : 0.0;
+  };
 
   for (int sg = t.seg_begin; sg < t.seg_end; ++sg) {
     const SegF64 s = segs[sg];
@@ -126,39 +155,48 @@ __device__ __forceinline__ void f64_tile(const TileF64& t, const SegF64* __restr
       }
       __syncthreads();
     }
-    if (DOTS) {  // this segment's dot with the wavefunction, then its coefficient
-      const double cf = coef[t.member * n_terms + s.coef];
-      double part = 0.0;
+    if (DOTS) {  // this segment's dots with the wavefunction, then its coefficients
+      const int ql = sg - t.seg_begin;
+      double* out = dot_out + (int64_t)(t.dot_base + ql) * F64_BMAX;
+      if (!by_col) {
+        // row partials: the 16 threads of a row are 16 consecutive lanes
 #pragma unroll
-      for (int i = 0; i < NI; ++i)
+        for (int i = 0; i < NI; ++i) {
+          double part = 0.0;
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) part = fma(sacc[DOTS ? i : 0][DOTS ? j : 0], xo(i, j), part);
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          if (tx == 0) out[ty + 16 * i] = part;
+          const double cf = coef[mrow[DOTS ? i : 0] * n_terms + s.coef];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) acc[i][j] = fma(cf, sacc[DOTS ? i : 0][DOTS ? j : 0], acc[i][j]);
+        }
+      } else {
+        // column partials: the 16 threads of a column sit in different warps
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-          part = fma(sacc[DOTS ? i : 0][DOTS ? j : 0], xo[DOTS ? i : 0][DOTS ? j : 0], part);
-          acc[i][j] = fma(cf, sacc[DOTS ? i : 0][DOTS ? j : 0], acc[i][j]);
-        }
+          double part = 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-      if ((tid & 31) == 0) sm.red[tid >> 5] = part;
-      __syncthreads();
-      if (tid == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < F64_THREADS / 32; ++w) tot += sm.red[w];
-        dot_out[t.dot_base + (sg - t.seg_begin)] = tot;
+          for (int i = 0; i < NI; ++i) part = fma(sacc[DOTS ? i : 0][DOTS ? j : 0], xo(i, j), part);
+          dsm->col[ty][tx + 16 * j] = part;
+          const double cf = coef[mcol[DOTS ? j : 0] * n_terms + s.coef];
+#pragma unroll
+          for (int i = 0; i < NI; ++i) acc[i][j] = fma(cf, sacc[DOTS ? i : 0][DOTS ? j : 0], acc[i][j]);
+        }
+        __syncthreads();
+        if (tid < BN) {
+          double tot = 0.0;
+#pragma unroll
+          for (int y2 = 0; y2 < 16; ++y2) tot += dsm->col[y2][tid];
+          out[tid] = tot;
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
 
   double* C = bufs.p[t.c_buf] + t.c_off;
-  // element offset of C(m, n) with the members stacked along M or N
-  auto coff = [&](int m, int n) -> int64_t {
-    int b = 0;
-    if (t.c_rm) {
-      if (t.c_axis == 0) { b = m / t.c_rm; m -= b * t.c_rm; }
-      else { b = n / t.c_rm; n -= b * t.c_rm; }
-    }
-    return (int64_t)b * t.c_bs + (t.c_trans ? (int64_t)n * t.ldc + m : (int64_t)m * t.ldc + n);
-  };
   if (t.mode == TM_STORE || t.mode == TM_STORE_DOTS) {
     const bool add = accumulate || t.add;
 #pragma unroll
@@ -206,7 +244,7 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
   if (skip && *skip) return;
   const TileF64 t = tiles[blockIdx.x];
 #define F64_CASE(I, J) \
-  case (I) | ((J) << 8): f64_tile<I, J, false>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm); break;
+  case (I) | ((J) << 8): f64_tile<I, J, false>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, nullptr); break;
   switch (t.shape) {
     F64_CASE(1, 1) F64_CASE(1, 2) F64_CASE(1, 3) F64_CASE(1, 4)
     F64_CASE(2, 1) F64_CASE(2, 2) F64_CASE(2, 3) F64_CASE(2, 4)
@@ -217,17 +255,20 @@ seg_gemm_f64_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict_
 #undef F64_CASE
 }
 
-// Product and per-segment dots in one pass (tiles of one member, mode
-// TM_STORE_DOTS); three accumulator sets per thread, so fewer blocks per SM.
+// Product and per-segment dots in one pass (mode TM_STORE_DOTS): partials
+// per (tile, segment, tile row) -- or tile column when the members are
+// stacked along N -- at dot_out[(dot_base + segment) * 64 + row or column].
+// Three accumulator sets per thread, so fewer blocks per SM.
 __global__ void __launch_bounds__(F64_THREADS, 2)
 seg_gemm_f64_dots_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs, Bufs bufs,
-                         const double* __restrict__ coef, int n_terms, double* __restrict__ dot_out,
+                         const double* __restrict__ coef, int n_terms, int accumulate, double* __restrict__ dot_out,
                          const int32_t* __restrict__ skip) {
   __shared__ F64Smem sm;
+  __shared__ F64DotSmem dsm;
   if (skip && *skip) return;
   const TileF64 t = tiles[blockIdx.x];
 #define F64_CASE(I, J) \
-  case (I) | ((J) << 8): f64_tile<I, J, true>(t, segs, bufs, coef, n_terms, 0, dot_out, sm); break;
+  case (I) | ((J) << 8): f64_tile<I, J, true>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, &dsm); break;
   switch (t.shape) {
     F64_CASE(1, 1) F64_CASE(1, 2) F64_CASE(1, 3) F64_CASE(1, 4)
     F64_CASE(2, 1) F64_CASE(2, 2) F64_CASE(2, 3) F64_CASE(2, 4)
@@ -239,10 +280,10 @@ seg_gemm_f64_dots_kernel(const TileF64* __restrict__ tiles, const SegF64* __rest
 }
 
 void launch_seg_gemm_f64_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
-                              double* dot_out, const int32_t* skip, cudaStream_t st) {
+                              int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st) {
   if (tl.n_tiles == 0) return;
   seg_gemm_f64_dots_kernel<<<(unsigned)tl.n_tiles, F64_THREADS, 0, st>>>(tl.d_tiles, tl.d_segs, bufs, coef, n_terms,
-                                                                        dot_out, skip);
+                                                                        accumulate, dot_out, skip);
 }
 
 void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,

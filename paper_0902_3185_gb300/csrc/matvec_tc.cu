@@ -113,60 +113,79 @@ __host__ __device__ inline int64_t panel_off(int64_t row, int64_t k, int64_t ato
 // consecutive granules along the row for a plain job (each thread reads a
 // contiguous run of its row) and consecutive panel rows for a transposed job
 // (each of a thread's loads is coalesced across the warp).  Granules reaching
-// into the K padding write zeros there.  Each thread finds its job by binary
-// search once, then walks.
+// into the K padding write zeros there.  The host records the job of every
+// block's first granule (block_job), so a thread finds its job in a few
+// steps; all of a thread's loads are issued before its first conversion.
 constexpr int STAGE_GRANULES_PER_THREAD = 2;
+
+struct StageAt {  // where one granule lives
+  const StageJob* j;
+  int row, kg, rows;
+  bool ok;
+};
+
+__device__ __forceinline__ StageAt stage_find(const StageJob* __restrict__ jobs, int n_jobs, int& jid, int64_t e,
+                                              int64_t total) {
+  StageAt a{nullptr, 0, 0, 0, false};
+  if (e >= total) return a;
+  while (jid + 1 < n_jobs && jobs[jid + 1].first <= e) ++jid;
+  const StageJob* j = jobs + jid;
+  const int rows = j->transpose ? j->c : j->r;
+  const int loc = (int)(e - j->first);  // < rows * nkg: 32-bit division
+  if (!j->transpose) { a.row = loc / j->nkg; a.kg = loc - a.row * j->nkg; }  // panel row a, K = c
+  else { a.kg = loc / rows; a.row = loc - a.kg * rows; }                      // panel row c', K = a
+  a.j = j;
+  a.rows = rows;
+  a.ok = true;
+  return a;
+}
 
 template <int PREC>
 __global__ void __launch_bounds__(256)
-tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, const double* __restrict__ x,
-                int64_t D, const double* __restrict__ coef, int n_terms, const int32_t* __restrict__ skip) {
+tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, const int32_t* __restrict__ block_job, int64_t total,
+                const double* __restrict__ x, int64_t D, const double* __restrict__ coef, int n_terms,
+                const int32_t* __restrict__ skip) {
   constexpr int G = PREC == DMRG_TF32 ? 4 : 8;  // values per 16-byte granule
   constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
+  constexpr int U = STAGE_GRANULES_PER_THREAD;
   if (skip && *skip) return;
   const int b = blockIdx.y;
-  const int64_t e0 = (int64_t)blockIdx.x * (256 * STAGE_GRANULES_PER_THREAD) + threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * (256 * U) + threadIdx.x;
   if (e0 >= total) return;
-  int lo = 0, hi = n_jobs - 1;  // last job with first <= e0
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].first <= e0) lo = mid;
-    else hi = mid - 1;
-  }
-  int jid = lo;
-  StageJob j = jobs[jid];
-  int rows = j.transpose ? j.c : j.r;
-  int64_t jend = j.first + (int64_t)rows * j.nkg;
-  float scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
+  int jid = block_job[blockIdx.x];
+  StageAt at[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) at[u] = stage_find(jobs, n_jobs, jid, e0 + (int64_t)u * 256, total);
   const double* xb = x + (int64_t)b * D;
-#pragma unroll 1
-  for (int u = 0; u < STAGE_GRANULES_PER_THREAD; ++u) {
-    const int64_t e = e0 + (int64_t)u * 256;
-    if (e >= total) break;
-    while (e >= jend) {
-      j = jobs[++jid];
-      rows = j.transpose ? j.c : j.r;
-      jend = j.first + (int64_t)rows * j.nkg;
-      scf = j.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j.term]) : 1.0f;
-    }
-    const int loc = (int)(e - j.first);  // < rows * nkg: 32-bit division
-    int row, kg;
-    if (!j.transpose) { row = loc / j.nkg; kg = loc - row * j.nkg; }  // panel row a, K = c
-    else { kg = loc / rows; row = loc - kg * rows; }                  // panel row c', K = a
-    const int K = j.transpose ? j.r : j.c;
-    const double* src = xb + j.src_off;
-    float v[G];
+  double raw[U][G];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const StageJob* j = at[u].j;
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-      const int k = kg * G + i;
-      v[i] = 0.0f;
-      if (k < K) v[i] = tc::d2f_rn(j.transpose ? src[(int64_t)k * j.c + row] : src[(int64_t)row * j.c + k]) * scf;
+      raw[u][i] = 0.0;
+      if (!at[u].ok) continue;
+      const int k = at[u].kg * G + i;
+      const int K = j->transpose ? j->r : j->c;
+      if (k < K) {
+        const double* src = xb + j->src_off;
+        raw[u][i] = j->transpose ? src[(int64_t)k * j->c + at[u].row] : src[(int64_t)at[u].row * j->c + k];
+      }
     }
-    const int64_t o = panel_off((int64_t)b * ((rows + 7) & ~7) + row, (int64_t)kg * G, j.atoms, es);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (!at[u].ok) continue;
+    const StageJob* j = at[u].j;
+    const float scf = j->term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j->term]) : 1.0f;
+    float v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) v[i] = tc::d2f_rn(raw[u][i]) * scf;
+    const int64_t o = panel_off((int64_t)b * ((at[u].rows + 7) & ~7) + at[u].row, (int64_t)at[u].kg * G, j->atoms, es);
     if (PREC == DMRG_TF32) {
       const uint4 w = make_uint4(__float_as_uint(tc::round_tf32(v[0])), __float_as_uint(tc::round_tf32(v[1])),
                                  __float_as_uint(tc::round_tf32(v[2])), __float_as_uint(tc::round_tf32(v[3])));
-      *reinterpret_cast<uint4*>(j.p + o) = w;
+      *reinterpret_cast<uint4*>(j->p + o) = w;
     } else {
       uint32_t wh[4], wl[4];  // hi = bf16(x), lo = bf16(x - hi), two K values per word
 #pragma unroll
@@ -174,8 +193,8 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, int64_t total, co
         wh[i] = tc::bf16x2_rn(v[2 * i], v[2 * i + 1]);
         wl[i] = tc::bf16x2_rn(v[2 * i] - __uint_as_float(wh[i] << 16), v[2 * i + 1] - __uint_as_float(wh[i] & 0xffff0000u));
       }
-      *reinterpret_cast<uint4*>(j.p + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-      *reinterpret_cast<uint4*>(j.p + j.p_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+      *reinterpret_cast<uint4*>(j->p + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+      *reinterpret_cast<uint4*>(j->p + j->p_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
   }
 }
@@ -627,6 +646,7 @@ struct Launch {  // one grouped GEMM launch
 
 struct PairSet {  // the forward pairs or their transposes
   StageJob* jobs = nullptr;
+  int32_t* block_job = nullptr;  // staging: job of each block's first granule
   int n_jobs = 0;
   int64_t n_gran = 0;  // staging granules per member
   Launch ph1, grpE, grpS;
@@ -669,6 +689,7 @@ void free_launch(Launch& l) {
 }
 void free_set(PairSet& s) {
   if (s.jobs) cudaFree(s.jobs);
+  if (s.block_job) cudaFree(s.block_job);
   free_launch(s.ph1);
   free_launch(s.grpE);
   free_launch(s.grpS);
@@ -994,6 +1015,21 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   out.jobs = up(jobs);
   out.n_jobs = (int)jobs.size();
   out.n_gran = n_gran;
+  {  // job of the first granule of every staging block (binary search on the prefix)
+    const int64_t per = 256 * STAGE_GRANULES_PER_THREAD;
+    std::vector<int32_t> bj((size_t)std::max<int64_t>(1, cdiv(n_gran, per)), 0);
+    for (size_t k = 0; k < bj.size(); ++k) {
+      const int64_t e = (int64_t)k * per;
+      size_t lo = 0, hi = jobs.empty() ? 0 : jobs.size() - 1;
+      while (lo < hi) {
+        const size_t mid = (lo + hi + 1) / 2;
+        if (jobs[mid].first <= e) lo = mid;
+        else hi = mid - 1;
+      }
+      bj[k] = (int32_t)lo;
+    }
+    out.block_job = up(bj);
+  }
   return cur - base_off;
 }
 
@@ -1146,7 +1182,7 @@ static void run_set(const State* s, const PairSet& ps, const double* x, double* 
                     int accumulate, const int32_t* skip, cudaStream_t st) {
   if (ps.n_gran > 0) {
     const int64_t blocks = cdiv(ps.n_gran, 256 * STAGE_GRANULES_PER_THREAD);
-    tc_stage_kernel<PREC><<<dim3((unsigned)blocks, sb->batch), 256, 0, st>>>(ps.jobs, ps.n_jobs, ps.n_gran, x, sb->D,
+    tc_stage_kernel<PREC><<<dim3((unsigned)blocks, sb->batch), 256, 0, st>>>(ps.jobs, ps.n_jobs, ps.block_job, ps.n_gran, x, sb->D,
                                                                             sb->d_coeffs, sb->n_terms, skip);
   }
   run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);

@@ -19,8 +19,8 @@
 //
 // Per-member scalars (float64, device): [0] theta, [1] |b|, [2] rr, [3] pq,
 // [4] s1 = <psi, q>, [5] alpha, [6] beta, [7] rr_new, [8] rho = <r, z>,
-// [9] gamma, [10] mu = <psi, M^-1 psi>, [11..13] <psi, M^-1 r>, <r, M^-1 r>,
-// <r, M^-1 psi>; control (int32):
+// [9] gamma, [10] mu = <psi, M^-1 psi>, [11..12] <psi, M^-1 r>, <r, M^-1 r>;
+// control (int32):
 // [b] done flag of the inner solve, [B + b] inner iterations, [2B] all
 // done, [2B + 1] inner iteration cap.
 
@@ -51,46 +51,68 @@ __device__ __forceinline__ double rf_block_sum(double v, double* red) {
     body                                                                             \
   }
 
-// q -= theta p ; part = <psi, q>
+// partials of <psi, q>, <p, q>, <p, p>, <p, psi> for q = H p (rows 0..3);
+// the projected operator's q = H p - theta p - s1 psi is formed in the update
 __global__ void __launch_bounds__(LZ_THREADS)
-k_rf_shift_dot(double* __restrict__ q, const double* __restrict__ p, const double* __restrict__ psi,
-               const double* __restrict__ sc, const int32_t* __restrict__ ctl, double* __restrict__ part,
-               int64_t D, int nchunk, const int32_t* __restrict__ stop) {
+k_rf_dots4(const double* __restrict__ q, const double* __restrict__ p, const double* __restrict__ psi,
+           const int32_t* __restrict__ ctl, double* __restrict__ part, int64_t D, int nchunk, int batch,
+           const int32_t* __restrict__ stop) {
   __shared__ double red[LZ_THREADS / 32];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if ((stop && *stop) || ctl[b]) return;
-  const double th = sc[b * RF_NSC + RF_THETA];
-  double acc = 0.0;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
   RF_LOOP({
-    const double v = q[i] - th * p[i];
-    q[i] = v;
-    acc = fma(psi[i], v, acc);
+    const double qi = q[i];
+    const double pi = p[i];
+    const double si = psi[i];
+    a[0] = fma(si, qi, a[0]);
+    a[1] = fma(pi, qi, a[1]);
+    a[2] = fma(pi, pi, a[2]);
+    a[3] = fma(pi, si, a[3]);
   })
-  acc = rf_block_sum(acc, red);
-  if (threadIdx.x == 0) part[(int64_t)b * nchunk + chunk] = acc;
+  const int64_t stride = (int64_t)batch * nchunk, at = (int64_t)b * nchunk + chunk;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double s = rf_block_sum(a[k], red);
+    if (threadIdx.x == 0) part[k * stride + at] = s;
+  }
 }
 
-// q -= s1 psi ; part = <p, q>
-__global__ void __launch_bounds__(LZ_THREADS)
-k_rf_proj_dot(double* __restrict__ q, const double* __restrict__ p, const double* __restrict__ psi,
-              const double* __restrict__ sc, const int32_t* __restrict__ ctl, double* __restrict__ part,
-              int64_t D, int nchunk, const int32_t* __restrict__ stop) {
-  __shared__ double red[LZ_THREADS / 32];
-  const int b = blockIdx.y, chunk = blockIdx.x;
+// s1 = <psi, Hp> - theta <psi, p>; pq = <p, Hp> - theta <p, p> - s1 <p, psi>;
+// alpha = rho / pq (a non-positive pq ends the member's solve).  One warp per
+// member: lane-strided chunk sums, then a fixed shuffle tree.
+__global__ void k_rf_alpha4(const double* __restrict__ part, double* __restrict__ sc, int32_t* __restrict__ ctl,
+                            int nchunk, int batch, const int32_t* __restrict__ stop) {
+  const int b = blockIdx.x;
   if ((stop && *stop) || ctl[b]) return;
-  const double s1 = sc[b * RF_NSC + RF_S1];
-  double acc = 0.0;
-  RF_LOOP({
-    const double v = q[i] - s1 * psi[i];
-    q[i] = v;
-    acc = fma(p[i], v, acc);
-  })
-  acc = rf_block_sum(acc, red);
-  if (threadIdx.x == 0) part[(int64_t)b * nchunk + chunk] = acc;
+  double v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double* row = part + ((int64_t)k * batch + b) * nchunk;
+    double t = 0.0;
+    for (int ch = threadIdx.x; ch < nchunk; ch += 32) t += row[ch];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    v[k] = t;
+  }
+  if (threadIdx.x != 0) return;
+  double* s = sc + b * RF_NSC;
+  const double th = s[RF_THETA];
+  const double s1 = v[0] - th * v[3];
+  const double pq = v[1] - th * v[2] - s1 * v[3];
+  s[RF_S1] = s1;
+  s[RF_PQ] = pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    ctl[b] = 2;
+    s[RF_ALPHA] = 0.0;
+    return;
+  }
+  s[RF_ALPHA] = s[RF_RHO] / pq;
 }
 
-// t += alpha p ; res -= alpha q ; partials of <res, res>, <psi, M^-1 res>,
-// <res, M^-1 res>, <res, M^-1 psi> at part + k B nchunk, k = 0..3
+// t += alpha p ; res -= alpha (q - theta p - s1 psi) with q = H p ; partials
+// of <res, res>, <psi, M^-1 res>, <res, M^-1 res> at part + k B nchunk,
+// k = 0..2 (<res, M^-1 psi> equals <psi, M^-1 res>: M is diagonal)
 __global__ void __launch_bounds__(LZ_THREADS)
 k_rf_update(double* __restrict__ t, double* __restrict__ res, const double* __restrict__ p,
             const double* __restrict__ q, const double* __restrict__ psi, const double* __restrict__ minv,
@@ -100,16 +122,18 @@ k_rf_update(double* __restrict__ t, double* __restrict__ res, const double* __re
   const int b = blockIdx.y, chunk = blockIdx.x;
   if ((stop && *stop) || ctl[b]) return;
   const double al = sc[b * RF_NSC + RF_ALPHA];
-  double rr = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const double th = sc[b * RF_NSC + RF_THETA], s1 = sc[b * RF_NSC + RF_S1];
+  double rr = 0.0, a1 = 0.0, a2 = 0.0;
   RF_LOOP({
-    t[i] = fma(al, p[i], t[i]);
-    const double v = fma(-al, q[i], res[i]);
+    const double pi = p[i];
+    t[i] = fma(al, pi, t[i]);
+    const double qp = fma(-s1, psi[i], fma(-th, pi, q[i]));  // (P (H - theta) P p)_i
+    const double v = fma(-al, qp, res[i]);
     res[i] = v;
     const double mv = minv[i] * v;
     rr = fma(v, v, rr);
     a1 = fma(psi[i], mv, a1);
     a2 = fma(v, mv, a2);
-    a3 = fma(minv[i] * psi[i], v, a3);
   })
   const int64_t stride = (int64_t)batch * nchunk, at = (int64_t)b * nchunk + chunk;
   rr = rf_block_sum(rr, red);
@@ -118,8 +142,6 @@ k_rf_update(double* __restrict__ t, double* __restrict__ res, const double* __re
   if (threadIdx.x == 0) part[stride + at] = a1;
   a2 = rf_block_sum(a2, red);
   if (threadIdx.x == 0) part[2 * stride + at] = a2;
-  a3 = rf_block_sum(a3, red);
-  if (threadIdx.x == 0) part[3 * stride + at] = a3;
 }
 
 // p = M^-1 (res - gamma psi) + beta p  (first: beta = 0)
@@ -158,15 +180,16 @@ __global__ void k_rf_minv(const double* __restrict__ diag, const double* __restr
     minv[(int64_t)b * D + d] = 1.0 / fmax(diag[(int64_t)b * D + d] - th, delta);
 }
 
-// sc[b][RR_NEW, A1, A2, A3] = sums of the four partial rows (fixed order)
+// sc[b][RR_NEW, A1, A2 (, MU)] = sums of the partial rows 0..2 (and 3 when
+// with_mu), fixed order
 __global__ void k_rf_sum4(const double* __restrict__ part, double* __restrict__ sc, int nchunk, int batch,
-                          const int32_t* __restrict__ ctl, const int32_t* __restrict__ stop) {
+                          int with_mu, const int32_t* __restrict__ ctl, const int32_t* __restrict__ stop) {
   const int b = blockIdx.x, k = threadIdx.x;
-  if (k >= 4 || (stop && *stop) || (ctl && ctl[b])) return;
+  if (k >= 3 + with_mu || (stop && *stop) || (ctl && ctl[b])) return;
   const double* row = part + ((int64_t)k * batch + b) * nchunk;
   double t = 0.0;
   for (int ch = 0; ch < nchunk; ++ch) t += row[ch];
-  const int slot[4] = {RF_RRNEW, RF_A1, RF_A2, RF_A3};
+  const int slot[4] = {RF_RRNEW, RF_A1, RF_A2, RF_MU};
   sc[b * RF_NSC + slot[k]] = t;
 }
 
@@ -179,31 +202,7 @@ __global__ void k_rf_rho0(double* __restrict__ sc, int batch) {
   s[RF_RR] = s[RF_RRNEW];
   s[RF_BNORM] = sqrt(s[RF_RRNEW]);
   s[RF_GAMMA] = s[RF_A1] / s[RF_MU];
-  s[RF_RHO] = s[RF_A2] - s[RF_GAMMA] * s[RF_A3];
-}
-
-// sc[b][slot] = sum of the chunk partials (fixed order)
-__global__ void k_rf_sum(const double* __restrict__ part, double* __restrict__ sc, int slot, int nchunk, int batch,
-                         const int32_t* __restrict__ ctl, const int32_t* __restrict__ stop) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= batch || (stop && *stop) || (ctl && ctl[b])) return;
-  double t = 0.0;
-  for (int ch = 0; ch < nchunk; ++ch) t += part[(int64_t)b * nchunk + ch];
-  sc[b * RF_NSC + slot] = t;
-}
-
-// alpha = rr / pq; a non-positive pq ends the member's solve
-__global__ void k_rf_alpha(double* __restrict__ sc, int32_t* __restrict__ ctl, int batch,
-                           const int32_t* __restrict__ stop) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= batch || (stop && *stop) || ctl[b]) return;
-  double* s = sc + b * RF_NSC;
-  if (!(s[RF_PQ] > 0.0) || !isfinite(s[RF_PQ])) {
-    ctl[b] = 2;
-    s[RF_ALPHA] = 0.0;
-    return;
-  }
-  s[RF_ALPHA] = s[RF_RHO] / s[RF_PQ];
+  s[RF_RHO] = s[RF_A2] - s[RF_GAMMA] * s[RF_A1];
 }
 
 // gamma, rho = <res, z>, beta = rho_new / rho; stop a member at
@@ -220,7 +219,7 @@ __global__ void k_rf_beta(double* __restrict__ sc, int32_t* __restrict__ ctl, co
       const double rn = s[RF_RRNEW];
       s[RF_RR] = rn;
       s[RF_GAMMA] = s[RF_A1] / s[RF_MU];
-      const double rho = s[RF_A2] - s[RF_GAMMA] * s[RF_A3];
+      const double rho = s[RF_A2] - s[RF_GAMMA] * s[RF_A1];
       s[RF_BETA] = rho / s[RF_RHO];
       s[RF_RHO] = rho;
       const int it = ++ctl[batch + b];
@@ -233,7 +232,7 @@ __global__ void k_rf_beta(double* __restrict__ sc, int32_t* __restrict__ ctl, co
 
 // outer step: r = w - theta psi into res (negated: the CG right-hand side is
 // -r), t = 0; partials of <res, res>, <psi, M^-1 res>, <res, M^-1 res>,
-// <res, M^-1 psi>, <psi, M^-1 psi> (rows 0..4)
+// <psi, M^-1 psi> (rows 0..3)
 __global__ void __launch_bounds__(LZ_THREADS)
 k_rf_start(const double* __restrict__ w, const double* __restrict__ psi, const double* __restrict__ minv,
            double* __restrict__ res, double* __restrict__ t, const double* __restrict__ sc, double* __restrict__ part,
@@ -241,7 +240,7 @@ k_rf_start(const double* __restrict__ w, const double* __restrict__ psi, const d
   __shared__ double red[LZ_THREADS / 32];
   const int b = blockIdx.y, chunk = blockIdx.x;
   const double th = sc[b * RF_NSC + RF_THETA];
-  double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
   RF_LOOP({
     const double v = th * psi[i] - w[i];
     res[i] = v;
@@ -251,12 +250,11 @@ k_rf_start(const double* __restrict__ w, const double* __restrict__ psi, const d
     a[0] = fma(v, v, a[0]);
     a[1] = fma(psi[i], mv, a[1]);
     a[2] = fma(v, mv, a[2]);
-    a[3] = fma(mp, v, a[3]);
-    a[4] = fma(mp, psi[i], a[4]);
+    a[3] = fma(mp, psi[i], a[3]);
   })
   const int64_t stride = (int64_t)batch * nchunk, at = (int64_t)b * nchunk + chunk;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 4; ++k) {
     const double s = rf_block_sum(a[k], red);
     if (threadIdx.x == 0) part[k * stride + at] = s;
   }
@@ -285,13 +283,13 @@ __global__ void k_rf_apply(double* __restrict__ psi, const double* __restrict__ 
 // ------------------------------------------------------------- launchers
 static dim3 vgrid(int64_t D, int batch) { return dim3(lz_nchunk(D), batch); }
 
-void rf_launch_shift_dot(double* q, const double* p, const double* psi, const double* sc, const int32_t* ctl,
-                         double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st) {
-  k_rf_shift_dot<<<vgrid(D, B), LZ_THREADS, 0, st>>>(q, p, psi, sc, ctl, part, D, lz_nchunk(D), stop);
+void rf_launch_dots4(const double* q, const double* p, const double* psi, const int32_t* ctl, double* part,
+                     int64_t D, int B, const int32_t* stop, cudaStream_t st) {
+  k_rf_dots4<<<vgrid(D, B), LZ_THREADS, 0, st>>>(q, p, psi, ctl, part, D, lz_nchunk(D), B, stop);
 }
-void rf_launch_proj_dot(double* q, const double* p, const double* psi, const double* sc, const int32_t* ctl,
-                        double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st) {
-  k_rf_proj_dot<<<vgrid(D, B), LZ_THREADS, 0, st>>>(q, p, psi, sc, ctl, part, D, lz_nchunk(D), stop);
+void rf_launch_alpha4(const double* part, double* sc, int32_t* ctl, int64_t D, int B, const int32_t* stop,
+                      cudaStream_t st) {
+  k_rf_alpha4<<<B, 32, 0, st>>>(part, sc, ctl, lz_nchunk(D), B, stop);
 }
 void rf_launch_update(double* t, double* res, const double* p, const double* q, const double* psi,
                       const double* minv, const double* sc, const int32_t* ctl, double* part, int64_t D, int B,
@@ -303,9 +301,9 @@ void rf_launch_dir(double* p, const double* res, const double* psi, const double
                    const int32_t* ctl, int64_t D, int B, int first, const int32_t* stop, cudaStream_t st) {
   k_rf_dir<<<vgrid(D, B), LZ_THREADS, 0, st>>>(p, res, psi, minv, sc, ctl, D, first, stop);
 }
-void rf_launch_sum4(const double* part, double* sc, int64_t D, int B, const int32_t* ctl, const int32_t* stop,
-                    cudaStream_t st) {
-  k_rf_sum4<<<B, 32, 0, st>>>(part, sc, lz_nchunk(D), B, ctl, stop);
+void rf_launch_sum4(const double* part, double* sc, int64_t D, int B, int with_mu, const int32_t* ctl,
+                    const int32_t* stop, cudaStream_t st) {
+  k_rf_sum4<<<B, 32, 0, st>>>(part, sc, lz_nchunk(D), B, with_mu, ctl, stop);
 }
 static int rf_vec_blocks(int64_t D) {
   const int64_t nb = (D + 255) / 256;
@@ -319,13 +317,6 @@ void rf_launch_minv(const double* diag, const double* sc, double* minv, int64_t 
   k_rf_minv<<<dim3(rf_vec_blocks(D), B), 256, 0, st>>>(diag, sc, minv, D);
 }
 void rf_launch_rho0(double* sc, int B, cudaStream_t st) { k_rf_rho0<<<(B + 63) / 64, 64, 0, st>>>(sc, B); }
-void rf_launch_sum(const double* part, double* sc, int slot, int64_t D, int B, const int32_t* ctl,
-                   const int32_t* stop, cudaStream_t st) {
-  k_rf_sum<<<(B + 63) / 64, 64, 0, st>>>(part, sc, slot, lz_nchunk(D), B, ctl, stop);
-}
-void rf_launch_alpha(double* sc, int32_t* ctl, int B, const int32_t* stop, cudaStream_t st) {
-  k_rf_alpha<<<(B + 63) / 64, 64, 0, st>>>(sc, ctl, B, stop);
-}
 void rf_launch_beta(double* sc, int32_t* ctl, const double* eps, int B, int32_t* stop, cudaStream_t st) {
   k_rf_beta<<<1, 32, 0, st>>>(sc, ctl, eps, B, stop);
 }

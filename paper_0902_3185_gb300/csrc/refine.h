@@ -9,30 +9,26 @@ namespace dmrg {
 
 // per-member scalar slots
 enum RfSlot : int { RF_THETA = 0, RF_BNORM = 1, RF_RR = 2, RF_PQ = 3, RF_S1 = 4, RF_ALPHA = 5, RF_BETA = 6,
-                    RF_RRNEW = 7, RF_RHO = 8, RF_GAMMA = 9, RF_MU = 10, RF_A1 = 11, RF_A2 = 12, RF_A3 = 13,
-                    RF_NSC = 14 };
+                    RF_RRNEW = 7, RF_RHO = 8, RF_GAMMA = 9, RF_MU = 10, RF_A1 = 11, RF_A2 = 12, RF_NSC = 13 };
 
 // Diagonal preconditioner M = max(diag(H) - theta, delta), delta = RF_DELTA max(1, |theta|)
 constexpr double RF_DELTA = 1e-2;
 
-void rf_launch_shift_dot(double* q, const double* p, const double* psi, const double* sc, const int32_t* ctl,
-                         double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st);
-void rf_launch_proj_dot(double* q, const double* p, const double* psi, const double* sc, const int32_t* ctl,
-                        double* part, int64_t D, int B, const int32_t* stop, cudaStream_t st);
+void rf_launch_dots4(const double* q, const double* p, const double* psi, const int32_t* ctl, double* part,
+                     int64_t D, int B, const int32_t* stop, cudaStream_t st);
+void rf_launch_alpha4(const double* part, double* sc, int32_t* ctl, int64_t D, int B, const int32_t* stop,
+                      cudaStream_t st);
 void rf_launch_update(double* t, double* res, const double* p, const double* q, const double* psi,
                       const double* minv, const double* sc, const int32_t* ctl, double* part, int64_t D, int B,
                       const int32_t* stop, cudaStream_t st);
 void rf_launch_dir(double* p, const double* res, const double* psi, const double* minv, const double* sc,
                    const int32_t* ctl, int64_t D, int B, int first, const int32_t* stop, cudaStream_t st);
-void rf_launch_sum4(const double* part, double* sc, int64_t D, int B, const int32_t* ctl, const int32_t* stop,
-                    cudaStream_t st);
+void rf_launch_sum4(const double* part, double* sc, int64_t D, int B, int with_mu, const int32_t* ctl,
+                    const int32_t* stop, cudaStream_t st);
 void rf_launch_diag(const double* dterm, const int32_t* terms, int nd, const double* coef, int n_terms,
                     double* diag, int64_t D, int B, cudaStream_t st);
 void rf_launch_minv(const double* diag, const double* sc, double* minv, int64_t D, int B, cudaStream_t st);
 void rf_launch_rho0(double* sc, int B, cudaStream_t st);
-void rf_launch_sum(const double* part, double* sc, int slot, int64_t D, int B, const int32_t* ctl,
-                   const int32_t* stop, cudaStream_t st);
-void rf_launch_alpha(double* sc, int32_t* ctl, int B, const int32_t* stop, cudaStream_t st);
 void rf_launch_beta(double* sc, int32_t* ctl, const double* eps, int B, int32_t* stop, cudaStream_t st);
 void rf_launch_start(const double* w, const double* psi, const double* minv, double* res, double* t,
                      const double* sc, double* part, int64_t D, int B, cudaStream_t st);
