@@ -55,6 +55,8 @@ struct TcSeg {
   int32_t l_atoms, r_atoms;  // atoms per K chunk in each panel
   int32_t kchunks;
   int32_t slot;       // accumulator slot (0: coefficients already applied)
+  int32_t col0;       // pieced tiles: first tile column of this piece (a multiple of 16)
+  int32_t ra;         // pieced tiles: atoms of R rows this piece copies
 };
 
 enum OutKind : int32_t { OUT_Y_ROW = 0, OUT_Y_COL = 1, OUT_PANEL = 2 };
@@ -80,6 +82,13 @@ struct TcTile {
   int32_t seg_begin, seg_end, out;
   int32_t slot_used;              // bit k: slot k receives at least one product
   int32_t slot_term[TC_MAX_SLOTS];  // slot k >= 1: its coefficient column (member from the row)
+  // pieced tile (phase 1): its segments are pieces -- products that share the
+  // L operand and K, with their R operands side by side along N (each from
+  // column col0); one MMA chain covers all, piece q's output is seg_outs[q].
+  // cmap: the piece of every 16-column chunk, 4 bits each (chunks 0-7 in
+  // cmap_lo, 8-15 in cmap_hi).  ra then counts the atoms of all pieces.
+  int32_t pieced;
+  uint32_t cmap_lo, cmap_hi;
   TcOut o;                        // the output this tile belongs to (a copy: one load per tile)
 };
 
@@ -218,7 +227,7 @@ constexpr int TC_CTRL_BYTES = 256 + 4 * TC_COEF_MAX;  // barriers etc., then the
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
-               double* __restrict__ y, int64_t D, const double* __restrict__ coef, int n_terms, int n_coef,
+               const TcOut* __restrict__ seg_outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef, int n_terms, int n_coef,
                int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
                int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride,
                int n_acc, int tile_split, int stall) {
@@ -285,6 +294,37 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         const int tn = t + gridDim.x;
         if (tn < n_tiles) tl_n = tiles[tn];
         const uint32_t lb = (uint32_t)tl.la * 1024u, rb = (uint32_t)tl.ra * 1024u;
+        if (tl.pieced) {
+          // one L tile and every piece's R rows per K chunk
+          const TcSeg sg = sg_n_idx == tl.seg_begin ? sg_n : segs[tl.seg_begin];
+          if (tn < n_tiles && tl_n.seg_begin < tl_n.seg_end) {
+            sg_n = segs[tl_n.seg_begin];
+            sg_n_idx = tl_n.seg_begin;
+          }
+          for (int kc = 0; kc < sg.kchunks; ++kc) {
+            if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) goto producer_done;
+            char* st = ring + (size_t)stage * stage_bytes;
+            const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * 1024;
+            tc::mbar_arrive_expect_tx(&full[stage], PREC == DMRG_TF32 ? lb + rb : 2u * (lb + rb));
+            tc::bulk_g2s(st, lsrc, lb, &full[stage]);
+            if (PREC == DMRG_BF16X3) tc::bulk_g2s(st + L_TILE_BYTES + r_tile_bytes, lsrc + sg.l_lo, lb, &full[stage]);
+            for (int q = tl.seg_begin; q < tl.seg_end; ++q) {
+              const TcSeg pq = segs[q];
+              const char* rsrc = pq.r + (int64_t)kc * pq.r_atoms * 1024;
+              const uint32_t at = (uint32_t)(pq.col0 / 8) * 1024u, nb = (uint32_t)pq.ra * 1024u;
+              tc::bulk_g2s(st + L_TILE_BYTES + at, rsrc, nb, &full[stage]);
+              if (PREC == DMRG_BF16X3)
+                tc::bulk_g2s(st + 2 * L_TILE_BYTES + r_tile_bytes + at, rsrc + pq.r_lo, nb, &full[stage]);
+            }
+            issued |= 1u << stage;
+            issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          continue;
+        }
         for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
           const TcSeg sg = sg_n_idx == s ? sg_n : segs[s];
           if (s + 1 < tl.seg_end) {
@@ -350,10 +390,11 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         const uint32_t d_acc = tmem_base + (uint32_t)(acc * acc_stride);
         const uint32_t idesc = tc::idesc_f32acc(fmt, 128, (uint32_t)tl.ntile);
         uint32_t started = 0;  // slots that already hold a partial sum
-        for (int s = tl.seg_begin; s < tl.seg_end; ++s) {
+        const int s_end = tl.pieced ? tl.seg_begin + 1 : tl.seg_end;  // a pieced tile is one MMA chain
+        for (int s = tl.seg_begin; s < s_end; ++s) {
           const int kch = kch_n;
           const int slot = slot_n;
-          if (s + 1 < tl.seg_end) {  // one segment ahead
+          if (s + 1 < s_end) {  // one segment ahead
             kch_n = segs[s + 1].kchunks;
             slot_n = segs[s + 1].slot;
           }
@@ -506,14 +547,26 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           constexpr int G = PREC == DMRG_TF32 ? 4 : 8;
           constexpr int LD = panel_ld<PREC>();
           uint32_t* pstg = reinterpret_cast<uint32_t*>(stg);
+          // the output of this 16-column chunk: the tile's, or its piece's
+          TcOut po = o;
+          int pcol0 = 0;
+          float pscf = scf;
+          if (tl.pieced) {
+            const int ci = c0 >> 4;
+            const int pi = (int)(((ci < 8 ? tl.cmap_lo >> (4 * ci) : tl.cmap_hi >> (4 * (ci - 8)))) & 15u);
+            po = seg_outs[tl.seg_begin + pi];
+            pcol0 = segs[tl.seg_begin + pi].col0;
+            pscf = (po.term >= 0 && mv) ? coef_f(b * n_terms + po.term) : 1.0f;
+          }
+          const int pend = tl.pieced ? po.N : nend;  // end column (a piece counts from its own first)
           if (PREC == DMRG_TF32) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) pstg[jj * LD + lane] = __float_as_uint(tc::round_tf32(v[jj] * scf));
+            for (int jj = 0; jj < 16; ++jj) pstg[jj * LD + lane] = __float_as_uint(tc::round_tf32(v[jj] * pscf));
           } else {
             // two columns per conversion instruction: hi = bf16(x), lo = bf16(x - hi)
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 2) {
-              const float x0 = v[jj] * scf, x1 = v[jj + 1] * scf;
+              const float x0 = v[jj] * pscf, x1 = v[jj + 1] * pscf;
               const uint32_t hp = tc::bf16x2_rn(x0, x1);
               const uint32_t lp = tc::bf16x2_rn(x0 - __uint_as_float(hp << 16), x1 - __uint_as_float(hp & 0xffff0000u));
               pstg[jj * LD + lane] = __byte_perm(hp, lp, 0x5410);        // hi | lo << 16 of column jj
@@ -529,21 +582,21 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           const int chunk = ((kfirst - kc * kce) * es) >> 4;
 #pragma unroll
           for (int blk = 0; blk < 16; blk += G) {
-            const int n = tl.n0 + c0 + blk + cg;
-            if (!gv || n >= nend) continue;
+            const int n = tl.n0 + c0 + blk + cg - pcol0;  // column of the (piece's) output
+            if (!gv || n >= pend) continue;
             const uint32_t* src = pstg + (blk + cg) * LD + g0;
-            const int prow = b * o.Np + n;
+            const int prow = b * po.Np + n;
             const int r8 = prow & 7;
-            const int off = (kc * o.p_atoms + (prow >> 3)) * 1024 + r8 * 128 + ((chunk ^ r8) << 4);
+            const int off = (kc * po.p_atoms + (prow >> 3)) * 1024 + r8 * 128 + ((chunk ^ r8) << 4);
             if (PREC == DMRG_TF32) {
-              *reinterpret_cast<uint4*>(o.p + off) = *reinterpret_cast<const uint4*>(src);
+              *reinterpret_cast<uint4*>(po.p + off) = *reinterpret_cast<const uint4*>(src);
             } else {
               const uint4 a = *reinterpret_cast<const uint4*>(src);
               const uint4 c4 = *reinterpret_cast<const uint4*>(src + 4);
-              *reinterpret_cast<uint4*>(o.p + off) =
+              *reinterpret_cast<uint4*>(po.p + off) =
                   make_uint4(__byte_perm(a.x, a.y, 0x5410), __byte_perm(a.z, a.w, 0x5410),
                              __byte_perm(c4.x, c4.y, 0x5410), __byte_perm(c4.z, c4.w, 0x5410));
-              *reinterpret_cast<uint4*>(o.p + o.p_lo + off) =
+              *reinterpret_cast<uint4*>(po.p + po.p_lo + off) =
                   make_uint4(__byte_perm(a.x, a.y, 0x7632), __byte_perm(a.z, a.w, 0x7632),
                              __byte_perm(c4.x, c4.y, 0x7632), __byte_perm(c4.z, c4.w, 0x7632));
             }
@@ -637,6 +690,7 @@ struct Launch {  // one grouped GEMM launch
   TcTile* tiles_by_out = nullptr;   // the same tiles grouped by output block
   std::vector<int> out_begin;       // per output: first tile in tiles_by_out (+ end)
   TcSeg* segs = nullptr;
+  TcOut* seg_outs = nullptr;        // per segment: the output of a piece (pieced tiles)
   int n_tiles = 0;
   int ntile_max = 16;
   int acc_cols = 16;         // TMEM columns per accumulator buffer (all slots)
@@ -683,7 +737,7 @@ struct State {
 };
 
 void free_launch(Launch& l) {
-  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs})
+  for (void* p : {(void*)l.tiles, (void*)l.tiles_by_out, (void*)l.segs, (void*)l.seg_outs})
     if (p) cudaFree(p);
   l = Launch{};
 }
@@ -837,6 +891,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   struct Build {
     std::vector<TcTile> tiles;
     std::vector<TcSeg> segs;
+    std::vector<TcOut> seg_outs;  // parallel to segs
     std::vector<TcOut> outs;
     std::vector<int64_t> weight;
     int ntile_max = 16;
@@ -871,6 +926,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     B.outs.push_back(o);
     const int s0 = (int)B.segs.size();
     B.segs.insert(B.segs.end(), sg.begin(), sg.end());
+    B.seg_outs.resize(B.segs.size());
     const int s1 = (int)B.segs.size();
     int64_t kw = 0;
     for (const TcSeg& g : sg) kw += g.kchunks;
@@ -903,10 +959,9 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
         B.weight.push_back(kw * (int64_t)t.ntile + 64);
       }
   };
-  // phase 1
-  for (size_t i = 0; i < np; ++i) {
+  // phase 1: the output (an operand panel of phase 2) of a two-GEMM pair
+  auto ph1_out = [&](size_t i) {
     const EPair& e = P[i];
-    if (e.flags & (DMRG_ID_A | DMRG_ID_B)) continue;
     const int64_t ro = r[e.s_out], ri = r[e.s_in], co = c[e.s_out], ci = c[e.s_in];
     TcOut o{};
     o.kind = OUT_PANEL;
@@ -917,17 +972,102 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     if (e.order == 1) {  // X_b = Psi_b B^T : rows (b, a'), cols beta; stored as X^T rows (b, beta), k = a'
       o.Rm = (int32_t)pad8(ri);
       o.Rv = (int32_t)ri;
-      o.M = (int32_t)(nb * o.Rm);
       o.N = (int32_t)co;
       o.Np = (int32_t)pad8(co);
-      add_out(L1, o, {seg(psiP[e.s_in], pB[i])}, {});
     } else {  // Z_b^T = Psi_b^T A^T : rows (b, beta'), cols alpha; stored as Z rows (b, alpha), k = beta'
       o.Rm = (int32_t)pad8(ci);
       o.Rv = (int32_t)ci;
-      o.M = (int32_t)(nb * o.Rm);
       o.N = (int32_t)ro;
       o.Np = (int32_t)pad8(ro);
-      add_out(L1, o, {seg(psiPT[e.s_in], pA[i])}, {});
+    }
+    o.M = (int32_t)(nb * o.Rm);
+    return o;
+  };
+  auto ph1_seg = [&](size_t i) {
+    const EPair& e = P[i];
+    return e.order == 1 ? seg(psiP[e.s_in], pB[i]) : seg(psiPT[e.s_in], pA[i]);
+  };
+  // Pairs that share the L operand (same s_in and order) are packed side by
+  // side along N into pieced tiles of at most max_ntile columns (each piece
+  // 16-column aligned), so one L tile feeds several products; pairs wider
+  // than half a tile keep tiles of their own.
+  std::vector<std::vector<size_t>> by_in(2 * (size_t)S);
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (e.flags & (DMRG_ID_A | DMRG_ID_B)) continue;
+    const TcOut o = ph1_out(i);
+    if (cdiv(o.N, 16) * 16 * 2 > max_ntile) {
+      add_out(L1, o, {ph1_seg(i)}, {});
+      continue;
+    }
+    by_in[(size_t)e.order * S + e.s_in].push_back(i);
+  }
+  for (auto& grp : by_in) {
+    if (grp.empty()) continue;
+    std::stable_sort(grp.begin(), grp.end(), [&](size_t a, size_t b) { return ph1_out(a).N > ph1_out(b).N; });
+    std::vector<std::vector<size_t>> bins;
+    std::vector<int64_t> used;
+    for (size_t i : grp) {  // first fit, widest first
+      const int64_t w = cdiv(ph1_out(i).N, 16) * 16;
+      size_t k = 0;
+      while (k < bins.size() && (used[k] + w > max_ntile || bins[k].size() >= 16)) ++k;
+      if (k == bins.size()) {
+        bins.emplace_back();
+        used.push_back(0);
+      }
+      bins[k].push_back(i);
+      used[k] += w;
+    }
+    for (size_t k = 0; k < bins.size(); ++k) {
+      std::vector<TcSeg> sg;
+      std::vector<TcOut> so;
+      uint64_t cmap = 0;
+      int32_t col = 0, ra = 0;
+      const TcOut o0 = ph1_out(bins[k][0]);
+      for (size_t pi = 0; pi < bins[k].size(); ++pi) {
+        const size_t i = bins[k][pi];
+        const TcOut o = ph1_out(i);
+        TcSeg g = ph1_seg(i);
+        check(o.M == o0.M && o.Rm == o0.Rm && g.kchunks == ph1_seg(bins[k][0]).kchunks &&
+                  g.l == ph1_seg(bins[k][0]).l, "pieces share L");
+        check(g.r_atoms == cdiv(o.N, 8) && g.l_atoms == cdiv(o.M, 8), "piece operand rows");
+        g.col0 = col;
+        g.ra = (int32_t)cdiv(o.N, 8);
+        const int32_t w = (int32_t)cdiv(o.N, 16) * 16;
+        for (int32_t cc = col / 16; cc < (col + w) / 16; ++cc) cmap |= (uint64_t)pi << (4 * cc);
+        col += w;
+        ra += g.ra;
+        sg.push_back(g);
+        so.push_back(o);
+      }
+      check(col <= max_ntile && col % 16 == 0 && col <= 256, "pieced tile width");
+      const int32_t s0 = (int32_t)L1.segs.size();
+      L1.segs.insert(L1.segs.end(), sg.begin(), sg.end());
+      L1.seg_outs.insert(L1.seg_outs.end(), so.begin(), so.end());
+      const int32_t s1 = (int32_t)L1.segs.size();
+      const int oid = (int)L1.outs.size();
+      L1.outs.push_back(o0);
+      for (int32_t m0 = 0; m0 < o0.M; m0 += 128) {
+        TcTile t{};
+        t.m0 = m0;
+        t.n0 = 0;
+        t.ntile = col;
+        t.la = (int32_t)std::min<int64_t>(16, cdiv(o0.M - m0, 8));
+        t.ra = ra;
+        t.seg_begin = s0;
+        t.seg_end = s1;
+        t.out = oid;
+        t.slot_used = 1;
+        t.pieced = 1;
+        t.cmap_lo = (uint32_t)cmap;
+        t.cmap_hi = (uint32_t)(cmap >> 32);
+        t.o = o0;
+        check(t.m0 / 8 + t.la <= cdiv(o0.M, 8), "tile past its panels");
+        L1.acc_cols = std::max(L1.acc_cols, col);
+        L1.ntile_max = std::max(L1.ntile_max, col);
+        L1.tiles.push_back(t);
+        L1.weight.push_back((int64_t)sg[0].kchunks * col + 64);
+      }
     }
   }
   // groups E and S per output sector
@@ -999,6 +1139,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       if (B.tiles[i].out != B.tiles[i - 1].out) L.out_begin.push_back((int)i);
     L.out_begin.push_back((int)B.tiles.size());
     L.segs = up(B.segs);
+    L.seg_outs = up(B.seg_outs);
     L.n_tiles = (int)t.size();
     L.ntile_max = B.ntile_max;
     L.acc_cols = B.acc_cols;
@@ -1164,13 +1305,13 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
     for (size_t o = 0; o + 1 < L.out_begin.size(); ++o) {
       const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
       tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
-          L.tiles_by_out + b0, n, L.segs, y, sb->D, sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms, accumulate, skip,
+          L.tiles_by_out + b0, n, L.segs, L.seg_outs, y, sb->D, sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms, accumulate, skip,
           sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, n_acc, 0, sb->test_stall);
     }
     return;
   }
   const int grid = std::min(L.n_tiles, s->num_sms);
-  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, y, sb->D,
+  tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.seg_outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms,
                                                        accumulate, skip,
                                                        sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
