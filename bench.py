@@ -13,9 +13,10 @@ refinement's float64 residual products after the first give H psi and the
 per-term dots in one pass).  value = algorithmic H*psi
 flops executed in the step / step time.
 
-roofline: the product kernel with the larger share of the step (tensor-core
-or float64), its algorithmic flops per product / its event-timed duration,
-against its peak; roofline_kernels lists both.  traffic: DRAM bytes per
+roofline: the product kernel with the largest event-timed share of the step
+(tensor-core, float64, or float64 with the per-term dots), its algorithmic
+flops per product / its event-timed duration, against its peak;
+roofline_kernels lists all three.  traffic: DRAM bytes per
 product from the committed ncu record (profiles/traffic.json), reported only
 while the kernel sources still hash to the recorded value.
 
@@ -430,13 +431,23 @@ def main():
             "ms_per_step": n_mixed * mv_ms}
     pk64 = FP64_FMA_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
     a_64 = flops_mv / (mv64_ms / 1e3) / 1e12
+    newton = prec != "fp64" and args.refine == "newton"
+    n_dots = max(0, n_f64 - 1) if newton else 0
     kernels["fp64_product"] = {
         "bound": "alu", "achieved": a_64, "peak": pk64, "unit": "TFLOP/s", "frac": a_64 / pk64,
         "traffic": recorded_traffic("fp64_product"),
-        "kernel": "grouped float64 product (3 launches per dmrg_apply_H; the gradient's dot pass is the same kernel)",
+        "kernel": "grouped float64 product, seg_gemm_f64_kernel (3 launches per dmrg_apply_H)",
         "peak_source": f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz (median SM clock of the timed region)",
-        "ms_per_step": (n_f64 * mv64_ms + t_grad if prec == "fp64" or args.refine != "newton"
-                        else mv64_ms + max(0, n_f64 - 1) * t_pdot)}
+        "ms_per_step": (n_f64 - n_dots) * mv64_ms + (0.0 if newton else t_grad)}
+    if n_dots:
+        a_d = flops_mv / (t_pdot / 1e3) / 1e12
+        kernels["fp64_product_with_dots"] = {
+            "bound": "alu", "achieved": a_d, "peak": pk64, "unit": "TFLOP/s", "frac": a_d / pk64,
+            "traffic": None,
+            "kernel": "float64 product with the per-term dots (unscaled intermediates + seg_gemm_f64_dots_kernel, "
+                      "the refinement's residuals after the first)",
+            "peak_source": f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz",
+            "ms_per_step": n_dots * t_pdot}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     roof = dict(kernels[dom])
     roof["share_of_step"] = roof["ms_per_step"] / ms_per_step

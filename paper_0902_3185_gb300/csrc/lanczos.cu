@@ -519,14 +519,19 @@ __global__ void k_div_rows(double* __restrict__ v, const double* __restrict__ nr
   v[i] /= nrm2[i / n_terms];
 }
 
-// dc[b*n_terms + k] = sum of the dot-tile partials of (b, k), in list order
-__global__ void k_reduce_terms(const double* __restrict__ part, const int32_t* __restrict__ ptr,
-                               const int32_t* __restrict__ idx, double* __restrict__ out, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// dc[b*n_terms + k] = sum of the dot-tile partials of (b, k): one block per
+// (b, k), thread-strided sums over its list, then a fixed-order block
+// reduction (deterministic)
+__global__ void __launch_bounds__(256)
+k_reduce_terms(const double* __restrict__ part, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+               double* __restrict__ out, int n) {
+  __shared__ double red[256 / 32];
+  const int i = blockIdx.x;
   if (i >= n) return;
   double t = 0.0;
-  for (int q = ptr[i]; q < ptr[i + 1]; ++q) t += part[idx[q]];
-  out[i] = t;
+  for (int q = ptr[i] + threadIdx.x; q < ptr[i + 1]; q += blockDim.x) t += part[idx[q]];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) out[i] = t;
 }
 
 // ------------------------------------------------------------- launchers
@@ -593,7 +598,7 @@ void lz_launch_div_rows(double* v, const double* nrm2, int n_terms, int batch, c
 void lz_launch_reduce_terms(const double* part, const int32_t* ptr, const int32_t* idx, double* out, int n,
                             cudaStream_t st) {
   if (n == 0) return;
-  k_reduce_terms<<<(n + 127) / 128, 128, 0, st>>>(part, ptr, idx, out, n);
+  k_reduce_terms<<<n, 256, 0, st>>>(part, ptr, idx, out, n);
 }
 
 }  // namespace dmrg
