@@ -186,9 +186,10 @@ dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, do
 /* Autotuner of the tensor-core product (no paper counterpart; the paper's
  * block loop has no tuning): times the product of this superblock, `reps`
  * launches per candidate after a warm-up, for every tile width (64, 128,
- * and 256 for TF32) and tile order (heaviest first, or as built), keeps the
- * fastest, and also times the baseline that launches one kernel per output
- * block.  Rebuilds task lists and operand panels (allocates); invalidates
+ * and 256 for TF32), tile order (heaviest first, or as built) and phase-1
+ * packing (pairs sharing their wavefunction operand side by side in one
+ * tile, or one tile set per pair), keeps the fastest, and also times the
+ * baseline that launches one kernel per output block.  Rebuilds task lists and operand panels (allocates); invalidates
  * captured Lanczos graphs.  Synchronises the stream. */
 typedef struct {
   double best_ms;        /* median product time with the chosen tuning */
@@ -197,7 +198,7 @@ typedef struct {
   int32_t best_tile_n;   /* chosen widest MMA N */
   int32_t heavy_first;   /* chosen tile order */
   int32_t candidates;
-  int32_t pad;
+  int32_t pieces;        /* chosen phase-1 packing (1: pairs side by side) */
 } dmrg_tune_info;
 dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream, dmrg_tune_info* info);
 

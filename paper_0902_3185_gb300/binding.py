@@ -56,7 +56,7 @@ class _Info(C.Structure):
 class TuneInfo(C.Structure):
     _fields_ = [("best_ms", C.c_double), ("default_ms", C.c_double), ("per_block_ms", C.c_double),
                 ("best_tile_n", C.c_int32), ("heavy_first", C.c_int32), ("candidates", C.c_int32),
-                ("pad", C.c_int32)]
+                ("pieces", C.c_int32)]
 
 
 class LanczosOpts(C.Structure):

@@ -1086,7 +1086,7 @@ dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream,
     return DMRG_EUNSUPPORTED;
   }
   return guard(sb, [&] {
-    double out[6] = {};
+    double out[7] = {};
     tc_autotune(sb, prec, reps, (cudaStream_t)stream, out);
     // captured graphs hold the old task lists
     for (int i = 0; i < 8; ++i)
@@ -1102,6 +1102,7 @@ dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream,
       info->best_tile_n = (int32_t)out[3];
       info->heavy_first = (int32_t)out[4];
       info->candidates = (int32_t)out[5];
+      info->pieces = (int32_t)out[6];
     }
     return DMRG_OK;
   });

@@ -723,6 +723,7 @@ struct Tune {         // picked by dmrg_autotune
   int max_ntile = 0;  // widest MMA N of a tile (0: default per precision)
   int heavy_first = 1;  // deal the heaviest tiles first (else build order)
   int per_block = 0;  // baseline: one launch per output block instead of one persistent launch
+  int pieces = 1;     // phase 1: pack pairs sharing their L operand side by side (pieced tiles)
 };
 
 struct State {
@@ -996,7 +997,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     const EPair& e = P[i];
     if (e.flags & (DMRG_ID_A | DMRG_ID_B)) continue;
     const TcOut o = ph1_out(i);
-    if (cdiv(o.N, 16) * 16 * 2 > max_ntile) {
+    if (!tune.pieces || cdiv(o.N, 16) * 16 * 2 > max_ntile) {
       add_out(L1, o, {ph1_seg(i)}, {});
       continue;
     }
@@ -1368,14 +1369,15 @@ void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out) 
   double best_ms = 1e30, default_ms = 0;
   int tried = 0;
   for (int w : widths)
-    for (int hf : {1, 0}) {
-      s->tune[fi] = Tune{w, hf, 0};
-      build_fmt(sb, s, fi);
-      const double t = time_it();
-      ++tried;
-      if (w == (prec == DMRG_TF32 ? 256 : 128) && hf == 1) default_ms = t;
-      if (t < best_ms) { best_ms = t; best = s->tune[fi]; }
-    }
+    for (int hf : {1, 0})
+      for (int pc : {1, 0}) {
+        s->tune[fi] = Tune{w, hf, 0, pc};
+        build_fmt(sb, s, fi);
+        const double t = time_it();
+        ++tried;
+        if (w == (prec == DMRG_TF32 ? 256 : 128) && hf == 1 && pc == 1) default_ms = t;
+        if (t < best_ms) { best_ms = t; best = s->tune[fi]; }
+      }
   s->tune[fi] = best;
   s->tune[fi].per_block = 1;
   build_fmt(sb, s, fi);
@@ -1392,6 +1394,7 @@ void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out) 
   out[3] = best.max_ntile;
   out[4] = best.heavy_first;
   out[5] = tried;
+  out[6] = best.pieces;
   (void)start;
 }
 
