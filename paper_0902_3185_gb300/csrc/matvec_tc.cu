@@ -24,11 +24,13 @@
 //
 // One persistent kernel runs a list of output tiles (128 x up to 256) per
 // launch: warp 0 streams operand tiles through a multi-stage shared-memory
-// ring, warp 1 issues tcgen05.mma into a double-buffered TMEM accumulator,
-// warps 2-13 drain the accumulator (tcgen05.ld) and either write the float64
-// output block or the next phase's operand panel (scaled by the member's
+// ring, warp 1 issues tcgen05.mma into two or three TMEM accumulator buffers,
+// warps 2-13 drain them (tcgen05.ld) and either write the float64 output
+// block or the next phase's operand panel (scaled by the member's
 // coefficient, rounded to TF32 or split into BF16 hi + lo, written in 16-byte
-// granules after a transpose across lanes).
+// granules after a transpose through shared memory).  Phase-1 pairs that
+// share their wavefunction operand run as one "pieced" tile: their operator
+// panels side by side along N behind one L tile.
 //
 // Precisions: TF32 (kind::tf32), and BF16x3: x = hi + lo, products
 // hi*hi + hi*lo + lo*hi in kind::f16 with an FP32 accumulator.
