@@ -172,17 +172,19 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, const int32_t* __
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const StageJob* j = at[u].j;
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-      raw[u][i] = 0.0;
-      if (!at[u].ok) continue;
-      const int k = at[u].kg * G + i;
-      const int K = j->transpose ? j->r : j->c;
-      if (k < K) {
-        const double* src = xb + j->src_off;
-        raw[u][i] = j->transpose ? src[(int64_t)k * j->c + at[u].row] : src[(int64_t)at[u].row * j->c + k];
-      }
+    // 32-bit offsets inside the sector block (r * c < 2^31): first element
+    // and the step between the granule's G values
+    int first = 0, step = 1, K = 0;
+    const double* src = xb;
+    if (at[u].ok) {
+      src = xb + j->src_off;
+      K = j->transpose ? j->r : j->c;
+      first = j->transpose ? at[u].kg * G * j->c + at[u].row : at[u].row * j->c + at[u].kg * G;
+      step = j->transpose ? j->c : 1;
     }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+      raw[u][i] = (at[u].ok && at[u].kg * G + i < K) ? src[first + i * step] : 0.0;
   }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -191,7 +193,7 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, const int32_t* __
     const float scf = j->term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j->term]) : 1.0f;
     float v[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) v[i] = tc::d2f_rn(raw[u][i]) * scf;
+    for (int i = 0; i < G; ++i) v[i] = tc::d2f_rn32(raw[u][i]) * scf;
     const int64_t o = panel_off((int64_t)b * ((at[u].rows + 7) & ~7) + at[u].row, (int64_t)at[u].kg * G, j->atoms, es);
     if (PREC == DMRG_TF32) {
       const uint4 w = make_uint4(__float_as_uint(tc::round_tf32(v[0])), __float_as_uint(tc::round_tf32(v[1])),
@@ -866,6 +868,8 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   int64_t n_gran = 0;
   auto add_job = [&](int s, int transpose, int term, const Panel& p) {
     if ((int64_t)r[s] * c[s] == 0) return;
+    if ((int64_t)r[s] * c[s] >= INT32_MAX)
+      throw std::logic_error("tensor-core staging: sector block too large for 32-bit offsets");
     StageJob j{};
     j.src_off = sb->off[s];
     j.first = n_gran;

@@ -197,9 +197,31 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return __uint_as_float(sign | bits);
 }
 
+// double -> float, round to nearest even, with 32-bit integer instructions
+// when the result is a normal float (the common case: one exponent test, the
+// 23 kept mantissa bits and a round-half-even increment whose carry moves
+// into the exponent); zeros, subnormal results, overflow, inf and NaN take
+// d2f_rn.
+__device__ __forceinline__ float d2f_rn32(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {  // float exponent e - 896 in 1..254
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    const uint32_t up = (uint32_t)(rem > 0x10000000u) | ((uint32_t)(rem == 0x10000000u) & m);
+    return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + m + (up & 1u)));
+  }
+  return d2f_rn(x);
+}
+
 // float -> double, exact
 __device__ __forceinline__ double f2d_exact(float f) {
   const uint32_t u = __float_as_uint(f);
+  const uint32_t ef = (u >> 23) & 0xffu;
+  if (ef - 1u < 254u) {  // normal float: rebias the exponent, shift the mantissa into place (32-bit halves)
+    const uint32_t m = u & 0x7fffffu;
+    return __hiloint2double((int)((u & 0x80000000u) | ((ef + 896u) << 20) | (m >> 3)), (int)(m << 29));
+  }
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
   const uint32_t e = (u >> 23) & 0xff;
   uint32_t m = u & 0x7fffffu;
