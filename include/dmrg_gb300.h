@@ -186,7 +186,7 @@ dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, do
 /* Autotuner of the tensor-core product (no paper counterpart; the paper's
  * block loop has no tuning): times the product of this superblock, `reps`
  * launches per candidate after a warm-up, for every tile width (64, 128,
- * and 256 for TF32), tile order (heaviest first, or as built) and phase-1
+ * 256), tile order (heaviest first, or as built) and phase-1
  * packing (pairs sharing their wavefunction operand side by side in one
  * tile, or one tile set per pair), keeps the fastest, and also times the
  * baseline that launches one kernel per output block.  Rebuilds task lists and operand panels (allocates); invalidates

@@ -233,18 +233,63 @@ __global__ void k_finalize_ab(const double* __restrict__ h, const double* __rest
   }
 }
 
-// Number of eigenvalues of T (diagonal a, off-diagonal e) below x: the
-// negative pivots of T - x I = L D L^T (Sylvester's law of inertia); a zero
-// pivot is nudged off zero.
+// Sign and zero test of a float / double from its bit pattern (integer
+// instructions: GB300's float64 pipe is narrow), and its biased exponent.
+__device__ __forceinline__ bool is_neg(float v) { return __float_as_int(v) < 0; }
+__device__ __forceinline__ bool is_neg(double v) { return __double2hiint(v) < 0; }
+__device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) & 0x7fffffff) == 0; }
+__device__ __forceinline__ bool is_zero(double v) {
+  return ((__double2hiint(v) & 0x7fffffff) | __double2loint(v)) == 0;
+}
+__device__ __forceinline__ int bexp(float v) { return (__float_as_int(v) >> 23) & 0xff; }
+__device__ __forceinline__ int bexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+// 2^(bias - e) for a biased exponent e: the factor that brings e to the bias
+__device__ __forceinline__ float pow2_to_one(int e, float) { return __int_as_float((254 - e) << 23); }
+__device__ __forceinline__ double pow2_to_one(int e, double) { return __hiloint2double((2046 - e) << 20, 0); }
+template <class T> struct SturmWindow;  // rescale when the larger minor leaves 2^(+-W)
+template <> struct SturmWindow<float> { static constexpr int bias = 127, W = 30; };
+template <> struct SturmWindow<double> { static constexpr int bias = 1023, W = 400; };
+
+// Power of two s with s * scale in [1/2, 1) (scale >= 1): Sturm counts are
+// evaluated on s (T - x I), whose entries are then O(1).
+__device__ __forceinline__ double sturm_scale(double scale) {
+  return __hiloint2double((2046 - bexp(scale) - 1) << 20, 0);
+}
+
+// Number of eigenvalues of T (diagonal a, off-diagonal squares e2) below x.
+// The leading principal minors p_i of s (T - x I) obey p_0 = 1,
+// p_1 = s (a_0 - x), p_{i+1} = s (a_i - x) p_i - s^2 e2_{i-1} p_{i-1}; each
+// sign change between consecutive minors is a negative pivot of the L D L^T
+// factorisation, and by Sylvester's law of inertia their number is the
+// count.  The recurrence needs no division (one fused multiply-add on its
+// dependency chain per step); rounding each term is a relative perturbation
+// of a_i - x or e2_{i-1}, as in the pivot form.  When the larger of the last
+// two minors leaves the exponent window both are scaled by the same power of
+// two (exact); a zero minor takes its predecessor's sign, which puts the
+// sign change on the next minor.
 template <class T>
-__device__ int sturm_count(const T* a, const T* e2, int n, T x, T tiny) {
-  int cnt = 0;
-  T d = a[0] - x;
-  if (d < T(0)) ++cnt;
+__device__ int sturm_count(const T* a, const T* e2, int n, T x, T s) {
+  constexpr int bias = SturmWindow<T>::bias, W = SturmWindow<T>::W;
+  const T s2 = s * s;
+  T pm = T(1);
+  T p = (a[0] - x) * s;
+  bool neg = is_neg(p) && !is_zero(p);
+  int cnt = neg ? 1 : 0;
   for (int i = 1; i < n; ++i) {
-    if (d == T(0)) d = tiny;
-    d = (a[i] - x) - e2[i - 1] / d;
-    if (d < T(0)) ++cnt;
+    const T t = (a[i] - x) * s;
+    const T q = (e2[i - 1] * s2) * pm;
+    const T pn = fma(t, p, -q);
+    const bool nn = is_zero(pn) ? neg : is_neg(pn);
+    cnt += nn != neg;
+    neg = nn;
+    pm = p;
+    p = pn;
+    const int em = max(bexp(p), bexp(pm));
+    if (em > bias + W || (em < bias - W && em > 0)) {
+      const T f = pow2_to_one(em, T(0));
+      p *= f;
+      pm *= f;
+    }
   }
   return cnt;
 }
@@ -253,14 +298,14 @@ __device__ int sturm_count(const T* a, const T* e2, int n, T x, T tiny) {
 // spaced points of [lo, hi] (count(lo) = 0 <= 1 <= count(hi) ... holds for
 // the lowest eigenvalue) and keep the sub-interval that holds it.
 template <class T>
-__device__ void multisection(const T* a, const T* e2, int n, T& lo, T& hi, T rel, int max_rounds, T tiny) {
+__device__ void multisection(const T* a, const T* e2, int n, T& lo, T& hi, T rel, int max_rounds, T s) {
   const int lane = threadIdx.x & 31;
   for (int round = 0; round < max_rounds; ++round) {
     const T w = hi - lo;
     if (!(w > rel * fmax(fabs(lo), fabs(hi))) || !(w > T(0))) break;
     const T step = w / T(33);
     const T x = lo + step * T(lane + 1);
-    const int cnt = sturm_count<T>(a, e2, n, x, tiny);
+    const int cnt = sturm_count<T>(a, e2, n, x, s);
     const unsigned ball = __ballot_sync(0xffffffffu, cnt >= 1);
     const int f = ball ? __ffs(ball) - 1 : 32;  // first point with an eigenvalue below it
     const T nlo = lo + step * T(f);
@@ -272,26 +317,40 @@ __device__ void multisection(const T* a, const T* e2, int n, T& lo, T& hi, T rel
 
 // Inverse iteration with a shift below lambda_min: T - sigma I is positive
 // definite, so its L D L^T factorisation needs no pivoting.  Lane 0 factors
-// once (reciprocal pivots) and solves `solves` times; returns in z the
-// normalised eigenvector estimate with z[0] >= 0.
+// once (reciprocal pivots rpiv, multipliers lm) and solves `solves` times,
+// from z = 1 or, with `given`, from the z passed in; returns in z the
+// normalised eigenvector estimate with z[0] >= 0.  Each solve is one forward
+// sweep (L y = z, then D^-1) and one backward sweep (L^T) that also
+// accumulates |z|^2.
 template <class T>
-__device__ void inverse_iteration(const T* a, const T* e, int n, T sigma, T* z, T* rpiv, int solves, T tiny) {
+__device__ void inverse_iteration(const T* a, const T* e, int n, T sigma, T* z, T* rpiv, T* lm, int solves, T tiny,
+                                  bool given) {
   if ((threadIdx.x & 31) != 0) return;
   T dp = a[0] - sigma;
   rpiv[0] = T(1) / (dp == T(0) ? tiny : dp);
   for (int i = 1; i < n; ++i) {
     const T l = e[i - 1] * rpiv[i - 1];
+    lm[i - 1] = l;
     dp = (a[i] - sigma) - l * e[i - 1];
     rpiv[i] = T(1) / (dp == T(0) ? tiny : dp);
   }
-  for (int i = 0; i < n; ++i) z[i] = T(1);
+  if (!given)
+    for (int i = 0; i < n; ++i) z[i] = T(1);
   for (int it = 0; it < solves; ++it) {
-    for (int i = 1; i < n; ++i) z[i] -= (e[i - 1] * rpiv[i - 1]) * z[i - 1];
-    for (int i = 0; i < n; ++i) z[i] *= rpiv[i];
-    for (int i = n - 2; i >= 0; --i) z[i] -= (e[i] * rpiv[i]) * z[i + 1];
-    T nz = T(0);
-    for (int i = 0; i < n; ++i) nz = fma(z[i], z[i], nz);
-    const T inv = (z[0] < T(0) ? T(-1) : T(1)) / sqrt(nz);
+    T y = z[0];
+    z[0] = y * rpiv[0];
+    for (int i = 1; i < n; ++i) {
+      y = fma(-lm[i - 1], y, z[i]);
+      z[i] = y * rpiv[i];
+    }
+    T zn = z[n - 1];
+    T nz = zn * zn;
+    for (int i = n - 2; i >= 0; --i) {
+      zn = fma(-lm[i], zn, z[i]);
+      z[i] = zn;
+      nz = fma(zn, zn, nz);
+    }
+    const T inv = (zn < T(0) ? T(-1) : T(1)) / sqrt(nz);  // zn = z[0]
     for (int i = 0; i < n; ++i) z[i] *= inv;
   }
 }
@@ -371,9 +430,12 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
   const float eps32 = 1.2e-7f;
   const float slack = (float)(8.0 * n * 6e-8 * scale_t);  // rounding of T to float32, Sturm backward error
   float lo = (float)glo - slack, hi = (float)ghi + slack;
-  multisection<float>(a32, e232, n, lo, hi, 4.0f * eps32, 12, 1e-30f);
+  const double ssc = sturm_scale(scale_t);
+  multisection<float>(a32, e232, n, lo, hi, 4.0f * eps32, 12, (float)ssc);
   const float th32 = 0.5f * (lo + hi);
-  inverse_iteration<float>(a32, e32, n, lo - 2.0f * slack - 1e-6f * (float)scale_t, z32, rp32, 3, 1e-30f);
+  // the multipliers overwrite e2 (the Sturm counts are done)
+  inverse_iteration<float>(a32, e32, n, lo - 2.0f * slack - 1e-6f * (float)scale_t, z32, rp32, e232, 3, 1e-30f,
+                           false);
   __syncwarp();
   const double est = beta * fabs((double)z32[n - 1]);
   const bool pass32 = est <= tol * fmax(1.0, fabs((double)th32));
@@ -389,11 +451,19 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
   // ---- float64 eigenpair
   double lo64 = (double)lo - 2.0 * slack, hi64 = (double)hi + 2.0 * slack;
   lo64 = fmax(lo64, glo - 1e-300);
-  if (sturm_count<double>(a, e2, n, lo64, 1e-300) != 0) lo64 = glo - 1e-300;  // bracket must hold lambda_min
-  if (sturm_count<double>(a, e2, n, hi64, 1e-300) == 0) hi64 = ghi + 1e-12 * scale_t;
-  multisection<double>(a, e2, n, lo64, hi64, 4.0 * 2.2e-16, 64, 1e-300);
+  {  // the bracket must hold lambda_min: lane 0 counts at lo64, lane 1 at hi64
+    const int c = sturm_count<double>(a, e2, n, lane == 0 ? lo64 : hi64, ssc);
+    const int c_lo = __shfl_sync(0xffffffffu, c, 0), c_hi = __shfl_sync(0xffffffffu, c, 1);
+    if (c_lo != 0) lo64 = glo - 1e-300;
+    if (c_hi == 0) hi64 = ghi + 1e-12 * scale_t;
+  }
+  multisection<double>(a, e2, n, lo64, hi64, 4.0 * 2.2e-16, 64, ssc);
   const double theta = 0.5 * (lo64 + hi64);
-  inverse_iteration<double>(a, e, n, lo64 - 4.0 * 2.2e-16 * scale_t, z, rp, 2, 1e-300);
+  // one solve from the float32 eigenvector: the shift is within a few ulps of
+  // lambda_min, so a solve reduces the error by (lambda_1 - sigma) / gap
+  for (int i = lane; i < n; i += 32) z[i] = isfinite(z32[i]) ? (double)z32[i] : 1.0;
+  __syncwarp();
+  inverse_iteration<double>(a, e, n, lo64 - 4.0 * 2.2e-16 * scale_t, z, rp, e2, 1, 1e-300, true);
   __syncwarp();
   if (lane == 0) {
     const double resid = beta * fabs(z[n - 1]);

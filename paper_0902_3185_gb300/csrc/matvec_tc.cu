@@ -16,8 +16,8 @@
 //
 // Every product is D = L R^T with both operands K-major, so operands are
 // kept in HBM already in the tensor cores' shared-memory image ("panels"):
-// 8-row atoms of 128-byte rows with the 128-byte swizzle, atoms of one
-// 128-byte K chunk stored contiguously.  A tile load is then one contiguous
+// 8-row atoms of 64-byte rows with the 64-byte swizzle, atoms of one
+// 64-byte K chunk stored contiguously.  A tile load is then one contiguous
 // cp.async.bulk per operand and no tensor maps are needed.  Zero padding in
 // K is written once; padding rows only feed accumulator rows/columns that
 // are never stored.
@@ -94,111 +94,95 @@ struct TcTile {
   TcOut o;                        // the output this tile belongs to (a copy: one load per tile)
 };
 
-struct StageJob {
-  int64_t src_off;    // sector block offset inside a member
-  int64_t first;      // first granule of this job in the flattened stream
-  char* p;
-  int64_t p_lo;
-  int32_t r, c;       // source block dims
-  int32_t transpose, term;
-  int32_t atoms;
-  int32_t nkg;        // granules per panel row: ceil(K / values per granule)
+struct StageOut {  // one operand panel fed by a sector block
+  char* p;          // hi panel (BF16x3: the lo panel follows at the arena's lo offset)
+  int32_t atoms;    // 8-row atoms per K chunk (member-stacked rows / 8)
+  int32_t transpose;  // panel rows are the block's columns (K = block rows)
+  int32_t term;     // scale by the member's coefficient of this term (-1: none)
+  int32_t pad_;
 };
+
+struct StageTile {  // a STAGE_T x STAGE_T tile of one sector block
+  int64_t src_off;  // sector block offset inside a member
+  int32_t r, c;     // block dims
+  int32_t r0, c0;   // tile origin
+  int32_t out_begin, out_end;  // its panels
+};
+
+// Operand panel layout: K split into chunks of PANEL_ROW_BYTES (32 BF16 or
+// 16 TF32 values: the sector blocks are narrow, and shorter chunks pad K
+// less), rows into 8-row atoms of ATOM_BYTES with the 64-byte swizzle (the
+// 16-byte piece q of row r of an atom is stored at piece q ^ ((r >> 1) & 3)),
+// all atoms of one K chunk contiguous.
+constexpr int PANEL_ROW_BYTES = 64;
+constexpr int ATOM_BYTES = 8 * PANEL_ROW_BYTES;
+constexpr int MMA_K_STEPS = PANEL_ROW_BYTES / 32;  // one MMA consumes 32 bytes of K
+__host__ __device__ constexpr int swz(int piece, int r8) { return piece ^ ((r8 >> 1) & 3); }
 
 // byte offset of element (row, k) inside a panel
 __host__ __device__ inline int64_t panel_off(int64_t row, int64_t k, int64_t atoms, int es) {
-  const int64_t kce = 128 / es;
+  const int64_t kce = PANEL_ROW_BYTES / es;
   const int64_t kc = k / kce, kk = k - kc * kce;
   const int64_t atom = row >> 3, r8 = row & 7;
   const int64_t byte = kk * es;
-  const int64_t chunk = (byte >> 4) ^ r8;
-  return (kc * atoms + atom) * 1024 + r8 * 128 + (chunk << 4) + (byte & 15);
+  return (kc * atoms + atom) * ATOM_BYTES + r8 * PANEL_ROW_BYTES + ((int64_t)swz((int)(byte >> 4), (int)r8) << 4) +
+         (byte & 15);
 }
 
 // ---------------------------------------------------------------- staging
-// float64 psi blocks -> operand panels (optionally transposed and scaled by
-// the member's coefficient), in 16-byte granules: 8 BF16 (hi and lo) or 4
-// TF32 consecutive K values of one panel row, converted once and written
-// with one vector store per half.  The jobs' granules form one flat stream
-// (jobs back to back, `first` = prefix).  Consecutive threads take
-// consecutive granules along the row for a plain job (each thread reads a
-// contiguous run of its row) and consecutive panel rows for a transposed job
-// (each of a thread's loads is coalesced across the warp).  Granules reaching
-// into the K padding write zeros there.  The host records the job of every
-// block's first granule (block_job), so a thread finds its job in a few
-// steps; all of a thread's loads are issued before its first conversion.
-constexpr int STAGE_GRANULES_PER_THREAD = 2;
-
-struct StageAt {  // where one granule lives
-  const StageJob* j;
-  int row, kg, rows;
-  bool ok;
-};
-
-__device__ __forceinline__ StageAt stage_find(const StageJob* __restrict__ jobs, int n_jobs, int& jid, int64_t e,
-                                              int64_t total) {
-  StageAt a{nullptr, 0, 0, 0, false};
-  if (e >= total) return a;
-  while (jid + 1 < n_jobs && jobs[jid + 1].first <= e) ++jid;
-  const StageJob* j = jobs + jid;
-  const int rows = j->transpose ? j->c : j->r;
-  const int loc = (int)(e - j->first);  // < rows * nkg: 32-bit division
-  if (!j->transpose) { a.row = loc / j->nkg; a.kg = loc - a.row * j->nkg; }  // panel row a, K = c
-  else { a.kg = loc / rows; a.row = loc - a.kg * rows; }                      // panel row c', K = a
-  a.j = j;
-  a.rows = rows;
-  a.ok = true;
-  return a;
-}
+// float64 psi blocks -> operand panels (plain or transposed, optionally
+// scaled by the member's coefficient of a term).  One CTA per 32 x 32 tile
+// of a sector block and member: the tile is read once (each warp one
+// contiguous row run), rounded to float once into shared memory, and every
+// panel the block feeds is written from there in 16-byte granules (8 BF16 hi
+// and lo, or 4 TF32 consecutive K values of one panel row; consecutive
+// threads take consecutive granules of a row, so a warp writes whole 64-byte
+// panel rows).  Tile entries outside the block are zero, so granules reaching
+// into the K padding write zeros there; padding rows are never written.
+constexpr int STAGE_T = 32;
 
 template <int PREC>
 __global__ void __launch_bounds__(256)
-tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, const int32_t* __restrict__ block_job, int64_t total,
-                const double* __restrict__ x, int64_t D, const double* __restrict__ coef, int n_terms,
+tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict__ outs, const double* __restrict__ x,
+                int64_t D, int64_t p_lo, const double* __restrict__ coef, int n_terms,
                 const int32_t* __restrict__ skip) {
   constexpr int G = PREC == DMRG_TF32 ? 4 : 8;  // values per 16-byte granule
   constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
-  constexpr int U = STAGE_GRANULES_PER_THREAD;
+  constexpr int NKG = STAGE_T / G;              // granules per tile row
+  __shared__ float tile[STAGE_T][STAGE_T + 1];
   if (skip && *skip) return;
+  const StageTile tl = tiles[blockIdx.x];
   const int b = blockIdx.y;
-  const int64_t e0 = (int64_t)blockIdx.x * (256 * U) + threadIdx.x;
-  if (e0 >= total) return;
-  int jid = block_job[blockIdx.x];
-  StageAt at[U];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int rows_t = min(STAGE_T, tl.r - tl.r0), cols_t = min(STAGE_T, tl.c - tl.c0);
+  // 32-bit offsets inside the sector block (r * c < 2^31)
+  const double* src = x + (int64_t)b * D + tl.src_off + tl.r0 * tl.c + tl.c0;
+  double raw[STAGE_T / 8];
 #pragma unroll
-  for (int u = 0; u < U; ++u) at[u] = stage_find(jobs, n_jobs, jid, e0 + (int64_t)u * 256, total);
-  const double* xb = x + (int64_t)b * D;
-  double raw[U][G];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const StageJob* j = at[u].j;
-    // 32-bit offsets inside the sector block (r * c < 2^31): first element
-    // and the step between the granule's G values
-    int first = 0, step = 1, K = 0;
-    const double* src = xb;
-    if (at[u].ok) {
-      src = xb + j->src_off;
-      K = j->transpose ? j->r : j->c;
-      first = j->transpose ? at[u].kg * G * j->c + at[u].row : at[u].row * j->c + at[u].kg * G;
-      step = j->transpose ? j->c : 1;
-    }
-#pragma unroll
-    for (int i = 0; i < G; ++i)
-      raw[u][i] = (at[u].ok && at[u].kg * G + i < K) ? src[first + i * step] : 0.0;
+  for (int i = 0; i < STAGE_T / 8; ++i) {
+    const int row = ty + 8 * i;
+    raw[i] = (row < rows_t && tx < cols_t) ? src[row * tl.c + tx] : 0.0;
   }
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    if (!at[u].ok) continue;
-    const StageJob* j = at[u].j;
-    const float scf = j->term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + j->term]) : 1.0f;
+  for (int i = 0; i < STAGE_T / 8; ++i) tile[ty + 8 * i][tx] = tc::d2f_rn32(raw[i]);
+  __syncthreads();
+  for (int o = tl.out_begin; o < tl.out_end; ++o) {
+    const StageOut so = outs[o];
+    const float scf = so.term >= 0 ? tc::d2f_rn(coef[(int64_t)b * n_terms + so.term]) : 1.0f;
+    const int prows = so.transpose ? cols_t : rows_t;            // panel rows in this tile
+    const int nkg = ((so.transpose ? rows_t : cols_t) + G - 1) / G;  // granules per panel row
+    const int pr = threadIdx.x / NKG, kg = threadIdx.x - pr * NKG;
+    if (pr >= prows || kg >= nkg) continue;
     float v[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) v[i] = tc::d2f_rn32(raw[u][i]) * scf;
-    const int64_t o = panel_off((int64_t)b * ((at[u].rows + 7) & ~7) + at[u].row, (int64_t)at[u].kg * G, j->atoms, es);
+    for (int i = 0; i < G; ++i) v[i] = (so.transpose ? tile[kg * G + i][pr] : tile[pr][kg * G + i]) * scf;
+    const int64_t panel_rows = so.transpose ? tl.c : tl.r;
+    const int64_t grow = (int64_t)b * ((panel_rows + 7) & ~7) + (so.transpose ? tl.c0 : tl.r0) + pr;
+    const int64_t o_b = panel_off(grow, (int64_t)(so.transpose ? tl.r0 : tl.c0) + kg * G, so.atoms, es);
     if (PREC == DMRG_TF32) {
       const uint4 w = make_uint4(__float_as_uint(tc::round_tf32(v[0])), __float_as_uint(tc::round_tf32(v[1])),
                                  __float_as_uint(tc::round_tf32(v[2])), __float_as_uint(tc::round_tf32(v[3])));
-      *reinterpret_cast<uint4*>(j->p + o) = w;
+      *reinterpret_cast<uint4*>(so.p + o_b) = w;
     } else {
       uint32_t wh[4], wl[4];  // hi = bf16(x), lo = bf16(x - hi), two K values per word
 #pragma unroll
@@ -206,8 +190,8 @@ tc_stage_kernel(const StageJob* __restrict__ jobs, int n_jobs, const int32_t* __
         wh[i] = tc::bf16x2_rn(v[2 * i], v[2 * i + 1]);
         wl[i] = tc::bf16x2_rn(v[2 * i] - __uint_as_float(wh[i] << 16), v[2 * i + 1] - __uint_as_float(wh[i] & 0xffff0000u));
       }
-      *reinterpret_cast<uint4*>(j->p + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-      *reinterpret_cast<uint4*>(j->p + j->p_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+      *reinterpret_cast<uint4*>(so.p + o_b) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+      *reinterpret_cast<uint4*>(so.p + p_lo + o_b) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
   }
 }
@@ -217,7 +201,7 @@ constexpr int TC_EPI_WARPS = 12;                   // three per TMEM lane quadra
 constexpr int TC_EPI_PARTS = TC_EPI_WARPS / 4;      // warps per TMEM lane quadrant
 constexpr int TC_MAX_ACC = 4;                        // accumulator buffers in TMEM
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer, MMA, epilogue
-constexpr int L_TILE_BYTES = 128 * 128;             // 128 rows x 128 B
+constexpr int L_TILE_BYTES = 128 * PANEL_ROW_BYTES;  // 128 rows of one K chunk
 constexpr int EPI_LD = 17;                          // staging row stride (doubles)
 constexpr int EPI_BYTES = TC_EPI_WARPS * 32 * EPI_LD * 8;
 // panel outputs: a warp's 16 x 32 block of packed words, column stride chosen
@@ -297,7 +281,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         tl = tl_n;
         const int tn = t + gridDim.x;
         if (tn < n_tiles) tl_n = tiles[tn];
-        const uint32_t lb = (uint32_t)tl.la * 1024u, rb = (uint32_t)tl.ra * 1024u;
+        const uint32_t lb = (uint32_t)tl.la * ATOM_BYTES, rb = (uint32_t)tl.ra * ATOM_BYTES;
         if (tl.pieced) {
           // one L tile and every piece's R rows per K chunk
           const TcSeg sg = sg_n_idx == tl.seg_begin ? sg_n : segs[tl.seg_begin];
@@ -308,14 +292,14 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           for (int kc = 0; kc < sg.kchunks; ++kc) {
             if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) goto producer_done;
             char* st = ring + (size_t)stage * stage_bytes;
-            const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * 1024;
+            const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * ATOM_BYTES;
             tc::mbar_arrive_expect_tx(&full[stage], PREC == DMRG_TF32 ? lb + rb : 2u * (lb + rb));
             tc::bulk_g2s(st, lsrc, lb, &full[stage]);
             if (PREC == DMRG_BF16X3) tc::bulk_g2s(st + L_TILE_BYTES + r_tile_bytes, lsrc + sg.l_lo, lb, &full[stage]);
             for (int q = tl.seg_begin; q < tl.seg_end; ++q) {
               const TcSeg pq = segs[q];
-              const char* rsrc = pq.r + (int64_t)kc * pq.r_atoms * 1024;
-              const uint32_t at = (uint32_t)(pq.col0 / 8) * 1024u, nb = (uint32_t)pq.ra * 1024u;
+              const char* rsrc = pq.r + (int64_t)kc * pq.r_atoms * ATOM_BYTES;
+              const uint32_t at = (uint32_t)(pq.col0 / 8) * ATOM_BYTES, nb = (uint32_t)pq.ra * ATOM_BYTES;
               tc::bulk_g2s(st + L_TILE_BYTES + at, rsrc, nb, &full[stage]);
               if (PREC == DMRG_BF16X3)
                 tc::bulk_g2s(st + 2 * L_TILE_BYTES + r_tile_bytes + at, rsrc + pq.r_lo, nb, &full[stage]);
@@ -341,8 +325,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           for (int kc = 0; kc < sg.kchunks; ++kc) {
             if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) goto producer_done;
             char* st = ring + (size_t)stage * stage_bytes;
-            const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * 1024;
-            const char* rsrc = sg.r + ((int64_t)kc * sg.r_atoms + tl.n0 / 8) * 1024;
+            const char* lsrc = sg.l + ((int64_t)kc * sg.l_atoms + tl.m0 / 8) * ATOM_BYTES;
+            const char* rsrc = sg.r + ((int64_t)kc * sg.r_atoms + tl.n0 / 8) * ATOM_BYTES;
             tc::mbar_arrive_expect_tx(&full[stage], PREC == DMRG_TF32 ? lb + rb : 2u * (lb + rb));
             tc::bulk_g2s(st, lsrc, lb, &full[stage]);
             tc::bulk_g2s(st + L_TILE_BYTES, rsrc, rb, &full[stage]);
@@ -409,19 +393,19 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
             if (!tc::mbar_wait(&full[stage], phase, abort_flag)) goto mma_done;
             tc::tc_fence_after();
             char* st = ring + (size_t)stage * stage_bytes;
-            const uint64_t ah = tc::sw128_desc(tc::smem_u32(st));
-            const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + L_TILE_BYTES));
+            const uint64_t ah = tc::sw64_desc(tc::smem_u32(st));
+            const uint64_t bh = tc::sw64_desc(tc::smem_u32(st + L_TILE_BYTES));
             if (PREC == DMRG_TF32) {
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
+              for (int k = 0; k < MMA_K_STEPS; ++k) {
                 tc::mma_tf32(d_tmem, ah + 2 * k, bh + 2 * k, idesc, accum);
                 accum = 1;
               }
             } else {
-              const uint64_t al = tc::sw128_desc(tc::smem_u32(st + L_TILE_BYTES + r_tile_bytes));
-              const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + 2 * L_TILE_BYTES + r_tile_bytes));
+              const uint64_t al = tc::sw64_desc(tc::smem_u32(st + L_TILE_BYTES + r_tile_bytes));
+              const uint64_t bl = tc::sw64_desc(tc::smem_u32(st + 2 * L_TILE_BYTES + r_tile_bytes));
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
+              for (int k = 0; k < MMA_K_STEPS; ++k) {
                 tc::mma_bf16(d_tmem, ah + 2 * k, bh + 2 * k, idesc, accum);
                 accum = 1;
                 tc::mma_bf16(d_tmem, ah + 2 * k, bl + 2 * k, idesc, 1);
@@ -580,7 +564,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           __syncwarp();
           const int cg = lane & (G - 1), g0 = lane & ~(G - 1);
           const bool gv = tl.m0 + 32 * q + g0 < o.M;  // the group's rows exist
-          constexpr int es = PREC == DMRG_TF32 ? 4 : 2, kce = 128 / es;
+          constexpr int es = PREC == DMRG_TF32 ? 4 : 2, kce = PANEL_ROW_BYTES / es;
           const int kfirst = i - cg;  // K index of row g0: a multiple of G
           const int kc = kfirst / kce;
           const int chunk = ((kfirst - kc * kce) * es) >> 4;
@@ -591,7 +575,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
             const uint32_t* src = pstg + (blk + cg) * LD + g0;
             const int prow = b * po.Np + n;
             const int r8 = prow & 7;
-            const int off = (kc * po.p_atoms + (prow >> 3)) * 1024 + r8 * 128 + ((chunk ^ r8) << 4);
+            const int off = (kc * po.p_atoms + (prow >> 3)) * ATOM_BYTES + r8 * PANEL_ROW_BYTES + (swz(chunk, r8) << 4);
             if (PREC == DMRG_TF32) {
               *reinterpret_cast<uint4*>(po.p + off) = *reinterpret_cast<const uint4*>(src);
             } else {
@@ -703,10 +687,10 @@ struct Launch {  // one grouped GEMM launch
 };
 
 struct PairSet {  // the forward pairs or their transposes
-  StageJob* jobs = nullptr;
-  int32_t* block_job = nullptr;  // staging: job of each block's first granule
-  int n_jobs = 0;
-  int64_t n_gran = 0;  // staging granules per member
+  StageTile* stage_tiles = nullptr;  // staging: psi tiles (per member) ...
+  StageOut* stage_outs = nullptr;    // ... and the panels they feed
+  int n_stage_tiles = 0;
+  int64_t p_lo = 0;                  // byte offset of the lo panels from the hi panels (BF16x3)
   Launch ph1, grpE, grpS;
 };
 
@@ -747,8 +731,8 @@ void free_launch(Launch& l) {
   l = Launch{};
 }
 void free_set(PairSet& s) {
-  if (s.jobs) cudaFree(s.jobs);
-  if (s.block_job) cudaFree(s.block_job);
+  if (s.stage_tiles) cudaFree(s.stage_tiles);
+  if (s.stage_outs) cudaFree(s.stage_outs);
   free_launch(s.ph1);
   free_launch(s.grpE);
   free_launch(s.grpS);
@@ -789,12 +773,13 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
                          PairSet& out, bool dry, const Tune& tune) {
   const int64_t nb = sb->batch;
   const int es = prec == DMRG_TF32 ? 4 : 2;
-  const int64_t kce = 128 / es;
+  const int64_t kce = PANEL_ROW_BYTES / es;
   const auto& r = sb->r;
   const auto& c = sb->c;
   const int S = sb->S;
-  // widest MMA N per tile: BF16x3 stages hold four operand tiles, so cap N at
-  // 128 to keep at least two pipeline stages in shared memory
+  // widest MMA N per tile: BF16x3 stages hold four operand tiles, so its
+  // default is 128 (more pipeline stages in shared memory); the autotuner
+  // also tries 256
   const int max_ntile = tune.max_ntile > 0 ? tune.max_ntile : (prec == DMRG_BF16X3 ? 128 : 256);
   int64_t cur = base_off;
   auto alloc = [&](int64_t rows, int64_t K) {
@@ -803,7 +788,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     p.K = K;
     p.atoms = cdiv(rows, 8);
     p.off = cur;
-    cur += p.atoms * cdiv(K, kce) * 1024;
+    cur += p.atoms * cdiv(K, kce) * ATOM_BYTES;
     return p;
   };
   const size_t np = P.size();
@@ -863,37 +848,34 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   }
   auto dptr = [&](const Panel& p) { return d_hi + p.off; };
 
-  // ---- staging jobs (one flat element stream)
-  std::vector<StageJob> jobs;
-  int64_t n_gran = 0;
-  auto add_job = [&](int s, int transpose, int term, const Panel& p) {
-    if ((int64_t)r[s] * c[s] == 0) return;
-    if ((int64_t)r[s] * c[s] >= INT32_MAX)
+  // ---- staging: the panels each sector block feeds, then its tiles
+  std::vector<std::vector<StageOut>> feeds((size_t)S);
+  auto add_feed = [&](int s_, int transpose, int term, const Panel& p) {
+    if ((int64_t)r[s_] * c[s_] >= INT32_MAX)
       throw std::logic_error("tensor-core staging: sector block too large for 32-bit offsets");
-    StageJob j{};
-    j.src_off = sb->off[s];
-    j.first = n_gran;
-    j.r = r[s];
-    j.c = c[s];
-    j.transpose = transpose;
-    j.term = term;
-    j.p = dptr(p);
-    j.p_lo = lo_delta;
-    j.atoms = (int32_t)p.atoms;
-    j.nkg = (int32_t)cdiv(transpose ? r[s] : c[s], 16 / es);  // 16-byte granules per panel row
-    jobs.push_back(j);
-    n_gran += (int64_t)(transpose ? c[s] : r[s]) * j.nkg;
+    feeds[(size_t)s_].push_back(StageOut{dptr(p), (int32_t)p.atoms, transpose, term, 0});
   };
-  for (int s = 0; s < S; ++s) {
-    if (needP[s]) add_job(s, 0, -1, psiP[s]);
-    if (needPT[s]) add_job(s, 1, -1, psiPT[s]);
+  for (int s_ = 0; s_ < S; ++s_) {
+    if (needP[s_]) add_feed(s_, 0, -1, psiP[s_]);
+    if (needPT[s_]) add_feed(s_, 1, -1, psiPT[s_]);
   }
   for (size_t i = 0; i < np; ++i) {
     const EPair& e = P[i];
     if (slot_of[i]) continue;
-    if (e.flags & DMRG_ID_A) add_job(e.s_in, 0, e.term, pS[i]);
-    else if (e.flags & DMRG_ID_B) add_job(e.s_in, 1, e.term, pS[i]);
+    if (e.flags & DMRG_ID_A) add_feed(e.s_in, 0, e.term, pS[i]);
+    else if (e.flags & DMRG_ID_B) add_feed(e.s_in, 1, e.term, pS[i]);
   }
+  std::vector<StageTile> stiles;
+  std::vector<StageOut> souts;
+  for (int s_ = 0; s_ < S; ++s_) {
+    if (feeds[(size_t)s_].empty() || (int64_t)r[s_] * c[s_] == 0) continue;
+    const int32_t ob = (int32_t)souts.size();
+    souts.insert(souts.end(), feeds[(size_t)s_].begin(), feeds[(size_t)s_].end());
+    for (int r0 = 0; r0 < r[s_]; r0 += STAGE_T)
+      for (int c0 = 0; c0 < c[s_]; c0 += STAGE_T)
+        stiles.push_back(StageTile{sb->off[s_], (int32_t)r[s_], (int32_t)c[s_], r0, c0, ob, (int32_t)souts.size()});
+  }
+  if (stiles.size() >= (size_t)INT32_MAX) throw std::logic_error("tensor-core staging: too many tiles");
   // ---- grouped launches
   struct Build {
     std::vector<TcTile> tiles;
@@ -1160,24 +1142,10 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   finish(L1, out.ph1);
   finish(LE, out.grpE);
   finish(LS, out.grpS);
-  out.jobs = up(jobs);
-  out.n_jobs = (int)jobs.size();
-  out.n_gran = n_gran;
-  {  // job of the first granule of every staging block (binary search on the prefix)
-    const int64_t per = 256 * STAGE_GRANULES_PER_THREAD;
-    std::vector<int32_t> bj((size_t)std::max<int64_t>(1, cdiv(n_gran, per)), 0);
-    for (size_t k = 0; k < bj.size(); ++k) {
-      const int64_t e = (int64_t)k * per;
-      size_t lo = 0, hi = jobs.empty() ? 0 : jobs.size() - 1;
-      while (lo < hi) {
-        const size_t mid = (lo + hi + 1) / 2;
-        if (jobs[mid].first <= e) lo = mid;
-        else hi = mid - 1;
-      }
-      bj[k] = (int32_t)lo;
-    }
-    out.block_job = up(bj);
-  }
+  out.stage_tiles = up(stiles);
+  out.stage_outs = up(souts);
+  out.n_stage_tiles = (int)stiles.size();
+  out.p_lo = lo_delta;
   return cur - base_off;
 }
 
@@ -1211,7 +1179,7 @@ int tc_launches(const dmrg_sb* sb, int prec) {
   const State* s = st_of(sb);
   if (!s || !s->ok) return 0;
   const PairSet& ps = s->f[prec == DMRG_TF32 ? 0 : 1].fwd;
-  return (ps.n_gran > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
+  return (ps.n_stage_tiles > 0) + (ps.ph1.n_tiles > 0) + (ps.grpE.n_tiles > 0) + (ps.grpS.n_tiles > 0);
 }
 
 // (Re)build the panels and task lists of one precision with its tuning.
@@ -1291,7 +1259,7 @@ template <int PREC>
 static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* sb, int accumulate,
                      const int32_t* skip, cudaStream_t st) {
   if (L.n_tiles == 0) return;
-  const int r_tile = L.ntile_max * 128;
+  const int r_tile = L.ntile_max * PANEL_ROW_BYTES;
   const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
   // epilogue staging: row-major float64 outputs, panel transposes
   const int epi = L.has_row_out ? EPI_BYTES : L.has_panel_out ? PANEL_EPI_BYTES : 0;
@@ -1328,11 +1296,9 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
 template <int PREC>
 static void run_set(const State* s, const PairSet& ps, const double* x, double* y, const dmrg_sb* sb,
                     int accumulate, const int32_t* skip, cudaStream_t st) {
-  if (ps.n_gran > 0) {
-    const int64_t blocks = cdiv(ps.n_gran, 256 * STAGE_GRANULES_PER_THREAD);
-    tc_stage_kernel<PREC><<<dim3((unsigned)blocks, sb->batch), 256, 0, st>>>(ps.jobs, ps.n_jobs, ps.block_job, ps.n_gran, x, sb->D,
-                                                                            sb->d_coeffs, sb->n_terms, skip);
-  }
+  if (ps.n_stage_tiles > 0)
+    tc_stage_kernel<PREC><<<dim3((unsigned)ps.n_stage_tiles, sb->batch), 256, 0, st>>>(
+        ps.stage_tiles, ps.stage_outs, x, sb->D, ps.p_lo, sb->d_coeffs, sb->n_terms, skip);
   run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
   run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, st);
   run_gemm<PREC>(s, ps.grpS, y, sb, accumulate, skip, st);
@@ -1368,8 +1334,7 @@ void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out) 
     std::sort(ms.begin(), ms.end());
     return (double)ms[ms.size() / 2];
   };
-  std::vector<int> widths = {64, 128};
-  if (prec == DMRG_TF32) widths.push_back(256);
+  const std::vector<int> widths = {64, 128, 256};
   const Tune start = s->tune[fi];
   Tune best = start;
   double best_ms = 1e30, default_ms = 0;

@@ -207,13 +207,13 @@ __global__ void k_rf_rho0(double* __restrict__ sc, int batch) {
 
 // gamma, rho = <res, z>, beta = rho_new / rho; stop a member at
 // |res| <= eps |b|, the cap, or a non-positive rho (preconditioned residual
-// vanished); one thread walks the (few) members so the "all done" test is exact
+// vanished); one thread per member, the block-wide AND gives the "all done" flag
 __global__ void k_rf_beta(double* __restrict__ sc, int32_t* __restrict__ ctl, const double* __restrict__ eps,
                           int batch, int32_t* __restrict__ stop) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || *stop) return;
+  if (blockIdx.x != 0 || *stop) return;  // uniform over the block
   const int max_inner = ctl[2 * batch + 1];
   int all = 1;
-  for (int b = 0; b < batch; ++b) {
+  for (int b = threadIdx.x; b < batch; b += blockDim.x) {  // one thread per member
     if (!ctl[b]) {
       double* s = sc + b * RF_NSC;
       const double rn = s[RF_RRNEW];
@@ -227,7 +227,7 @@ __global__ void k_rf_beta(double* __restrict__ sc, int32_t* __restrict__ ctl, co
     }
     all &= ctl[b] != 0;
   }
-  if (all) *stop = 1;
+  if (__syncthreads_and(all) && threadIdx.x == 0) *stop = 1;
 }
 
 // outer step: r = w - theta psi into res (negated: the CG right-hand side is
@@ -318,7 +318,8 @@ void rf_launch_minv(const double* diag, const double* sc, double* minv, int64_t 
 }
 void rf_launch_rho0(double* sc, int B, cudaStream_t st) { k_rf_rho0<<<(B + 63) / 64, 64, 0, st>>>(sc, B); }
 void rf_launch_beta(double* sc, int32_t* ctl, const double* eps, int B, int32_t* stop, cudaStream_t st) {
-  k_rf_beta<<<1, 32, 0, st>>>(sc, ctl, eps, B, stop);
+  const int threads = B >= 1024 ? 1024 : ((B + 31) / 32) * 32;
+  k_rf_beta<<<1, threads < 32 ? 32 : threads, 0, st>>>(sc, ctl, eps, B, stop);
 }
 void rf_launch_start(const double* w, const double* psi, const double* minv, double* res, double* t,
                      const double* sc, double* part, int64_t D, int B, cudaStream_t st) {

@@ -97,17 +97,17 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // ----------------------------------------------------------- descriptors
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle.  Rows
-// are 128 B (one K chunk), 8-row atoms of 1024 B are stacked along M/N, so
-// the stride between atoms (SBO) is 1024 B; the leading offset is unused for
-// this layout.  Version bits 46-47 = 1; layout type (bits 61-63) 2 = SW128.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle.  Rows
+// are 64 B (one K chunk), 8-row atoms of 512 B are stacked along M/N, so the
+// stride between atoms (SBO) is 512 B; the leading offset is unused for this
+// layout.  Version bits 46-47 = 1; layout type (bits 61-63) 4 = SW64.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t smem_addr) {
   uint64_t d = 0;
   d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)(512 >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)4 << 61;
   return d;
 }
 
