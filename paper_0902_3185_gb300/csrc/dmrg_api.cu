@@ -472,13 +472,15 @@ void lz_free(dmrg_sb* sb) {
       sb->lz_graph_key[i] = 0;
     }
   for (double* p : {sb->lz_V, sb->lz_w, sb->lz_vcur, sb->lz_partial, sb->lz_h, sb->lz_npart, sb->lz_ab, sb->lz_s,
-                    sb->lz_out, sb->rf_res, sb->rf_p, sb->rf_q, sb->rf_t, sb->rf_sc, sb->rf_diag, sb->rf_minv,
-                    sb->rf_part})
+                    sb->lz_out, sb->rf_q, sb->rf_sc, sb->rf_diag, sb->rf_part})
+    if (p) cudaFree(p);
+  for (float* p : {sb->rf_res, sb->rf_p, sb->rf_hp, sb->rf_t, sb->rf_psi32, sb->rf_minv})
     if (p) cudaFree(p);
   if (sb->lz_ctl) cudaFree(sb->lz_ctl);
   if (sb->lz_gate) cudaFree(sb->lz_gate);
   if (sb->rf_ctl) cudaFree(sb->rf_ctl);
-  sb->rf_res = sb->rf_p = sb->rf_q = sb->rf_t = sb->rf_sc = sb->rf_diag = sb->rf_minv = sb->rf_part = nullptr;
+  sb->rf_q = sb->rf_sc = sb->rf_diag = sb->rf_part = nullptr;
+  sb->rf_res = sb->rf_p = sb->rf_hp = sb->rf_t = sb->rf_psi32 = sb->rf_minv = nullptr;
   sb->rf_ctl = nullptr;
   if (sb->h_ctl) cudaFreeHost(sb->h_ctl);
   sb->lz_V = sb->lz_w = sb->lz_vcur = sb->lz_partial = sb->lz_h = sb->lz_npart = sb->lz_ab = sb->lz_s =
@@ -508,14 +510,16 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   CK(cudaMallocHost(&hp, sizeof(int32_t) * (LZ_CTL_MEMBER + 2 * B)));
   sb->h_ctl = static_cast<int32_t*>(hp);
   CK(cudaMemset(sb->lz_ab, 0, sizeof(double) * 2 * B * cap));
-  sb->rf_res = dalloc<double>((size_t)(B * D));
-  sb->rf_p = dalloc<double>((size_t)(B * D));
+  sb->rf_res = dalloc<float>((size_t)(B * D));
+  sb->rf_p = dalloc<float>((size_t)(B * D));
   sb->rf_q = dalloc<double>((size_t)(B * D));
-  sb->rf_t = dalloc<double>((size_t)(B * D));
+  sb->rf_hp = dalloc<float>((size_t)(B * D));
+  sb->rf_t = dalloc<float>((size_t)(B * D));
+  sb->rf_psi32 = dalloc<float>((size_t)(B * D));
   sb->rf_sc = dalloc<double>((size_t)(RF_NSC * B + 2));
   sb->rf_ctl = dalloc<int32_t>((size_t)(2 * B + 2));
   sb->rf_diag = dalloc<double>((size_t)(B * D));
-  sb->rf_minv = dalloc<double>((size_t)(B * D));
+  sb->rf_minv = dalloc<float>((size_t)(B * D));
   sb->rf_part = dalloc<double>((size_t)(4 * B * sb->lz_nchunk));
   sb->lz_cap = cap;
 }
@@ -537,11 +541,11 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   const int ndot = lz_dot_nchunk(D);
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st);
   lz_launch_reduce_rows(sb->lz_partial, hA, ctl, ndot, cap, B, 2, nullptr, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hA, nA, ctl, D, B, cap, nch, 2, nullptr, st);
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st);
+  // pass A's update runs inside pass B's dot sweep (norm partials per dot chunk)
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA);
   lz_launch_reduce_rows(sb->lz_partial, hB, ctl, ndot, cap, B, 0, nullptr, st);
   lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st);
-  lz_launch_dgks(nA, nB, sb->lz_gate, ctl, B, nch, st);
+  lz_launch_dgks(nA, nB, sb->lz_gate, ctl, B, ndot, nch, st);
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st);
   lz_launch_reduce_rows(sb->lz_partial, hC, ctl, ndot, cap, B, 0, sb->lz_gate, st);
   lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st);
@@ -594,7 +598,7 @@ int matvec_launches(const dmrg_sb* sb, int prec) {
     return (sb->f64_fwd1.n_tiles > 0) + (sb->f64_fwd2.n_tiles > 0) + (sb->f64_fwd3.n_tiles > 0);
   return tc_launches(sb, prec);
 }
-constexpr int LZ_KERNELS_PER_ITER = 14;  // everything in lz_enqueue_iteration besides the product
+constexpr int LZ_KERNELS_PER_ITER = 13;  // everything in lz_enqueue_iteration besides the product
 
 // Lanczos from psi0 (device [batch][D]) to psi_out; returns per-member results.
 LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double tol, int max_iter,
@@ -656,11 +660,11 @@ void rf_enqueue_inner(dmrg_sb* sb, int prec, cudaStream_t st) {
   int32_t* ctl = sb->rf_ctl;
   int32_t* stop = ctl + 2 * B;
   double* sc = sb->rf_sc;
-  const double* psi = sb->lz_vcur;  // the current float64 iterate lives in lz_vcur during refinement
-  matvec(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st);  // q = H p (mixed)
-  rf_launch_dots4(sb->rf_q, sb->rf_p, psi, ctl, sb->rf_part, D, B, stop, st);
+  const float* psi = sb->rf_psi32;  // the current iterate, rounded for the inner solve
+  tc_matvec_f32in(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st);  // q = H p (mixed)
+  rf_launch_dots4(sb->rf_q, sb->rf_p, psi, sb->rf_hp, sc, ctl, sb->rf_part, D, B, stop, st);
   rf_launch_alpha4(sb->rf_part, sc, ctl, D, B, stop, st);
-  rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_q, psi, sb->rf_minv, sc, ctl, sb->rf_part, D, B, stop,
+  rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_hp, psi, sb->rf_minv, sc, ctl, sb->rf_part, D, B, stop,
                    st);
   rf_launch_sum4(sb->rf_part, sc, D, B, 0, ctl, stop, st);
   rf_launch_beta(sc, ctl, sc + RF_NSC * B, B, stop, st);
@@ -748,10 +752,11 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
     rf_launch_set(sb->rf_sc, tmp, RF_THETA, B, 0, st);
     // preconditioner, right-hand side -r, first direction p = K (-r)
     rf_launch_minv(sb->rf_diag, sb->rf_sc, sb->rf_minv, D, B, st);
-    rf_launch_start(sb->lz_w, cur, sb->rf_minv, sb->rf_res, sb->rf_t, sb->rf_sc, sb->rf_part, D, B, st);
+    rf_launch_start(sb->lz_w, cur, sb->rf_minv, sb->rf_res, sb->rf_t, sb->rf_psi32, sb->rf_sc, sb->rf_part, D, B,
+                    st);
     rf_launch_sum4(sb->rf_part, sb->rf_sc, D, B, 1, nullptr, nullptr, st);
     rf_launch_rho0(sb->rf_sc, B, st);
-    rf_launch_dir(sb->rf_p, sb->rf_res, cur, sb->rf_minv, sb->rf_sc, nullptr, D, B, 1, nullptr, st);
+    rf_launch_dir(sb->rf_p, sb->rf_res, sb->rf_psi32, sb->rf_minv, sb->rf_sc, nullptr, D, B, 1, nullptr, st);
     CK(cudaMemcpyAsync(hsc.data(), sb->rf_sc, sizeof(double) * RF_NSC * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     r.launches += 9 + (with_dots ? 4 : matvec_launches(sb, DMRG_FP64));

@@ -130,14 +130,16 @@ struct dmrg_sb {
   int32_t* h_ctl = nullptr;      // pinned host mirror
   int32_t lz_nchunk = 0;
   // float64 refinement (Newton step with mixed CG) buffers, allocated with Lanczos
-  double* rf_res = nullptr;      // [batch][D]
-  double* rf_p = nullptr;
-  double* rf_q = nullptr;
-  double* rf_t = nullptr;
+  float* rf_res = nullptr;       // [batch][D] inner CG vectors (float32)
+  float* rf_p = nullptr;
+  double* rf_q = nullptr;        // [batch][D] mixed product H p (float64 output)
+  float* rf_hp = nullptr;        // (H - theta) p
+  float* rf_t = nullptr;
+  float* rf_psi32 = nullptr;     // the iterate, rounded for the inner solve
   double* rf_sc = nullptr;       // [batch][8] scalars, then eps
   int32_t* rf_ctl = nullptr;     // [2 batch + 2]
   double* rf_diag = nullptr;     // [batch][D] diag(H) per member (preconditioner)
-  double* rf_minv = nullptr;     // [batch][D] 1 / max(diag - theta, delta)
+  float* rf_minv = nullptr;      // [batch][D] 1 / max(diag - theta, delta)
   double* rf_part = nullptr;     // [4][batch][nchunk] reduction partials
   // terms with diagonal blocks (s_out == s_in): their diagonals, [n][D]
   std::vector<int32_t> dg_terms;

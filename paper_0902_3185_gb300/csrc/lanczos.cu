@@ -60,10 +60,14 @@ __device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j
 // LZ_DOT_EPT elements of w in registers, takes 8 rows at a time, and the 8
 // row sums are reduced across the warp by a butterfly that halves the values
 // per lane at each step (4+2+1+1+1 shuffle-adds for 8 rows, not 8 x 5).
+// With h_pre != NULL the previous pass's update (the three-term step,
+// w -= h_pre[j-1] v_{j-1} + h_pre[j] v_j, in that order) is applied first,
+// written back to w, and its per-chunk sum of squares stored in npart_pre:
+// one sweep instead of an update sweep followed by a dot sweep.
 __global__ void __launch_bounds__(LZ_THREADS)
-k_multidot(const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ partial,
+k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restrict__ partial,
            const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk, int win,
-           const int32_t* __restrict__ gate) {
+           const int32_t* __restrict__ gate, const double* __restrict__ h_pre, double* __restrict__ npart_pre) {
   __shared__ double red[LZ_THREADS / 32][8];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (member_skip(ctl, gate, b)) return;
@@ -71,10 +75,38 @@ k_multidot(const double* __restrict__ V, const double* __restrict__ w, double* _
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double wv[LZ_DOT_EPT];
   const int64_t base = (int64_t)chunk * LZ_DOT_CHUNK + threadIdx.x;
+  // the pre-update's rows (j - 1 when it exists, then j) and coefficients
+  const bool two = j >= 1;
+  const double* v0 = V + ((int64_t)(two ? j - 1 : j) * batch + b) * D;
+  const double* v1 = V + ((int64_t)j * batch + b) * D;
+  const double h0 = h_pre && two ? h_pre[(int64_t)b * cap + j - 1] : 0.0;
+  const double h1 = h_pre ? h_pre[(int64_t)b * cap + j] : 0.0;
+  double nrm = 0.0;
 #pragma unroll
   for (int e = 0; e < LZ_DOT_EPT; ++e) {
     const int64_t d = base + e * LZ_THREADS;
-    wv[e] = d < D ? w[(int64_t)b * D + d] : 0.0;
+    double x = 0.0;
+    if (d < D) {
+      x = w[(int64_t)b * D + d];
+      if (h_pre) {
+        if (two) x = fma(-v0[d], h0, x);
+        x = fma(-v1[d], h1, x);
+        w[(int64_t)b * D + d] = x;
+        nrm = fma(x, x, nrm);
+      }
+    }
+    wv[e] = x;
+  }
+  if (h_pre) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    if (lane == 0) red[wid][0] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < LZ_THREADS / 32; ++w2) t += red[w2][0];
+      npart_pre[(int64_t)b * nchunk + chunk] = t;
+    }
   }
   const bool full = base + (LZ_DOT_EPT - 1) * LZ_THREADS < D;
   for (int i0 = first_row(j, win); i0 <= j; i0 += 8) {
@@ -206,10 +238,10 @@ __device__ __forceinline__ double warp_sum_chunks(const double* __restrict__ par
 // Daniel-Gragg-Kaufman-Stewart test after pass B: gate[b] = 1 (run pass C)
 // unless |w_B|^2 >= |w_A|^2 / 2.  One warp per member.
 __global__ void k_dgks(const double* __restrict__ npart_a, const double* __restrict__ npart_b,
-                       int32_t* __restrict__ gate, const int32_t* __restrict__ ctl, int nchunk) {
+                       int32_t* __restrict__ gate, const int32_t* __restrict__ ctl, int nchunk_a, int nchunk) {
   const int b = blockIdx.x;
   if (member_done(ctl, b)) return;
-  const double na = warp_sum_chunks(npart_a + (int64_t)b * nchunk, nchunk);
+  const double na = warp_sum_chunks(npart_a + (int64_t)b * nchunk_a, nchunk_a);
   const double nb = warp_sum_chunks(npart_b + (int64_t)b * nchunk, nchunk);
   if (threadIdx.x == 0) gate[b] = (nb >= 0.5 * na) ? 0 : 1;  // NaN: run pass C, then the NaN check stops it
 }
@@ -605,10 +637,11 @@ k_reduce_terms(const double* __restrict__ part, const int32_t* __restrict__ ptr,
 }
 
 // ------------------------------------------------------------- launchers
-void lz_launch_multidot(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
-                        int batch, int cap, int win, const int32_t* gate, cudaStream_t st) {
+void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
+                        int batch, int cap, int win, const int32_t* gate, cudaStream_t st, const double* h_pre,
+                        double* npart_pre) {
   k_multidot<<<dim3(lz_dot_nchunk(D), batch), LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap,
-                                                                  lz_dot_nchunk(D), win, gate);
+                                                                  lz_dot_nchunk(D), win, gate, h_pre, npart_pre);
 }
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st) {
@@ -622,8 +655,8 @@ void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* no
                                                                             batch, cap, nchunk, win, gate);
 }
 void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate, const int32_t* ctl, int batch,
-                    int nchunk, cudaStream_t st) {
-  k_dgks<<<batch, 32, 0, st>>>(npart_a, npart_b, gate, ctl, nchunk);
+                    int nchunk_a, int nchunk, cudaStream_t st) {
+  k_dgks<<<batch, 32, 0, st>>>(npart_a, npart_b, gate, ctl, nchunk_a, nchunk);
 }
 void lz_launch_finalize_ab(const double* h, const double* npart_b, const double* npart_c, const int32_t* gate,
                            double* ab, const int32_t* ctl, int batch, int cap, int nchunk, cudaStream_t st) {

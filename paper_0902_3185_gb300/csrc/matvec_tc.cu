@@ -140,10 +140,12 @@ __host__ __device__ inline int64_t panel_off(int64_t row, int64_t k, int64_t ato
 // panel rows).  Tile entries outside the block are zero, so granules reaching
 // into the K padding write zeros there; padding rows are never written.
 constexpr int STAGE_T = 32;
+__device__ __forceinline__ float to_float(double v) { return tc::d2f_rn32(v); }
+__device__ __forceinline__ float to_float(float v) { return v; }
 
-template <int PREC>
+template <int PREC, class TIn>
 __global__ void __launch_bounds__(256)
-tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict__ outs, const double* __restrict__ x,
+tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict__ outs, const TIn* __restrict__ x,
                 int64_t D, int64_t p_lo, const double* __restrict__ coef, int n_terms,
                 const int32_t* __restrict__ skip) {
   constexpr int G = PREC == DMRG_TF32 ? 4 : 8;  // values per 16-byte granule
@@ -156,15 +158,15 @@ tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict_
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int rows_t = min(STAGE_T, tl.r - tl.r0), cols_t = min(STAGE_T, tl.c - tl.c0);
   // 32-bit offsets inside the sector block (r * c < 2^31)
-  const double* src = x + (int64_t)b * D + tl.src_off + tl.r0 * tl.c + tl.c0;
-  double raw[STAGE_T / 8];
+  const TIn* src = x + (int64_t)b * D + tl.src_off + tl.r0 * tl.c + tl.c0;
+  TIn raw[STAGE_T / 8];
 #pragma unroll
   for (int i = 0; i < STAGE_T / 8; ++i) {
     const int row = ty + 8 * i;
-    raw[i] = (row < rows_t && tx < cols_t) ? src[row * tl.c + tx] : 0.0;
+    raw[i] = (row < rows_t && tx < cols_t) ? src[row * tl.c + tx] : TIn(0);
   }
 #pragma unroll
-  for (int i = 0; i < STAGE_T / 8; ++i) tile[ty + 8 * i][tx] = tc::d2f_rn32(raw[i]);
+  for (int i = 0; i < STAGE_T / 8; ++i) tile[ty + 8 * i][tx] = to_float(raw[i]);
   __syncthreads();
   for (int o = tl.out_begin; o < tl.out_end; ++o) {
     const StageOut so = outs[o];
@@ -1293,11 +1295,11 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
                                                        L.acc_cols, n_acc, tile_split, sb->test_stall);
 }
 
-template <int PREC>
-static void run_set(const State* s, const PairSet& ps, const double* x, double* y, const dmrg_sb* sb,
+template <int PREC, class TIn>
+static void run_set(const State* s, const PairSet& ps, const TIn* x, double* y, const dmrg_sb* sb,
                     int accumulate, const int32_t* skip, cudaStream_t st) {
   if (ps.n_stage_tiles > 0)
-    tc_stage_kernel<PREC><<<dim3((unsigned)ps.n_stage_tiles, sb->batch), 256, 0, st>>>(
+    tc_stage_kernel<PREC, TIn><<<dim3((unsigned)ps.n_stage_tiles, sb->batch), 256, 0, st>>>(
         ps.stage_tiles, ps.stage_outs, x, sb->D, ps.p_lo, sb->d_coeffs, sb->n_terms, skip);
   run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
   run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, st);
@@ -1376,6 +1378,15 @@ void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate
   if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st);
   else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st);
   sb->test_stall = 0;  // the hook applies to one product
+}
+
+void tc_matvec_f32in(dmrg_sb* sb, int prec, const float* x, double* y, int accumulate, const int32_t* skip,
+                     cudaStream_t st) {
+  const State* s = st_of(sb);
+  if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
+  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st);
+  else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st);
+  sb->test_stall = 0;
 }
 
 void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st) {

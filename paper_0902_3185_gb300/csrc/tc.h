@@ -17,6 +17,9 @@ double tc_operand_bytes(const dmrg_sb* sb);
 int tc_launches(const dmrg_sb* sb, int prec);  // kernels one product launches
 void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
                cudaStream_t st);
+// the same product of a float32 x (the mixed products round x to float32 first anyway)
+void tc_matvec_f32in(dmrg_sb* sb, int prec, const float* x, double* y, int accumulate, const int32_t* skip,
+                     cudaStream_t st);
 void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st);
 // out: best ms, default ms, per-block baseline ms, best tile N, heavy-first flag, candidates
 void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out);
