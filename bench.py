@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--mixed-tol", type=float, default=1e-4)
-    ap.add_argument("--refine", default="newton", choices=["newton", "lanczos", "none"])
+    ap.add_argument("--refine", default="newton_df64", choices=["newton", "newton_df64", "lanczos", "none"])
     return ap.parse_args()
 
 
@@ -147,6 +147,11 @@ def measured_peaks():
 
 # float64 FMA issue rate of the chip (ncu: 304 DFMA thread-instructions per cycle, 2 per SM x 152)
 FP64_FMA_PER_CLK = 304
+# float32 lanes of the chip per cycle (128 per SM x 152) and the float32
+# operations of one double-float multiply-add (product with its error terms,
+# two-sum, error accumulation)
+FP32_OPS_PER_CLK = 128 * 152
+DF_OPS_PER_FMA = 12
 
 
 def source_sha(files):
@@ -405,7 +410,19 @@ def main():
     # Hellmann-Feynman gradient alone (float64 per-term dots), and the float64
     # product that also gives the per-term dots
     t_grad, _ = timed(lambda: g.energy_grad(psi))
-    t_pdot, _ = timed(lambda: g.apply_H_term_dots(x0))
+    df = prec != "fp64" and args.refine == "newton_df64"
+    rprec = "df64" if df else "fp64"  # arithmetic of the refinement's residual products
+    t_pdot, _ = timed(lambda: g.apply_H_term_dots(x0, prec=rprec))
+    mvr_ms = mv64_ms
+    if df:
+        for _ in range(2):
+            g.apply_H(x0, y, prec="df64")
+        a.record(stream)
+        for _ in range(5):
+            g.apply_H(x0, y, prec="df64")
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        mvr_ms = a.elapsed_time(b) / 5
     # Lanczos iteration rate at fixed Krylov length j (no early stop)
     fixed_j = {}
     for pj in ([prec, "fp64"] if prec != "fp64" else ["fp64"]):
@@ -433,23 +450,33 @@ def main():
                             else f"{kind} bf16 peak x nominal 1100/2250"),
             "ms_per_step": n_mixed * mv_ms}
     pk64 = FP64_FMA_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
-    a_64 = flops_mv / (mv64_ms / 1e3) / 1e12
-    newton = prec != "fp64" and args.refine == "newton"
+    pkdf = FP32_OPS_PER_CLK / DF_OPS_PER_FMA * 2 * sm_mhz * 1e6 / 1e12
+    newton = prec != "fp64" and args.refine.startswith("newton")
     n_dots = max(0, n_f64 - 1) if newton else 0
-    kernels["fp64_product"] = {
-        "bound": "alu", "achieved": a_64, "peak": pk64, "unit": "TFLOP/s", "frac": a_64 / pk64,
-        "traffic": recorded_traffic("fp64_product"),
-        "kernel": "grouped float64 product, seg_gemm_f64_kernel (3 launches per dmrg_apply_H)",
-        "peak_source": f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz (median SM clock of the timed region)",
-        "ms_per_step": (n_f64 - n_dots) * mv64_ms + (0.0 if newton else t_grad)}
+    if df:
+        pk_r, name_r = pkdf, "df64"
+        src_r = (f"{FP32_OPS_PER_CLK} float32 ops/clock / {DF_OPS_PER_FMA} per double-float FMA x 2 x "
+                 f"{sm_mhz:.0f} MHz (median SM clock of the timed region)")
+        kern_r = "grouped double-float product, seg_gemm_df_kernel (3 launches per product)"
+        kern_d = ("double-float product with the per-term dots (unscaled intermediates + seg_gemm_df_dots_kernel, "
+                  "the refinement's residuals after the first)")
+    else:
+        pk_r, name_r = pk64, "fp64"
+        src_r = f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz (median SM clock of the timed region)"
+        kern_r = "grouped float64 product, seg_gemm_f64_kernel (3 launches per dmrg_apply_H)"
+        kern_d = ("float64 product with the per-term dots (unscaled intermediates + seg_gemm_f64_dots_kernel, "
+                  "the refinement's residuals after the first)")
+    a_r = flops_mv / (mvr_ms / 1e3) / 1e12
+    kernels[f"{name_r}_product"] = {
+        "bound": "alu", "achieved": a_r, "peak": pk_r, "unit": "TFLOP/s", "frac": a_r / pk_r,
+        "traffic": recorded_traffic(f"{name_r}_product"),
+        "kernel": kern_r, "peak_source": src_r,
+        "ms_per_step": (n_f64 - n_dots) * mvr_ms + (0.0 if newton else t_grad)}
     if n_dots:
         a_d = flops_mv / (t_pdot / 1e3) / 1e12
-        kernels["fp64_product_with_dots"] = {
-            "bound": "alu", "achieved": a_d, "peak": pk64, "unit": "TFLOP/s", "frac": a_d / pk64,
-            "traffic": None,
-            "kernel": "float64 product with the per-term dots (unscaled intermediates + seg_gemm_f64_dots_kernel, "
-                      "the refinement's residuals after the first)",
-            "peak_source": f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz",
+        kernels[f"{name_r}_product_with_dots"] = {
+            "bound": "alu", "achieved": a_d, "peak": pk_r, "unit": "TFLOP/s", "frac": a_d / pk_r,
+            "traffic": None, "kernel": kern_d, "peak_source": src_r,
             "ms_per_step": n_dots * t_pdot}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     roof = dict(kernels[dom])
@@ -470,9 +497,10 @@ def main():
            "lanczos_steps_per_s": world * it_count / (ms / 1e3),
            "matvec_ms": mv_ms, "matvec_tflops": achieved, "matvec_fp64_ms": mv64_ms,
            "matvec_fp64_tflops": flops_mv / (mv64_ms / 1e3) / 1e12,
+           "residual_products": rprec, "matvec_residual_ms": mvr_ms,
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
-           "breakdown": dict(breakdown, energy_grad_ms=t_grad, fp64_product_with_dots_ms=t_pdot),
+           "breakdown": dict(breakdown, energy_grad_ms=t_grad, residual_product_with_dots_ms=t_pdot),
            "lanczos_fixed_j": fixed_j,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:

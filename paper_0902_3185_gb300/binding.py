@@ -17,8 +17,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdmrg_gb300.so")
 
-FP64, TF32, BF16X3 = 0, 1, 2
-PREC = {"fp64": FP64, "tf32": TF32, "bf16x3": BF16X3}
+FP64, TF32, BF16X3, DF64 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "tf32": TF32, "bf16x3": BF16X3, "df64": DF64}
 ID_A, ID_B = 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN",
           6: "ETIMEOUT", 7: "ENAN", 8: "EUNSUPPORTED"}
@@ -106,7 +106,7 @@ def load(build_if_missing: bool = True):
     lib.dmrg_sync_status.argtypes = [vp, vp]
     lib.dmrg_test_inject.argtypes = [vp, i32]
     lib.dmrg_lanczos_ground_grad.argtypes = [vp, dp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
-    lib.dmrg_apply_H_term_dots.argtypes = [vp, dp, dp, dp, vp]
+    lib.dmrg_apply_H_term_dots.argtypes = [vp, dp, dp, dp, i32, vp]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -233,12 +233,13 @@ class GpuSuperblock:
         self._check(self.lib.dmrg_energy_grad(self.h, _ptr(psi), _ptr(out), _prec(prec), _stream(stream)))
         return out
 
-    REFINE = {None: 0, False: 0, "none": 0, "lanczos": 1, True: 2, "newton": 2}
+    REFINE = {None: 0, False: 0, "none": 0, "lanczos": 1, True: 2, "newton": 2, "newton_df64": 3}
 
     def lanczos_ground(self, psi0, tol=1e-12, max_iter=300, prec="fp64", refine="newton", refine_tol=1e-10,
                        check_every=1, graph_iters=8, psi_out=None, stream=None, grad=False):
         """Lowest eigenpair of every member.  With a mixed precision, refine =
         "newton" (float64 residual + mixed CG correction steps, default),
+        "newton_df64" (the same with double-float residual products),
         "lanczos" (float64 Lanczos restarted from the mixed result) or "none".
         Returns (e0, psi, infos, status); with grad=True also the
         Hellmann-Feynman gradient [batch][n_terms] of psi, as a fifth value."""
@@ -262,11 +263,13 @@ class GpuSuperblock:
             return e0, psi_out, infos, st, dE
         return e0, psi_out, infos, st
 
-    def apply_H_term_dots(self, psi, stream=None):
-        """y = H psi (float64) and dots[b][k] = <psi_b, (A_k (x) B_k) psi_b>, one pass."""
+    def apply_H_term_dots(self, psi, prec="fp64", stream=None):
+        """y = H psi and dots[b][k] = <psi_b, (A_k (x) B_k) psi_b>, one pass
+        (prec "fp64" or "df64")."""
         y = self.empty()
         dots = torch.empty(self.batch, self.n_terms, dtype=torch.float64, device=self.device)
-        self._check(self.lib.dmrg_apply_H_term_dots(self.h, _ptr(psi), _ptr(y), _ptr(dots), _stream(stream)))
+        self._check(self.lib.dmrg_apply_H_term_dots(self.h, _ptr(psi), _ptr(y), _ptr(dots), _prec(prec),
+                                                    _stream(stream)))
         return y, dots
 
 

@@ -439,18 +439,30 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
     launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, skip, st);
     launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
     launch_seg_gemm_f64(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
+  } else if (prec == DMRG_DF64) {  // the same task lists in double-float arithmetic
+    Bufs bufs{{const_cast<double*>(x), y, sb->d_T, sb->d_ops, nullptr}};
+    launch_seg_gemm_df(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, skip, st);
+    launch_seg_gemm_df(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
+    launch_seg_gemm_df(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
   } else {
     tc_matvec(sb, prec, x, y, accumulate, skip, st);
   }
   CK(cudaGetLastError());
 }
 
-// y = H psi (float64) and dc[b][k] = <psi_b, (A_k x B_k) psi_b> in one pass
-void matvec_f64_dots(dmrg_sb* sb, const double* psi, double* y, double* dc, cudaStream_t st) {
+// y = H psi and dc[b][k] = <psi_b, (A_k x B_k) psi_b> in one pass, in float64
+// or (df) double-float arithmetic
+void matvec_f64_dots(dmrg_sb* sb, const double* psi, double* y, double* dc, cudaStream_t st, bool df = false) {
   Bufs bufs{{const_cast<double*>(psi), y, sb->d_T, sb->d_ops, nullptr}};
-  launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
-  launch_seg_gemm_f64_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
-  launch_seg_gemm_f64_dots(sb->f64_pdot3, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+  if (df) {
+    launch_seg_gemm_df(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+    launch_seg_gemm_df_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+    launch_seg_gemm_df_dots(sb->f64_pdot3, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+  } else {
+    launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
+    launch_seg_gemm_f64_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+    launch_seg_gemm_f64_dots(sb->f64_pdot3, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+  }
   lz_launch_reduce_terms(sb->d_pdot_partial, sb->d_pdot_ptr, sb->d_pdot_idx, dc, sb->batch * sb->n_terms, st);
   CK(cudaGetLastError());
 }
@@ -594,7 +606,7 @@ struct LzRun {
 };
 
 int matvec_launches(const dmrg_sb* sb, int prec) {
-  if (prec == DMRG_FP64)
+  if (prec == DMRG_FP64 || prec == DMRG_DF64)
     return (sb->f64_fwd1.n_tiles > 0) + (sb->f64_fwd2.n_tiles > 0) + (sb->f64_fwd3.n_tiles > 0);
   return tc_launches(sb, prec);
 }
@@ -720,8 +732,8 @@ struct RfRun {
 // dc != NULL the float64 residual products after the first also give the
 // per-term dots <psi, (A_k x B_k) psi> (one pass, f64_pdot2/3); the last one is
 // of the returned psi.
-RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, int max_inner, double eps_in, int K,
-               cudaStream_t st, double* dc = nullptr) {
+RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, int rprec, double tol, int max_outer, int max_inner,
+               double eps_in, int K, cudaStream_t st, double* dc = nullptr) {
   const int64_t D = sb->D;
   const int B = sb->batch, nch = sb->lz_nchunk;
   double* part = sb->lz_partial;
@@ -744,8 +756,8 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
     // float64 residual of the current iterate (the first outer step is never
     // the last in practice: the mixed solve stops far above the tolerance)
     const bool with_dots = dc && o >= 1;
-    if (with_dots) matvec_f64_dots(sb, cur, sb->lz_w, dc, st);
-    else matvec(sb, DMRG_FP64, cur, sb->lz_w, 0, nullptr, st);
+    if (with_dots) matvec_f64_dots(sb, cur, sb->lz_w, dc, st, rprec == DMRG_DF64);
+    else matvec(sb, rprec, cur, sb->lz_w, 0, nullptr, st);
     r.dots_final = with_dots;
     lz_launch_dot(cur, sb->lz_w, part, D, B, nch, st);
     lz_launch_sum_chunks(part, tmp, nch, B, st);
@@ -759,7 +771,7 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, double tol, int max_outer, in
     rf_launch_dir(sb->rf_p, sb->rf_res, sb->rf_psi32, sb->rf_minv, sb->rf_sc, nullptr, D, B, 1, nullptr, st);
     CK(cudaMemcpyAsync(hsc.data(), sb->rf_sc, sizeof(double) * RF_NSC * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    r.launches += 9 + (with_dots ? 4 : matvec_launches(sb, DMRG_FP64));
+    r.launches += 9 + (with_dots ? 4 : matvec_launches(sb, rprec));
     ++r.outer;
     bool all = true;
     for (int b = 0; b < B; ++b) {
@@ -1044,11 +1056,11 @@ dmrg_status dmrg_apply_H(dmrg_sb* sb, const double* psi, double* y, int32_t accu
     sb->err = "apply_H: null or aliased psi / y";
     return DMRG_EINVAL;
   }
-  if (prec < DMRG_FP64 || prec > DMRG_BF16X3) {
+  if (prec < DMRG_FP64 || prec > DMRG_DF64) {
     sb->err = "apply_H: unknown precision";
     return DMRG_EINVAL;
   }
-  if (prec != DMRG_FP64 && !tc_available(sb)) {
+  if ((prec == DMRG_TF32 || prec == DMRG_BF16X3) && !tc_available(sb)) {
     sb->err = "apply_H: tensor-core path not available on this device";
     return DMRG_EUNSUPPORTED;
   }
@@ -1154,7 +1166,8 @@ dmrg_status dmrg_energy_grad(dmrg_sb* sb, const double* psi, double* dE_dc, int3
 static dmrg_status lanczos_impl(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0, double* dE_dc,
                                 const dmrg_lanczos_opts* opts, dmrg_lanczos_info* info, void* stream) {
   if (!sb || !psi0 || !psi_out || !e0 || !opts) return DMRG_EINVAL;
-  if (opts->prec < DMRG_FP64 || opts->prec > DMRG_BF16X3 || !(opts->tol > 0) || opts->max_iter < 1) {
+  if (opts->prec < DMRG_FP64 || opts->prec > DMRG_BF16X3 || !(opts->tol > 0) || opts->max_iter < 1 ||
+      opts->refine < 0 || opts->refine > 3) {
     sb->err = "lanczos: bad options";
     return DMRG_EINVAL;
   }
@@ -1174,7 +1187,7 @@ static dmrg_status lanczos_impl(dmrg_sb* sb, const double* psi0, double* psi_out
     if (mode == 1)
       rr = lz_solve(sb, psi_out, psi_out, DMRG_FP64, rtol, opts->max_iter, opts->check_every, ge, st);
     else if (mode >= 2)
-      rn = rf_solve(sb, psi_out, opts->prec, rtol, 8, 400, 1e-2, ge, st, dE_dc);
+      rn = rf_solve(sb, psi_out, opts->prec, mode == 3 ? DMRG_DF64 : DMRG_FP64, rtol, 8, 400, 1e-2, ge, st, dE_dc);
     int64_t grad_launches = 0;
     if (dE_dc) {
       // Hellmann-Feynman: dots of the returned psi / <psi, psi>, from the
@@ -1229,14 +1242,19 @@ dmrg_status dmrg_lanczos_ground_grad(dmrg_sb* sb, const double* psi0, double* ps
   return lanczos_impl(sb, psi0, psi_out, e0, dE_dc, opts, info, stream);
 }
 
-dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, double* dots, void* stream) {
+dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, double* dots, int32_t prec,
+                                   void* stream) {
   if (!sb) return DMRG_EINVAL;
   if (!psi || !y || !dots || psi == y) {
     sb->err = "apply_H_term_dots: null or aliased psi / y / dots";
     return DMRG_EINVAL;
   }
+  if (prec != DMRG_FP64 && prec != DMRG_DF64) {
+    sb->err = "apply_H_term_dots: precision must be DMRG_FP64 or DMRG_DF64";
+    return DMRG_EINVAL;
+  }
   return guard(sb, [&] {
-    matvec_f64_dots(sb, psi, y, dots, (cudaStream_t)stream);
+    matvec_f64_dots(sb, psi, y, dots, (cudaStream_t)stream, prec == DMRG_DF64);
     return DMRG_OK;
   });
 }

@@ -74,6 +74,11 @@ void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* 
 // tiles of mode TM_STORE_DOTS (product and per-segment dots in one pass)
 void launch_seg_gemm_f64_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
                               int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
+// the same task lists in double-float arithmetic (matvec_df.cu)
+void launch_seg_gemm_df(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms, int accumulate,
+                        double* dot_out, const int32_t* skip, cudaStream_t st);
+void launch_seg_gemm_df_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
+                             int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
 
 // ------------------------------------------------------------ host pair info
 struct PairH {

@@ -1,0 +1,340 @@
+// Grouped sector GEMM in double-float arithmetic: the float64 product's task
+// lists (same tiles, segments and outputs as matvec_f64.cu), with every
+// multiply-add done on float32 pairs.
+//
+// A double-float number is an unevaluated pair hi + lo of float32 values
+// (about 48 significant bits).  Inputs are float64; each is split into
+// hi = RN24(v) and lo = RN24(v - hi) with integer instructions, products use
+// Dekker's splitting-free form with a fused multiply-add (the error of
+// hi_a * hi_b is exact, the cross terms are added to it, lo_a * lo_b -- 2^-46
+// relative -- is dropped), and sums use Knuth's two-sum, so one multiply-add
+// costs 12 float32 operations and has a relative error near 2^-46; the pair
+// is renormalised after every K tile of 16 (without it the low sum's own
+// rounding grows like K 2^-48: 1e-12 at K = 200).  GB300
+// runs float64 at 1/64 of its float32 rate (2 DFMA per clock per SM against
+// 128 FFMA), so this runs the superblock product about four to five times
+// faster than the float64 kernel at that accuracy: enough for residuals
+// r = H psi - theta psi down to |r| ~ 1e-12 |H psi|.  Outputs are written as
+// float64 (hi + lo).  Paper Sec. 3.3: the product x += H y, system,
+// environment and connection parts, on the fly.
+
+#include "internal.h"
+#include "tc_kernel.cuh"
+
+namespace dmrg {
+
+constexpr int DF_BMAX = 64, DF_BK = 16, DF_THREADS = 256;
+
+struct DFSmem {
+  float2 L[DF_BK][DF_BMAX + 1];
+  float2 R[DF_BK][DF_BMAX + 1];
+  double red[DF_THREADS / 32];
+};
+struct DFDotSmem {
+  double col[16][DF_BMAX + 1];
+};
+
+// v = hi + lo with hi = RN24(v) and lo = RN24(v - hi).  For hi in the normal
+// float range: v - hi = +-(rem - up 2^29) 2^(e - 1075) from the 29 mantissa
+// bits below hi's (rem) and hi's rounding carry (up); lo is dropped when that
+// scale is below the float range (|v| < 2^-74).  Other inputs: hi only.
+__device__ __forceinline__ float2 df_split(double v) {
+  const uint32_t h = (uint32_t)__double2hiint(v), l = (uint32_t)__double2loint(v);
+  const uint32_t e = (h >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {
+    const uint32_t sign = h & 0x80000000u;
+    const uint32_t m = ((h & 0xfffffu) << 3) | (l >> 29);
+    const uint32_t rem = l & 0x1fffffffu;
+    const uint32_t up = ((uint32_t)(rem > 0x10000000u) | ((uint32_t)(rem == 0x10000000u) & m)) & 1u;
+    const float hi = __uint_as_float(sign | (((e - 896u) << 23) + m + up));
+    const int r = (int)rem - (int)(up << 29);
+    const int se = (int)e - 948;  // biased float exponent of 2^(e - 1075)
+    float lo = se >= 1 ? __fmul_rn(__int2float_rn(r), __int_as_float(se << 23)) : 0.0f;
+    return make_float2(hi, sign ? -lo : lo);
+  }
+  return make_float2(tc::d2f_rn(v), 0.0f);
+}
+
+// a * b as an unevaluated pair (p, e): p = RN(a.hi b.hi), e = its exact error
+// plus the cross terms
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return make_float2(p, e);
+}
+
+// (s, c) += a * b: the product's leading part enters s through a two-sum
+// whose exact error, with the product's error terms, goes to c
+__device__ __forceinline__ void df_fma(float2 a, float2 b, float& s, float& c) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float t = __fadd_rn(s, p);
+  const float bv = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  c = __fadd_rn(c, __fadd_rn(err, e));
+  s = t;
+}
+
+__device__ __forceinline__ double df_value(float s, float c) { return tc::f2d_exact(s) + tc::f2d_exact(c); }
+
+template <int NI, int NJ, bool DOTS>
+__device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restrict__ segs, const Bufs& bufs,
+                                        const double* __restrict__ coef, int n_terms, int accumulate,
+                                        double* __restrict__ dot_out, DFSmem& sm, DFDotSmem* dsm) {
+  constexpr int BM = 16 * NI, BN = 16 * NJ;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  // double-float sums: of the whole tile, or (DOTS) of the current segment
+  float s_[NI][NJ], c_[NI][NJ];
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) s_[i][j] = c_[i][j] = 0.0f;
+  double accd[DOTS ? NI : 1][DOTS ? NJ : 1];  // DOTS: the coefficient-weighted sum in float64
+#pragma unroll
+  for (int i = 0; i < (DOTS ? NI : 1); ++i)
+#pragma unroll
+    for (int j = 0; j < (DOTS ? NJ : 1); ++j) accd[i][j] = 0.0;
+  auto coff = [&](int m, int n) -> int64_t {
+    int b = 0;
+    if (t.c_rm) {
+      if (t.c_axis == 0) { b = m / t.c_rm; m -= b * t.c_rm; }
+      else { b = n / t.c_rm; n -= b * t.c_rm; }
+    }
+    return (int64_t)b * t.c_bs + (t.c_trans ? (int64_t)n * t.ldc + m : (int64_t)m * t.ldc + n);
+  };
+  const bool by_col = t.c_rm && t.c_axis == 1;
+  const double* X = bufs.p[BUF_X] + t.c_off;
+  // DOTS, computed where needed (registers go to the double-float sums): the
+  // member of row i / column j and the wavefunction at output element (i, j)
+  auto mrow = [&](int i) -> int {
+    const int m = t.m0 + ty + 16 * i;
+    return (t.c_rm && t.c_axis == 0) ? m / t.c_rm : (t.c_rm ? 0 : t.member);
+  };
+  auto mcol = [&](int j) -> int { return by_col ? (t.n0 + tx + 16 * j) / t.c_rm : 0; };
+  auto xo = [&](int i, int j) -> double {
+    const int m = t.m0 + ty + 16 * i, n = t.n0 + tx + 16 * j;
+    return (m < t.M && n < t.N) ? X[coff(m, n)] : 0.0;
+  };
+
+  for (int sg = t.seg_begin; sg < t.seg_end; ++sg) {
+    const SegF64 s = segs[sg];
+    if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) s_[i][j] = c_[i][j] = 0.0f;
+    }
+    const double* L = bufs.p[s.l_buf] + s.l_off;
+    const double* R = bufs.p[s.r_buf] + s.r_off;
+    const bool uscaled = s.coef_mode == 0 && s.coef >= 0;
+    const float2 uscale = df_split(uscaled ? coef[s.coef] : 1.0);
+    for (int k0 = 0; k0 < s.K; k0 += DF_BK) {
+#pragma unroll
+      for (int e = 0; e < NI; ++e) {  // BM x BK elements, 256 per pass
+        const int idx = tid + e * DF_THREADS;
+        int m, k;
+        if (s.l_trans) { k = idx / BM; m = idx % BM; }
+        else { m = idx / DF_BK; k = idx % DF_BK; }
+        const int gm = t.m0 + m, gk = k0 + k;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (gm < t.M && gk < s.K) {
+          int bl = 0, mm = gm;
+          if (s.l_rm) { bl = gm / s.l_rm; mm = gm - bl * s.l_rm; }
+          const double* Lb = L + (int64_t)bl * s.l_bs;
+          v = df_split(s.l_trans ? Lb[(int64_t)gk * s.ldl + mm] : Lb[(int64_t)mm * s.ldl + gk]);
+          if (s.coef_mode == 1) v = df_mul(v, df_split(coef[bl * n_terms + s.coef]));
+          else if (uscaled) v = df_mul(v, uscale);
+        }
+        sm.L[k][m] = v;
+      }
+#pragma unroll
+      for (int e = 0; e < NJ; ++e) {  // BN x BK elements
+        const int idx = tid + e * DF_THREADS;
+        int n, k;
+        if (s.r_trans) { n = idx / DF_BK; k = idx % DF_BK; }
+        else { k = idx / BN; n = idx % BN; }
+        const int gn = t.n0 + n, gk = k0 + k;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (gn < t.N && gk < s.K) {
+          int br = 0, nn = gn;
+          if (s.r_rm) { br = gn / s.r_rm; nn = gn - br * s.r_rm; }
+          const double* Rb = R + (int64_t)br * s.r_bs;
+          v = df_split(s.r_trans ? Rb[(int64_t)nn * s.ldr + gk] : Rb[(int64_t)gk * s.ldr + nn]);
+          if (s.coef_mode == 2) v = df_mul(v, df_split(coef[br * n_terms + s.coef]));
+        }
+        sm.R[k][n] = v;
+      }
+      __syncthreads();
+      const int kmax = min(DF_BK, s.K - k0);
+      auto step = [&](int k) {
+        float2 a[NI], b[NJ];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) a[i] = sm.L[k][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) b[j] = sm.R[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) df_fma(a[i], b[j], s_[i][j], c_[i][j]);
+      };
+      if (kmax == DF_BK) {
+#pragma unroll
+        for (int k = 0; k < DF_BK; ++k) step(k);
+      } else {
+        for (int k = 0; k < kmax; ++k) step(k);  // no work on the zero padding of K
+      }
+      // renormalise (fast two-sum, |c| << |s|): c restarts near ulp(s) / 2,
+      // so its own rounding stays near 2^-48 |s| per K step of the next tile
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const float t2 = __fadd_rn(s_[i][j], c_[i][j]);
+          c_[i][j] = __fsub_rn(c_[i][j], __fsub_rn(t2, s_[i][j]));
+          s_[i][j] = t2;
+        }
+      __syncthreads();
+    }
+    if (DOTS) {  // this segment's dots with the wavefunction (float64), then its coefficients
+      const int ql = sg - t.seg_begin;
+      double* out = dot_out + (int64_t)(t.dot_base + ql) * DF_BMAX;
+      if (!by_col) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          double part = 0.0;
+          const double cf = coef[mrow(i) * n_terms + s.coef];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const double v = df_value(s_[i][j], c_[i][j]);
+            part = fma(v, xo(i, j), part);
+            accd[DOTS ? i : 0][DOTS ? j : 0] = fma(cf, v, accd[DOTS ? i : 0][DOTS ? j : 0]);
+          }
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          if (tx == 0) out[ty + 16 * i] = part;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          double part = 0.0;
+          const double cf = coef[mcol(j) * n_terms + s.coef];
+#pragma unroll
+          for (int i = 0; i < NI; ++i) {
+            const double v = df_value(s_[i][j], c_[i][j]);
+            part = fma(v, xo(i, j), part);
+            accd[DOTS ? i : 0][DOTS ? j : 0] = fma(cf, v, accd[DOTS ? i : 0][DOTS ? j : 0]);
+          }
+          dsm->col[ty][tx + 16 * j] = part;
+        }
+        __syncthreads();
+        if (tid < BN) {
+          double tot = 0.0;
+#pragma unroll
+          for (int y2 = 0; y2 < 16; ++y2) tot += dsm->col[y2][tid];
+          out[tid] = tot;
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  double* C = bufs.p[t.c_buf] + t.c_off;
+  if (t.mode == TM_STORE || t.mode == TM_STORE_DOTS) {
+    const bool add = accumulate || t.add;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int m = t.m0 + ty + 16 * i;
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int n = t.n0 + tx + 16 * j;
+        if (n >= t.N) continue;
+        const double v = DOTS ? accd[DOTS ? i : 0][DOTS ? j : 0] : df_value(s_[i][j], c_[i][j]);
+        double* p = C + coff(m, n);
+        *p = add ? *p + v : v;
+      }
+    }
+  } else {  // TM_DOT: sum over the tile of acc .* C, fixed-order block reduction
+    double part = 0.0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int m = t.m0 + ty + 16 * i;
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int n = t.n0 + tx + 16 * j;
+        if (n >= t.N) continue;
+        part = fma(df_value(s_[i][j], c_[i][j]), C[coff(m, n)], part);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) sm.red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < DF_THREADS / 32; ++w) tot += sm.red[w];
+      dot_out[blockIdx.x] = tot;
+    }
+  }
+}
+
+#define DF_SHAPES(CASE)                                         \
+  CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(2, 1) CASE(2, 2) \
+  CASE(2, 3) CASE(2, 4) CASE(3, 1) CASE(3, 2) CASE(3, 3) CASE(3, 4) \
+  CASE(4, 1) CASE(4, 2) CASE(4, 3) CASE(4, 4)
+
+__global__ void __launch_bounds__(DF_THREADS, 2)
+seg_gemm_df_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs, Bufs bufs,
+                   const double* __restrict__ coef, int n_terms, int accumulate, double* __restrict__ dot_out,
+                   const int32_t* __restrict__ skip) {
+  __shared__ DFSmem sm;
+  if (skip && *skip) return;
+  const TileF64 t = tiles[blockIdx.x];
+#define DF_CASE(I, J) \
+  case (I) | ((J) << 8): df_tile<I, J, false>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, nullptr); break;
+  switch (t.shape) {
+    DF_SHAPES(DF_CASE)
+    default: break;  // the host builds only the shapes above
+  }
+#undef DF_CASE
+}
+
+__global__ void __launch_bounds__(DF_THREADS, 2)
+seg_gemm_df_dots_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs, Bufs bufs,
+                        const double* __restrict__ coef, int n_terms, int accumulate, double* __restrict__ dot_out,
+                        const int32_t* __restrict__ skip) {
+  __shared__ DFSmem sm;
+  __shared__ DFDotSmem dsm;
+  if (skip && *skip) return;
+  const TileF64 t = tiles[blockIdx.x];
+#define DF_CASE(I, J) \
+  case (I) | ((J) << 8): df_tile<I, J, true>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, &dsm); break;
+  switch (t.shape) {
+    DF_SHAPES(DF_CASE)
+    default: break;
+  }
+#undef DF_CASE
+}
+#undef DF_SHAPES
+
+void launch_seg_gemm_df(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms, int accumulate,
+                        double* dot_out, const int32_t* skip, cudaStream_t st) {
+  if (tl.n_tiles == 0) return;
+  seg_gemm_df_kernel<<<(unsigned)tl.n_tiles, DF_THREADS, 0, st>>>(tl.d_tiles, tl.d_segs, bufs, coef, n_terms,
+                                                                  accumulate, dot_out, skip);
+}
+
+void launch_seg_gemm_df_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
+                             int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st) {
+  if (tl.n_tiles == 0) return;
+  seg_gemm_df_dots_kernel<<<(unsigned)tl.n_tiles, DF_THREADS, 0, st>>>(tl.d_tiles, tl.d_segs, bufs, coef, n_terms,
+                                                                       accumulate, dot_out, skip);
+}
+
+}  // namespace dmrg

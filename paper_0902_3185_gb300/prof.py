@@ -25,6 +25,7 @@ TRAFFIC_SOURCES = {
     "tensor_product_bf16x3": ["paper_0902_3185_gb300/csrc/matvec_tc.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
     "tensor_product_tf32": ["paper_0902_3185_gb300/csrc/matvec_tc.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
     "fp64_product": ["paper_0902_3185_gb300/csrc/matvec_f64.cu"],
+    "df64_product": ["paper_0902_3185_gb300/csrc/matvec_df.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
 }
 
 
@@ -60,7 +61,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="ladder_m1000", choices=["ladder_m1000", "random64"])
     ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3", "df64"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--lanczos-iters", type=int, default=0, help="also run a fixed-length Lanczos")
     ap.add_argument("--autotune", action="store_true", help="autotune, then time eager and graph-captured products")
@@ -79,7 +80,7 @@ def main():
     y = g.empty()
     for _ in range(a.reps):
         g.apply_H(x, y, prec=a.prec)
-    if a.autotune and a.prec != "fp64":
+    if a.autotune and a.prec in ("tf32", "bf16x3"):
         import json
         rep = g.autotune(prec=a.prec, reps=7)
         # products replayed from a CUDA graph (the library launches on the capturing stream)

@@ -1,6 +1,8 @@
 """GPU parity of the float64 path against the CPU oracle, through the C ABI.
 
-Tolerances (float64 products, different summation order than NumPy):
+Tolerances (float64 products, different summation order than NumPy; the
+double-float product, 48 significant bits, about 2^-46 relative per
+multiply-add, meets the same bar):
 element-wise |y_gpu - y_oracle| <= 1e-12 * max|y_oracle| for the product,
 its transpose and the term dots; |dE0| <= 1e-10 * |E0| for Lanczos
 (the paper's solver tolerance is the residual; the energy error is its
@@ -72,6 +74,39 @@ def test_apply_H_fp64(dev, name):
     yt = yt.cpu().numpy()
     for b in range(sb.batch):
         assert close(yt[b], y0[b] + osb.apply_H(sb, X[b], b))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_H_df64(dev, name):
+    """The double-float product against the float64 oracle, every element,
+    plain and accumulating."""
+    sb = CASES[name]()
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(10 + b, sb.dim) for b in range(sb.batch)])
+    y = g.apply_H(to_dev(X), prec="df64").cpu().numpy()
+    y0 = np.stack([seeded_normal(50 + b, sb.dim) for b in range(sb.batch)])
+    yt = to_dev(y0)
+    g.apply_H(to_dev(X), y=yt, accumulate=True, prec="df64")
+    yt = yt.cpu().numpy()
+    for b in range(sb.batch):
+        ref = osb.apply_H(sb, X[b], b)
+        assert close(y[b], ref), (name, b)
+        assert close(yt[b], y0[b] + ref)
+
+
+def test_df64_split_edge_values(dev):
+    """Inputs outside the double-float range of the split (zeros, values
+    below 2^-74 whose low part is dropped, signs) still give the product to
+    the float64 bar in the max norm."""
+    sb = CASES["ragged"]()
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(70 + b, sb.dim) for b in range(sb.batch)])
+    X[:, ::7] = 0.0
+    X[:, 1::11] *= 1e-30
+    X[:, 2::13] *= -1.0
+    y = g.apply_H(to_dev(X), prec="df64").cpu().numpy()
+    for b in range(sb.batch):
+        assert close(y[b], osb.apply_H(sb, X[b], b))
 
 
 @pytest.mark.parametrize("name", ["ragged", "random16", "hub_ladder_grown"])
@@ -166,24 +201,29 @@ def test_set_coeffs_and_autograd(dev):
 
 @pytest.mark.slow
 def test_full_size_ladder_m1000_sampled(dev):
-    """The 2 x 32 ladder at m = 1000, 16 members: float64 product of two
-    members against the oracle, every element."""
+    """The 2 x 32 ladder at m = 1000, 16 members: float64 and double-float
+    products of two members against the oracle, every element."""
     sb = ladder_m1000(batch=16)
     g = gpu_sb(sb)
     X = np.stack([seeded_normal(100 + b, sb.dim) for b in range(sb.batch)])
     y = g.apply_H(to_dev(X)).cpu().numpy()
+    yd = g.apply_H(to_dev(X), prec="df64").cpu().numpy()
     for b in (0, 15):
-        assert close(y[b], osb.apply_H(sb, X[b], b))
+        ref = osb.apply_H(sb, X[b], b)
+        assert close(y[b], ref)
+        assert close(yd[b], ref)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_apply_H_term_dots(dev, name):
+def test_apply_H_term_dots(dev, name, prec):
     """One pass gives H psi (as the float64 product) and the per-term dots
-    <psi, (A_k x B_k) psi> (as the oracle's term products)."""
+    <psi, (A_k x B_k) psi> (as the oracle's term products), in float64 or
+    double-float arithmetic."""
     sb = CASES[name]()
     g = gpu_sb(sb)
     X = np.stack([seeded_normal(30 + b, sb.dim) for b in range(sb.batch)])
-    y, dots = g.apply_H_term_dots(to_dev(X))
+    y, dots = g.apply_H_term_dots(to_dev(X), prec=prec)
     y, dots = y.cpu().numpy(), dots.cpu().numpy()
     for b in range(sb.batch):
         assert close(y[b], osb.apply_H(sb, X[b], b))
@@ -193,7 +233,7 @@ def test_apply_H_term_dots(dev, name):
 
 
 @pytest.mark.parametrize("prec,refine", [("bf16x3", "newton"), ("tf32", "newton"), ("fp64", "none"),
-                                         ("bf16x3", "lanczos")])
+                                         ("bf16x3", "lanczos"), ("bf16x3", "newton_df64")])
 def test_lanczos_ground_grad(dev, prec, refine):
     """The gradient returned with the solve (from the refinement's last float64
     product, or computed after it) equals dmrg_energy_grad of the returned
