@@ -133,41 +133,111 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
     const double* R = bufs.p[s.r_buf] + s.r_off;
     const bool uscaled = s.coef_mode == 0 && s.coef >= 0;
     const float2 uscale = df_split(uscaled ? coef[s.coef] : 1.0);
-    for (int k0 = 0; k0 < s.K; k0 += DF_BK) {
+    // this thread's load slots, fixed over the segment: tile row / column,
+    // local k, element offset at k = 0 (-1: outside the output), the K stride
+    // and the (member) coefficient as a double-float pair.  Kept in
+    // registers by the plain kernel; the dots kernel, whose float64 sums take
+    // those registers, recomputes them per K tile.
+    constexpr bool HOIST = !DOTS;
+    constexpr int HI = HOIST ? NI : 1, HJ = HOIST ? NJ : 1;
+    int lm[HI], lk[HI], loff[HI];
+    float2 lcf[HI];
+    const int lks = s.l_trans ? s.ldl : 1;
+    int rn_[HJ], rk[HJ], roff_[HJ];
+    float2 rcf[HJ];
+    const int rks = s.r_trans ? 1 : s.ldr;
+    if constexpr (HOIST) {
 #pragma unroll
-      for (int e = 0; e < NI; ++e) {  // BM x BK elements, 256 per pass
+      for (int e = 0; e < NI; ++e) {
         const int idx = tid + e * DF_THREADS;
-        int m, k;
-        if (s.l_trans) { k = idx / BM; m = idx % BM; }
-        else { m = idx / DF_BK; k = idx % DF_BK; }
-        const int gm = t.m0 + m, gk = k0 + k;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (gm < t.M && gk < s.K) {
-          int bl = 0, mm = gm;
-          if (s.l_rm) { bl = gm / s.l_rm; mm = gm - bl * s.l_rm; }
-          const double* Lb = L + (int64_t)bl * s.l_bs;
-          v = df_split(s.l_trans ? Lb[(int64_t)gk * s.ldl + mm] : Lb[(int64_t)mm * s.ldl + gk]);
-          if (s.coef_mode == 1) v = df_mul(v, df_split(coef[bl * n_terms + s.coef]));
-          else if (uscaled) v = df_mul(v, uscale);
-        }
-        sm.L[k][m] = v;
+        if (s.l_trans) { lk[e] = idx / BM; lm[e] = idx % BM; }
+        else { lm[e] = idx / DF_BK; lk[e] = idx % DF_BK; }
+        const int gm = t.m0 + lm[e];
+        int bl = 0, mm = gm;
+        if (s.l_rm) { bl = gm / s.l_rm; mm = gm - bl * s.l_rm; }
+        loff[e] = gm < t.M ? (int)((int64_t)bl * s.l_bs + (s.l_trans ? (int64_t)mm : (int64_t)mm * s.ldl)) : -1;
+        lcf[e] = s.coef_mode == 1 && gm < t.M ? df_split(coef[bl * n_terms + s.coef]) : uscale;
       }
 #pragma unroll
-      for (int e = 0; e < NJ; ++e) {  // BN x BK elements
+      for (int e = 0; e < NJ; ++e) {
         const int idx = tid + e * DF_THREADS;
-        int n, k;
-        if (s.r_trans) { n = idx / DF_BK; k = idx % DF_BK; }
-        else { k = idx / BN; n = idx % BN; }
-        const int gn = t.n0 + n, gk = k0 + k;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (gn < t.N && gk < s.K) {
-          int br = 0, nn = gn;
-          if (s.r_rm) { br = gn / s.r_rm; nn = gn - br * s.r_rm; }
-          const double* Rb = R + (int64_t)br * s.r_bs;
-          v = df_split(s.r_trans ? Rb[(int64_t)nn * s.ldr + gk] : Rb[(int64_t)gk * s.ldr + nn]);
-          if (s.coef_mode == 2) v = df_mul(v, df_split(coef[br * n_terms + s.coef]));
+        if (s.r_trans) { rn_[e] = idx / DF_BK; rk[e] = idx % DF_BK; }
+        else { rk[e] = idx / BN; rn_[e] = idx % BN; }
+        const int gn = t.n0 + rn_[e];
+        int br = 0, nn = gn;
+        if (s.r_rm) { br = gn / s.r_rm; nn = gn - br * s.r_rm; }
+        roff_[e] = gn < t.N ? (int)((int64_t)br * s.r_bs + (s.r_trans ? (int64_t)nn * s.ldr : (int64_t)nn)) : -1;
+        rcf[e] = s.coef_mode == 2 && gn < t.N ? df_split(coef[br * n_terms + s.coef]) : make_float2(1.0f, 0.0f);
+      }
+    }
+    const bool lscaled = s.coef_mode == 1 || uscaled, rscaled = s.coef_mode == 2;
+    // plain kernel: the raw float64 values of the next K tile are loaded
+    // before the current tile's multiply-adds (software prefetch)
+    double pl[HI], pr[HJ];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int e = 0; e < HI; ++e) {
+        const int gk = k0 + lk[e];
+        pl[e] = (loff[e] >= 0 && gk < s.K) ? L[loff[e] + (int64_t)gk * lks] : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < HJ; ++e) {
+        const int gk = k0 + rk[e];
+        pr[e] = (roff_[e] >= 0 && gk < s.K) ? R[roff_[e] + (int64_t)gk * rks] : 0.0;
+      }
+    };
+    if constexpr (HOIST) fetch(0);
+    for (int k0 = 0; k0 < s.K; k0 += DF_BK) {
+      if constexpr (HOIST) {
+#pragma unroll
+        for (int e = 0; e < NI; ++e) {  // BM x BK elements, 256 per pass
+          float2 v = df_split(pl[e]);
+          if (lscaled) v = df_mul(v, lcf[e]);
+          sm.L[lk[e]][lm[e]] = v;
         }
-        sm.R[k][n] = v;
+#pragma unroll
+        for (int e = 0; e < NJ; ++e) {  // BN x BK elements
+          float2 v = df_split(pr[e]);
+          if (rscaled) v = df_mul(v, rcf[e]);
+          sm.R[rk[e]][rn_[e]] = v;
+        }
+        if (k0 + DF_BK < s.K) fetch(k0 + DF_BK);
+      } else {
+#pragma unroll
+        for (int e = 0; e < NI; ++e) {
+          const int idx = tid + e * DF_THREADS;
+          int m, k;
+          if (s.l_trans) { k = idx / BM; m = idx % BM; }
+          else { m = idx / DF_BK; k = idx % DF_BK; }
+          const int gm = t.m0 + m, gk = k0 + k;
+          float2 v = make_float2(0.0f, 0.0f);
+          if (gm < t.M && gk < s.K) {
+            int bl = 0, mm = gm;
+            if (s.l_rm) { bl = gm / s.l_rm; mm = gm - bl * s.l_rm; }
+            const double* Lb = L + (int64_t)bl * s.l_bs;
+            v = df_split(s.l_trans ? Lb[(int64_t)gk * s.ldl + mm] : Lb[(int64_t)mm * s.ldl + gk]);
+            if (s.coef_mode == 1) v = df_mul(v, df_split(coef[bl * n_terms + s.coef]));
+            else if (uscaled) v = df_mul(v, uscale);
+          }
+          sm.L[k][m] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < NJ; ++e) {
+          const int idx = tid + e * DF_THREADS;
+          int n, k;
+          if (s.r_trans) { n = idx / DF_BK; k = idx % DF_BK; }
+          else { k = idx / BN; n = idx % BN; }
+          const int gn = t.n0 + n, gk = k0 + k;
+          float2 v = make_float2(0.0f, 0.0f);
+          if (gn < t.N && gk < s.K) {
+            int br = 0, nn = gn;
+            if (s.r_rm) { br = gn / s.r_rm; nn = gn - br * s.r_rm; }
+            const double* Rb = R + (int64_t)br * s.r_bs;
+            v = df_split(s.r_trans ? Rb[(int64_t)nn * s.ldr + gk] : Rb[(int64_t)gk * s.ldr + nn]);
+            if (s.coef_mode == 2) v = df_mul(v, df_split(coef[br * n_terms + s.coef]));
+          }
+          sm.R[k][n] = v;
+        }
       }
       __syncthreads();
       const int kmax = min(DF_BK, s.K - k0);
