@@ -486,6 +486,20 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
 #pragma unroll
       for (int k = 1; k < TC_MAX_SLOTS; ++k)
         slot_sc[k] = ((tl.slot_used >> k) & 1) && mv ? coef_f(b * n_terms + tl.slot_term[k]) : 0.0f;
+      // pieced tiles: lane l holds piece l's output (panel, rows per member,
+      // atoms, columns, coefficient column, first column), which each chunk
+      // then reads with shuffles instead of dependent loads
+      char* pc_p = nullptr;
+      int pc_np = 0, pc_at = 0, pc_n = 0, pc_term = -1, pc_col0 = 0;
+      if (tl.pieced && lane < tl.seg_end - tl.seg_begin) {
+        const TcOut& so = seg_outs[tl.seg_begin + lane];
+        pc_p = so.p;
+        pc_np = so.Np;
+        pc_at = so.p_atoms;
+        pc_n = so.N;
+        pc_term = so.term;
+        pc_col0 = segs[tl.seg_begin + lane].col0;
+      }
       const int c_first = tile_split ? 0 : 16 * half, c_step = tile_split ? 16 : 16 * TC_EPI_PARTS;
       const int c_end = tl.m0 + 32 * q < o.M ? tl.ntile : 0;  // no rows of this quadrant: nothing to drain
       for (int c0 = c_first; c0 < c_end; c0 += c_step) {
@@ -544,8 +558,13 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           if (tl.pieced) {
             const int ci = c0 >> 4;
             const int pi = (int)(((ci < 8 ? tl.cmap_lo >> (4 * ci) : tl.cmap_hi >> (4 * (ci - 8)))) & 15u);
-            po = seg_outs[tl.seg_begin + pi];
-            pcol0 = segs[tl.seg_begin + pi].col0;
+            po.p = reinterpret_cast<char*>(
+                __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(pc_p), pi));
+            po.Np = __shfl_sync(0xffffffffu, pc_np, pi);
+            po.p_atoms = __shfl_sync(0xffffffffu, pc_at, pi);
+            po.N = __shfl_sync(0xffffffffu, pc_n, pi);
+            po.term = __shfl_sync(0xffffffffu, pc_term, pi);
+            pcol0 = __shfl_sync(0xffffffffu, pc_col0, pi);
             pscf = (po.term >= 0 && mv) ? coef_f(b * n_terms + po.term) : 1.0f;
           }
           const int pend = tl.pieced ? po.N : nend;  // end column (a piece counts from its own first)
