@@ -94,11 +94,6 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
   for (int i = 0; i < NI; ++i)
 #pragma unroll
     for (int j = 0; j < NJ; ++j) s_[i][j] = c_[i][j] = 0.0f;
-  double accd[DOTS ? NI : 1][DOTS ? NJ : 1];  // DOTS: the coefficient-weighted sum in float64
-#pragma unroll
-  for (int i = 0; i < (DOTS ? NI : 1); ++i)
-#pragma unroll
-    for (int j = 0; j < (DOTS ? NJ : 1); ++j) accd[i][j] = 0.0;
   auto coff = [&](int m, int n) -> int64_t {
     int b = 0;
     if (t.c_rm) {
@@ -121,6 +116,15 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
     return (m < t.M && n < t.N) ? X[coff(m, n)] : 0.0;
   };
 
+  // DOTS: each segment's coefficient-weighted sum goes straight to the
+  // output (written by the first segment, added by the others), which keeps
+  // the registers of a float64 accumulator free for the load pipeline
+  auto put = [&](int i, int j, double v, bool first) {
+    const int m = t.m0 + ty + 16 * i, n = t.n0 + tx + 16 * j;
+    if (m >= t.M || n >= t.N) return;
+    double* p = bufs.p[t.c_buf] + t.c_off + coff(m, n);
+    *p = (first && !(accumulate || t.add)) ? v : *p + v;
+  };
   for (int sg = t.seg_begin; sg < t.seg_end; ++sg) {
     const SegF64 s = segs[sg];
     if (DOTS) {
@@ -135,18 +139,15 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
     const float2 uscale = df_split(uscaled ? coef[s.coef] : 1.0);
     // this thread's load slots, fixed over the segment: tile row / column,
     // local k, element offset at k = 0 (-1: outside the output), the K stride
-    // and the (member) coefficient as a double-float pair.  Kept in
-    // registers by the plain kernel; the dots kernel, whose float64 sums take
-    // those registers, recomputes them per K tile.
-    constexpr bool HOIST = !DOTS;
-    constexpr int HI = HOIST ? NI : 1, HJ = HOIST ? NJ : 1;
+    // and the (member) coefficient as a double-float pair
+    constexpr int HI = NI, HJ = NJ;
     int lm[HI], lk[HI], loff[HI];
     float2 lcf[HI];
     const int lks = s.l_trans ? s.ldl : 1;
     int rn_[HJ], rk[HJ], roff_[HJ];
     float2 rcf[HJ];
     const int rks = s.r_trans ? 1 : s.ldr;
-    if constexpr (HOIST) {
+    {
 #pragma unroll
       for (int e = 0; e < NI; ++e) {
         const int idx = tid + e * DF_THREADS;
@@ -171,8 +172,8 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
       }
     }
     const bool lscaled = s.coef_mode == 1 || uscaled, rscaled = s.coef_mode == 2;
-    // plain kernel: the raw float64 values of the next K tile are loaded
-    // before the current tile's multiply-adds (software prefetch)
+    // the raw float64 values of the next K tile are loaded before the
+    // current tile's multiply-adds (software prefetch)
     double pl[HI], pr[HJ];
     auto fetch = [&](int k0) {
 #pragma unroll
@@ -186,9 +187,9 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
         pr[e] = (roff_[e] >= 0 && gk < s.K) ? R[roff_[e] + (int64_t)gk * rks] : 0.0;
       }
     };
-    if constexpr (HOIST) fetch(0);
+    fetch(0);
     for (int k0 = 0; k0 < s.K; k0 += DF_BK) {
-      if constexpr (HOIST) {
+      {
 #pragma unroll
         for (int e = 0; e < NI; ++e) {  // BM x BK elements, 256 per pass
           float2 v = df_split(pl[e]);
@@ -202,42 +203,6 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
           sm.R[rk[e]][rn_[e]] = v;
         }
         if (k0 + DF_BK < s.K) fetch(k0 + DF_BK);
-      } else {
-#pragma unroll
-        for (int e = 0; e < NI; ++e) {
-          const int idx = tid + e * DF_THREADS;
-          int m, k;
-          if (s.l_trans) { k = idx / BM; m = idx % BM; }
-          else { m = idx / DF_BK; k = idx % DF_BK; }
-          const int gm = t.m0 + m, gk = k0 + k;
-          float2 v = make_float2(0.0f, 0.0f);
-          if (gm < t.M && gk < s.K) {
-            int bl = 0, mm = gm;
-            if (s.l_rm) { bl = gm / s.l_rm; mm = gm - bl * s.l_rm; }
-            const double* Lb = L + (int64_t)bl * s.l_bs;
-            v = df_split(s.l_trans ? Lb[(int64_t)gk * s.ldl + mm] : Lb[(int64_t)mm * s.ldl + gk]);
-            if (s.coef_mode == 1) v = df_mul(v, df_split(coef[bl * n_terms + s.coef]));
-            else if (uscaled) v = df_mul(v, uscale);
-          }
-          sm.L[k][m] = v;
-        }
-#pragma unroll
-        for (int e = 0; e < NJ; ++e) {
-          const int idx = tid + e * DF_THREADS;
-          int n, k;
-          if (s.r_trans) { n = idx / DF_BK; k = idx % DF_BK; }
-          else { k = idx / BN; n = idx % BN; }
-          const int gn = t.n0 + n, gk = k0 + k;
-          float2 v = make_float2(0.0f, 0.0f);
-          if (gn < t.N && gk < s.K) {
-            int br = 0, nn = gn;
-            if (s.r_rm) { br = gn / s.r_rm; nn = gn - br * s.r_rm; }
-            const double* Rb = R + (int64_t)br * s.r_bs;
-            v = df_split(s.r_trans ? Rb[(int64_t)nn * s.ldr + gk] : Rb[(int64_t)gk * s.ldr + nn]);
-            if (s.coef_mode == 2) v = df_mul(v, df_split(coef[br * n_terms + s.coef]));
-          }
-          sm.R[k][n] = v;
-        }
       }
       __syncthreads();
       const int kmax = min(DF_BK, s.K - k0);
@@ -282,7 +247,7 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
           for (int j = 0; j < NJ; ++j) {
             const double v = df_value(s_[i][j], c_[i][j]);
             part = fma(v, xo(i, j), part);
-            accd[DOTS ? i : 0][DOTS ? j : 0] = fma(cf, v, accd[DOTS ? i : 0][DOTS ? j : 0]);
+            put(i, j, cf * v, sg == t.seg_begin);
           }
 #pragma unroll
           for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -297,7 +262,7 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
           for (int i = 0; i < NI; ++i) {
             const double v = df_value(s_[i][j], c_[i][j]);
             part = fma(v, xo(i, j), part);
-            accd[DOTS ? i : 0][DOTS ? j : 0] = fma(cf, v, accd[DOTS ? i : 0][DOTS ? j : 0]);
+            put(i, j, cf * v, sg == t.seg_begin);
           }
           dsm->col[ty][tx + 16 * j] = part;
         }
@@ -313,8 +278,14 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
     }
   }
 
+  if (DOTS && t.seg_begin == t.seg_end) {  // an output no segment writes
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) put(i, j, 0.0, true);
+  }
   double* C = bufs.p[t.c_buf] + t.c_off;
-  if (t.mode == TM_STORE || t.mode == TM_STORE_DOTS) {
+  if (t.mode == TM_STORE) {
     const bool add = accumulate || t.add;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
@@ -324,12 +295,12 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
       for (int j = 0; j < NJ; ++j) {
         const int n = t.n0 + tx + 16 * j;
         if (n >= t.N) continue;
-        const double v = DOTS ? accd[DOTS ? i : 0][DOTS ? j : 0] : df_value(s_[i][j], c_[i][j]);
+        const double v = df_value(s_[i][j], c_[i][j]);
         double* p = C + coff(m, n);
         *p = add ? *p + v : v;
       }
     }
-  } else {  // TM_DOT: sum over the tile of acc .* C, fixed-order block reduction
+  } else if (t.mode == TM_DOT) {  // sum over the tile of acc .* C, fixed-order block reduction
     double part = 0.0;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
