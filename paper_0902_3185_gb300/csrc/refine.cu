@@ -196,16 +196,18 @@ __global__ void k_rf_minv(const double* __restrict__ diag, const double* __restr
 }
 
 // sc[b][RR_NEW, A1, A2 (, MU)] = sums of the partial rows 0..2 (and 3 when
-// with_mu), fixed order
+// with_mu), fixed order; one warp per row
 __global__ void k_rf_sum4(const double* __restrict__ part, double* __restrict__ sc, int nchunk, int batch,
                           int with_mu, const int32_t* __restrict__ ctl, const int32_t* __restrict__ stop) {
-  const int b = blockIdx.x, k = threadIdx.x;
+  const int b = blockIdx.x, k = threadIdx.x >> 5, lane = threadIdx.x & 31;  // one warp per row
   if (k >= 3 + with_mu || (stop && *stop) || (ctl && ctl[b])) return;
   const double* row = part + ((int64_t)k * batch + b) * nchunk;
   double t = 0.0;
-  for (int ch = 0; ch < nchunk; ++ch) t += row[ch];
+  for (int ch = lane; ch < nchunk; ch += 32) t += row[ch];  // lane-strided, then a fixed shuffle tree
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   const int slot[4] = {RF_RRNEW, RF_A1, RF_A2, RF_MU};
-  sc[b * RF_NSC + slot[k]] = t;
+  if (lane == 0) sc[b * RF_NSC + slot[k]] = t;
 }
 
 // start of an outer step: gamma = a1 / mu, rho = a2 - gamma a3 from the
@@ -321,7 +323,7 @@ void rf_launch_dir(float* p, const float* res, const float* psi, const float* mi
 }
 void rf_launch_sum4(const double* part, double* sc, int64_t D, int B, int with_mu, const int32_t* ctl,
                     const int32_t* stop, cudaStream_t st) {
-  k_rf_sum4<<<B, 32, 0, st>>>(part, sc, lz_nchunk(D), B, with_mu, ctl, stop);
+  k_rf_sum4<<<B, 128, 0, st>>>(part, sc, lz_nchunk(D), B, with_mu, ctl, stop);
 }
 static int rf_vec_blocks(int64_t D) {
   const int64_t nb = (D + 255) / 256;
