@@ -33,16 +33,25 @@ def record_traffic(name, csv_path, note=""):
     import csv
     import hashlib
     import json
-    rows = list(csv.reader(open(csv_path)))
-    hdr, units = rows[0], rows[1]
+    rows = [r for r in csv.reader(open(csv_path)) if r and not r[0].startswith("==")]
+    hdr = rows[0]
+    scales = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}
     total, launches = 0.0, 0
-    for r in rows[2:]:
-        d = dict(zip(hdr, r))
-        for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            u = units[hdr.index(k)].lower()
-            scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}[u]
-            total += float(d[k]) * scale
-        launches += 1
+    if "Metric Name" in hdr:  # --csv --log-file: one row per (launch, metric)
+        ids = set()
+        for r in rows[1:]:
+            d = dict(zip(hdr, r))
+            if d.get("Metric Name") in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                total += float(d["Metric Value"].replace(",", "")) * scales[d["Metric Unit"].lower()]
+                ids.add(d["ID"])
+        launches = len(ids)
+    else:  # --page raw --csv: one row per launch, units in the second row
+        units = rows[1]
+        for r in rows[2:]:
+            d = dict(zip(hdr, r))
+            for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                total += float(d[k]) * scales[units[hdr.index(k)].lower()]
+            launches += 1
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES[name]:
         h.update(open(os.path.join(ROOT, f), "rb").read())
