@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=300)
-    ap.add_argument("--mixed-tol", type=float, default=1e-4)
+    ap.add_argument("--mixed-tol", type=float, default=2e-4)
     ap.add_argument("--refine", default="newton_df64", choices=["newton", "newton_df64", "lanczos", "none"])
     return ap.parse_args()
 

@@ -643,6 +643,9 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
     if (sb->h_ctl[LZ_CTL_ALLDONE]) break;
     if (launched > max_iter + K) throw Invalid{"Lanczos control did not terminate"};
   }
+  // float64 eigenpairs of the members that stopped on the float32 test, side by side
+  lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, sb->lz_ctl, sb->lz_out + 4 * B, B, cap, D, st, 1);
+  CK(cudaMemcpyAsync(sb->h_ctl, sb->lz_ctl, sizeof(int32_t) * (LZ_CTL_MEMBER + 2 * B), cudaMemcpyDeviceToHost, st));
   lz_launch_ritz(sb->lz_V, sb->lz_s, sb->lz_ctl, psi_out, D, B, cap, st);
   lz_launch_sumsq(psi_out, part, D, B, nch, st);
   lz_launch_sum_chunks(part, nrm2, nch, B, st);
@@ -655,7 +658,7 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
   CK(cudaGetLastError());
   if (tc_err) throw Timeout{"a tensor-core kernel gave up a bounded wait"};
   LzRun r;
-  r.launches = 3 + (int64_t)launched * (LZ_KERNELS_PER_ITER + matvec_launches(sb, prec)) + 4;
+  r.launches = 3 + (int64_t)launched * (LZ_KERNELS_PER_ITER + matvec_launches(sb, prec)) + 5;
   for (int b = 0; b < B; ++b) {
     r.code.push_back(sb->h_ctl[LZ_CTL_MEMBER + b]);
     r.iters.push_back(sb->h_ctl[LZ_CTL_MEMBER + B + b]);

@@ -17,7 +17,8 @@
 //
 // Control words (int32, device): [0] j = index of the current Krylov vector,
 // [1] max_iter, [2] check_every, [3] all members done, then per member b:
-// [4 + b] done code (0 running, 1 converged, 2 breakdown, 3 NaN, 4 cap hit)
+// [4 + b] done code (0 running, 1 converged, 2 breakdown, 3 NaN, 4 cap hit,
+// 5 pending: stopped on the float32 test, float64 check after the loop)
 // and [4 + batch + b] number of Lanczos vectors in its tridiagonal matrix.
 
 #include <cfloat>
@@ -392,15 +393,22 @@ __device__ void inverse_iteration(const T* a, const T* e, int n, T sigma, T* z, 
 //  - every check: float32 multisection and float32 inverse iteration give
 //    theta and the last Ritz-vector component to a few digits, enough for the
 //    test beta_j |s_j| <= tol max(1, |theta|);
-//  - when the test passes (or at breakdown / the cap) the eigenpair is
-//    recomputed in float64 (multisection from the float32 bracket, widened by
-//    its rounding bound, then inverse iteration), the test is repeated with
-//    the float64 values, and s is stored for the Ritz vector.
+//  - when the float32 test passes with a factor 2 to spare, the member stops
+//    as LZ_PENDING; after the iteration loop one launch (final_pass) redoes
+//    the float32 step for every pending member at its own length, computes
+//    the eigenpair in float64 (multisection from the float32 bracket, widened
+//    by its rounding bound, then inverse iteration), repeats the test with
+//    the float64 values (a member that then misses the tolerance ends as
+//    LZ_CAP) and stores s for the Ritz vector: the members' float64 solves
+//    run side by side in one launch instead of each in the launch where its
+//    member converged;
+//  - at breakdown or the cap the float64 eigenpair is computed at once.
 // GB300 issues float64 at 1/64 of the float32 rate, which is why the per-
 // iteration test runs in float32.
 __global__ void __launch_bounds__(32)
 k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __restrict__ out,
-          int32_t* __restrict__ ctl, const double* __restrict__ tolp, int batch, int cap, int64_t D) {
+          int32_t* __restrict__ ctl, const double* __restrict__ tolp, int batch, int cap, int64_t D,
+          int final_pass) {
   extern __shared__ double sm[];
   double* a = sm;
   double* e = sm + cap;
@@ -414,9 +422,8 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
   float* rp32 = z32 + cap;
   const int b = blockIdx.x;
   const int lane = threadIdx.x;
-  if (member_done(ctl, b)) return;
-  const int j = ctl[LZ_CTL_J];
-  const int n = j + 1;
+  if (final_pass ? ctl[LZ_CTL_MEMBER + b] != LZ_PENDING : member_done(ctl, b)) return;
+  const int n = final_pass ? ctl[LZ_CTL_MEMBER + batch + b] : ctl[LZ_CTL_J] + 1;
   const int max_iter = ctl[LZ_CTL_MAXIT];
   const int check_every = ctl[LZ_CTL_CHECK];
   const double tol = *tolp;
@@ -456,7 +463,7 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
     }
     return;
   }
-  if (!((n % check_every == 0) || last || small_beta)) return;
+  if (!final_pass && !((n % check_every == 0) || last || small_beta)) return;
 
   // ---- float32 estimate
   const float eps32 = 1.2e-7f;
@@ -470,12 +477,16 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
                            false);
   __syncwarp();
   const double est = beta * fabs((double)z32[n - 1]);
-  const bool pass32 = est <= tol * fmax(1.0, fabs((double)th32));
-  if (!(pass32 || small_beta || last)) {
+  const bool pass32 = est <= 0.5 * tol * fmax(1.0, fabs((double)th32));
+  if (!final_pass && !(small_beta || last)) {
     if (lane == 0) {
       out[b * 4 + 0] = th32;
       out[b * 4 + 1] = est;
       out[b * 4 + 2] = beta;
+      if (pass32) {
+        ctl[LZ_CTL_MEMBER + b] = LZ_PENDING;
+        ctl[LZ_CTL_MEMBER + batch + b] = n;
+      }
     }
     return;
   }
@@ -504,7 +515,7 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
     if (!isfinite(theta) || !isfinite(resid)) code = LZ_NAN;
     else if (small_beta || beta < 1e-14 * scale || (int64_t)n >= D) code = LZ_BREAKDOWN;
     else if (resid <= tol * scale) code = LZ_CONVERGED;
-    else if (n >= max_iter) code = LZ_CAP;
+    else if (n >= max_iter || final_pass) code = LZ_CAP;
     out[b * 4 + 0] = theta;
     out[b * 4 + 1] = resid;
     out[b * 4 + 2] = beta;
@@ -663,9 +674,9 @@ void lz_launch_finalize_ab(const double* h, const double* npart_b, const double*
   k_finalize_ab<<<batch, 32, 0, st>>>(h, npart_b, npart_c, gate, ab, ctl, batch, cap, nchunk);
 }
 void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
-                       int cap, int64_t D, cudaStream_t st) {
+                       int cap, int64_t D, cudaStream_t st, int final_pass) {
   k_tridiag<<<batch, 32, (5 * cap * sizeof(double) + 5 * cap * sizeof(float)), st>>>(ab, s, out, ctl, tol, batch,
-                                                                                   cap, D);
+                                                                                   cap, D, final_pass);
 }
 static int vec_blocks(int64_t D) {
   int64_t nb = (D + 255) / 256;

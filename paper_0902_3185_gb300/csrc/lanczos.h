@@ -16,7 +16,8 @@ constexpr int LZ_DOT_EPT = 16;    // elements per thread in the reorthogonalisat
 constexpr int LZ_DOT_CHUNK = LZ_THREADS * LZ_DOT_EPT;
 
 enum LzCtl : int { LZ_CTL_J = 0, LZ_CTL_MAXIT = 1, LZ_CTL_CHECK = 2, LZ_CTL_ALLDONE = 3, LZ_CTL_MEMBER = 4 };
-enum LzCode : int { LZ_RUNNING = 0, LZ_CONVERGED = 1, LZ_BREAKDOWN = 2, LZ_NAN = 3, LZ_CAP = 4 };
+// LZ_PENDING: stopped on the float32 test, float64 eigenpair not yet computed
+enum LzCode : int { LZ_RUNNING = 0, LZ_CONVERGED = 1, LZ_BREAKDOWN = 2, LZ_NAN = 3, LZ_CAP = 4, LZ_PENDING = 5 };
 
 inline int lz_nchunk(int64_t D) { return (int)((D + LZ_CHUNK - 1) / LZ_CHUNK); }
 inline int lz_dot_nchunk(int64_t D) { return (int)((D + LZ_DOT_CHUNK - 1) / LZ_DOT_CHUNK); }
@@ -38,7 +39,7 @@ void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate,
 void lz_launch_finalize_ab(const double* h, const double* npart_b, const double* npart_c, const int32_t* gate,
                            double* ab, const int32_t* ctl, int batch, int cap, int nchunk, cudaStream_t st);
 void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
-                       int cap, int64_t D, cudaStream_t st);
+                       int cap, int64_t D, cudaStream_t st, int final_pass = 0);
 void lz_launch_next_vector(const double* w, const double* ab, double* V, double* vcur, const int32_t* ctl,
                            int64_t D, int batch, int cap, cudaStream_t st);
 void lz_launch_advance(int32_t* ctl, int batch, cudaStream_t st);
