@@ -795,14 +795,17 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, int rprec, double tol, int ma
     }
     hctl[2 * B] = 0;
     hctl[2 * B + 1] = max_inner;
-    // inner accuracy: enough to reach the tolerance in one more outer step
-    // (with a factor 4 margin), within [1e-5, eps_in]; the mixed product's own
-    // error bounds what the correction can achieve anyway
+    // inner accuracy, within [1e-5, eps_in]: each outer step shrinks the
+    // residual by about the inner solve's relative accuracy (until the mixed
+    // product's own error bounds it), so from the mixed solve's result the
+    // reduction still needed (tolerance / residual, with a factor 4 margin) is
+    // split evenly over two outer steps (its square root), and a later step
+    // asks for all of what remains
     double eps = eps_in;
     for (int b = 0; b < B; ++b) {
       if (conv[b]) continue;
       const double need = 0.25 * tol * std::max(1.0, std::fabs(r.theta[b])) / std::max(r.resid[b], 1e-300);
-      eps = std::min(eps, std::max(need, 1e-5));
+      eps = std::min(eps, std::max(o == 0 ? std::sqrt(need) : need, 1e-5));
     }
     CK(cudaMemcpyAsync(sb->rf_ctl, hctl.data(), sizeof(int32_t) * (2 * B + 2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(sb->rf_sc + RF_NSC * B, &eps, sizeof(double), cudaMemcpyHostToDevice, st));

@@ -174,6 +174,31 @@ def test_lanczos_cap_reports_noconv(dev):
     assert st == 4 and all(i["status"] == 4 and i["iters"] == 3 for i in infos)
 
 
+@pytest.mark.parametrize("check_every", [1, 3])
+def test_lanczos_members_stop_apart(dev, check_every):
+    """Members that pass the float32 test at different iterations stop as
+    pending; the float64 eigenpairs computed after the loop meet the
+    tolerance: status 0, the reported residual within tol, the true residual
+    |H psi - E psi| of the returned state within a few tol, energies equal to
+    the oracle's."""
+    sb = CASES["hub_ladder_grown"]()
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(40 + b, sb.dim) for b in range(sb.batch)])
+    tol = 1e-10
+    e0, psi, infos, st = g.lanczos_ground(to_dev(X), tol=tol, max_iter=400, check_every=check_every)
+    assert st == 0, infos
+    P = psi.cpu().numpy()
+    for b in range(sb.batch):
+        scale = max(1.0, abs(e0[b]))
+        assert infos[b]["status"] == 0 and infos[b]["residual"] <= tol * scale
+        if check_every > 1:
+            assert infos[b]["iters"] % check_every == 0 or infos[b]["iters"] >= 400
+        r = osb.apply_H(sb, P[b], b) - e0[b] * P[b]
+        assert np.linalg.norm(r) <= 10 * tol * scale
+        ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v, b), X[b], tol=1e-12, max_iter=400)
+        assert abs(e0[b] - ref.e0) <= 1e-10 * abs(ref.e0)
+
+
 def test_lanczos_breakdown_exact(dev):
     # a start vector inside a small invariant subspace: the Krylov space closes
     sb = ragged_small(seed=1)
