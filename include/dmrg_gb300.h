@@ -98,8 +98,8 @@ typedef struct {
   int32_t refine;      /* after a mixed-precision solve: 0 none; 1 restart FP64 Lanczos from its psi;
                           2 Newton steps: FP64 residual, correction equation by mixed-precision CG
                           preconditioned with diag(H); 3 as 2 with the residual products in
-                          DMRG_DF64 (about 4x faster on GB300, residuals accurate to ~1e-13 |H psi|) */
-  double refine_tol;   /* FP64 residual tolerance of the refinement, relative to max(1, |theta|) */
+                          DMRG_DF64 (about 2x faster on GB300, residuals accurate to ~1e-13 |H psi|) */
+  double refine_tol;   /* residual tolerance of the refinement (float64 or double-float residual), relative to max(1, |theta|) */
   int32_t check_every; /* run the tridiagonal test every this many iterations (>= 1) */
   int32_t graph_iters; /* iterations captured per CUDA graph launch (>= 1) */
 } dmrg_lanczos_opts;

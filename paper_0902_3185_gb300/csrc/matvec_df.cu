@@ -12,9 +12,10 @@
 // is renormalised after every K tile of 16 (without it the low sum's own
 // rounding grows like K 2^-48: 1e-12 at K = 200).  GB300
 // runs float64 at 1/64 of its float32 rate (2 DFMA per clock per SM against
-// 128 FFMA), so this runs the superblock product about four to five times
-// faster than the float64 kernel at that accuracy: enough for residuals
-// r = H psi - theta psi down to |r| ~ 1e-12 |H psi|.  Outputs are written as
+// 128 FFMA), so the arithmetic alone allows five times the float64 kernel's
+// rate; with the input splits, the shared-memory tiles and their barriers the
+// superblock product runs about twice as fast as the float64 kernel, at an
+// accuracy enough for residuals r = H psi - theta psi down to |r| ~ 1e-12 |H psi|.  Outputs are written as
 // float64 (hi + lo).  Paper Sec. 3.3: the product x += H y, system,
 // environment and connection parts, on the fly.
 
