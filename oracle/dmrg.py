@@ -297,6 +297,7 @@ class StepResult:
     iters: int
     superblock: Optional[Superblock] = None
     psi: Optional[np.ndarray] = None
+    blocks: Optional[tuple] = None  # (S', E') of the step, with keep_superblocks
 
 
 def _solve(model, Sp, Ep, L_k, seed, tol, max_iter, keep_sb):
@@ -338,7 +339,8 @@ def infinite_dmrg(model: Model, L: int, m: int, seed: int = 0, tol: float = 1e-1
         right[E.n] = E
         steps.append(StepResult(L_k, Sp.n, res.e0, eS, eE, res.iters,
                                 sb if keep_superblocks else None,
-                                res.psi if keep_superblocks else None))
+                                res.psi if keep_superblocks else None,
+                                (Sp, Ep) if keep_superblocks else None))
     return steps, left, right
 
 

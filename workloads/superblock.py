@@ -147,6 +147,24 @@ class Superblock:
                           get("q_labels"))
 
 
+def transition(r_out, c_out, r_in, c_in, blocks, batch: int = 1, name: str = "O") -> Superblock:
+    """An operator between two target spaces as one container: sectors of the
+    output space first, then those of the input space; one term (coefficient
+    1 for every member) whose pairs are ``blocks`` = [(s_out, s_in, A, B)]
+    with s_out, s_in counted in their own spaces.  Applying it to
+    [0 (output space), psi] gives [O psi, 0].  An identity side must be given
+    explicitly (the sectors differ)."""
+    r_out, c_out = np.asarray(r_out, dtype=np.int64), np.asarray(c_out, dtype=np.int64)
+    n_out = len(r_out)
+    pairs = [Pair(0, int(so), n_out + int(si), np.ascontiguousarray(A, dtype=np.float64),
+                  np.ascontiguousarray(B, dtype=np.float64)) for (so, si, A, B) in blocks]
+    sb = Superblock(np.concatenate([r_out, np.asarray(r_in, dtype=np.int64)]),
+                    np.concatenate([c_out, np.asarray(c_in, dtype=np.int64)]),
+                    np.ones((batch, 1)), pairs, [name])
+    sb.meta.update(kind="transition", n_out=n_out, dim_out=int(np.sum(r_out * c_out)))
+    return sb
+
+
 def seeded_normal(seed: int, shape) -> np.ndarray:
     """N(0,1) float64 draws from numpy's PCG64 stream ``seed``.
 
