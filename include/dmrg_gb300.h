@@ -190,6 +190,37 @@ dmrg_status dmrg_lanczos_ground_grad(dmrg_sb* sb, const double* psi0, double* ps
 dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, double* dots, int32_t prec,
                                    void* stream);
 
+/* Lanczos coefficients for continued fractions (paper: the local density of
+ * states from the continued fraction of the Lanczos coefficients of the
+ * superblock Hamiltonian started from c_i |psi>).  Runs min(n_max, 768, D)
+ * steps of the same Lanczos iteration as dmrg_lanczos_ground (float64
+ * scalars, full reorthogonalisation, products in `prec`: DMRG_FP64, TF32 or
+ * BF16X3) from phi0 / |phi0| (device [batch][D], not modified) with no
+ * convergence test; a member stops early only at an invariant subspace.
+ * Writes, for every member b: norm2[b] = |phi0_b|^2 (device [batch]);
+ * alpha[b][j] = <v_j, H v_j> and beta[b][j] = |w_j| (the coupling of v_j and
+ * v_{j+1}), j < n_out[b], into device arrays [batch][n_max] (row length
+ * n_max; entries past n_out[b] are unspecified); n_out[b] (HOST [batch],
+ * written after an internal stream synchronisation) = number of coefficients.
+ * DMRG_EINVAL for NULL pointers, n_max < 1 or another precision; DMRG_ENAN
+ * when a member met NaN or Inf. */
+dmrg_status dmrg_lanczos_coeffs(dmrg_sb* sb, const double* phi0, int32_t n_max, int32_t prec, double* alpha,
+                                double* beta, double* norm2, int32_t* n_out, void* stream);
+
+/* Continued fractions G_b(z) = norm2[b] / (z - alpha[b][0] - beta[b][0]^2 /
+ * (z - alpha[b][1] - ... - beta[b][k-2]^2 / (z - alpha[b][k-1]))), k = n[b],
+ * at n_z complex points per member: z = z_re + i z_im, device [batch][n_z];
+ * the result into g_re, g_im (device [batch][n_z]).  alpha, beta: device
+ * [batch][ld] (as written by dmrg_lanczos_coeffs with ld = n_max); n, norm2:
+ * device [batch]; n[b] is clamped to [0, ld] (0 gives G = 0).  Points must lie
+ * off the spectrum (Im z > 0 for the densities of states: -Im G / pi is then
+ * a sum of Lorentzians).  One thread per (member, point), evaluated from the
+ * deepest level up in float64.  Stream-ordered; DMRG_EINVAL for NULL
+ * pointers, batch < 0, ld < 1 or n_z < 0. */
+dmrg_status dmrg_continued_fraction(const double* norm2, const double* alpha, const double* beta, const int32_t* n,
+                                    int32_t batch, int32_t ld, const double* z_re, const double* z_im, int32_t n_z,
+                                    double* g_re, double* g_im, void* stream);
+
 /* Autotuner of the tensor-core product (no paper counterpart; the paper's
  * block loop has no tuning): times the product of this superblock, `reps`
  * launches per candidate after a warm-up, for every tile width (64, 128,

@@ -27,7 +27,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREA
 SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error", "dmrg_query",
            "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
            "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune", "dmrg_sync_status",
-           "dmrg_test_inject", "dmrg_lanczos_ground_grad", "dmrg_apply_H_term_dots"]
+           "dmrg_test_inject", "dmrg_lanczos_ground_grad", "dmrg_apply_H_term_dots", "dmrg_lanczos_coeffs",
+           "dmrg_continued_fraction"]
 
 
 class DmrgError(RuntimeError):
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True):
     lib.dmrg_test_inject.argtypes = [vp, i32]
     lib.dmrg_lanczos_ground_grad.argtypes = [vp, dp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
     lib.dmrg_apply_H_term_dots.argtypes = [vp, dp, dp, dp, i32, vp]
+    lib.dmrg_lanczos_coeffs.argtypes = [vp, dp, i32, i32, dp, dp, dp, dp, vp]
+    lib.dmrg_continued_fraction.argtypes = [dp, dp, dp, dp, i32, i32, dp, dp, i32, dp, dp, vp]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -271,6 +274,39 @@ class GpuSuperblock:
         self._check(self.lib.dmrg_apply_H_term_dots(self.h, _ptr(psi), _ptr(y), _ptr(dots), _prec(prec),
                                                     _stream(stream)))
         return y, dots
+
+
+    def lanczos_coeffs(self, phi0, n_max, prec="fp64", stream=None):
+        """Lanczos coefficients from phi0 (no convergence test): returns
+        (norm2 [batch], alpha [batch][n_max], beta [batch][n_max], n [batch]
+        numpy int32); row b holds n[b] coefficients (beta[b][j] couples
+        Krylov vectors j and j + 1)."""
+        alpha = torch.empty(self.batch, n_max, dtype=torch.float64, device=self.device)
+        beta = torch.empty_like(alpha)
+        norm2 = torch.empty(self.batch, dtype=torch.float64, device=self.device)
+        n = np.zeros(self.batch, dtype=np.int32)
+        self._check(self.lib.dmrg_lanczos_coeffs(self.h, _ptr(phi0.contiguous()), int(n_max), _prec(prec),
+                                                 _ptr(alpha), _ptr(beta), _ptr(norm2), n.ctypes.data,
+                                                 _stream(stream)))
+        return norm2, alpha, beta, n
+
+
+def continued_fraction(norm2, alpha, beta, n, z, stream=None):
+    """G_b(z) for complex z [batch][n_z] (device tensor) from Lanczos
+    coefficients (as returned by GpuSuperblock.lanczos_coeffs); complex128."""
+    lib = load()
+    batch, ld = alpha.shape
+    z = z.to(torch.complex128)
+    zr, zi = z.real.contiguous(), z.imag.contiguous()
+    gr, gi = torch.empty_like(zr), torch.empty_like(zi)
+    nd = torch.as_tensor(np.asarray(n, dtype=np.int32), device=alpha.device)
+    alpha, beta = alpha.contiguous(), beta.contiguous()
+    st = lib.dmrg_continued_fraction(_ptr(norm2), _ptr(alpha), _ptr(beta), nd.data_ptr(),
+                                     int(batch), int(ld), _ptr(zr), _ptr(zi), int(zr.shape[1]), _ptr(gr),
+                                     _ptr(gi), _stream(stream))
+    if st != 0:
+        raise DmrgError(st, "continued_fraction")
+    return torch.complex(gr, gi)
 
 
 class ApplyH(torch.autograd.Function):

@@ -1265,4 +1265,51 @@ dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, do
   });
 }
 
+dmrg_status dmrg_lanczos_coeffs(dmrg_sb* sb, const double* phi0, int32_t n_max, int32_t prec, double* alpha,
+                                double* beta, double* norm2, int32_t* n_out, void* stream) {
+  if (!sb) return DMRG_EINVAL;
+  if (!phi0 || !alpha || !beta || !norm2 || !n_out || n_max < 1 || prec < DMRG_FP64 || prec > DMRG_BF16X3) {
+    sb->err = "lanczos_coeffs: bad pointers, n_max or precision";
+    return DMRG_EINVAL;
+  }
+  if (prec != DMRG_FP64 && !tc_available(sb)) {
+    sb->err = "lanczos_coeffs: tensor-core path not available on this device";
+    return DMRG_EUNSUPPORTED;
+  }
+  return guard(sb, [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t D = sb->D;
+    const int B = sb->batch;
+    const int nmax = (int)std::min<int64_t>(std::min(n_max, 768), D);
+    lz_alloc(sb, nmax + 1);
+    lz_launch_sumsq(phi0, sb->lz_partial, D, B, sb->lz_nchunk, st);  // |phi0|^2 before it is normalised
+    lz_launch_sum_chunks(sb->lz_partial, norm2, sb->lz_nchunk, B, st);
+    // no convergence test (tolerance 0, tridiagonal check only at the cap or an
+    // invariant subspace); the Ritz vector goes to scratch
+    LzRun r = lz_solve(sb, phi0, sb->rf_q, prec, 0.0, nmax, nmax + 1, 8, st);
+    const int cap = sb->lz_cap;
+    CK(cudaMemcpy2DAsync(alpha, sizeof(double) * (size_t)n_max, sb->lz_ab, sizeof(double) * (size_t)cap,
+                         sizeof(double) * (size_t)nmax, (size_t)B, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync(beta, sizeof(double) * (size_t)n_max, sb->lz_ab + (size_t)B * cap,
+                         sizeof(double) * (size_t)cap, sizeof(double) * (size_t)nmax, (size_t)B,
+                         cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    dmrg_status s = DMRG_OK;
+    for (int b = 0; b < B; ++b) {
+      n_out[b] = r.iters[b];
+      if (r.code[b] == LZ_NAN) s = DMRG_ENAN;
+    }
+    return s;
+  });
+}
+
+dmrg_status dmrg_continued_fraction(const double* norm2, const double* alpha, const double* beta, const int32_t* n,
+                                    int32_t batch, int32_t ld, const double* z_re, const double* z_im, int32_t n_z,
+                                    double* g_re, double* g_im, void* stream) {
+  if (!norm2 || !alpha || !beta || !n || !z_re || !z_im || !g_re || !g_im || batch < 0 || ld < 1 || n_z < 0)
+    return DMRG_EINVAL;
+  lz_launch_cfrac(norm2, alpha, beta, n, ld, z_re, z_im, n_z, g_re, g_im, batch, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? DMRG_OK : DMRG_ECUDA;
+}
+
 }  // extern "C"

@@ -647,7 +647,45 @@ k_reduce_terms(const double* __restrict__ part, const int32_t* __restrict__ ptr,
   if (threadIdx.x == 0) out[i] = t;
 }
 
+// G_b(z) = norm2_b / (z - a_0 - b_0^2 / (z - a_1 - ... - b_{n-2}^2 / (z - a_{n-1})))
+// for complex z, one thread per (member, z), evaluated from the deepest level
+// up (paper: the local density of states by the continued-fraction method)
+__global__ void k_cfrac(const double* __restrict__ norm2, const double* __restrict__ alpha,
+                        const double* __restrict__ beta, const int32_t* __restrict__ n, int ld,
+                        const double* __restrict__ zr, const double* __restrict__ zi, int n_z,
+                        double* __restrict__ gr, double* __restrict__ gi) {
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_z) return;
+  const int64_t at = (int64_t)b * n_z + k;
+  const double xr = zr[at], xi = zi[at];
+  const int nb = min(max(n[b], 0), ld);  // a count beyond the row length is clamped, never read past
+  const double* a = alpha + (int64_t)b * ld;
+  const double* bb = beta + (int64_t)b * ld;
+  double tr = 0.0, ti = 0.0;  // t = z - a_j - b_j^2 / t_{j+1}
+  if (nb > 0) {
+    tr = xr - a[nb - 1];
+    ti = xi;
+    for (int j = nb - 2; j >= 0; --j) {
+      const double d = tr * tr + ti * ti;   // b_j^2 / t = b_j^2 conj(t) / |t|^2
+      const double f = bb[j] * bb[j] / d;
+      tr = xr - a[j] - f * tr;
+      ti = xi + f * ti;
+    }
+  }
+  const double d = tr * tr + ti * ti;
+  const double s = nb > 0 ? norm2[b] / d : 0.0;  // norm2 / t
+  gr[at] = s * tr;
+  gi[at] = -s * ti;
+}
+
 // ------------------------------------------------------------- launchers
+void lz_launch_cfrac(const double* norm2, const double* alpha, const double* beta, const int32_t* n, int ld,
+                     const double* zr, const double* zi, int n_z, double* gr, double* gi, int batch,
+                     cudaStream_t st) {
+  if (n_z <= 0 || batch <= 0) return;
+  k_cfrac<<<dim3((n_z + 127) / 128, batch), 128, 0, st>>>(norm2, alpha, beta, n, ld, zr, zi, n_z, gr, gi);
+}
 void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int win, const int32_t* gate, cudaStream_t st, const double* h_pre,
                         double* npart_pre) {

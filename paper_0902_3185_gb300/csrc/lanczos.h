@@ -38,6 +38,10 @@ void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate,
                     int nchunk_a, int nchunk, cudaStream_t st);
 void lz_launch_finalize_ab(const double* h, const double* npart_b, const double* npart_c, const int32_t* gate,
                            double* ab, const int32_t* ctl, int batch, int cap, int nchunk, cudaStream_t st);
+// continued fractions of Lanczos coefficients at complex points (per member)
+void lz_launch_cfrac(const double* norm2, const double* alpha, const double* beta, const int32_t* n, int ld,
+                     const double* zr, const double* zi, int n_z, double* gr, double* gi, int batch,
+                     cudaStream_t st);
 void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
                        int cap, int64_t D, cudaStream_t st, int final_pass = 0);
 void lz_launch_next_vector(const double* w, const double* ab, double* V, double* vcur, const int32_t* ctl,
