@@ -104,3 +104,27 @@ def test_transition_container_layout():
     psi_in = x[off[3]:off[4]].reshape(2, 4)
     assert np.allclose(y[off[0]:off[1]].reshape(2, 4), A @ psi_in)
     assert np.all(y[off[1]:] == 0.0)
+
+
+def test_grown_inputs_equal_ed():
+    """The bench's input builder (isometry-grown blocks; here nothing is
+    truncated) gives the N, N - 1 and N + 1 superblocks and the c (x) 1
+    transitions on one growth: its densities equal exact diagonalisation."""
+    from oracle import lanczos as olz
+    from workloads.grown import grown_ldos_inputs
+    L, U = 6, 2.0
+    inp = grown_ldos_inputs(L, "chain", 3, 3, m=1000, cut=3, U_values=[U])
+    sbN = inp["N"]
+    r = olz.lanczos_ground(lambda v: osb.apply_H(sbN, v), seeded_normal(0, sbN.dim), tol=1e-12, max_iter=400)
+    h_ed, p_ed, e0 = ldos.hubbard_ldos_ed(L, inp["site"], "up", 3, 3, 1.0, U, OMEGA, ETA)
+    assert r.e0 == pytest.approx(e0, abs=1e-10)
+    cf = {}
+    for part in ("hole", "particle"):
+        sb, tr = inp[part]
+        tr.validate()
+        sb.validate()
+        n_out = tr.meta["dim_out"]
+        y = osb.apply_H(tr, np.concatenate([np.zeros(n_out), r.psi]))
+        cf[part] = ldos.lanczos_coefficients(lambda v: osb.apply_H(sb, v), y[:n_out], sb.dim)
+    h, p = ldos.ldos_from_fractions(cf["hole"], cf["particle"], r.e0, OMEGA, ETA)
+    assert np.max(np.abs(h - h_ed)) < 1e-9 and np.max(np.abs(p - p_ed)) < 1e-9

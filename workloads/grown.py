@@ -34,7 +34,7 @@ from typing import Dict, List, Tuple
 
 import numpy as np
 
-from .superblock import Pair, Superblock
+from .superblock import Pair, Superblock, transition
 
 # --------------------------------------------------------------------- site
 _E, _UP, _DN, _UD = 0, 1, 2, 3
@@ -327,13 +327,9 @@ def chain_bonds(n_sites: int):
     return [(i, i + 1) for i in range(n_sites - 1)]
 
 
-def grown_hubbard_superblock(n_sites: int = 64, geometry: str = "ladder",
-                             n_up: int = 28, n_dn: int = 28, m: int = 1000,
-                             cut: int | None = None, t: float = 1.0,
-                             U_values=(8.0,), seed: int = 0) -> Superblock:
-    """Superblock S' = sites [0, cut), E' = sites [cut, n_sites) of the Hubbard
-    model, both blocks grown site by site and projected to at most m states
-    per step, in the (n_up, n_dn) target sector.  One batch member per U."""
+def _grown_blocks(n_sites, geometry, n_up, n_dn, m, cut, seed):
+    """S' = sites [0, cut) and E' = sites [cut, n_sites), grown site by site and
+    projected to at most m states per step with the (n_up, n_dn) weights."""
     bonds = ladder_bonds(n_sites) if geometry == "ladder" else chain_bonds(n_sites)
     if cut is None:
         cut = n_sites // 2 + (1 if geometry == "ladder" and (n_sites // 2) % 2 == 0 else 0)
@@ -357,8 +353,12 @@ def grown_hubbard_superblock(n_sites: int = 64, geometry: str = "ladder",
         nb = [j for (i, j) in bonds if i == y and j > y]
         E, _ = _grow(E, y, nb, Q, left=True)
     E.c = {k: v for k, v in E.c.items() if k[0] < cut + reach}
+    return S, E, bonds, cut
 
-    # superblock sectors
+
+def _target_sectors(S, E, n_up, n_dn):
+    """S' sectors of the (n_up, n_dn) target with both sides present, and the
+    dimensions (r from S', c from the partner sector of E')."""
     e_idx = E.basis.index()
     dims_e = dict(zip(E.basis.sectors, E.basis.dims))
     sec_S, r, c = [], [], []
@@ -368,6 +368,11 @@ def grown_hubbard_superblock(n_sites: int = 64, geometry: str = "ladder",
             sec_S.append(z)
             r.append(d)
             c.append(dims_e[ze])
+    return sec_S, r, c
+
+
+def _assemble(S, E, bonds, cut, n_up, n_dn, t, U_values, meta) -> Superblock:
+    sec_S, r, c = _target_sectors(S, E, n_up, n_dn)
     sidx = {z: i for i, z in enumerate(sec_S)}
     partner = lambda z: (n_up - z[0], n_dn - z[1])
 
@@ -425,10 +430,55 @@ def grown_hubbard_superblock(n_sites: int = 64, geometry: str = "ladder",
     sb = Superblock(np.array(r), np.array(c), coeffs, pairs, names, classes,
                     term_class, term_mult, couplings,
                     q_labels=np.array(sec_S, dtype=np.int64))
-    sb.meta.update(kind="grown_hubbard", geometry=geometry, n_sites=n_sites,
-                   n_up=n_up, n_dn=n_dn, m=m, cut=cut, seed=seed,
+    sb.meta.update(meta, n_up=n_up, n_dn=n_dn,
                    dim_S=int(sum(S.basis.dims)), dim_E=int(sum(E.basis.dims)))
     return sb
+
+
+def grown_hubbard_superblock(n_sites: int = 64, geometry: str = "ladder",
+                             n_up: int = 28, n_dn: int = 28, m: int = 1000,
+                             cut: int | None = None, t: float = 1.0,
+                             U_values=(8.0,), seed: int = 0) -> Superblock:
+    """Superblock S' = sites [0, cut), E' = sites [cut, n_sites) of the Hubbard
+    model, both blocks grown site by site and projected to at most m states
+    per step, in the (n_up, n_dn) target sector.  One batch member per U."""
+    S, E, bonds, cut = _grown_blocks(n_sites, geometry, n_up, n_dn, m, cut, seed)
+    return _assemble(S, E, bonds, cut, n_up, n_dn, t, U_values,
+                     dict(kind="grown_hubbard", geometry=geometry, n_sites=n_sites, m=m, cut=cut, seed=seed))
+
+
+def grown_ldos_inputs(n_sites: int = 64, geometry: str = "ladder", n_up: int = 28, n_dn: int = 28,
+                      m: int = 1000, cut: int | None = None, t: float = 1.0, U_values=(8.0,),
+                      seed: int = 0, spin: str = "up"):
+    """One growth of S', E' (as grown_hubbard_superblock) and, on those
+    blocks, the superblocks of the (n_up, n_dn) target and of one particle
+    of `spin` less and more, with the transition containers of c (x) 1 and
+    c^dag (x) 1 for the last site of S' (block-local operator, Jordan-Wigner
+    string inside S'; E' holds the higher labels).  Returns
+    {"N": sb, "hole": (sb, trans), "particle": (sb, trans), "site": i}."""
+    S, E, bonds, cut = _grown_blocks(n_sites, geometry, n_up, n_dn, m, cut, seed)
+    meta = dict(kind="grown_hubbard", geometry=geometry, n_sites=n_sites, m=m, cut=cut, seed=seed)
+    site = cut - 1
+    d = (1, 0) if spin == "up" else (0, 1)
+    batch = len(np.atleast_1d(U_values))
+    out = {"N": _assemble(S, E, bonds, cut, n_up, n_dn, t, U_values, meta), "site": site}
+    sec_in, r_in, c_in = _target_sectors(S, E, n_up, n_dn)
+    c_op = S.c[(site, spin)]
+    for part, sgn, op in (("hole", -1, c_op), ("particle", +1, _dag(c_op))):
+        nu, nd = n_up + sgn * d[0], n_dn + sgn * d[1]
+        sb = _assemble(S, E, bonds, cut, nu, nd, t, U_values, meta)
+        sec_out, r_out, c_out = _target_sectors(S, E, nu, nd)
+        iin = {z: k for k, z in enumerate(sec_in)}
+        blocks = []
+        for so, zo in enumerate(sec_out):
+            zi = (zo[0] - sgn * d[0], zo[1] - sgn * d[1])
+            if zi in iin and (zo, zi) in op and np.any(op[(zo, zi)]):
+                si = iin[zi]
+                blocks.append((so, si, op[(zo, zi)], np.eye(c_out[so])))
+        tr = transition(r_out, c_out, r_in, c_in, blocks, batch=batch,
+                        name=("c" if sgn < 0 else "c+") + f"_{site}{spin}")
+        out[part] = (sb, tr)
+    return out
 
 
 def ladder_m1000(batch: int = 16, seed: int = 0) -> Superblock:
