@@ -181,6 +181,54 @@ def make_workload(batch, rank):
     return ladder_m1000(batch=batch, seed=rank)
 
 
+def measure_ldos(binding, torch, inp, psi, e0, prec, dev, stream, n_coef=100, n_omega=801, eta=0.1):
+    """Local density of states of the last system site (spin up) for every
+    member, from the refined ground states: c|psi> and c^dag|psi> by the
+    transition products (float64), n_coef Lanczos coefficients on the N - 1
+    and N + 1 superblocks (products in `prec`, float64 scalars and full
+    reorthogonalisation), continued fractions at n_omega points of [-8, 8]
+    with broadening eta.  Superblock creation stays outside the timed region;
+    one untimed run first."""
+    omega = np.linspace(-8.0, 8.0, n_omega)
+    objs = {}
+    for part, sgn in (("hole", -1.0), ("particle", 1.0)):
+        sb_p, tr = inp[part]
+        gp = binding.GpuSuperblock(sb_p, device=dev)
+        gt = binding.GpuSuperblock(tr, device=dev)
+        n_out = tr.meta["dim_out"]
+        x = torch.zeros(psi.shape[0], tr.dim, dtype=torch.float64, device=dev)
+        x[:, n_out:] = psi
+        z = torch.from_numpy((e0[:, None] + sgn * omega[None, :]) + 1j * eta).to(dev)
+        objs[part] = (gp, gt, n_out, x, z, sb_p.dim)
+
+    def run():
+        out = {}
+        for part, (gp, gt, n_out, x, z, _) in objs.items():
+            y = gt.apply_H(x)
+            norm2, a, b, n = gp.lanczos_coeffs(y[:, :n_out].contiguous(), n_coef, prec=prec)
+            out[part] = (binding.continued_fraction(norm2, a, b, n, z), norm2, n)
+        return out
+
+    run()
+    torch.cuda.synchronize(dev)
+    ea = torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    out = run()
+    eb.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ea.elapsed_time(eb)
+    dens = sum(-o[0].imag / np.pi for o in out.values())
+    dw = omega[1] - omega[0]
+    return {"ms": ms, "members": int(psi.shape[0]), "site": int(inp["site"]), "spin": "up",
+            "coefficients": int(n_coef), "n_omega": int(n_omega), "eta": eta, "prec": prec,
+            "dims": {p: int(o[5]) for p, o in objs.items()},
+            "lanczos_steps_per_s": 2 * n_coef / (ms / 1e3),
+            "sum_rule_max_dev": float((out["hole"][1] + out["particle"][1] - 1.0).abs().max()),
+            "weight_in_window": float((dens.sum(dim=1) * dw).mean()),
+            "min_coefficients": int(min(o[2].min() for o in out.values()))}
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, on the host cores: a bounded sample of the
@@ -282,7 +330,9 @@ def main():
     from paper_0902_3185_gb300 import binding
     from workloads.superblock import seeded_normal
 
-    sb = make_workload(args.batch, rank)
+    from workloads.grown import ladder_m1000_ldos
+    ldos_inp = ladder_m1000_ldos(batch=args.batch, seed=rank)  # the bench superblock and its N -/+ 1 partners
+    sb = ldos_inp["N"]
     g = binding.GpuSuperblock(sb, device=dev)
     prec = args.prec
     if prec == "auto":
@@ -430,6 +480,8 @@ def main():
             t_j, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=j, prec=pj, refine="none",
                                                     graph_iters=10))
             fixed_j[f"{pj}_j{j}_steps_per_s"] = j / (t_j / 1e3)
+    # local density of states from the refined ground states (paper: continued fractions)
+    ldos = measure_ldos(binding, torch, ldos_inp, psi, np.asarray(e0h, dtype=np.float64), prec, dev, stream)
     # one full Gram-Schmidt pass reads the Krylov basis twice (dots, then update)
     for j in (20, 100):
         fixed_j[f"reorth_bytes_per_step_j{j}"] = 2 * (j + 1) * sb.batch * sb.dim * 8
@@ -501,7 +553,7 @@ def main():
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
            "breakdown": dict(breakdown, energy_grad_ms=t_grad, residual_product_with_dots_ms=t_pdot),
-           "lanczos_fixed_j": fixed_j,
+           "lanczos_fixed_j": fixed_j, "ldos": ldos,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline_sample(sb)

@@ -488,3 +488,11 @@ def ladder_m1000(batch: int = 16, seed: int = 0) -> Superblock:
     Us = 4.0 + 8.0 * np.arange(batch) / max(batch - 1, 1)
     return grown_hubbard_superblock(64, "ladder", 28, 28, 1000, cut=33,
                                     U_values=Us, seed=seed)
+
+
+def ladder_m1000_ldos(batch: int = 16, seed: int = 0, spin: str = "up"):
+    """ladder_m1000 (the same growth, the same "N" superblock) with the N - 1
+    and N + 1 superblocks and the c (x) 1, c^dag (x) 1 transitions of the last
+    system site (grown_ldos_inputs)."""
+    Us = 4.0 + 8.0 * np.arange(batch) / max(batch - 1, 1)
+    return grown_ldos_inputs(64, "ladder", 28, 28, 1000, cut=33, U_values=Us, seed=seed, spin=spin)
