@@ -13,6 +13,10 @@ refinement's float64 residual products after the first give H psi and the
 per-term dots in one pass).  value = algorithmic H*psi
 flops executed in the step / step time.
 
+Outside the timed step, `ldos` times the local density of states of the
+last system site from the refined ground states (transition products,
+Lanczos coefficients on the N -/+ 1 superblocks, continued fractions).
+
 roofline: the product kernel with the largest event-timed share of the step
 (tensor-core, float64, or float64 with the per-term dots), its algorithmic
 flops per product / its event-timed duration, against its peak;
@@ -181,15 +185,16 @@ def make_workload(batch, rank):
     return ladder_m1000(batch=batch, seed=rank)
 
 
-def measure_ldos(binding, torch, inp, psi, e0, prec, dev, stream, n_coef=100, n_omega=801, eta=0.1):
+def measure_ldos(binding, torch, inp, psi, e0, prec, dev, stream, n_coef=100, n_omega=2001, eta=0.1):
     """Local density of states of the last system site (spin up) for every
     member, from the refined ground states: c|psi> and c^dag|psi> by the
     transition products (float64), n_coef Lanczos coefficients on the N - 1
     and N + 1 superblocks (products in `prec`, float64 scalars and full
-    reorthogonalisation), continued fractions at n_omega points of [-8, 8]
+    reorthogonalisation), continued fractions at n_omega points of [-20, 20] (the
+    whole spectrum of these superblocks: weight_in_window checks it)
     with broadening eta.  Superblock creation stays outside the timed region;
     one untimed run first."""
-    omega = np.linspace(-8.0, 8.0, n_omega)
+    omega = np.linspace(-20.0, 20.0, n_omega)
     objs = {}
     for part, sgn in (("hole", -1.0), ("particle", 1.0)):
         sb_p, tr = inp[part]
