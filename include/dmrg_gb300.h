@@ -201,9 +201,10 @@ dmrg_status dmrg_apply_H_term_dots(dmrg_sb* sb, const double* psi, double* y, do
  * alpha[b][j] = <v_j, H v_j> and beta[b][j] = |w_j| (the coupling of v_j and
  * v_{j+1}), j < n_out[b], into device arrays [batch][n_max] (row length
  * n_max; entries past n_out[b] are unspecified); n_out[b] (HOST [batch],
- * written after an internal stream synchronisation) = number of coefficients.
+ * written after an internal stream synchronisation) = number of coefficients
+ * (0 for a member whose phi0 is zero: its continued fraction is 0).
  * DMRG_EINVAL for NULL pointers, n_max < 1 or another precision; DMRG_ENAN
- * when a member met NaN or Inf. */
+ * when a member with a nonzero phi0 met NaN or Inf. */
 dmrg_status dmrg_lanczos_coeffs(dmrg_sb* sb, const double* phi0, int32_t n_max, int32_t prec, double* alpha,
                                 double* beta, double* norm2, int32_t* n_out, void* stream);
 

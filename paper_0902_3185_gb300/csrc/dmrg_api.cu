@@ -1293,11 +1293,14 @@ dmrg_status dmrg_lanczos_coeffs(dmrg_sb* sb, const double* phi0, int32_t n_max, 
     CK(cudaMemcpy2DAsync(beta, sizeof(double) * (size_t)n_max, sb->lz_ab + (size_t)B * cap,
                          sizeof(double) * (size_t)cap, sizeof(double) * (size_t)nmax, (size_t)B,
                          cudaMemcpyDeviceToDevice, st));
+    std::vector<double> hn2((size_t)B);
+    CK(cudaMemcpyAsync(hn2.data(), norm2, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     dmrg_status s = DMRG_OK;
     for (int b = 0; b < B; ++b) {
       n_out[b] = r.iters[b];
-      if (r.code[b] == LZ_NAN) s = DMRG_ENAN;
+      if (hn2[b] == 0.0) n_out[b] = 0;  // phi0 = 0 (e.g. c on an empty site): no coefficients, G = 0
+      else if (r.code[b] == LZ_NAN) s = DMRG_ENAN;
     }
     return s;
   });

@@ -134,3 +134,27 @@ def test_truncated_chain_against_oracle(binding):
     hm, _, pm, _ = device_ldos(binding, inp, psis, e0s, n_max, prec="bf16x3")
     peak = max(h.max(), p.max())
     assert np.max(np.abs(hm - h)) <= 0.02 * peak and np.max(np.abs(pm - p)) <= 0.02 * peak
+
+
+def test_zero_start_vector_member(binding):
+    """A member whose start vector is zero (c on an empty site) gets no
+    coefficients and G = 0; the other members are unaffected."""
+    L, U = 6, 2.0
+    model = dmrg.hubbard_chain(1.0, U, Lmax=L)
+    steps, _, _ = dmrg.infinite_dmrg(model, L, m=1000, keep_superblocks=True)
+    last = steps[-1]
+    Sp, Ep = last.blocks
+    inp = ldos.superblock_ldos_inputs(model, Sp, Ep, last.L, Sp.n - 1, "up", couplings_batch=[[1.0, U]] * 2)
+    sb, tr = inp["hole"]
+    n_out = tr.meta["dim_out"]
+    phi1 = osb.apply_H(tr, np.concatenate([np.zeros(n_out), last.psi]))[:n_out]
+    phi = np.stack([np.zeros(n_out), phi1])
+    g = binding.GpuSuperblock(sb)
+    norm2, a, b, n = g.lanczos_coeffs(to_dev(phi), 30)
+    assert n[0] == 0 and n[1] == 30 and float(norm2[0]) == 0.0
+    z = np.tile(last.energy - OMEGA + 1j * ETA, (2, 1))
+    G = binding.continued_fraction(norm2, a, b, n, to_dev(z)).cpu().numpy()
+    assert np.all(G[0] == 0)
+    ref_n2, ra, rb = ldos.lanczos_coefficients(lambda v: osb.apply_H(sb, v, 1), phi1, 30)
+    ref = ldos.continued_fraction(ref_n2, ra, rb, z[1])
+    assert np.max(np.abs(G[1] - ref)) <= 1e-8 * np.max(np.abs(ref))
