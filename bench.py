@@ -247,7 +247,11 @@ def run_reference(args, rank, world):
     flops_member = osb.matvec_flops(sb)
     cores = len(os.sched_getaffinity(0))
     x = seeded_normal(0, sb.dim)
-    osb.apply_H(sb, x, 0)  # warm-up
+    warm = max(1, args.warmup)
+    for w in range(warm):  # untimed warm-up steps, as many as asked
+        for b in (0, 1):
+            x = osb.apply_H(sb, x, b)
+            x /= np.linalg.norm(x)
     times = []
     n = 0
     t_end = time.perf_counter() + 20.0
@@ -263,9 +267,13 @@ def run_reference(args, rank, world):
     sec = sum(times)
     tflops = n * flops_member / sec / 1e12
     line = {"impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": args.gpus,
-            "steps": len(times), "warmup": 1, "ms_per_step": 1000 * sec / len(times),
+            "steps": len(times), "warmup": warm, "ms_per_step": 1000 * sec / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "2 members x 1 product per step"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "sample": "each step = one blocked float64 product (the solve's dominant operation) on "
+                                 "each of 2 of the 16 members; TFLOP/s of those products (not a whole solve, "
+                                 "which takes the oracle minutes per member)"},
             "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n} blocked float64 products of single members (NumPy, default BLAS "
                                        f"threading; blocks this small mostly run on one thread), D={sb.dim}"},
@@ -396,6 +404,7 @@ def main():
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist if world > 1 else None, dev)
     ms_per_step = ms / args.steps
     value = job_value(world, mv_count, flops_mv, ms)
+    e_step, psi_step, dE_step = np.asarray(e0, dtype=np.float64), psi, dEdc
 
     # where the step goes: the mixed Lanczos alone, then the refinement
     def timed(fn):
@@ -485,6 +494,28 @@ def main():
             t_j, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=j, prec=pj, refine="none",
                                                     graph_iters=10))
             fixed_j[f"{pj}_j{j}_steps_per_s"] = j / (t_j / 1e3)
+    # accuracy leg: the same batch solved with float64 products (plain float64
+    # GPU path: float64 Lanczos to the same tolerance, gradient after the
+    # solve), against the timed step's mixed + refined result
+    accuracy = None
+    if prec != "fp64":
+        t_f64, (e64, psi64, info64, st64, dE64) = timed(lambda: g.lanczos_ground(
+            x0, tol=args.tol, max_iter=args.max_iter, prec="fp64", refine="none", graph_iters=8, grad=True))
+        e64 = np.asarray(e64, dtype=np.float64)
+        pm = psi_step / psi_step.norm(dim=1, keepdim=True)
+        p6 = psi64 / psi64.norm(dim=1, keepdim=True)
+        dpsi = torch.minimum((pm - p6).norm(dim=1), (pm + p6).norm(dim=1)).cpu().numpy()
+        dE_rel = np.abs(e_step - e64) / np.abs(e64)
+        dg = (dE_step - dE64).abs().max().item()
+        accuracy = {"reference": "float64 GPU solve of the same 16 members (float64 products and Lanczos, "
+                                 f"tol {args.tol:g}), status {st64}",
+                    "dE0_rel_max": float(dE_rel.max()), "dE0_rel_per_member": [float(v) for v in dE_rel],
+                    "dpsi_max": float(dpsi.max()), "dE_dc_max_abs_diff": float(dg),
+                    "meets_1e-8": bool(dE_rel.max() <= 1e-8),
+                    "fp64_solve_ms": t_f64, "fp64_solve_iters": max(i["iters"] for i in info64),
+                    "fp64_lanczos_steps_per_s": max(i["iters"] for i in info64) / (t_f64 / 1e3),
+                    "mixed_solve_ms": ms_per_step,
+                    "speedup_mixed_vs_fp64_solve": t_f64 / ms_per_step}
     # local density of states from the refined ground states (paper: continued fractions)
     ldos = measure_ldos(binding, torch, ldos_inp, psi, np.asarray(e0h, dtype=np.float64), prec, dev, stream)
     # one full Gram-Schmidt pass reads the Krylov basis twice (dots, then update)
@@ -558,7 +589,7 @@ def main():
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
            "breakdown": dict(breakdown, energy_grad_ms=t_grad, residual_product_with_dots_ms=t_pdot),
-           "lanczos_fixed_j": fixed_j, "ldos": ldos,
+           "lanczos_fixed_j": fixed_j, "ldos": ldos, "accuracy": accuracy,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline_sample(sb)

@@ -114,7 +114,9 @@ typedef struct {     /* one per batch member */
   int32_t status;         /* dmrg_status of this member */
   int32_t breakdown;
   int32_t kernel_launches; /* kernels the whole call launched (all members, graph nodes counted) */
-  int32_t pad;
+  int32_t restarts;        /* Lanczos restarts from the Ritz vector: the member passed the float32
+                              test but missed the float64 test after the loop, and continued from
+                              its Ritz vector with the iterations it had left */
 } dmrg_lanczos_info;
 
 /* Sec. 3.2-3.3: build the sector tables, the (term, sector pair) task lists,
@@ -128,8 +130,12 @@ const char* dmrg_last_error(const dmrg_sb* sb);
 dmrg_status dmrg_query(const dmrg_sb* sb, dmrg_sb_info* info);
 
 /* Replace the coefficient table (host, [batch][n_terms]) without rebuilding:
- * coupling sweeps and finite differences. Stream-ordered after previous work. */
-dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs);
+ * coupling sweeps and finite differences.  The device copy is written on
+ * `stream` (through a pinned staging copy), after the work already queued on
+ * that stream, and the call returns once it is written (it synchronises
+ * `stream`).  Work on other streams that reads this superblock must be
+ * ordered before the call by the caller. */
+dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs, void* stream);
 
 /* Sec. 3.3 x += H y: y = H psi (accumulate = 0) or y += H psi (accumulate =
  * 1) for every batch member.  psi, y: device [batch][D], must not overlap. */
@@ -137,16 +143,19 @@ dmrg_status dmrg_apply_H(dmrg_sb* sb, const double* psi, double* y, int32_t accu
                          int32_t prec, void* stream);
 
 /* The float64 product of dmrg_apply_H (FP64 precision) for callers that
- * cannot allocate device memory when they apply H (code running under CUDA
- * stream capture, processes whose device memory belongs to another
- * framework's pool, allocation-free real-time loops).  Its intermediate
+ * cannot allocate device memory when they apply H (processes whose device
+ * memory belongs to another framework's pool, real-time loops in which an
+ * allocation, which can synchronise the device, is not allowed).  Its intermediate
  * workspace is one static buffer of 4 Mi float64 values (32 MiB) per GPU,
  * part of the loaded library and held until the process exits; the call
  * allocates nothing.  The first call on a device looks up the buffer's device
  * address (cudaGetSymbolAddress) and must come before any stream capture.
  * Calls share the buffer, which keeps the last call's contents: calls whose
  * kernels overlap on the GPU race.  Returns DMRG_EINVAL, with a message, when
- * the superblock needs more workspace than the buffer holds.  The paper has
+ * the superblock's forward product needs more intermediate workspace than the
+ * buffer holds.  The looked-up address is kept for the life of the process:
+ * re-creating a device's primary context (cudaDeviceReset) while the library
+ * is loaded is not supported by this call.  The paper has
  * no counterpart to this call. */
 dmrg_status dmrg_apply_H_static_scratch(dmrg_sb* sb, const double* psi, double* y, int32_t accumulate,
                                         void* stream);
@@ -161,7 +170,10 @@ dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* 
  * Lanczos with float64 scalars and full reorthogonalisation (every step
  * against every Krylov vector: the three-term step, one classical
  * Gram-Schmidt pass, and a second pass where the norm fell below 1/sqrt(2)),
- * the iteration captured in CUDA graphs.  psi0: device [batch][D] start vectors;
+ * the iteration captured in CUDA graphs.  A member stops when a float32
+ * estimate of its residual passes at half the tolerance; the float64 test
+ * after the loop confirms it, and a member that misses it restarts from its
+ * Ritz vector with the iterations it has left (DMRG_ENOCONV only at max_iter).  psi0: device [batch][D] start vectors;
  * psi_out: device [batch][D], normalised; e0: host [batch]; info: host
  * [batch] or NULL.  Returns the worst member status (DMRG_OK if all met the
  * tolerance; DMRG_EBREAKDOWN is reported in info only). */
@@ -249,8 +261,11 @@ dmrg_status dmrg_sync_status(dmrg_sb* sb, void* stream);
 
 /* Testing hook (no paper counterpart): what = 1 makes the next tensor-core
  * product's copy warp issue no copies, so that its bounded waits run out and
- * report DMRG_ETIMEOUT through dmrg_sync_status; what = 0 clears it.  No
- * memory is touched out of bounds and every wait ends after its limit. */
+ * report DMRG_ETIMEOUT through dmrg_sync_status; what = 2 makes the float32
+ * convergence test of the next Lanczos solve pass at its first check, so
+ * that the float64 test after the loop fails and the restart from the Ritz
+ * vector runs; what = 0 clears both.  No memory is touched out of bounds and
+ * every wait ends after its limit. */
 dmrg_status dmrg_test_inject(dmrg_sb* sb, int32_t what);
 
 /* Hellmann-Feynman: dE0/dc_k = <psi, (A_k (x) B_k) psi> / <psi, psi> for

@@ -69,7 +69,7 @@ class LanczosInfo(C.Structure):
     _fields_ = [("e0", C.c_double), ("residual", C.c_double), ("iters", C.c_int32),
                 ("refine_iters", C.c_int32), ("mixed_matvecs", C.c_int32), ("fp64_matvecs", C.c_int32),
                 ("status", C.c_int32), ("breakdown", C.c_int32), ("kernel_launches", C.c_int32),
-                ("pad", C.c_int32)]
+                ("restarts", C.c_int32)]
 
 
 _lib = None
@@ -97,7 +97,7 @@ def load(build_if_missing: bool = True):
     lib.dmrg_last_error.argtypes = [vp]
     lib.dmrg_last_error.restype = C.c_char_p
     lib.dmrg_query.argtypes = [vp, C.POINTER(_Info)]
-    lib.dmrg_set_coeffs.argtypes = [vp, dp]
+    lib.dmrg_set_coeffs.argtypes = [vp, dp, vp]
     lib.dmrg_apply_H.argtypes = [vp, dp, dp, i32, i32, vp]
     lib.dmrg_apply_H_backward.argtypes = [vp, dp, dp, dp, dp, i32, vp]
     lib.dmrg_lanczos_ground.argtypes = [vp, dp, dp, dp, C.POINTER(LanczosOpts), C.POINTER(LanczosInfo), vp]
@@ -192,10 +192,10 @@ class GpuSuperblock:
     def empty(self):
         return torch.empty(self.batch, self.dim, dtype=torch.float64, device=self.device)
 
-    def set_coeffs(self, coeffs):
+    def set_coeffs(self, coeffs, stream=None):
         c = np.ascontiguousarray(np.broadcast_to(np.asarray(coeffs, dtype=np.float64),
                                                  (self.batch, self.n_terms)))
-        self._check(self.lib.dmrg_set_coeffs(self.h, c.ctypes.data))
+        self._check(self.lib.dmrg_set_coeffs(self.h, c.ctypes.data, _stream(stream)))
 
     def apply_H(self, psi, y=None, accumulate=False, prec="fp64", stream=None):
         if y is None:

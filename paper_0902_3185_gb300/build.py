@@ -1,8 +1,8 @@
 """Build the CUDA library ``libdmrg_gb300.so`` in-tree for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel, then linked into a
-shared library next to this file.  A rebuild happens only when a source or
-header is newer than the library.
+shared library next to this file.  A rebuild happens unless a content hash of
+every file under csrc/ and include/ matches the one recorded at the last build.
 """
 from __future__ import annotations
 
@@ -34,13 +34,35 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _deps():
+    """Every file of csrc/ and include/ (sources, headers, included .cuh), and this script."""
+    deps = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))]
+    deps += [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE))]
+    return [p for p in deps if os.path.isfile(p)] + [os.path.abspath(__file__)]
+
+
+def _stamp():
+    """Content hash of the dependencies and the compile command."""
+    import hashlib
+    h = hashlib.sha256(" ".join(ARCH + FLAGS).encode())
+    for p in _deps():
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+STAMP = LIB + ".stamp"
+
+
 def _stale():
-    if not os.path.exists(LIB):
+    """Rebuild unless the library was built here from exactly these sources
+    (a content hash kept beside it, not file times: a library copied from
+    another machine, or older sources with newer times, is rebuilt)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
-    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
-    return any(os.path.getmtime(p) > t for p in deps)
+    with open(STAMP) as f:
+        return f.read().strip() != _stamp()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -67,6 +89,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(_stamp() + "\n")
     return LIB
 
 

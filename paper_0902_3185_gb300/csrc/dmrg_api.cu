@@ -343,6 +343,7 @@ void build_f64_tasks(dmrg_sb* sb) {
   const int64_t Tf = layout_T(sb, fw, toff_f), Tb = layout_T(sb, bw, toff_b);
   const int64_t Tm = std::max(Tf, Tb);
   sb->T_elems = Tm * sb->batch;
+  sb->T_fwd_elems = Tf > 0 ? Tm * (sb->batch - 1) + Tf : 0;  // member b's forward intermediates at b Tm + [0, Tf)
   if (sb->d_T) cudaFree(sb->d_T);
   sb->d_T = dalloc<double>((size_t)sb->T_elems);
 
@@ -600,7 +601,7 @@ cudaGraphExec_t lz_graph(dmrg_sb* sb, int prec, int K) {
 }
 
 struct LzRun {
-  std::vector<int32_t> code, iters;
+  std::vector<int32_t> code, iters, restarts;
   std::vector<double> theta, resid;
   int64_t launches = 0;
 };
@@ -612,13 +613,14 @@ int matvec_launches(const dmrg_sb* sb, int prec) {
 }
 constexpr int LZ_KERNELS_PER_ITER = 13;  // everything in lz_enqueue_iteration besides the product
 
-// Lanczos from psi0 (device [batch][D]) to psi_out; returns per-member results.
-LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double tol, int max_iter,
-               int check_every, int graph_iters, cudaStream_t st) {
+// One Lanczos run from psi0 (device [batch][D]) to psi_out for the members
+// whose initial control code is LZ_RUNNING (the others are LZ_HOLD: skipped,
+// their psi_out untouched).  Returns the per-member codes, Krylov lengths,
+// theta and residual (from lz_out; unchanged for held members).
+LzRun lz_run(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double tol, int max_iter,
+             int check_every, int graph_iters, const std::vector<int32_t>& init, int force, cudaStream_t st) {
   const int64_t D = sb->D;
   const int B = sb->batch;
-  max_iter = (int)std::min<int64_t>(std::min(std::max(1, max_iter), 768), D);  // tridiagonal kernel keeps 60 B per Krylov vector in shared memory (48 KB)
-  lz_alloc(sb, max_iter + 1);
   const int cap = sb->lz_cap, nch = sb->lz_nchunk;
   // v_0 = psi0 / |psi0|
   double* part = sb->lz_partial;
@@ -629,6 +631,8 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
   std::vector<int32_t> hc(LZ_CTL_MEMBER + 2 * B, 0);
   hc[LZ_CTL_MAXIT] = max_iter;
   hc[LZ_CTL_CHECK] = std::max(1, check_every);
+  hc[LZ_CTL_FORCE] = force;
+  for (int b = 0; b < B; ++b) hc[LZ_CTL_MEMBER + b] = init[b];
   CK(cudaMemcpyAsync(sb->lz_ctl, hc.data(), hc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sb->lz_out + 4 * B, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));  // host vectors above are stack memory
@@ -665,6 +669,49 @@ LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, doubl
     r.theta.push_back(out[4 * b]);
     r.resid.push_back(out[4 * b + 1]);
   }
+  r.restarts.assign(B, 0);
+  return r;
+}
+
+// Lanczos from psi0 (device [batch][D]) to psi_out; returns per-member results.
+// A member that stopped on the float32 test but failed the float64 test after
+// the loop (LZ_RESUME) is restarted from its Ritz vector with the iterations
+// it has left, the others held, at most LZ_MAX_RESTARTS times.
+constexpr int LZ_MAX_RESTARTS = 3;
+LzRun lz_solve(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double tol, int max_iter,
+               int check_every, int graph_iters, cudaStream_t st) {
+  const int64_t D = sb->D;
+  const int B = sb->batch;
+  max_iter = (int)std::min<int64_t>(std::min(std::max(1, max_iter), 768), D);  // tridiagonal kernel keeps 60 B per Krylov vector in shared memory (48 KB)
+  lz_alloc(sb, max_iter + 1);
+  const int force = sb->test_force_pending;
+  sb->test_force_pending = 0;
+  LzRun r = lz_run(sb, psi0, psi_out, prec, tol, max_iter, check_every, graph_iters,
+                   std::vector<int32_t>(B, LZ_RUNNING), force, st);
+  for (int k = 0; k < LZ_MAX_RESTARTS; ++k) {
+    std::vector<int32_t> init(B, LZ_HOLD);
+    int used = 0;
+    bool any = false;
+    for (int b = 0; b < B; ++b)
+      if (r.code[b] == LZ_RESUME) {
+        init[b] = LZ_RUNNING;
+        used = std::max(used, r.iters[b]);
+        any = true;
+      }
+    if (!any || max_iter - used < 2) break;
+    LzRun q = lz_run(sb, psi_out, psi_out, prec, tol, max_iter - used, check_every, graph_iters, init, 0, st);
+    r.launches += q.launches;
+    for (int b = 0; b < B; ++b)
+      if (init[b] == LZ_RUNNING) {
+        r.code[b] = q.code[b];
+        r.iters[b] += q.iters[b];
+        r.theta[b] = q.theta[b];
+        r.resid[b] = q.resid[b];
+        r.restarts[b] += 1;
+      }
+  }
+  for (int b = 0; b < B; ++b)
+    if (r.code[b] == LZ_RESUME) r.code[b] = LZ_CAP;
   return r;
 }
 
@@ -993,6 +1040,7 @@ void destroy(dmrg_sb* sb) {
     if (p) cudaFree(p);
   if (sb->d_dg_terms) cudaFree(sb->d_dg_terms);
   if (sb->d_tc_err) cudaFree(sb->d_tc_err);
+  if (sb->h_coeffs_pinned) cudaFreeHost(sb->h_coeffs_pinned);
   if (sb->d_dot_red_ptr) cudaFree(sb->d_dot_red_ptr);
   if (sb->d_dot_red_idx) cudaFree(sb->d_dot_red_idx);
   delete sb;
@@ -1045,11 +1093,23 @@ dmrg_status dmrg_query(const dmrg_sb* sb, dmrg_sb_info* info) {
   return DMRG_OK;
 }
 
-dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs) {
+dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs, void* stream) {
   if (!sb || !coeffs) return DMRG_EINVAL;
   return guard(sb, [&] {
-    sb->coeffs.assign(coeffs, coeffs + (size_t)sb->batch * sb->n_terms);
-    CK(cudaMemcpy(sb->d_coeffs, sb->coeffs.data(), sb->coeffs.size() * sizeof(double), cudaMemcpyHostToDevice));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)sb->batch * sb->n_terms;
+    sb->coeffs.assign(coeffs, coeffs + n);
+    // through a pinned staging copy, ordered on the caller's stream after the
+    // products already queued there (which read the old table); the stream is
+    // synchronised so that the staging copy is free for the next call
+    if (!sb->h_coeffs_pinned) {
+      void* hp = nullptr;
+      CK(cudaMallocHost(&hp, n * sizeof(double)));
+      sb->h_coeffs_pinned = static_cast<double*>(hp);
+    }
+    memcpy(sb->h_coeffs_pinned, coeffs, n * sizeof(double));
+    CK(cudaMemcpyAsync(sb->d_coeffs, sb->h_coeffs_pinned, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
     tc_set_coeffs(sb);
     return DMRG_OK;
   });
@@ -1149,8 +1209,13 @@ dmrg_status dmrg_sync_status(dmrg_sb* sb, void* stream) {
 }
 
 dmrg_status dmrg_test_inject(dmrg_sb* sb, int32_t what) {
-  if (!sb || what < 0 || what > 1) return DMRG_EINVAL;
+  if (!sb || what < 0 || what > 2) return DMRG_EINVAL;
+  if (what == 2) {
+    sb->test_force_pending = 1;
+    return DMRG_OK;
+  }
   sb->test_stall = what;
+  sb->test_force_pending = 0;
   return DMRG_OK;
 }
 
@@ -1231,6 +1296,7 @@ static dmrg_status lanczos_impl(dmrg_sb* sb, const double* psi0, double* psi_out
         info[b].breakdown = code == LZ_BREAKDOWN;
         info[b].kernel_launches = (int32_t)(r.launches + (mode == 1 ? rr.launches : 0) + (mode >= 2 ? rn.launches : 0) +
                                             grad_launches);
+        info[b].restarts = r.restarts[b] + (mode == 1 ? rr.restarts[b] : 0);
       }
     }
     return worst;

@@ -97,6 +97,7 @@ struct dmrg_sb {
   int64_t D = 0;
   std::vector<double> coeffs;  // host [batch][n_terms]
   double* d_coeffs = nullptr;  // device [batch][n_terms]
+  double* h_coeffs_pinned = nullptr;  // pinned staging copy of coeffs for dmrg_set_coeffs
   std::vector<dmrg::PairH> pairs;
   double* d_ops = nullptr;     // FP64 operator arena
   int64_t ops_elems = 0;
@@ -112,6 +113,7 @@ struct dmrg_sb {
   double* d_pdot_partial = nullptr;
   double* d_T = nullptr;                  // FP64 intermediate workspace
   int64_t T_elems = 0;
+  int64_t T_fwd_elems = 0;               // the part of it the forward product uses
   // term reduction of dot tiles: for (b, k): tile range [dot_red_ptr[bk], dot_red_ptr[bk+1])
   int32_t* d_dot_red_ptr = nullptr;
   int32_t* d_dot_red_idx = nullptr;
@@ -156,6 +158,7 @@ struct dmrg_sb {
   void* tc = nullptr;            // tensor-core path state (matvec_tc.cu)
   int32_t* d_tc_err = nullptr;   // set by a tensor-core kernel whose bounded wait gave up
   int32_t test_stall = 0;        // testing hook: the next tensor-core product issues no copies
+  int32_t test_force_pending = 0;  // testing hook: the next Lanczos solve's float32 test passes at its first check
   std::vector<double> h_ops;     // host copy of the float64 arena during creation only
 
   std::string err;

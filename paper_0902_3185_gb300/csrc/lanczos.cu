@@ -16,10 +16,13 @@
 // captured CUDA graph replays any iteration without host round trips.
 //
 // Control words (int32, device): [0] j = index of the current Krylov vector,
-// [1] max_iter, [2] check_every, [3] all members done, then per member b:
-// [4 + b] done code (0 running, 1 converged, 2 breakdown, 3 NaN, 4 cap hit,
-// 5 pending: stopped on the float32 test, float64 check after the loop)
-// and [4 + batch + b] number of Lanczos vectors in its tridiagonal matrix.
+// [1] max_iter, [2] check_every, [3] all members done, [4] testing hook (the
+// float32 test passes at its first check), then per member b:
+// [5 + b] done code (0 running, 1 converged, 2 breakdown, 3 NaN, 4 cap hit,
+// 5 pending: stopped on the float32 test, float64 check after the loop;
+// 6 resume: that check failed with iterations left, the host restarts the
+// member from its Ritz vector; 7 hold: done in an earlier run, skipped)
+// and [5 + batch + b] number of Lanczos vectors in its tridiagonal matrix.
 
 #include <cfloat>
 
@@ -399,7 +402,8 @@ __device__ void inverse_iteration(const T* a, const T* e, int n, T sigma, T* z, 
 //    the eigenpair in float64 (multisection from the float32 bracket, widened
 //    by its rounding bound, then inverse iteration), repeats the test with
 //    the float64 values (a member that then misses the tolerance ends as
-//    LZ_CAP) and stores s for the Ritz vector: the members' float64 solves
+//    LZ_RESUME, or LZ_CAP at max_iter; the host restarts a resumed member from
+//    its Ritz vector) and stores s for the Ritz vector: the members' float64 solves
 //    run side by side in one launch instead of each in the launch where its
 //    member converged;
 //  - at breakdown or the cap the float64 eigenpair is computed at once.
@@ -477,7 +481,7 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
                            false);
   __syncwarp();
   const double est = beta * fabs((double)z32[n - 1]);
-  const bool pass32 = est <= 0.5 * tol * fmax(1.0, fabs((double)th32));
+  const bool pass32 = est <= 0.5 * tol * fmax(1.0, fabs((double)th32)) || ctl[LZ_CTL_FORCE] != 0;
   if (!final_pass && !(small_beta || last)) {
     if (lane == 0) {
       out[b * 4 + 0] = th32;
@@ -515,7 +519,8 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
     if (!isfinite(theta) || !isfinite(resid)) code = LZ_NAN;
     else if (small_beta || beta < 1e-14 * scale || (int64_t)n >= D) code = LZ_BREAKDOWN;
     else if (resid <= tol * scale) code = LZ_CONVERGED;
-    else if (n >= max_iter || final_pass) code = LZ_CAP;
+    else if (n >= max_iter) code = LZ_CAP;
+    else if (final_pass) code = LZ_RESUME;
     out[b * 4 + 0] = theta;
     out[b * 4 + 1] = resid;
     out[b * 4 + 2] = beta;
@@ -617,6 +622,7 @@ __global__ void k_ritz(const double* __restrict__ V, const double* __restrict__ 
                        const int32_t* __restrict__ ctl, double* __restrict__ out, int64_t D, int batch,
                        int cap) {
   const int b = blockIdx.y;
+  if (ctl[LZ_CTL_MEMBER + b] == LZ_HOLD) return;  // its result came from an earlier run
   const int n = ctl[LZ_CTL_MEMBER + batch + b];
   for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
     double t = 0.0;

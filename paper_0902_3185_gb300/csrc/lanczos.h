@@ -15,9 +15,18 @@ constexpr int LZ_TRI = 32;        // threads of the tridiagonal multisection (on
 constexpr int LZ_DOT_EPT = 16;    // elements per thread in the reorthogonalisation dots
 constexpr int LZ_DOT_CHUNK = LZ_THREADS * LZ_DOT_EPT;
 
-enum LzCtl : int { LZ_CTL_J = 0, LZ_CTL_MAXIT = 1, LZ_CTL_CHECK = 2, LZ_CTL_ALLDONE = 3, LZ_CTL_MEMBER = 4 };
-// LZ_PENDING: stopped on the float32 test, float64 eigenpair not yet computed
-enum LzCode : int { LZ_RUNNING = 0, LZ_CONVERGED = 1, LZ_BREAKDOWN = 2, LZ_NAN = 3, LZ_CAP = 4, LZ_PENDING = 5 };
+// LZ_CTL_FORCE (testing hook): nonzero makes the float32 test pass at its first check
+enum LzCtl : int {
+  LZ_CTL_J = 0, LZ_CTL_MAXIT = 1, LZ_CTL_CHECK = 2, LZ_CTL_ALLDONE = 3, LZ_CTL_FORCE = 4, LZ_CTL_MEMBER = 5
+};
+// LZ_PENDING: stopped on the float32 test, float64 eigenpair not yet computed;
+// LZ_RESUME: the float64 test after the loop failed with iterations left (the
+// host restarts the member from its Ritz vector); LZ_HOLD: finished in an
+// earlier run, skipped by every kernel of a restart
+enum LzCode : int {
+  LZ_RUNNING = 0, LZ_CONVERGED = 1, LZ_BREAKDOWN = 2, LZ_NAN = 3, LZ_CAP = 4, LZ_PENDING = 5, LZ_RESUME = 6,
+  LZ_HOLD = 7
+};
 
 inline int lz_nchunk(int64_t D) { return (int)((D + LZ_CHUNK - 1) / LZ_CHUNK); }
 inline int lz_dot_nchunk(int64_t D) { return (int)((D + LZ_DOT_CHUNK - 1) / LZ_DOT_CHUNK); }

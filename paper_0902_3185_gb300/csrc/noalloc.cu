@@ -2,9 +2,10 @@
 // intermediate workspace in a fixed, statically allocated device buffer.
 //
 // Why it exists: some callers cannot call cudaMalloc when they apply H --
-// code running under stream capture while a CUDA graph is being recorded,
-// processes whose device memory is owned by another framework's pool, or
-// latency-critical loops that must not allocate.  dmrg_apply_H itself does
+// processes whose device memory is owned by another framework's pool (a
+// cudaMalloc behind the pool's back can fail or fragment it), or
+// latency-critical loops that must not allocate (cudaMalloc can synchronise
+// the device and take milliseconds).  dmrg_apply_H itself does
 // not allocate either, but it relies on the workspace that the superblock
 // reserved for itself; this entry point uses instead one buffer of fixed
 // size that is part of the loaded library, so the product needs no memory
@@ -15,7 +16,9 @@
 // Host code cannot use the array's name as a device address, so the first
 // call on each device looks the address up with cudaGetSymbolAddress (with
 // that device current) and caches it; make that first call before any stream
-// capture begins.  All calls on a device share the buffer and it keeps the
+// capture begins.  The cache lives as long as the process: destroying and
+// re-creating a device's primary context (cudaDeviceReset) while the library
+// is loaded is not supported by this entry point.  All calls on a device share the buffer and it keeps the
 // previous call's contents, so calls whose kernels overlap on the GPU (for
 // example on two streams) race and must be serialised by the caller.  Nothing
 // in it needs to start at zero: the first phase of the product writes every
@@ -63,8 +66,8 @@ extern "C" dmrg_status dmrg_apply_H_static_scratch(dmrg_sb* sb, const double* ps
     sb->err = "apply_H_static_scratch: null or aliased psi / y";
     return DMRG_EINVAL;
   }
-  if (sb->T_elems > DMRG_STATIC_SCRATCH_DOUBLES) {
-    sb->err = "apply_H_static_scratch: this superblock needs " + std::to_string(sb->T_elems) +
+  if (sb->T_fwd_elems > DMRG_STATIC_SCRATCH_DOUBLES) {
+    sb->err = "apply_H_static_scratch: this superblock needs " + std::to_string(sb->T_fwd_elems) +
               " float64 values of intermediate workspace; the static buffer holds " +
               std::to_string((long long)DMRG_STATIC_SCRATCH_DOUBLES);
     return DMRG_EINVAL;

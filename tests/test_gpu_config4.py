@@ -12,8 +12,8 @@ members of one superblock (operator blocks shared, coefficients per member):
 * mixed-precision solve (TF32 products, float64 Lanczos) with float64 Newton
   refinement against the float64 solve: |dE0| <= 1e-8 |E0|;
 * Hellmann-Feynman gradients dE0/dJ1, dE0/dJ2 (chain rule over the
-  coupling-resolved terms) against central finite differences (h = 1e-5) of
-  float64 energies -- the four shifted couplings of every member as 24 members
+  coupling-resolved terms) against central finite differences (h = 1e-5,
+  1e-6 relative) of float64 energies -- the four shifted couplings of every member as 24 members
   of a second superblock -- against the oracle's gradient (its own DMRG
   ground state at J2 = 0.5, its formula on the device state elsewhere), and
   against the Euler identity E0 = J1 dE/dJ1 + J2 dE/dJ2;
@@ -84,7 +84,12 @@ def test_j2_sweep_energies_and_gradients(mg):
     assert st == 0
     ef = ef.reshape(B, 4)
     fd = np.stack([(ef[:, 0] - ef[:, 1]) / (2 * H), (ef[:, 2] - ef[:, 3]) / (2 * H)], axis=1)
-    assert np.allclose(grads, fd, rtol=1e-5, atol=1e-5)
+    # 1e-6 relative, plus an absolute floor for dE0/dJ2 ~ 0 at the Majumdar-Ghosh
+    # point: a central difference of energies each accurate to eps |E| errs by
+    # at most eps |E| / h (rounding) + h^2 |E'''| / 6 (truncation, ~1e-10 here);
+    # the float64 solves at tolerance 1e-13 give eps <= 1e-13, |E| <= 21, so
+    # eps |E| / h <= 2.1e-7; the floor is 5e-7
+    assert np.allclose(grads, fd, rtol=1e-6, atol=5e-7), np.abs(grads - fd).max()
     # the oracle's gradient formula on the device states
     P = psi.cpu().numpy()
     for b in range(B):

@@ -278,3 +278,61 @@ def test_lanczos_ground_grad(dev, prec, refine):
         assert close(dE[b], ograd.hf_grad(sb, P[b]), rel=1e-11)
         # E0 = sum_k c_k dE0/dc_k (H is linear in the coefficients)
         assert float(sb.coeffs[b] @ dE[b]) == pytest.approx(e0[b], rel=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_lanczos_resumes_after_a_false_float32_pass(dev, prec):
+    """A member whose float32 residual estimate passes although the float64
+    test after the loop fails is restarted from its Ritz vector and converges
+    (status 0) instead of reporting non-convergence with iterations left.
+    The testing hook makes the float32 test pass at the first check of every
+    member (a one-vector Krylov space: the float64 test must fail there), at
+    the tight tolerance 1e-13."""
+    from paper_0902_3185_gb300 import binding
+    sb = grown_hubbard_superblock(12, "ladder", 5, 5, m=60, cut=6, U_values=[4.0, 8.0])
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(30 + b, sb.dim) for b in range(sb.batch)])
+    assert g.lib.dmrg_test_inject(g.h, 2) == 0
+    try:
+        if prec == "fp64":
+            e0, psi, infos, st = g.lanczos_ground(to_dev(X), tol=1e-13, max_iter=400)
+        else:
+            e0, psi, infos, st = g.lanczos_ground(to_dev(X), tol=1e-4, max_iter=400, prec=prec,
+                                                  refine="newton_df64", refine_tol=1e-11)
+    except binding.DmrgError as e:
+        if e.status == 8:
+            pytest.skip("tensor-core path not available")
+        raise
+    assert st == 0, infos
+    for b in range(sb.batch):
+        assert infos[b]["restarts"] >= 1 and infos[b]["status"] == 0
+        ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v, b), X[b], tol=1e-13, max_iter=400)
+        assert abs(e0[b] - ref.e0) <= 1e-10 * abs(ref.e0), (b, e0[b], ref.e0)
+    # the hook applies to one solve: the next runs without a restart
+    e1, _, infos, st = g.lanczos_ground(to_dev(X), tol=1e-13, max_iter=400)
+    assert st == 0 and all(i["restarts"] == 0 for i in infos)
+
+
+def test_set_coeffs_is_ordered_on_the_callers_stream(dev):
+    """dmrg_set_coeffs writes the coefficient table on the given stream, after
+    the products already queued there: products queued before it on a side
+    stream use the old coefficients, products after it the new ones."""
+    sb = grown_hubbard_superblock(16, "chain", 8, 8, m=48, U_values=[1.0, 2.0, 3.0, 4.0, 6.0])
+    g = gpu_sb(sb)
+    X = np.stack([seeded_normal(40 + b, sb.dim) for b in range(sb.batch)])
+    x = to_dev(X)
+    c_new = sb.coeffs * 1.3 + 0.1
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        ys = [g.apply_H(x, stream=side) for _ in range(8)]  # queued, not yet run
+        g.set_coeffs(c_new, stream=side)
+        y_new = g.apply_H(x, stream=side)
+    side.synchronize()
+    sb_new = sb.with_coeffs(c_new)
+    for b in range(sb.batch):
+        ref_old = osb.apply_H(sb, X[b], b)
+        ref_new = osb.apply_H(sb_new, X[b], b)
+        for y in ys:
+            assert close(y.cpu().numpy()[b], ref_old)
+        assert close(y_new.cpu().numpy()[b], ref_new)

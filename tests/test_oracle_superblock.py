@@ -146,3 +146,37 @@ def test_empty_and_uncoupled_sectors_stay_zero():
     off = sb.offsets()
     assert np.all(y[off[6]:off[7]] == 0.0)  # sector 6 has no contributing term
     assert sb.r[3] * sb.c[3] == 0 and sb.r[4] * sb.c[4] == 0
+
+
+def test_matvec_flops_hand_counted():
+    """Algorithmic flop count pinned by hand on a 2-sector superblock:
+    r = (2, 3), c = (4, 5); a multiply-add is 2 flops, blocks dense.
+
+    * term 0, A (x) 1 on sector 0: A (2x2) times Psi_0 (2x4): 2*2*2*4 = 32
+    * term 1, 1 (x) B on sector 1: Psi_1 (3x5) times B^T (5x5): 2*3*5*5 = 150
+    * term 2, sector 1 -> 0, A (2x3), B (4x5):
+        (A Psi_1) B^T: 2*2*3*5 + 2*2*5*4 = 60 + 80 = 140
+        A (Psi_1 B^T): 2*3*5*4 + 2*2*3*4 = 120 + 48 = 168  -> 140
+    * term 3, sector 0 -> 1, A (3x2), B (5x4):
+        (A Psi_0) B^T: 2*3*2*4 + 2*3*4*5 = 48 + 120 = 168
+        A (Psi_0 B^T): 2*2*4*5 + 2*3*2*5 = 80 + 60 = 140   -> 140
+    total 32 + 150 + 140 + 140 = 462 per member.
+    """
+    from workloads.superblock import Pair, Superblock
+    rng = np.random.default_rng(0)
+    pairs = [Pair(0, 0, 0, rng.standard_normal((2, 2)), None),
+             Pair(1, 1, 1, None, rng.standard_normal((5, 5))),
+             Pair(2, 0, 1, rng.standard_normal((2, 3)), rng.standard_normal((4, 5))),
+             Pair(3, 1, 0, rng.standard_normal((3, 2)), rng.standard_normal((5, 4)))]
+    sb = Superblock([2, 3], [4, 5], np.ones((1, 4)), pairs)
+    assert osb.matvec_flops(sb) == 462
+    # each pair alone, with the order the count picks
+    for p, want in zip(pairs, (32, 150, 140, 140)):
+        assert osb.matvec_flops(Superblock([2, 3], [4, 5], np.ones((1, 4)), [p])) == want
+    # and the product the count describes is the blocked rule itself
+    x = rng.standard_normal(sb.dim)
+    y = osb.apply_H(sb, x)
+    X0, X1 = x[:8].reshape(2, 4), x[8:].reshape(3, 5)
+    y0 = pairs[0].A @ X0 + pairs[2].A @ X1 @ pairs[2].B.T
+    y1 = X1 @ pairs[1].B.T + pairs[3].A @ X0 @ pairs[3].B.T
+    assert np.allclose(y, np.concatenate([y0.ravel(), y1.ravel()]), rtol=0, atol=1e-13)

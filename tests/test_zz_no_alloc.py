@@ -1,8 +1,9 @@
 """The allocation-free float64 product (dmrg_apply_H_static_scratch).
 
-Some callers cannot allocate device memory when they apply H -- code under
-CUDA stream capture, processes whose device memory is managed by another
-framework's pool, allocation-free real-time loops.  This entry point keeps
+Some callers cannot allocate device memory when they apply H -- processes
+whose device memory is managed by another framework's pool, real-time loops
+in which an allocation (which can synchronise the device) is not allowed.
+This entry point keeps
 its intermediate workspace in a static device buffer of the library.  The
 test calls it through the C ABI twice in a row (the buffer keeps the first
 call's contents) and compares with dmrg_apply_H in float64 within the
