@@ -500,7 +500,8 @@ def main():
     accuracy = None
     if prec != "fp64":
         t_f64, (e64, psi64, info64, st64, dE64) = timed(lambda: g.lanczos_ground(
-            x0, tol=args.tol, max_iter=args.max_iter, prec="fp64", refine="none", graph_iters=8, grad=True))
+            x0, tol=args.tol, max_iter=max(600, args.max_iter), prec="fp64", refine="none", graph_iters=8,
+            grad=True))
         e64 = np.asarray(e64, dtype=np.float64)
         pm = psi_step / psi_step.norm(dim=1, keepdim=True)
         p6 = psi64 / psi64.norm(dim=1, keepdim=True)
