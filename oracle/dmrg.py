@@ -12,8 +12,9 @@ product of transformed operators is not the transformed product).  The
 truncation error is eps = sum of discarded eigenvalues (Sec. 2).
 
 Readings where the paper is silent (see the design notes): one-site blocks;
-eigenvalues of rho sorted globally, ties broken by (-lambda, q, index), exactly
-m kept; infinite-phase target N = round(density * L_k) rounded to even with
+eigenvalues of rho sorted globally in decreasing order, values within tie_tol
+(1e-12; rho has trace 1) of their neighbour counted as equal and ordered by
+(q, index within the sector), exactly m kept; infinite-phase target N = round(density * L_k) rounded to even with
 N_up = N_dn = N/2 for Hubbard and N_up = L_k/2 for Heisenberg; the finite
 algorithm (Sec. 2, "not discussed here, see code") is the standard sweep at
 fixed L, one sweep = a left-to-right plus a right-to-left pass, starting and
@@ -245,9 +246,13 @@ def make_superblock(model: Model, Sp: DBlock, Ep: DBlock, L_k: int,
     return sb, terms
 
 
-def _truncate(b: DBlock, rho_blocks, m: int, keep_keys) -> Tuple[DBlock, float]:
+def _truncate(b: DBlock, rho_blocks, m: int, keep_keys, tie_tol: float = 1e-12):
     """Keep the m eigenvectors of the block-diagonal rho with the largest
-    eigenvalues (ties: q, then index within the sector), then H <- W^T H W."""
+    eigenvalues, then H <- W^T H W.  Ties: eigenvalues within tie_tol of
+    their neighbour in decreasing order count as equal (one cluster), and a
+    cluster is taken in the order (q, index within the sector).  Returns
+    (block, discarded weight, gap at the cut: the m-th kept value minus the
+    first discarded one, 0 when nothing is cut)."""
     cand = []  # (-lambda, q, index, sector indices, vector)
     for q in sorted(set(b.q.tolist())):
         idx = np.nonzero(b.q == q)[0]
@@ -261,11 +266,22 @@ def _truncate(b: DBlock, rho_blocks, m: int, keep_keys) -> Tuple[DBlock, float]:
         for a in range(len(idx)):
             cand.append((-w[a], q, a, idx, V[:, a]))
     cand.sort(key=lambda t: (t[0], t[1], t[2]))
+    # clusters of equal eigenvalues (equal up to rounding): a new cluster
+    # starts where the value drops by more than tie_tol from its predecessor
+    clustered, cl = [], 0
+    for i, t in enumerate(cand):
+        if i > 0 and (-cand[i - 1][0]) - (-t[0]) > tie_tol:
+            cl += 1
+        clustered.append((cl, t))
+    clustered.sort(key=lambda ct: (ct[0], ct[1][1], ct[1][2]))
+    cand = [t for _, t in clustered]
     total = sum(-t[0] for t in cand)
     if m >= len(cand):
         keep = cand
+        gap = 0.0
     else:
         keep = cand[:m]
+        gap = float(-cand[m - 1][0] - (-cand[m][0]))
     eps = max(0.0, total - sum(-t[0] for t in keep))
     keep.sort(key=lambda t: (t[1], t[2]))  # new basis in q order
     W = np.zeros((b.dim, len(keep)))
@@ -275,7 +291,7 @@ def _truncate(b: DBlock, rho_blocks, m: int, keep_keys) -> Tuple[DBlock, float]:
     Nn = np.array([b.N[t[3][0]] for t in keep], dtype=np.int64)
     H = {k: W.T @ h @ W for k, h in b.H.items()}
     ops = {k: W.T @ M @ W for k, M in b.ops.items() if k[0] in keep_keys}
-    return DBlock(b.n, qn, Nn, H, ops), eps
+    return DBlock(b.n, qn, Nn, H, ops), eps, gap
 
 
 def _rho(sb: Superblock, psi, side):
@@ -298,6 +314,8 @@ class StepResult:
     superblock: Optional[Superblock] = None
     psi: Optional[np.ndarray] = None
     blocks: Optional[tuple] = None  # (S', E') of the step, with keep_superblocks
+    gap_S: float = 0.0  # lambda_m - lambda_{m+1} at the cut of each truncated side (0: nothing cut)
+    gap_E: float = 0.0
 
 
 def _solve(model, Sp, Ep, L_k, seed, tol, max_iter, keep_sb):
@@ -316,7 +334,7 @@ def _rho_by_q(sb, psi, blockS: DBlock, blockE: DBlock, Q_t):
 
 
 def infinite_dmrg(model: Model, L: int, m: int, seed: int = 0, tol: float = 1e-12,
-                  max_iter: int = 300, keep_superblocks: bool = False):
+                  max_iter: int = 300, keep_superblocks: bool = False, tie_tol: float = 1e-12):
     """Returns (steps, left_blocks, right_blocks); left_blocks[n] is the
     truncated block of the n leftmost sites (n = 1 .. L/2 - 1 plus the
     final untruncated halves are not stored)."""
@@ -333,25 +351,25 @@ def infinite_dmrg(model: Model, L: int, m: int, seed: int = 0, tol: float = 1e-1
         Q_t = model.target(L_k)
         rS, rE = _rho_by_q(sb, res.psi, Sp, Ep, Q_t)
         keep = set(range(Sp.n - model.reach, Sp.n))
-        S, eS = _truncate(Sp, rS, m, keep)
-        E, eE = _truncate(Ep, rE, m, keep)
+        S, eS, gS = _truncate(Sp, rS, m, keep, tie_tol)
+        E, eE, gE = _truncate(Ep, rE, m, keep, tie_tol)
         left[S.n] = S
         right[E.n] = E
         steps.append(StepResult(L_k, Sp.n, res.e0, eS, eE, res.iters,
                                 sb if keep_superblocks else None,
                                 res.psi if keep_superblocks else None,
-                                (Sp, Ep) if keep_superblocks else None))
+                                (Sp, Ep) if keep_superblocks else None, gS, gE))
     return steps, left, right
 
 
 def finite_dmrg(model: Model, L: int, m: int, n_sweeps: int = 2, seed: int = 0,
                 tol: float = 1e-12, max_iter: int = 300, keep_superblocks: bool = False,
-                m_infinite: Optional[int] = None):
+                m_infinite: Optional[int] = None, tie_tol: float = 1e-12):
     """Infinite phase to L sites, then n_sweeps sweeps at fixed L.  A step at
     split l has S' = sites [0, l), E' = sites [l, L); S' = left[l-1] (x) site,
     E' = site (x) right[L-l-1]."""
     steps, left, right = infinite_dmrg(model, L, m if m_infinite is None else m_infinite,
-                                       seed, tol, max_iter, keep_superblocks)
+                                       seed, tol, max_iter, keep_superblocks, tie_tol)
     out = list(steps)
     half = L // 2
     path = []
@@ -367,13 +385,13 @@ def finite_dmrg(model: Model, L: int, m: int, n_sweeps: int = 2, seed: int = 0,
         rS, rE = _rho_by_q(sb, res.psi, Sp, Ep, Q_t)
         if direction == "right":
             keepS = set(range(Sp.n - model.reach, Sp.n))
-            left[Sp.n], eS = _truncate(Sp, rS, m, keepS)
-            eE = 0.0
+            left[Sp.n], eS, gS = _truncate(Sp, rS, m, keepS, tie_tol)
+            eE, gE = 0.0, 0.0
         else:
             keepE = set(range(Ep.n - model.reach, Ep.n))
-            right[Ep.n], eE = _truncate(Ep, rE, m, keepE)
-            eS = 0.0
+            right[Ep.n], eE, gE = _truncate(Ep, rE, m, keepE, tie_tol)
+            eS, gS = 0.0, 0.0
         out.append(StepResult(L, Sp.n, res.e0, eS, eE, res.iters,
                               sb if keep_superblocks else None,
-                              res.psi if keep_superblocks else None))
+                              res.psi if keep_superblocks else None, None, gS, gE))
     return out

@@ -28,7 +28,8 @@ SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error
            "dmrg_set_coeffs", "dmrg_apply_H", "dmrg_apply_H_backward", "dmrg_lanczos_ground",
            "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune", "dmrg_sync_status",
            "dmrg_test_inject", "dmrg_lanczos_ground_grad", "dmrg_apply_H_term_dots", "dmrg_lanczos_coeffs",
-           "dmrg_continued_fraction"]
+           "dmrg_continued_fraction", "dmrg_sys_create", "dmrg_sys_destroy", "dmrg_sys_last_error",
+           "dmrg_sys_infinite", "dmrg_sys_sweeps", "dmrg_sys_last_superblock"]
 
 
 class DmrgError(RuntimeError):
@@ -72,6 +73,37 @@ class LanczosInfo(C.Structure):
                 ("restarts", C.c_int32)]
 
 
+class _BondTerm(C.Structure):
+    _fields_ = [("coef", C.c_double), ("op_a", C.c_int32), ("trans_a", C.c_int32), ("op_b", C.c_int32),
+                ("trans_b", C.c_int32)]
+
+
+class _ModelDesc(C.Structure):
+    _fields_ = [("d", C.c_int32), ("site_q", C.c_void_p), ("site_parity", C.c_void_p), ("n_ops", C.c_int32),
+                ("ops", C.c_void_p), ("op_fermion", C.c_void_p), ("n_classes", C.c_int32),
+                ("couplings", C.c_void_p), ("n_onsite", C.c_int32), ("onsite_class", C.c_void_p),
+                ("onsite", C.c_void_p), ("n_bond_rules", C.c_int32), ("bond_rules", C.c_void_p),
+                ("n_bond_terms", C.c_int32), ("bond_terms", C.c_void_p), ("density", C.c_double),
+                ("Q", C.c_int64)]
+
+
+class SysOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("prec", C.c_int32), ("refine", C.c_int32),
+                ("guess", C.c_int32), ("mixed_tol", C.c_double), ("tie_tol", C.c_double), ("seed", C.c_uint64)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("L", C.c_int32), ("n_sys", C.c_int32), ("direction", C.c_int32), ("status", C.c_int32),
+                ("dim", C.c_int64), ("energy", C.c_double), ("eps_S", C.c_double), ("eps_E", C.c_double),
+                ("gap_S", C.c_double), ("gap_E", C.c_double), ("iters", C.c_int32), ("kept_S", C.c_int32),
+                ("kept_E", C.c_int32), ("n_terms", C.c_int32), ("ms", C.c_double)]
+
+
+class _SbView(C.Structure):
+    _fields_ = [("desc", _Desc), ("term_class", C.c_void_p), ("term_mult", C.c_void_p), ("sector_q", C.c_void_p),
+                ("n_sys", C.c_int32), ("L", C.c_int32)]
+
+
 _lib = None
 
 
@@ -110,8 +142,16 @@ def load(build_if_missing: bool = True):
     lib.dmrg_apply_H_term_dots.argtypes = [vp, dp, dp, dp, i32, vp]
     lib.dmrg_lanczos_coeffs.argtypes = [vp, dp, i32, i32, dp, dp, dp, dp, vp]
     lib.dmrg_continued_fraction.argtypes = [dp, dp, dp, dp, i32, i32, dp, dp, i32, dp, dp, vp]
+    lib.dmrg_sys_create.argtypes = [C.POINTER(_ModelDesc), i32, i32, C.POINTER(SysOpts), C.POINTER(vp)]
+    lib.dmrg_sys_destroy.argtypes = [vp]
+    lib.dmrg_sys_destroy.restype = None
+    lib.dmrg_sys_last_error.argtypes = [vp]
+    lib.dmrg_sys_last_error.restype = C.c_char_p
+    lib.dmrg_sys_infinite.argtypes = [vp, C.POINTER(StepInfo), C.POINTER(C.c_int32)]
+    lib.dmrg_sys_sweeps.argtypes = [vp, i32, C.POINTER(StepInfo), C.POINTER(C.c_int32)]
+    lib.dmrg_sys_last_superblock.argtypes = [vp, C.POINTER(_SbView), dp]
     for name in SYMBOLS:
-        if name not in ("dmrg_destroy_superblock", "dmrg_last_error"):
+        if name not in ("dmrg_destroy_superblock", "dmrg_last_error", "dmrg_sys_destroy", "dmrg_sys_last_error"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -334,3 +374,111 @@ class ApplyH(torch.autograd.Function):
 
 def apply_H(psi, coeffs, gsb: GpuSuperblock, prec="fp64"):
     return ApplyH.apply(psi, coeffs, gsb, prec)
+
+
+class GpuDmrg:
+    """The infinite- and finite-system DMRG with every block operation on the
+    device (dmrg_sys_*): growth, superblock, Lanczos, density matrices,
+    truncation, change of basis.  `model` is a workloads.lattice_models.ModelDesc."""
+
+    def __init__(self, model, L, m, tol=1e-12, max_iter=300, prec="fp64", refine="newton", mixed_tol=1e-6,
+                 tie_tol=1e-12, seed=0, guess=False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.lib = load()
+        self.model = model
+        self.L, self.m = int(L), int(m)
+        d = model.d
+        self._keep = [np.ascontiguousarray(model.site_q, dtype=np.int64),
+                      np.ascontiguousarray(model.site_parity, dtype=np.int32),
+                      np.ascontiguousarray(model.ops, dtype=np.float64).reshape(-1, d, d),
+                      np.ascontiguousarray(model.op_fermion, dtype=np.int32),
+                      np.ascontiguousarray(model.couplings, dtype=np.float64),
+                      np.ascontiguousarray(model.onsite_class, dtype=np.int32),
+                      np.ascontiguousarray(model.onsite, dtype=np.float64).reshape(-1, d, d) if len(model.onsite_class)
+                      else np.zeros((1, d, d)),
+                      np.ascontiguousarray(model.bond_rules, dtype=np.int32).reshape(-1, 4)]
+        terms = (_BondTerm * max(1, len(model.bond_terms)))()
+        for i, (c, a, ta, b, tb) in enumerate(model.bond_terms):
+            terms[i] = _BondTerm(c, a, ta, b, tb)
+        self._keep.append(terms)
+        k = self._keep
+        desc = _ModelDesc(d, k[0].ctypes.data, k[1].ctypes.data, len(model.op_names), k[2].ctypes.data,
+                          k[3].ctypes.data, len(model.class_names), k[4].ctypes.data, len(model.onsite_class),
+                          k[5].ctypes.data, k[6].ctypes.data, len(k[7]), k[7].ctypes.data, len(model.bond_terms),
+                          C.cast(terms, C.c_void_p), float(model.density), int(model.Q))
+        mode = refine if isinstance(refine, int) and not isinstance(refine, bool) else GpuSuperblock.REFINE[refine]
+        opts = SysOpts(tol, max_iter, _prec(prec), mode, 1 if guess else 0, mixed_tol, tie_tol, seed)
+        h = C.c_void_p()
+        st = self.lib.dmrg_sys_create(C.byref(desc), self.L, self.m, C.byref(opts), C.byref(h))
+        if st != 0:
+            raise DmrgError(st, "dmrg_sys_create failed (see stderr)")
+        self.h = h
+
+    def _check(self, st, ok=(0,)):
+        if st not in ok:
+            raise DmrgError(st, (self.lib.dmrg_sys_last_error(self.h) or b"").decode())
+
+    @staticmethod
+    def _steps(arr, n):
+        return [{k: getattr(arr[i], k) for k, _ in StepInfo._fields_} for i in range(n)]
+
+    def infinite(self):
+        """L/2 - 1 infinite-algorithm steps; one dict per step."""
+        n_max = self.L // 2 - 1
+        arr = (StepInfo * n_max)()
+        n = C.c_int32()
+        self._check(self.lib.dmrg_sys_infinite(self.h, arr, C.byref(n)), ok=(0, 4))
+        return self._steps(arr, n.value)
+
+    def sweeps(self, n_sweeps):
+        """Finite-algorithm sweeps at fixed L (2 (L - 3) steps each)."""
+        n_max = max(1, n_sweeps * 2 * (self.L - 3))
+        arr = (StepInfo * n_max)()
+        n = C.c_int32()
+        self._check(self.lib.dmrg_sys_sweeps(self.h, int(n_sweeps), arr, C.byref(n)), ok=(0, 4))
+        return self._steps(arr, n.value)
+
+    def last_superblock(self):
+        """The last step's superblock as a workloads Superblock (host copies)
+        and its ground state (numpy [D])."""
+        from workloads.superblock import Pair, Superblock
+        v = _SbView()
+        self._check(self.lib.dmrg_sys_last_superblock(self.h, C.byref(v), None))
+        d = v.desc
+        S, nt, npairs = d.n_sectors, d.n_terms, d.n_pairs
+        r = np.ctypeslib.as_array(C.cast(d.r, C.POINTER(C.c_int32)), shape=(S,)).astype(np.int64)
+        c = np.ctypeslib.as_array(C.cast(d.c, C.POINTER(C.c_int32)), shape=(S,)).astype(np.int64)
+        coeffs = np.ctypeslib.as_array(C.cast(d.coeffs, C.POINTER(C.c_double)), shape=(nt,)).copy()
+        pairs_c = C.cast(d.pairs, C.POINTER(_Pair))
+        pairs = []
+        for i in range(npairs):
+            p = pairs_c[i]
+            ro, ri, co, ci = r[p.s_out], r[p.s_in], c[p.s_out], c[p.s_in]
+            A = B = None
+            if not p.flags & ID_A:
+                A = np.ctypeslib.as_array(C.cast(p.A, C.POINTER(C.c_double)), shape=(int(ro), int(p.lda)))[:, :ri].copy()
+            if not p.flags & ID_B:
+                B = np.ctypeslib.as_array(C.cast(p.B, C.POINTER(C.c_double)), shape=(int(co), int(p.ldb)))[:, :ci].copy()
+            pairs.append(Pair(int(p.term), int(p.s_out), int(p.s_in), A, B))
+        sb = Superblock(r, c, coeffs[None, :], pairs)
+        sb.term_class = np.ctypeslib.as_array(C.cast(v.term_class, C.POINTER(C.c_int32)), shape=(nt,)).copy()
+        sb.term_mult = np.ctypeslib.as_array(C.cast(v.term_mult, C.POINTER(C.c_double)), shape=(nt,)).copy()
+        sb.q_labels = np.ctypeslib.as_array(C.cast(v.sector_q, C.POINTER(C.c_int64)), shape=(S,)).copy()
+        sb.class_names = list(self.model.class_names)
+        sb.couplings = np.asarray(self.model.couplings, dtype=np.float64)[None, :].copy()
+        sb.meta.update(L=v.L, nS=v.n_sys)
+        psi = np.zeros(sb.dim)
+        self._check(self.lib.dmrg_sys_last_superblock(self.h, C.byref(v), psi.ctypes.data))
+        return sb, psi
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmrg_sys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

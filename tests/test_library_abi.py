@@ -51,3 +51,12 @@ def test_no_cpu_fallback_without_gpu():
     from workloads.synthetic import ragged_small
     with pytest.raises(RuntimeError):
         binding.GpuSuperblock(ragged_small())
+
+
+def test_dmrg_sys_struct_layouts_match_header():
+    # sizes of include/dmrg_sys.h's structs under the LP64 C layout rules
+    assert ctypes.sizeof(binding._BondTerm) == 8 + 4 * 4
+    assert ctypes.sizeof(binding._ModelDesc) == 136
+    assert ctypes.sizeof(binding.SysOpts) == 8 + 4 * 4 + 8 + 8 + 8
+    assert ctypes.sizeof(binding.StepInfo) == 4 * 4 + 8 + 8 * 5 + 4 * 4 + 8
+    assert ctypes.sizeof(binding._SbView) == ctypes.sizeof(binding._Desc) + 8 * 3 + 4 * 2
