@@ -105,6 +105,10 @@ typedef struct {      /* one per DMRG step */
   int32_t kept_S, kept_E; /* states kept (0 for a side not truncated) */
   int32_t n_terms;    /* superblock terms */
   double ms;          /* wall time of the step */
+  double ms_grow, ms_superblock, ms_solve, ms_truncate; /* its parts: growth of S' and E', superblock
+                         assembly and creation, the Lanczos solve, density matrices to W^T O W */
+  int32_t max_sector; /* largest symmetry sector of the truncated block(s) (eigensolve size) */
+  int32_t pad;
 } dmrg_step_info;
 
 /* A DMRG run on a lattice of L (even, >= 4) sites keeping m states.  Builds

@@ -847,8 +847,13 @@ struct dmrg_sys {
 
 namespace {
 
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 void solve_step(dmrg_sys* sys, const Blk& Sp, const Blk& Ep, int L, dmrg_step_info& info, DBufP& psi_out,
                 const double* guess, cudaStream_t st) {
+  const double t0 = now_ms();
   build_superblock(sys->M, Sp, Ep, L, sys->view, st);
   SbView& V = sys->view;
   dmrg_sb_desc desc{};
@@ -867,6 +872,8 @@ void solve_step(dmrg_sys* sys, const Blk& Sp, const Blk& Ep, int L, dmrg_step_in
     dmrg_sb* p;
     ~SbGuard() { dmrg_destroy_superblock(p); }
   } guard{sb};
+  const double t1 = now_ms();
+  info.ms_superblock = t1 - t0;
   DBuf psi0((size_t)V.D);
   if (guess) SYS_CK(cudaMemcpyAsync(psi0.p, guess, V.D * sizeof(double), cudaMemcpyDeviceToDevice, st));
   else launch_start_vector(psi0.p, V.D, sys->opts.seed * 1000003ull + (uint64_t)sys->step_count, st);
@@ -898,6 +905,13 @@ void solve_step(dmrg_sys* sys, const Blk& Sp, const Blk& Ep, int L, dmrg_step_in
   sys->last_nS = Sp.n;
   sys->last_L = L;
   ++sys->step_count;
+  info.ms_solve = now_ms() - t1;
+}
+
+int max_dim(const Blk& b) {
+  int m = 0;
+  for (int d : b.bs.dim) m = std::max(m, d);
+  return m;
 }
 
 template <class F>
@@ -918,10 +932,6 @@ dmrg_status sys_guard(dmrg_sys* sys, F&& fn) {
     const cudaError_t ce = cudaGetLastError();
     return ce == cudaErrorMemoryAllocation ? DMRG_ENOMEM : DMRG_ECUDA;
   }
-}
-
-double now_ms() {
-  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 }  // namespace
@@ -974,12 +984,17 @@ dmrg_status dmrg_sys_infinite(dmrg_sys* sys, dmrg_step_info* steps, int32_t* n_s
     for (int k = 0; k < sys->L / 2 - 1; ++k) {
       const double t0 = now_ms();
       BlkP Sp = grow(M, *S, true, st), Ep = grow(M, *E, false, st);
+      SYS_CK(cudaStreamSynchronize(st));
       const int Lk = Sp->n + Ep->n;
       dmrg_step_info info{};
+      info.ms_grow = now_ms() - t0;
       DBufP psi;
       solve_step(sys, *Sp, *Ep, Lk, info, psi, nullptr, st);
+      const double t2 = now_ms();
       TruncOut ts = truncate(M, *Sp, true, sys->view, psi->p, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
       TruncOut te = truncate(M, *Ep, false, sys->view, psi->p, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
+      info.ms_truncate = now_ms() - t2;
+      info.max_sector = std::max(max_dim(*Sp), max_dim(*Ep));
       S = ts.blk;
       E = te.blk;
       sys->left[S->n] = S;
@@ -1024,9 +1039,13 @@ dmrg_status dmrg_sys_sweeps(dmrg_sys* sys, int32_t n_sweeps, dmrg_step_info* ste
       auto ir = sys->right.find(L - l - 1);
       if (il == sys->left.end() || ir == sys->right.end()) throw std::logic_error("sweep: missing block on the stack");
       BlkP Sp = grow(M, *il->second, true, st), Ep = grow(M, *ir->second, false, st);
+      SYS_CK(cudaStreamSynchronize(st));
       dmrg_step_info info{};
+      info.ms_grow = now_ms() - t0;
       DBufP psi;
       solve_step(sys, *Sp, *Ep, L, info, psi, nullptr, st);
+      const double t2 = now_ms();
+      info.max_sector = dir > 0 ? max_dim(*Sp) : max_dim(*Ep);
       if (dir > 0) {
         TruncOut ts = truncate(M, *Sp, true, sys->view, psi->p, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
         sys->left[Sp->n] = ts.blk;
@@ -1041,6 +1060,7 @@ dmrg_status dmrg_sys_sweeps(dmrg_sys* sys, int32_t n_sweeps, dmrg_step_info* ste
         info.kept_E = te.kept;
       }
       info.direction = dir;
+      info.ms_truncate = now_ms() - t2;
       info.ms = now_ms() - t0;
       steps[k] = info;
       *n_steps = ++k;
