@@ -108,7 +108,7 @@ typedef struct {      /* one per DMRG step */
   double ms_grow, ms_superblock, ms_solve, ms_truncate; /* its parts: growth of S' and E', superblock
                          assembly and creation, the Lanczos solve, density matrices to W^T O W */
   int32_t max_sector; /* largest symmetry sector of the truncated block(s) (eigensolve size) */
-  int32_t pad;
+  int32_t guessed;    /* 1: the Lanczos solve started from the transformed previous ground state */
 } dmrg_step_info;
 
 /* A DMRG run on a lattice of L (even, >= 4) sites keeping m states.  Builds

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <new>
@@ -828,6 +829,235 @@ TruncOut truncate(const Model& M, const Blk& G, bool sideS, const SbView& V, con
   return out;
 }
 
+// ------------------------------------------------- wavefunction transformation
+// The previous step's ground state carried to the next step's basis (White's
+// wavefunction transformation, named in the paper's closing notes as the
+// initial guess that cuts the Lanczos iterations of the finite algorithm).
+// Index structure of a superblock (no data):
+struct SbIdx {
+  std::vector<int32_t> r, c, zS, zE, tsecS, tsecE;
+  std::vector<int64_t> off;
+  int64_t D = 0;
+};
+SbIdx index_of(const SbView& V) {
+  SbIdx x;
+  x.r = V.r;
+  x.c = V.c;
+  x.zS = V.zS;
+  x.zE = V.zE;
+  x.tsecS = V.tsecS;
+  x.tsecE = V.tsecE;
+  x.off = V.off;
+  x.D = V.D;
+  return x;
+}
+
+struct Prev {
+  bool valid = false;
+  int l = 0, dir = 0;  // split (sites of S') and direction of the step
+  SbIdx ix;
+  BlkP Sp, Ep;         // its grown blocks (their product structure)
+  DBufP psi;
+};
+
+std::vector<int> inverse_newsec(const Trunc& t) {
+  int n = 0;
+  for (int v : t.newsec) n = std::max(n, v + 1);
+  std::vector<int> inv(n, -1);
+  for (size_t z = 0; z < t.newsec.size(); ++z)
+    if (t.newsec[z] >= 0) inv[t.newsec[z]] = (int)z;
+  return inv;
+}
+
+bool same_basis(const Basis& a, const Basis& b) { return a.q == b.q && a.dim == b.dim; }
+
+// Move to the right (split l -> l + 1).  Old state Psi(alpha', beta') with
+// alpha' in S' (truncated to A = left[l] by W_S) and beta' in E' = site (x) B.
+// New S'' = A (x) site, E'' = site (x) B'' with B = trunc(E'') by W_E:
+//   X = W_S^T Psi;  beta' = (t, b) regrouped so that (a, t) = alpha'';
+//   Psi''(alpha'', beta'') = sum_b X(alpha'', b) W_E(beta'', b).
+bool guess_right(const Prev& P, const Blk& A, const Blk& Snew, const Blk& B, const Blk& Enew, const SbView& Vn,
+                 double* out, cudaStream_t st) {
+  if (!A.trunc || !B.trunc || !same_basis(B.trunc->grown, Enew.bs) || !same_basis(A.trunc->grown, P.Sp->bs))
+    return false;
+  const Trunc& TA = *A.trunc;
+  const Trunc& TB = *B.trunc;
+  const SbIdx& ix = P.ix;
+  const int ns = (int)ix.r.size();
+  std::vector<int64_t> xo(ns + 1, 0);
+  std::vector<GemmJob> ga;
+  for (int s = 0; s < ns; ++s) {
+    const int z = ix.zS[s], k = TA.k[z];
+    xo[s + 1] = xo[s] + (int64_t)k * ix.c[s];
+  }
+  DBuf X((size_t)std::max<int64_t>(xo[ns], 1));
+  for (int s = 0; s < ns; ++s) {
+    const int z = ix.zS[s], k = TA.k[z];
+    if (k == 0) continue;
+    GemmJob j{};
+    j.A = TA.V->p + TA.voff[z];  // W_S^T: A(m, kk) = V[kk * n + m]
+    j.lda = ix.r[s];
+    j.ta = 1;
+    j.M = k;
+    j.K = ix.r[s];
+    j.B = P.psi->p + ix.off[s];
+    j.ldb = ix.c[s];
+    j.N = ix.c[s];
+    j.C = X.p + xo[s];
+    j.ldc = ix.c[s];
+    j.alpha = 1.0;
+    ga.push_back(j);
+  }
+  launch_gemm(ga, st);
+  const std::vector<int> invA = inverse_newsec(TA);
+  const int nn = (int)Vn.r.size();
+  std::vector<int64_t> po(nn + 1, 0);
+  std::vector<int> ky(nn, 0);
+  for (int s = 0; s < nn; ++s) {
+    const int y = TB.newsec[Vn.zE[s]];
+    ky[s] = y >= 0 ? B.bs.dim[y] : 0;
+    po[s + 1] = po[s] + (int64_t)Vn.r[s] * ky[s];
+  }
+  DBuf P2((size_t)std::max<int64_t>(po[nn], 1));
+  SYS_CK(cudaMemsetAsync(P2.p, 0, std::max<int64_t>(po[nn], 1) * sizeof(double), st));
+  std::vector<ScatJob> jobs;
+  for (int s2 = 0; s2 < nn; ++s2) {
+    if (ky[s2] == 0) continue;
+    const int y = TB.newsec[Vn.zE[s2]];
+    for (const Comp& cp : Snew.comps[Vn.zS[s2]]) {
+      const int zold = cp.z < (int)invA.size() ? invA[cp.z] : -1;
+      if (zold < 0) continue;
+      auto w = P.Ep->where.find({y, cp.t});
+      if (w == P.Ep->where.end()) continue;
+      const int s = ix.tsecS[zold];
+      if (s < 0 || ix.zE[s] != w->second.first) continue;
+      ScatJob j{};
+      j.src = X.p + xo[s] + w->second.second;
+      j.ld_src = ix.c[s];
+      j.rows = A.bs.dim[cp.z];
+      j.cols = ky[s2];
+      j.dst = P2.p + po[s2] + (int64_t)cp.off * ky[s2];
+      j.ld_dst = ky[s2];
+      j.scale = 1.0;
+      jobs.push_back(j);
+    }
+  }
+  launch_scatter(jobs, st);
+  SYS_CK(cudaMemsetAsync(out, 0, Vn.D * sizeof(double), st));
+  std::vector<GemmJob> gc;
+  for (int s2 = 0; s2 < nn; ++s2) {
+    if (ky[s2] == 0) continue;
+    const int e = Vn.zE[s2];
+    GemmJob j{};
+    j.A = P2.p + po[s2];
+    j.lda = ky[s2];
+    j.M = Vn.r[s2];
+    j.K = ky[s2];
+    j.B = TB.V->p + TB.voff[e];  // W_E^T: B(kk, n) = V[n * c + kk]
+    j.ldb = Vn.c[s2];
+    j.tb = 1;
+    j.N = Vn.c[s2];
+    j.C = out + Vn.off[s2];
+    j.ldc = Vn.c[s2];
+    j.alpha = 1.0;
+    gc.push_back(j);
+  }
+  launch_gemm(gc, st);
+  SYS_CK(cudaStreamSynchronize(st));
+  return true;
+}
+
+// Move to the left (split l -> l - 1), the mirror image: X = Psi W_E (E'
+// truncated to A = right[L - l]); alpha' = (a, t) regrouped so that (t, b) =
+// beta''; Psi''(alpha'', beta'') = sum_a W_S(alpha'', a) X(a, beta'') with
+// B = left[l - 1] = trunc(S'') by W_S.
+bool guess_left(const Prev& P, const Blk& A, const Blk& Enew, const Blk& B, const Blk& Snew, const SbView& Vn,
+                double* out, cudaStream_t st) {
+  if (!A.trunc || !B.trunc || !same_basis(B.trunc->grown, Snew.bs) || !same_basis(A.trunc->grown, P.Ep->bs))
+    return false;
+  const Trunc& TA = *A.trunc;
+  const Trunc& TB = *B.trunc;
+  const SbIdx& ix = P.ix;
+  const int ns = (int)ix.r.size();
+  std::vector<int64_t> xo(ns + 1, 0);
+  for (int s = 0; s < ns; ++s) xo[s + 1] = xo[s] + (int64_t)ix.r[s] * TA.k[ix.zE[s]];
+  DBuf X((size_t)std::max<int64_t>(xo[ns], 1));
+  std::vector<GemmJob> ga;
+  for (int s = 0; s < ns; ++s) {
+    const int e = ix.zE[s], k = TA.k[e];
+    if (k == 0) continue;
+    GemmJob j{};
+    j.A = P.psi->p + ix.off[s];
+    j.lda = ix.c[s];
+    j.M = ix.r[s];
+    j.K = ix.c[s];
+    j.B = TA.V->p + TA.voff[e];  // W_E: B(kk, n) = V[kk * c + n]
+    j.ldb = ix.c[s];
+    j.N = k;
+    j.C = X.p + xo[s];
+    j.ldc = k;
+    j.alpha = 1.0;
+    ga.push_back(j);
+  }
+  launch_gemm(ga, st);
+  const std::vector<int> invA = inverse_newsec(TA);
+  const int nn = (int)Vn.r.size();
+  std::vector<int64_t> po(nn + 1, 0);
+  std::vector<int> kx(nn, 0);
+  for (int s = 0; s < nn; ++s) {
+    const int x = TB.newsec[Vn.zS[s]];
+    kx[s] = x >= 0 ? B.bs.dim[x] : 0;
+    po[s + 1] = po[s] + (int64_t)kx[s] * Vn.c[s];
+  }
+  DBuf P2((size_t)std::max<int64_t>(po[nn], 1));
+  SYS_CK(cudaMemsetAsync(P2.p, 0, std::max<int64_t>(po[nn], 1) * sizeof(double), st));
+  std::vector<ScatJob> jobs;
+  for (int s2 = 0; s2 < nn; ++s2) {
+    if (kx[s2] == 0) continue;
+    const int x = TB.newsec[Vn.zS[s2]];
+    for (const Comp& cp : Enew.comps[Vn.zE[s2]]) {
+      const int eold = cp.z < (int)invA.size() ? invA[cp.z] : -1;
+      if (eold < 0) continue;
+      auto w = P.Sp->where.find({x, cp.t});
+      if (w == P.Sp->where.end()) continue;
+      const int s = ix.tsecS[w->second.first];
+      if (s < 0 || ix.zE[s] != eold) continue;
+      const int kE = TA.k[eold];
+      ScatJob j{};
+      j.src = X.p + xo[s] + (int64_t)w->second.second * kE;
+      j.ld_src = kE;
+      j.rows = kx[s2];
+      j.cols = kE;
+      j.dst = P2.p + po[s2] + cp.off;
+      j.ld_dst = Vn.c[s2];
+      j.scale = 1.0;
+      jobs.push_back(j);
+    }
+  }
+  launch_scatter(jobs, st);
+  SYS_CK(cudaMemsetAsync(out, 0, Vn.D * sizeof(double), st));
+  std::vector<GemmJob> gc;
+  for (int s2 = 0; s2 < nn; ++s2) {
+    if (kx[s2] == 0) continue;
+    const int z = Vn.zS[s2];
+    GemmJob j{};
+    j.A = TB.V->p + TB.voff[z];  // W_S: A(m, kk) = V[m * r + kk]
+    j.lda = Vn.r[s2];
+    j.M = Vn.r[s2];
+    j.K = kx[s2];
+    j.B = P2.p + po[s2];
+    j.ldb = Vn.c[s2];
+    j.N = Vn.c[s2];
+    j.C = out + Vn.off[s2];
+    j.ldc = Vn.c[s2];
+    j.alpha = 1.0;
+    gc.push_back(j);
+  }
+  launch_gemm(gc, st);
+  SYS_CK(cudaStreamSynchronize(st));
+  return true;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ system
@@ -842,6 +1072,7 @@ struct dmrg_sys {
   SbView view;
   std::vector<double> psi_host;
   int last_nS = 0, last_L = 0;
+  Prev prev;  // the previous step, for the wavefunction transformation
   std::string err;
 };
 
@@ -851,8 +1082,14 @@ double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-void solve_step(dmrg_sys* sys, const Blk& Sp, const Blk& Ep, int L, dmrg_step_info& info, DBufP& psi_out,
-                const double* guess, cudaStream_t st) {
+// guess(V, out): writes a start vector for the superblock V into out and
+// returns true, or returns false (random start)
+using GuessFn = std::function<bool(const SbView&, double*)>;
+
+void solve_step(dmrg_sys* sys, const BlkP& SpP, const BlkP& EpP, int L, int dir, dmrg_step_info& info,
+                const GuessFn& guess, cudaStream_t st) {
+  const Blk& Sp = *SpP;
+  const Blk& Ep = *EpP;
   const double t0 = now_ms();
   build_superblock(sys->M, Sp, Ep, L, sys->view, st);
   SbView& V = sys->view;
@@ -875,9 +1112,10 @@ void solve_step(dmrg_sys* sys, const Blk& Sp, const Blk& Ep, int L, dmrg_step_in
   const double t1 = now_ms();
   info.ms_superblock = t1 - t0;
   DBuf psi0((size_t)V.D);
-  if (guess) SYS_CK(cudaMemcpyAsync(psi0.p, guess, V.D * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  else launch_start_vector(psi0.p, V.D, sys->opts.seed * 1000003ull + (uint64_t)sys->step_count, st);
-  psi_out = std::make_shared<DBuf>((size_t)V.D);
+  const bool guessed = sys->opts.guess && guess && guess(V, psi0.p);
+  if (!guessed) launch_start_vector(psi0.p, V.D, sys->opts.seed * 1000003ull + (uint64_t)sys->step_count, st);
+  info.guessed = guessed ? 1 : 0;
+  DBufP psi_out = std::make_shared<DBuf>((size_t)V.D);
   dmrg_lanczos_opts o{};
   const bool mixed = sys->opts.prec != DMRG_FP64;
   o.tol = mixed ? sys->opts.mixed_tol : sys->opts.tol;
@@ -906,6 +1144,14 @@ void solve_step(dmrg_sys* sys, const Blk& Sp, const Blk& Ep, int L, dmrg_step_in
   sys->last_L = L;
   ++sys->step_count;
   info.ms_solve = now_ms() - t1;
+  Prev& P = sys->prev;
+  P.valid = true;
+  P.l = Sp.n;
+  P.dir = dir;
+  P.ix = index_of(V);
+  P.Sp = SpP;
+  P.Ep = EpP;
+  P.psi = psi_out;
 }
 
 int max_dim(const Blk& b) {
@@ -988,11 +1234,11 @@ dmrg_status dmrg_sys_infinite(dmrg_sys* sys, dmrg_step_info* steps, int32_t* n_s
       const int Lk = Sp->n + Ep->n;
       dmrg_step_info info{};
       info.ms_grow = now_ms() - t0;
-      DBufP psi;
-      solve_step(sys, *Sp, *Ep, Lk, info, psi, nullptr, st);
+      solve_step(sys, Sp, Ep, Lk, 0, info, nullptr, st);
+      const double* psi = sys->prev.psi->p;
       const double t2 = now_ms();
-      TruncOut ts = truncate(M, *Sp, true, sys->view, psi->p, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
-      TruncOut te = truncate(M, *Ep, false, sys->view, psi->p, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
+      TruncOut ts = truncate(M, *Sp, true, sys->view, psi, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
+      TruncOut te = truncate(M, *Ep, false, sys->view, psi, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
       info.ms_truncate = now_ms() - t2;
       info.max_sector = std::max(max_dim(*Sp), max_dim(*Ep));
       S = ts.blk;
@@ -1042,18 +1288,40 @@ dmrg_status dmrg_sys_sweeps(dmrg_sys* sys, int32_t n_sweeps, dmrg_step_info* ste
       SYS_CK(cudaStreamSynchronize(st));
       dmrg_step_info info{};
       info.ms_grow = now_ms() - t0;
-      DBufP psi;
-      solve_step(sys, *Sp, *Ep, L, info, psi, nullptr, st);
+      const BlkP Sold = il->second, Eold = ir->second;
+      GuessFn guess = [&](const SbView& Vn, double* out) -> bool {
+        const Prev& P = sys->prev;
+        if (!P.valid) return false;
+        if (P.l == l && P.ix.D == Vn.D && P.ix.r == Vn.r && P.ix.c == Vn.c) {  // same superblock (turning point)
+          SYS_CK(cudaMemcpyAsync(out, P.psi->p, Vn.D * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          return true;
+        }
+        if (l == P.l + 1 && P.dir >= 0) {  // moved right: S' of the last step was truncated into left[l - 1]
+          auto a = sys->left.find(P.l);
+          auto b = sys->right.find(L - l);
+          if (a == sys->left.end() || b == sys->right.end() || a->second != Sold) return false;
+          return guess_right(P, *a->second, *Sp, *b->second, *Ep, Vn, out, st);
+        }
+        if (l == P.l - 1 && P.dir < 0) {  // moved left: E' of the last step was truncated into right[L - l - 1]
+          auto a = sys->right.find(L - P.l);
+          auto b = sys->left.find(l);
+          if (a == sys->right.end() || b == sys->left.end() || a->second != Eold) return false;
+          return guess_left(P, *a->second, *Ep, *b->second, *Sp, Vn, out, st);
+        }
+        return false;
+      };
+      solve_step(sys, Sp, Ep, L, dir, info, guess, st);
+      const double* psi = sys->prev.psi->p;
       const double t2 = now_ms();
       info.max_sector = dir > 0 ? max_dim(*Sp) : max_dim(*Ep);
       if (dir > 0) {
-        TruncOut ts = truncate(M, *Sp, true, sys->view, psi->p, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
+        TruncOut ts = truncate(M, *Sp, true, sys->view, psi, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
         sys->left[Sp->n] = ts.blk;
         info.eps_S = ts.eps;
         info.gap_S = ts.gap;
         info.kept_S = ts.kept;
       } else {
-        TruncOut te = truncate(M, *Ep, false, sys->view, psi->p, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
+        TruncOut te = truncate(M, *Ep, false, sys->view, psi, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
         sys->right[Ep->n] = te.blk;
         info.eps_E = te.eps;
         info.gap_E = te.gap;

@@ -114,3 +114,49 @@ def test_hubbard_ladder_against_oracle(gpu):
     gs = g.infinite() + g.sweeps(1)
     os_ = dmrg.finite_dmrg(dmrg.hubbard_ladder(1.0, 0.7, 6.0), 8, m=40, n_sweeps=1)
     compare(gs, os_)
+
+
+@pytest.mark.parametrize("make,L,m", [(lambda: lm.hubbard_chain(1.0, 4.0), 12, 48),
+                                      (lambda: lm.hubbard_ladder(1.0, 0.7, 6.0), 10, 48),
+                                      (lambda: lm.heisenberg_chain(1.0, 0.35), 14, 24)])
+def test_wavefunction_transformation_cuts_iterations(gpu, make, L, m):
+    """Finite steps started from the previous ground state carried to the new
+    basis (White's wavefunction transformation, the paper's closing notes):
+    the same energies as random starts (to 1e-10), every finite step started
+    from the transformed state, and far fewer Lanczos iterations."""
+    runs = {}
+    for guess in (False, True):
+        g = gpu.GpuDmrg(make(), L, m=m, guess=guess)
+        g.infinite()
+        runs[guess] = g.sweeps(2)
+    rnd, gss = runs[False], runs[True]
+    assert len(rnd) == len(gss)
+    for a, b in zip(rnd, gss):
+        assert a["status"] == 0 and b["status"] == 0
+        assert abs(a["energy"] - b["energy"]) <= 1e-10 * abs(a["energy"])
+        assert b["guessed"] == 1 and a["guessed"] == 0
+    it_r = sum(s["iters"] for s in rnd)
+    it_g = sum(s["iters"] for s in gss)
+    assert it_g < 0.5 * it_r, (it_g, it_r)
+
+
+@pytest.mark.slow
+def test_config2_hubbard32_m200_two_sweeps(gpu):
+    """Hubbard chain L = 32, U = 4, half filling, m = 200: the infinite
+    algorithm and two finite sweeps on the device, end to end.  Every step
+    converges; the sweeps lower the middle-split energy below the infinite
+    phase's and the second sweep changes it by less than 1e-6 relative;
+    the last superblock, exported, gives the same E0 under the oracle's own
+    Lanczos (1e-10)."""
+    g = gpu.GpuDmrg(lm.hubbard_chain(1.0, 4.0), 32, m=200, tol=1e-10, guess=True)
+    inf = g.infinite()
+    sw = g.sweeps(2)
+    assert all(s["status"] == 0 for s in inf + sw)
+    assert all(s["guessed"] == 1 for s in sw)
+    e_inf = inf[-1]["energy"]
+    mids = [s["energy"] for s in sw if s["n_sys"] == 16]
+    assert mids[-1] <= e_inf + 1e-9
+    assert abs(mids[-1] - mids[-3]) <= 1e-6 * abs(mids[-1])
+    sb, psi = g.last_superblock()
+    ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v), seeded_normal(5, sb.dim), tol=1e-11, max_iter=600)
+    assert abs(ref.e0 - sw[-1]["energy"]) <= 1e-10 * abs(ref.e0)
