@@ -142,6 +142,20 @@ typedef struct {
 } dmrg_sys_superblock_view;
 dmrg_status dmrg_sys_last_superblock(dmrg_sys* sys, dmrg_sys_superblock_view* out, double* psi);
 
+/* The batched symmetric eigensolver of the DMRG step (the per-sector
+ * eigen-decompositions of rho_S and rho_E, Eqs. rhoSystem, rhoEnviron):
+ * for each of `count` symmetric matrices A[i] (device, n[i] x n[i]
+ * row-major, not modified) the eigenvalues w[i] (device [n[i]], decreasing)
+ * and eigenvectors V[i] (device n[i] x n[i] row-major, column j for w[i][j]),
+ * by cyclic Jacobi rotations in float64: one thread block per matrix up to
+ * n = 110 (in its shared memory), a cluster of 16 blocks up to n = 448 (in
+ * their distributed shared memory), one block over global memory above that
+ * (n <= 4096).  n, A, V, w: host arrays of [count]; stream-ordered (workspace
+ * is allocated on the stream).  DMRG_EINVAL for n[i] < 0 or > 4096 or NULL
+ * pointers. */
+dmrg_status dmrg_sym_eig_batched(int32_t count, const int32_t* n, const double* const* A, double* const* V,
+                                 double* const* w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

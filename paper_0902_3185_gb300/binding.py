@@ -29,7 +29,7 @@ SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error
            "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune", "dmrg_sync_status",
            "dmrg_test_inject", "dmrg_lanczos_ground_grad", "dmrg_apply_H_term_dots", "dmrg_lanczos_coeffs",
            "dmrg_continued_fraction", "dmrg_sys_create", "dmrg_sys_destroy", "dmrg_sys_last_error",
-           "dmrg_sys_infinite", "dmrg_sys_sweeps", "dmrg_sys_last_superblock"]
+           "dmrg_sys_infinite", "dmrg_sys_sweeps", "dmrg_sys_last_superblock", "dmrg_sym_eig_batched"]
 
 
 class DmrgError(RuntimeError):
@@ -152,6 +152,7 @@ def load(build_if_missing: bool = True):
     lib.dmrg_sys_infinite.argtypes = [vp, C.POINTER(StepInfo), C.POINTER(C.c_int32)]
     lib.dmrg_sys_sweeps.argtypes = [vp, i32, C.POINTER(StepInfo), C.POINTER(C.c_int32)]
     lib.dmrg_sys_last_superblock.argtypes = [vp, C.POINTER(_SbView), dp]
+    lib.dmrg_sym_eig_batched.argtypes = [i32, vp, vp, vp, vp, vp]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error", "dmrg_sys_destroy", "dmrg_sys_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -484,3 +485,22 @@ class GpuDmrg:
             self.close()
         except Exception:
             pass
+
+
+def sym_eig_batched(mats, stream=None):
+    """Eigen-decompositions of symmetric float64 CUDA matrices (list of
+    [n, n] tensors): returns [(w decreasing, V with eigenvectors as columns)]."""
+    lib = load()
+    mats = [m.contiguous() for m in mats]
+    ws = [torch.empty(m.shape[0], dtype=torch.float64, device=m.device) for m in mats]
+    Vs = [torch.empty_like(m) for m in mats]
+    cnt = len(mats)
+    n = np.array([m.shape[0] for m in mats], dtype=np.int32)
+    pa = (C.c_void_p * max(1, cnt))(*[_ptr(m) for m in mats])
+    pv = (C.c_void_p * max(1, cnt))(*[_ptr(v) for v in Vs])
+    pw = (C.c_void_p * max(1, cnt))(*[_ptr(w) for w in ws])
+    st = lib.dmrg_sym_eig_batched(cnt, n.ctypes.data, C.cast(pa, C.c_void_p), C.cast(pv, C.c_void_p),
+                                  C.cast(pw, C.c_void_p), _stream(stream))
+    if st != 0:
+        raise DmrgError(st, "sym_eig_batched")
+    return list(zip(ws, Vs))

@@ -16,6 +16,8 @@
 #include <stdexcept>
 #include <string>
 
+#include <cooperative_groups.h>
+
 #include "blockops.h"
 
 namespace dmrg {
@@ -299,7 +301,218 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig(const EigJob* __restrict__ 
   }
 }
 
-void launch_eig(const std::vector<EigJob>& jobs, cudaStream_t st) {
+// The same cyclic Jacobi for a matrix too large for one block's shared
+// memory, on a cluster of EIG_CLUSTER blocks whose shared memories together
+// hold A and V (thread-block clusters with distributed shared memory).  Row i
+// of A and of V lives in block i % C (local row i / C).  A round of disjoint
+// rotations: (1) the owner of row p = min(p, q) of each pair computes (c, s)
+// from a_pp, a_pq (local) and a_qq (remote); (2) every block gathers all
+// rotations, and the owner of p rotates rows p (local) and q (remote, read
+// and written through distributed shared memory) -- no other block touches
+// them; (3) every block rotates columns p, q of its own rows of A and V.
+// Cluster barriers separate the phases.  All blocks sum the convergence test
+// in the same order, so they leave the sweep loop together.
+constexpr int EIG_CLUSTER = 16;
+
+__global__ void __launch_bounds__(EIG_THREADS) k_eig_cluster(const EigJob* __restrict__ jobs) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double sm[];
+  __shared__ double red[EIG_THREADS / 32];
+  __shared__ double sums[2];
+  __shared__ int n_own;
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const EigJob jb = jobs[blockIdx.x / C];
+  const int n = jb.n;
+  const int n2 = (n + 1) & ~1;
+  const int np = n2 / 2;
+  const int R = (n + C - 1) / C;
+  const int rows = rank < n ? (n - 1 - rank) / C + 1 : 0;  // own rows: rank, rank + C, ...
+  double* a = sm;                       // [R][n]
+  double* v = sm + (size_t)R * n;       // [R][n]
+  double* par = v + (size_t)R * n;      // [np][2] rotations of the pairs this block owns
+  double* allp = par + 2 * np;          // [np][2] all rotations of the round
+  double* dg = allp + 2 * np;           // [n] diagonal (final ordering)
+  int* own = reinterpret_cast<int*>(dg + n);  // [np] pairs this block owns
+  int* rk = own + np;                         // [n]
+  const int tid = threadIdx.x;
+  for (int e = tid; e < rows * n; e += EIG_THREADS) {
+    const int li = e / n, j = e % n, i = rank + C * li;
+    a[li * n + j] = jb.A[(int64_t)i * n + j];
+    v[li * n + j] = i == j ? 1.0 : 0.0;
+  }
+  cl.sync();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dgs = 0.0;
+    for (int e = tid; e < rows * n; e += EIG_THREADS) {
+      const int li = e / n, j = e % n, i = rank + C * li;
+      const double x = a[li * n + j];
+      if (i == j) dgs = fma(x, x, dgs);
+      else off = fma(x, x, off);
+    }
+    off = eig_block_sum(off, red);
+    dgs = eig_block_sum(dgs, red);
+    if (tid == 0) {
+      sums[0] = off;
+      sums[1] = dgs;
+    }
+    cl.sync();
+    double to = 0.0, td = 0.0;
+    for (int b = 0; b < C; ++b) {  // the same order in every block
+      const double* rs = cl.map_shared_rank(sums, b);
+      to += rs[0];
+      td += rs[1];
+    }
+    cl.sync();  // the sums are read before any block writes the next ones
+    if (to <= 1e-30 * td || to <= 1e-300) break;
+    for (int r = 0; r < n2 - 1; ++r) {
+      if (tid == 0) n_own = 0;
+      __syncthreads();
+      for (int k = tid; k < np; k += EIG_THREADS) {
+        int p = rr_player(k, r, n2), q = rr_player(n2 - 1 - k, r, n2);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (p % C != rank) continue;
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = a[(p / C) * n + q];
+          if (apq != 0.0) {
+            const double* ra = cl.map_shared_rank(a, q % C);
+            const double aqq = ra[(q / C) * n + q];
+            const double tau = (aqq - a[(p / C) * n + p]) / (2.0 * apq);
+            double t;
+            if (fabs(tau) > 1e150) t = 0.5 / tau;
+            else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        par[2 * k] = c;
+        par[2 * k + 1] = s;
+        if (s != 0.0) own[atomicAdd(&n_own, 1)] = k;
+      }
+      cl.sync();
+      for (int k = tid; k < np; k += EIG_THREADS) {  // gather every pair's rotation
+        int p = rr_player(k, r, n2), q = rr_player(n2 - 1 - k, r, n2);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const double* rp = cl.map_shared_rank(par, p % C);
+        allp[2 * k] = rp[2 * k];
+        allp[2 * k + 1] = rp[2 * k + 1];
+      }
+      const int no = n_own;
+      for (int e = tid; e < no * n; e += EIG_THREADS) {  // rows p (local) and q (remote) of owned pairs
+        const int k = own[e / n], j = e % n;
+        int p = rr_player(k, r, n2), q = rr_player(n2 - 1 - k, r, n2);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const double c = par[2 * k], s = par[2 * k + 1];
+        double* rq = cl.map_shared_rank(a, q % C) + (size_t)(q / C) * n;
+        double* rowp = a + (size_t)(p / C) * n;
+        const double x = rowp[j], y = rq[j];
+        rowp[j] = c * x - s * y;
+        rq[j] = s * x + c * y;
+      }
+      cl.sync();
+      for (int e = tid; e < rows * np; e += EIG_THREADS) {  // columns p, q of own rows of A and V
+        const int li = e / np, k = e % np;
+        const double s = allp[2 * k + 1];
+        if (s == 0.0) continue;
+        const double c = allp[2 * k];
+        int p = rr_player(k, r, n2), q = rr_player(n2 - 1 - k, r, n2);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double* ra = a + (size_t)li * n;
+        double* rv = v + (size_t)li * n;
+        const double x = ra[p], y = ra[q];
+        ra[p] = c * x - s * y;
+        ra[q] = s * x + c * y;
+        const double xv = rv[p], yv = rv[q];
+        rv[p] = c * xv - s * yv;
+        rv[q] = s * xv + c * yv;
+      }
+      cl.sync();
+    }
+  }
+  // decreasing order: every block gathers the diagonal, ranks it, and writes its own rows of V
+  for (int i = tid; i < n; i += EIG_THREADS) {
+    const double* ra = cl.map_shared_rank(a, i % C);
+    dg[i] = ra[(i / C) * n + i];
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += EIG_THREADS) {
+    const double wi = dg[i];
+    int r2 = 0;
+    for (int j = 0; j < n; ++j) r2 += (dg[j] > wi) || (dg[j] == wi && j < i);
+    rk[i] = r2;
+  }
+  __syncthreads();
+  if (rank == 0)
+    for (int i = tid; i < n; i += EIG_THREADS) jb.w[rk[i]] = dg[i];
+  for (int e = tid; e < rows * n; e += EIG_THREADS) {
+    const int li = e / n, j = e % n, i = rank + C * li;
+    jb.V[(int64_t)i * n + rk[j]] = v[li * n + j];
+  }
+  cl.sync();  // no block leaves while others may still read its shared memory
+}
+
+size_t eig_cluster_smem(int n) {
+  const size_t R = (size_t)(n + EIG_CLUSTER - 1) / EIG_CLUSTER, np = (size_t)(n + 1) / 2;
+  return 2 * R * n * sizeof(double) + 4 * np * sizeof(double) + n * sizeof(double) + (np + n) * sizeof(int);
+}
+
+// largest n the cluster kernel takes (A and V in the cluster's shared memory)
+constexpr int EIG_CLUSTER_MAX_N = 448;
+
+// -1: not tried, 0: unavailable on this device, 1: available
+int g_cluster_ok = -1;
+
+bool launch_eig_cluster(const std::vector<EigJob>& jobs, cudaStream_t st) {
+  if (jobs.empty()) return true;
+  size_t smem = 0;
+  for (const EigJob& j : jobs) smem = std::max(smem, eig_cluster_smem(j.n));
+  smem = (smem + 15) & ~(size_t)15;
+  if (g_cluster_ok == 0) return false;
+  if (cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    g_cluster_ok = 0;
+    return false;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(EIG_CLUSTER * jobs.size()));
+  cfg.blockDim = dim3(EIG_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = EIG_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_eig_cluster, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    g_cluster_ok = 0;
+    return false;
+  }
+  g_cluster_ok = 1;
+  EigJob* dj = upload_async(jobs, st);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_eig_cluster, (const EigJob*)dj);
+  if (e != cudaSuccess) throw std::runtime_error(std::string("k_eig_cluster: ") + cudaGetErrorString(e));
+  cudaFreeAsync(dj, st);
+  return true;
+}
+
+void launch_eig(const std::vector<EigJob>& all, cudaStream_t st) {
+  if (all.empty()) return;
+  // sizes between the one-block shared-memory limit and the cluster limit go to
+  // the cluster kernel when the device runs it; the rest to the one-block kernel
+  std::vector<EigJob> mid, jobs;
+  for (const EigJob& j : all) (j.n > EIG_SMEM_MAX_N && j.n <= EIG_CLUSTER_MAX_N ? mid : jobs).push_back(j);
+  if (!launch_eig_cluster(mid, st))
+    for (const EigJob& j : mid) {
+      if (!j.work) throw std::logic_error("eigensolve: missing workspace");
+      jobs.push_back(j);
+    }
   if (jobs.empty()) return;
   size_t smem = 0;
   for (const EigJob& j : jobs) {

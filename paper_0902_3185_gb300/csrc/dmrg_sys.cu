@@ -1362,4 +1362,41 @@ dmrg_status dmrg_sys_last_superblock(dmrg_sys* sys, dmrg_sys_superblock_view* ou
   return DMRG_OK;
 }
 
+dmrg_status dmrg_sym_eig_batched(int32_t count, const int32_t* n, const double* const* A, double* const* V,
+                                 double* const* w, void* stream) {
+  if (count < 0 || (count > 0 && (!n || !A || !V || !w))) return DMRG_EINVAL;
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<EigJob> jobs;
+    int64_t work = 0;
+    for (int i = 0; i < count; ++i) {
+      if (n[i] < 0 || n[i] > 4096 || (n[i] > 0 && (!A[i] || !V[i] || !w[i]))) return DMRG_EINVAL;
+      if (n[i] > EIG_SMEM_MAX_N) work += 2 * (int64_t)n[i] * (n[i] + 1);
+    }
+    double* ws = nullptr;
+    if (work > 0) SYS_CK(cudaMallocAsync(reinterpret_cast<void**>(&ws), work * sizeof(double), st));
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+      if (n[i] == 0) continue;
+      EigJob j{};
+      j.A = A[i];
+      j.V = V[i];
+      j.w = w[i];
+      j.n = n[i];
+      if (n[i] > EIG_SMEM_MAX_N) {
+        j.work = ws + off;
+        off += 2 * (int64_t)n[i] * (n[i] + 1);
+      }
+      jobs.push_back(j);
+    }
+    launch_eig(jobs, st);
+    if (ws) SYS_CK(cudaFreeAsync(ws, st));
+    return DMRG_OK;
+  } catch (const std::logic_error&) {
+    return DMRG_EINVAL;
+  } catch (const std::exception&) {
+    return DMRG_ECUDA;
+  }
+}
+
 }  // extern "C"
