@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--mixed-tol", type=float, default=2e-4)
     ap.add_argument("--refine", default="newton_df64", choices=["newton", "newton_df64", "lanczos", "none"])
+    ap.add_argument("--no-real", action="store_true", help="skip the real DMRG superblock variant")
     return ap.parse_args()
 
 
@@ -232,6 +233,108 @@ def measure_ldos(binding, torch, inp, psi, e0, prec, dev, stream, n_coef=100, n_
             "sum_rule_max_dev": float((out["hole"][1] + out["particle"][1] - 1.0).abs().max()),
             "weight_in_window": float((dens.sum(dim=1) * dw).mean()),
             "min_coefficients": int(min(o[2].min() for o in out.values()))}
+
+
+def measure_real(binding, torch, args, dev, stream, peaks, kind, sm_mhz):
+    """The same step on a real DMRG superblock: the device DMRG driver runs the
+    infinite algorithm on the 2 x 32 Hubbard ladder (U = 8, N_up = N_dn = 28,
+    m = 1000; BF16x3 Lanczos refined to 1e-10 with double-float residuals in
+    every step), and the last step's superblock (density-matrix basis, real
+    sector sizes) carries the 16 members U = 4 .. 12.  Reported: the driver's
+    time, the product in each precision, the timed step (mixed solve + gradient)
+    with its roofline, and an FP64 certificate of the energies: the residual
+    r = H psi - theta psi recomputed with the float64 product, which bounds
+    |theta - E0| by |r| (Weinstein) for every member."""
+    from workloads import lattice_models as lm
+    from workloads.superblock import seeded_normal
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    dm = binding.GpuDmrg(lm.hubbard_ladder(1.0, 1.0, 8.0, density=56 / 64), 64, m=1000, tol=1e-10,
+                         prec="bf16x3", refine="newton_df64", mixed_tol=2e-4, seed=1)
+    steps = dm.infinite()
+    dmrg_s = time.perf_counter() - t0
+    sb1, _ = dm.last_superblock()
+    dm.close()
+    Us = 4.0 + 8.0 * np.arange(args.batch) / max(args.batch - 1, 1)
+    cp = np.zeros((args.batch, len(sb1.class_names)))
+    cp[:] = sb1.couplings[0]
+    cp[:, sb1.class_names.index("U")] = Us
+    sb = sb1.with_coeffs(sb1.coeffs_from_couplings(cp))
+    gs = binding.GpuSuperblock(sb, device=dev)
+    tune = gs.autotune(prec="bf16x3", reps=5)
+    flops = gs.info["flops_per_matvec"]
+    X0 = torch.from_numpy(np.stack([seeded_normal(5000 + b, sb.dim) for b in range(sb.batch)])).to(dev)
+    y = gs.empty()
+    prod = {}
+    for prec, reps in (("bf16x3", 20), ("df64", 3), ("fp64", 2)):
+        gs.apply_H(X0, y, prec=prec)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            gs.apply_H(X0, y, prec=prec)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        prod[prec] = a.elapsed_time(b) / reps
+
+    def step():
+        return gs.lanczos_ground(X0, tol=args.mixed_tol, max_iter=args.max_iter, prec="bf16x3",
+                                 refine="newton_df64", refine_tol=args.tol, graph_iters=8, grad=True)
+    for _ in range(max(3, args.warmup)):
+        e0, psi, infos, st, dE = step()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n_t = max(1, min(args.steps, 5))
+    ms_t, mv = 0.0, 0
+    for k in range(n_t):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e0, psi, infos, st, dE = step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_t += a.elapsed_time(b)
+        mv += max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
+    ms_step = ms_t / n_t
+    # float64 certificate of the returned eigenpairs
+    hp = gs.apply_H(psi, prec="fp64")
+    nrm = psi.norm(dim=1)
+    theta = (psi * hp).sum(dim=1) / nrm ** 2
+    res = (hp - theta[:, None] * psi).norm(dim=1) / nrm
+    e0 = np.asarray(e0, dtype=np.float64)
+    th = theta.cpu().numpy()
+    rel = (res.cpu().numpy() / np.abs(th))
+    pk = peaks["bf16_tflops"] / 3.0
+    a_t = flops / (prod["bf16x3"] / 1e3) / 1e12
+    pkdf = FP32_OPS_PER_CLK / DF_OPS_PER_FMA * 2 * sm_mhz * 1e6 / 1e12
+    pk64 = FP64_FMA_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
+    mixed_products = n_t and max(i["mixed_matvecs"] for i in infos)
+    return {
+        "workload": "hubbard_ladder_2x32_m1000_dmrg_U4-12_batch16",
+        "source": "device DMRG, infinite algorithm to L = 64 at m = 1000 (the last step's superblock)",
+        "D": sb.dim, "sectors": sb.n_sectors, "pairs": len(sb.pairs), "max_sector": int(max(sb.r.max(), sb.c.max())),
+        "flops_per_matvec": flops,
+        "dmrg": {"s": dmrg_s, "steps": len(steps), "energy_L64_U8": steps[-1]["energy"],
+                 "truncation_s": sum(x["ms_truncate"] for x in steps) / 1e3,
+                 "superblock_s": sum(x["ms_superblock"] for x in steps) / 1e3,
+                 "solve_s": sum(x["ms_solve"] for x in steps) / 1e3,
+                 "eps_last": steps[-1]["eps_S"], "status": max(x["status"] for x in steps)},
+        "autotune": tune,
+        "matvec_ms": prod, "matvec_tflops": {p: flops / (v / 1e3) / 1e12 for p, v in prod.items()},
+        "speedup_bf16x3_vs_fp64_matvec": prod["fp64"] / prod["bf16x3"],
+        "step_ms": ms_step, "step_tflops": mv / n_t * flops / (ms_step / 1e3) / 1e12, "timed_steps": n_t,
+        "lanczos_iters": max(i["iters"] for i in infos), "mixed_products": mixed_products,
+        "fp64_class_products": max(i["fp64_matvecs"] for i in infos), "status": st,
+        "fp64_certificate": {"residual_rel_max": float(rel.max()),
+                             "weinstein_bound_dE0_rel_max": float(rel.max()),
+                             "theta_fp64_vs_e0_rel_max": float(np.max(np.abs(th - e0) / np.abs(th)))},
+        "roofline": {"bound": "tensor", "achieved": a_t, "peak": pk, "unit": "TFLOP/s", "frac": a_t / pk,
+                     "traffic": recorded_traffic("tensor_product_bf16x3_real"),
+                     "kernel": "tcgen05 product, bf16x3 (staging + 3 grouped launches per dmrg_apply_H)",
+                     "peak_source": f"{kind} bf16 peak / 3 (three bf16 MMAs per algorithmic product)"},
+        "df64_frac": flops / (prod["df64"] / 1e3) / 1e12 / pkdf,
+        "fp64_frac": flops / (prod["fp64"] / 1e3) / 1e12 / pk64,
+    }
 
 
 # ------------------------------------------------------------ reference arm
@@ -519,12 +622,17 @@ def main():
                     "speedup_mixed_vs_fp64_solve": t_f64 / ms_per_step}
     # local density of states from the refined ground states (paper: continued fractions)
     ldos = measure_ldos(binding, torch, ldos_inp, psi, np.asarray(e0h, dtype=np.float64), prec, dev, stream)
+    peaks, kind = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    real = None
+    if prec == "bf16x3" and not args.no_real:
+        del g
+        torch.cuda.empty_cache()
+        real = measure_real(binding, torch, args, dev, stream, peaks, kind, sm_mhz)
     # one full Gram-Schmidt pass reads the Krylov basis twice (dots, then update)
     for j in (20, 100):
         fixed_j[f"reorth_bytes_per_step_j{j}"] = 2 * (j + 1) * sb.batch * sb.dim * 8
 
-    peaks, kind = measured_peaks()
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_mixed = mv_count / args.steps - max(i["fp64_matvecs"] for i in infos) if prec != "fp64" else 0
     n_f64 = max(i["fp64_matvecs"] for i in infos) if prec != "fp64" else mv_count / args.steps
     kernels = {}
@@ -590,7 +698,7 @@ def main():
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
            "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
            "breakdown": dict(breakdown, energy_grad_ms=t_grad, residual_product_with_dots_ms=t_pdot),
-           "lanczos_fixed_j": fixed_j, "ldos": ldos, "accuracy": accuracy,
+           "lanczos_fixed_j": fixed_j, "ldos": ldos, "accuracy": accuracy, "real_superblock": real,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline_sample(sb)
