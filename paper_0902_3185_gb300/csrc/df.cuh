@@ -1,8 +1,9 @@
 // Double-float arithmetic on float32 pairs (hi + lo, about 48 significant
-// bits), shared by the double-float product and the Gram-Schmidt passes:
-// float64 inputs split into pairs with integer instructions, Dekker's product
-// with a fused multiply-add and Knuth's two-sum.  GB300 issues float64 at
-// 1/64 of its float32 rate, so these run on the float32 pipes.
+// bits) for the double-float product: float64 inputs split into pairs with
+// integer instructions, Dekker's product with a fused multiply-add and
+// Knuth's two-sum.  GB300 issues float64 at 1/64 of its float32 rate, so
+// these run on the float32 pipes; the integer split (about 28 instructions)
+// pays off only where a split value is reused, as in a product tile.
 #pragma once
 
 #include <cstdint>

@@ -552,20 +552,16 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   double* nB = sb->lz_npart + (size_t)B * nch;
   double* nC = sb->lz_npart + (size_t)2 * B * nch;
   const int ndot = lz_dot_nchunk(D);
-  // the full passes (B, C) in double-float arithmetic for mixed-precision
-  // solves (about 48 bits, HBM-bound), float64 for float64 solves; the
-  // three-term step (A) in float64 always
-  const bool df = prec != DMRG_FP64;
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st);
   lz_launch_reduce_rows(sb->lz_partial, hA, ctl, ndot, cap, B, 2, nullptr, st);
   // pass A's update runs inside pass B's dot sweep (norm partials per dot chunk)
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA, df);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA);
   lz_launch_reduce_rows(sb->lz_partial, hB, ctl, ndot, cap, B, 0, nullptr, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st, df);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st);
   lz_launch_dgks(nA, nB, sb->lz_gate, ctl, B, ndot, nch, st);
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st, nullptr, nullptr, df);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st);
   lz_launch_reduce_rows(sb->lz_partial, hC, ctl, ndot, cap, B, 0, sb->lz_gate, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st, df);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st);
   lz_launch_finalize_ab(sb->lz_h, nB, nC, sb->lz_gate, sb->lz_ab, ctl, B, cap, nch, st);
   lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, ctl, sb->lz_out + 4 * B, B, cap, D, st);  // tol at out[4B]
   lz_launch_next_vector(sb->lz_w, sb->lz_ab, sb->lz_V, sb->lz_vcur, ctl, D, B, cap, st);

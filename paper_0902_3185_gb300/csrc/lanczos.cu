@@ -26,7 +26,6 @@
 
 #include <cfloat>
 
-#include "df.cuh"
 #include "internal.h"
 #include "lanczos.h"
 
@@ -69,8 +68,7 @@ __device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j
 // w -= h_pre[j-1] v_{j-1} + h_pre[j] v_j, in that order) is applied first,
 // written back to w, and its per-chunk sum of squares stored in npart_pre:
 // one sweep instead of an update sweep followed by a dot sweep.
-template <bool DF>
-__global__ void __launch_bounds__(LZ_THREADS, DF ? 2 : 1)
+__global__ void __launch_bounds__(LZ_THREADS)
 k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restrict__ partial,
            const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk, int win,
            const int32_t* __restrict__ gate, const double* __restrict__ h_pre, double* __restrict__ npart_pre) {
@@ -79,8 +77,7 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double wv[LZ_DOT_EPT];  // w (float64 dots)
-  float2 wf[LZ_DOT_EPT];  // w split into double-float pairs (DF dots)
+  double wv[LZ_DOT_EPT];
   const int64_t base = (int64_t)chunk * LZ_DOT_CHUNK + threadIdx.x;
   // the pre-update's rows (j - 1 when it exists, then j) and coefficients
   const bool two = j >= 1;
@@ -102,8 +99,7 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
         nrm = fma(x, x, nrm);
       }
     }
-    if (DF) wf[e] = df_split(x);
-    else wv[e] = x;
+    wv[e] = x;
   }
   if (h_pre) {
 #pragma unroll
@@ -117,42 +113,21 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
     }
   }
   const bool full = base + (LZ_DOT_EPT - 1) * LZ_THREADS < D;
-  // DF (the mixed-precision solves): the dots in double-float arithmetic on
-  // the float32 pipes (w split once; each Krylov element split with integer
-  // instructions), about 48 significant bits: per element the work drops
-  // below the HBM time of its 8 bytes, where a float64 fused multiply-add (2
-  // per clock per SM) stays above it.  Otherwise (the float64 solves) float64.
   for (int i0 = first_row(j, win); i0 <= j; i0 += 8) {
     double p[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+      p[q] = 0.0;
       const int i = i0 + q;
-      if (DF) {
-        float ps = 0.0f, pc = 0.0f;
-        if (i <= j) {
-          const double* v = V + ((int64_t)i * batch + b) * D + base;
-          if (full) {
+      if (i <= j) {
+        const double* v = V + ((int64_t)i * batch + b) * D + base;
+        if (full) {
 #pragma unroll
-            for (int e = 0; e < LZ_DOT_EPT; ++e) df_fma(df_split(v[e * LZ_THREADS]), wf[e], ps, pc);
-          } else {
+          for (int e = 0; e < LZ_DOT_EPT; ++e) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
+        } else {
 #pragma unroll
-            for (int e = 0; e < LZ_DOT_EPT; ++e)
-              if (base + e * LZ_THREADS < D) df_fma(df_split(v[e * LZ_THREADS]), wf[e], ps, pc);
-          }
-        }
-        p[q] = df_value(ps, pc);
-      } else {
-        p[q] = 0.0;
-        if (i <= j) {
-          const double* v = V + ((int64_t)i * batch + b) * D + base;
-          if (full) {
-#pragma unroll
-            for (int e = 0; e < LZ_DOT_EPT; ++e) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < LZ_DOT_EPT; ++e)
-              if (base + e * LZ_THREADS < D) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
-          }
+          for (int e = 0; e < LZ_DOT_EPT; ++e)
+            if (base + e * LZ_THREADS < D) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
         }
       }
     }
@@ -227,38 +202,25 @@ k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h, const 
 
 // w[b] -= sum_{i0<=i<=j} V[i][b] h[b][i] (i0 = first_row(j, win)); with
 // norm_partial != NULL also the per-chunk sum of squares of the new w.
-template <bool DF>
 __global__ void __launch_bounds__(LZ_THREADS)
 k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* __restrict__ h,
             double* __restrict__ norm_partial, const int32_t* __restrict__ ctl, int64_t D, int batch,
             int cap, int nchunk, int win, const int32_t* __restrict__ gate) {
-  extern __shared__ double sh[];  // the coefficients: float64, or (DF) split into double-float pairs
-  float2* shf = reinterpret_cast<float2*>(sh);
+  extern __shared__ double sh[];
   __shared__ double red[LZ_THREADS / 32];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
   const int i0 = first_row(j, win);
-  for (int i = i0 + threadIdx.x; i <= j; i += blockDim.x) {
-    if (DF) shf[i] = df_split(h[(int64_t)b * cap + i]);
-    else sh[i] = h[(int64_t)b * cap + i];
-  }
+  for (int i = i0 + threadIdx.x; i <= j; i += blockDim.x) sh[i] = h[(int64_t)b * cap + i];
   __syncthreads();
   double nrm = 0.0;
-  // DF: sum_i V[i] h[i] per element in double-float arithmetic (float32
-  // pipes), subtracted from w in float64; otherwise float64 throughout
 #pragma unroll
   for (int e = 0; e < LZ_EPT; ++e) {
     const int64_t d = (int64_t)chunk * LZ_CHUNK + e * LZ_THREADS + threadIdx.x;
     if (d >= D) continue;
     double acc = w[(int64_t)b * D + d];
-    if (DF) {
-      float ss = 0.0f, sc = 0.0f;
-      for (int i = i0; i <= j; ++i) df_fma(df_split(V[((int64_t)i * batch + b) * D + d]), shf[i], ss, sc);
-      acc -= df_value(ss, sc);
-    } else {
-      for (int i = i0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
-    }
+    for (int i = i0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
     w[(int64_t)b * D + d] = acc;
     nrm = fma(acc, acc, nrm);
   }
@@ -732,14 +694,9 @@ void lz_launch_cfrac(const double* norm2, const double* alpha, const double* bet
 }
 void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int win, const int32_t* gate, cudaStream_t st, const double* h_pre,
-                        double* npart_pre, bool df) {
-  const dim3 g(lz_dot_nchunk(D), batch);
-  if (df)
-    k_multidot<true><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D), win, gate, h_pre,
-                                               npart_pre);
-  else
-    k_multidot<false><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D), win, gate,
-                                                h_pre, npart_pre);
+                        double* npart_pre) {
+  k_multidot<<<dim3(lz_dot_nchunk(D), batch), LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap,
+                                                                  lz_dot_nchunk(D), win, gate, h_pre, npart_pre);
 }
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st) {
@@ -748,13 +705,9 @@ void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl,
 }
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
                          const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, int win,
-                         const int32_t* gate, cudaStream_t st, bool df) {
-  if (df)
-    k_multiaxpy<true><<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl, D,
-                                                                                   batch, cap, nchunk, win, gate);
-  else
-    k_multiaxpy<false><<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl,
-                                                                                    D, batch, cap, nchunk, win, gate);
+                         const int32_t* gate, cudaStream_t st) {
+  k_multiaxpy<<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl, D,
+                                                                            batch, cap, nchunk, win, gate);
 }
 void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate, const int32_t* ctl, int batch,
                     int nchunk_a, int nchunk, cudaStream_t st) {

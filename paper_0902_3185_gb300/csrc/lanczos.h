@@ -34,17 +34,15 @@ inline int lz_dot_nchunk(int64_t D) { return (int)((D + LZ_DOT_CHUNK - 1) / LZ_D
 // Gram-Schmidt passes over the Krylov rows first_row(j, win)..j (win = 0: all
 // rows); members with gate != NULL and gate[b] == 0 are skipped.
 // h_pre / npart_pre: apply the three-term update with coefficients h_pre
-// first (written back to w, per-chunk norm partials into npart_pre).
-// df: dots (and, in lz_launch_multiaxpy, the update sums) in double-float
-// arithmetic on the float32 pipes (mixed-precision solves) instead of float64
+// first (written back to w, per-chunk norm partials into npart_pre)
 void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int win, const int32_t* gate, cudaStream_t st,
-                        const double* h_pre = nullptr, double* npart_pre = nullptr, bool df = false);
+                        const double* h_pre = nullptr, double* npart_pre = nullptr);
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st);
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
                          const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, int win,
-                         const int32_t* gate, cudaStream_t st, bool df = false);
+                         const int32_t* gate, cudaStream_t st);
 void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate, const int32_t* ctl, int batch,
                     int nchunk_a, int nchunk, cudaStream_t st);
 void lz_launch_finalize_ab(const double* h, const double* npart_b, const double* npart_c, const int32_t* gate,
