@@ -1,28 +1,30 @@
 """Benchmark of the superblock H*psi + Lanczos hot path on GB300.
 
-Workload (default): the 2 x 32 Hubbard ladder at m = 1000 kept states,
-N_up = N_dn = 28 (1/8 hole doping), 16 superblocks with U = 4 .. 12 that
-share every operator block (isometry-grown, seeded; see workloads/grown.py).
+Workload (default, config 5): the 2 x 32 Hubbard ladder at m = 1000 kept
+states, N_up = N_dn = 28 (1/8 hole doping).  The superblock is built by the
+device DMRG driver (infinite algorithm to L = 64 at U = 8, untimed setup):
+the last step's superblock, in its density-matrix basis, carries 16 members
+with U = 4 .. 12 that share every operator block.
 
 One timed step = the whole hot path for the 16-member batch: a ground-state
 solve (dmrg_lanczos_ground: products, float64 Lanczos scalars, full
 reorthogonalisation, tridiagonal test, CUDA graphs; mixed precision followed
-by float64 refinement when a tensor-core precision is selected) with the
-Hellmann-Feynman gradient of the refined state (dmrg_lanczos_ground_grad: the
-refinement's float64 residual products after the first give H psi and the
-per-term dots in one pass).  value = algorithmic H*psi
-flops executed in the step / step time.
+by double-float Newton refinement) with the Hellmann-Feynman gradient of the
+refined state (dmrg_lanczos_ground_grad).  value = algorithmic H*psi flops
+executed in the step / step time.
 
-Outside the timed step, `ldos` times the local density of states of the
-last system site from the refined ground states (transition products,
-Lanczos coefficients on the N -/+ 1 superblocks, continued fractions).
+Outside the timed step: the accuracy leg (a float64 residual certificate of
+every returned state, and the float64 GPU solve of the same batch),
+kernel-only product times, Lanczos rates at fixed Krylov length, and the
+isometry-grown stand-in of config 5 (the earlier headline workload) with its
+own accuracy leg and the local density of states.
 
 roofline: the product kernel with the largest event-timed share of the step
-(tensor-core, float64, or float64 with the per-term dots), its algorithmic
-flops per product / its event-timed duration, against its peak;
-roofline_kernels lists all three.  traffic: DRAM bytes per
-product from the committed ncu record (profiles/traffic.json), reported only
-while the kernel sources still hash to the recorded value.
+(tensor-core, double-float or float64), its algorithmic flops per product /
+its event-timed duration, against its peak; roofline_kernels lists them.
+traffic: DRAM bytes per product from the committed ncu record
+(profiles/traffic.json), reported only while the kernel sources still hash to
+the recorded value.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own batch (weak scaling, no collective on
@@ -46,7 +48,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("H·ψ TFLOP/s & Lanczos steps/s at m=1000, mixed vs FP64 same GPU, "
           "|ΔE0|≤1e-8")
-WORKLOAD = "hubbard_ladder_2x32_m1000_U4-12_batch16"
+WORKLOAD = "hubbard_ladder_2x32_m1000_dmrg_U4-12_batch16"
+GROWN_WORKLOAD = "hubbard_ladder_2x32_m1000_isogrown_U4-12_batch16"
 
 
 def parse():
@@ -61,7 +64,9 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--mixed-tol", type=float, default=2e-4)
     ap.add_argument("--refine", default="newton_df64", choices=["newton", "newton_df64", "lanczos", "none"])
-    ap.add_argument("--no-real", action="store_true", help="skip the real DMRG superblock variant")
+    ap.add_argument("--no-grown", action="store_true", help="skip the isometry-grown stand-in leg")
+    ap.add_argument("--no-fp64-solve", action="store_true",
+                    help="skip the float64 solve of the accuracy leg (about 90 s on the headline superblock)")
     return ap.parse_args()
 
 
@@ -235,108 +240,6 @@ def measure_ldos(binding, torch, inp, psi, e0, prec, dev, stream, n_coef=100, n_
             "min_coefficients": int(min(o[2].min() for o in out.values()))}
 
 
-def measure_real(binding, torch, args, dev, stream, peaks, kind, sm_mhz):
-    """The same step on a real DMRG superblock: the device DMRG driver runs the
-    infinite algorithm on the 2 x 32 Hubbard ladder (U = 8, N_up = N_dn = 28,
-    m = 1000; BF16x3 Lanczos refined to 1e-10 with double-float residuals in
-    every step), and the last step's superblock (density-matrix basis, real
-    sector sizes) carries the 16 members U = 4 .. 12.  Reported: the driver's
-    time, the product in each precision, the timed step (mixed solve + gradient)
-    with its roofline, and an FP64 certificate of the energies: the residual
-    r = H psi - theta psi recomputed with the float64 product, which bounds
-    |theta - E0| by |r| (Weinstein) for every member."""
-    from workloads import lattice_models as lm
-    from workloads.superblock import seeded_normal
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    dm = binding.GpuDmrg(lm.hubbard_ladder(1.0, 1.0, 8.0, density=56 / 64), 64, m=1000, tol=1e-10,
-                         prec="bf16x3", refine="newton_df64", mixed_tol=2e-4, seed=1)
-    steps = dm.infinite()
-    dmrg_s = time.perf_counter() - t0
-    sb1, _ = dm.last_superblock()
-    dm.close()
-    Us = 4.0 + 8.0 * np.arange(args.batch) / max(args.batch - 1, 1)
-    cp = np.zeros((args.batch, len(sb1.class_names)))
-    cp[:] = sb1.couplings[0]
-    cp[:, sb1.class_names.index("U")] = Us
-    sb = sb1.with_coeffs(sb1.coeffs_from_couplings(cp))
-    gs = binding.GpuSuperblock(sb, device=dev)
-    tune = gs.autotune(prec="bf16x3", reps=5)
-    flops = gs.info["flops_per_matvec"]
-    X0 = torch.from_numpy(np.stack([seeded_normal(5000 + b, sb.dim) for b in range(sb.batch)])).to(dev)
-    y = gs.empty()
-    prod = {}
-    for prec, reps in (("bf16x3", 20), ("df64", 3), ("fp64", 2)):
-        gs.apply_H(X0, y, prec=prec)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            gs.apply_H(X0, y, prec=prec)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        prod[prec] = a.elapsed_time(b) / reps
-
-    def step():
-        return gs.lanczos_ground(X0, tol=args.mixed_tol, max_iter=args.max_iter, prec="bf16x3",
-                                 refine="newton_df64", refine_tol=args.tol, graph_iters=8, grad=True)
-    for _ in range(max(3, args.warmup)):
-        e0, psi, infos, st, dE = step()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    n_t = max(1, min(args.steps, 5))
-    ms_t, mv = 0.0, 0
-    for k in range(n_t):
-        flush.fill_(float(k))
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e0, psi, infos, st, dE = step()
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        ms_t += a.elapsed_time(b)
-        mv += max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
-    ms_step = ms_t / n_t
-    # float64 certificate of the returned eigenpairs
-    hp = gs.apply_H(psi, prec="fp64")
-    nrm = psi.norm(dim=1)
-    theta = (psi * hp).sum(dim=1) / nrm ** 2
-    res = (hp - theta[:, None] * psi).norm(dim=1) / nrm
-    e0 = np.asarray(e0, dtype=np.float64)
-    th = theta.cpu().numpy()
-    rel = (res.cpu().numpy() / np.abs(th))
-    pk = peaks["bf16_tflops"] / 3.0
-    a_t = flops / (prod["bf16x3"] / 1e3) / 1e12
-    pkdf = FP32_OPS_PER_CLK / DF_OPS_PER_FMA * 2 * sm_mhz * 1e6 / 1e12
-    pk64 = FP64_FMA_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
-    mixed_products = n_t and max(i["mixed_matvecs"] for i in infos)
-    return {
-        "workload": "hubbard_ladder_2x32_m1000_dmrg_U4-12_batch16",
-        "source": "device DMRG, infinite algorithm to L = 64 at m = 1000 (the last step's superblock)",
-        "D": sb.dim, "sectors": sb.n_sectors, "pairs": len(sb.pairs), "max_sector": int(max(sb.r.max(), sb.c.max())),
-        "flops_per_matvec": flops,
-        "dmrg": {"s": dmrg_s, "steps": len(steps), "energy_L64_U8": steps[-1]["energy"],
-                 "truncation_s": sum(x["ms_truncate"] for x in steps) / 1e3,
-                 "superblock_s": sum(x["ms_superblock"] for x in steps) / 1e3,
-                 "solve_s": sum(x["ms_solve"] for x in steps) / 1e3,
-                 "eps_last": steps[-1]["eps_S"], "status": max(x["status"] for x in steps)},
-        "autotune": tune,
-        "matvec_ms": prod, "matvec_tflops": {p: flops / (v / 1e3) / 1e12 for p, v in prod.items()},
-        "speedup_bf16x3_vs_fp64_matvec": prod["fp64"] / prod["bf16x3"],
-        "step_ms": ms_step, "step_tflops": mv / n_t * flops / (ms_step / 1e3) / 1e12, "timed_steps": n_t,
-        "lanczos_iters": max(i["iters"] for i in infos), "mixed_products": mixed_products,
-        "fp64_class_products": max(i["fp64_matvecs"] for i in infos), "status": st,
-        "fp64_certificate": {"residual_rel_max": float(rel.max()),
-                             "weinstein_bound_dE0_rel_max": float(rel.max()),
-                             "theta_fp64_vs_e0_rel_max": float(np.max(np.abs(th - e0) / np.abs(th)))},
-        "roofline": {"bound": "tensor", "achieved": a_t, "peak": pk, "unit": "TFLOP/s", "frac": a_t / pk,
-                     "traffic": recorded_traffic("tensor_product_bf16x3_real"),
-                     "kernel": "tcgen05 product, bf16x3 (staging + 3 grouped launches per dmrg_apply_H)",
-                     "peak_source": f"{kind} bf16 peak / 3 (three bf16 MMAs per algorithmic product)"},
-        "df64_frac": flops / (prod["df64"] / 1e3) / 1e12 / pkdf,
-        "fp64_frac": flops / (prod["fp64"] / 1e3) / 1e12 / pk64,
-    }
-
-
 # ------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, on the host cores: a bounded sample of the
@@ -373,10 +276,13 @@ def run_reference(args, rank, world):
             "steps": len(times), "warmup": warm, "ms_per_step": 1000 * sec / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD,
+            "config": {"workload": GROWN_WORKLOAD,
                        "sample": "each step = one blocked float64 product (the solve's dominant operation) on "
                                  "each of 2 of the 16 members; TFLOP/s of those products (not a whole solve, "
-                                 "which takes the oracle minutes per member)"},
+                                 "which takes the oracle minutes per member)",
+                       "note": "the headline superblock comes from the device DMRG driver, which this arm does "
+                               "not run; the oracle's product is timed on the isometry-grown superblock of the "
+                               "same lattice, m and members (D = 165,055 per member instead of 886,884)"},
             "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n} blocked float64 products of single members (NumPy, default BLAS "
                                        f"threading; blocks this small mostly run on one thread), D={sb.dim}"},
@@ -432,6 +338,134 @@ def cpu_baseline_sample(sb):
 
 
 # ------------------------------------------------------------------- ours
+def build_real(binding, batch, seed):
+    """Config 5 from the device DMRG driver: the infinite algorithm on the
+    2 x 32 Hubbard ladder (t_leg = t_rung = 1, U = 8, N_up = N_dn = 28,
+    m = 1000; BF16x3 Lanczos refined to 1e-10 in every step); the last step's
+    superblock (density-matrix basis) carries `batch` members U = 4 .. 12."""
+    from workloads import lattice_models as lm
+    t0 = time.perf_counter()
+    dm = binding.GpuDmrg(lm.hubbard_ladder(1.0, 1.0, 8.0, density=56 / 64), 64, m=1000, tol=1e-10,
+                         prec="bf16x3", refine="newton_df64", mixed_tol=2e-4, seed=1 + seed)
+    steps = dm.infinite()
+    sb1, _ = dm.last_superblock()
+    dm.close()
+    secs = time.perf_counter() - t0
+    Us = 4.0 + 8.0 * np.arange(batch) / max(batch - 1, 1)
+    cp = np.zeros((batch, len(sb1.class_names)))
+    cp[:] = sb1.couplings[0]
+    cp[:, sb1.class_names.index("U")] = Us
+    sb = sb1.with_coeffs(sb1.coeffs_from_couplings(cp))
+    stats = {"driver": "device DMRG (dmrg_sys_infinite), 31 steps to L = 64, m = 1000, BF16x3 + double-float "
+                       "refinement to 1e-10 per step", "s": secs, "steps": len(steps),
+             "energy_L64_U8": steps[-1]["energy"], "eps_last": steps[-1]["eps_S"],
+             "truncation_s": sum(x["ms_truncate"] for x in steps) / 1e3,
+             "superblock_s": sum(x["ms_superblock"] for x in steps) / 1e3,
+             "solve_s": sum(x["ms_solve"] for x in steps) / 1e3,
+             "status": max(x["status"] for x in steps)}
+    return sb, stats
+
+
+def event_ms(torch, stream, dev, fn, reps=1):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        r = fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / reps, r
+
+
+def product_ms(torch, g, x, stream, dev, prec, reps):
+    y = g.empty()
+    g.apply_H(x, y, prec=prec)
+    return event_ms(torch, stream, dev, lambda: g.apply_H(x, y, prec=prec), reps)[0]
+
+
+def dpsi_max(torch, p, q):
+    p = p / p.norm(dim=1, keepdim=True)
+    q = q / q.norm(dim=1, keepdim=True)
+    return float(torch.minimum((p - q).norm(dim=1), (p + q).norm(dim=1)).max())
+
+
+def measure_grown(binding, torch, args, prec, dev, stream, rank):
+    """The isometry-grown stand-in of config 5 (the workload of the earlier
+    headline): the same step, its float64 solve of the same batch, and the
+    local density of states of the last system site."""
+    from workloads.grown import ladder_m1000_ldos
+    from workloads.superblock import seeded_normal
+    inp = ladder_m1000_ldos(batch=args.batch, seed=rank)
+    sb = inp["N"]
+    g = binding.GpuSuperblock(sb, device=dev)
+    tune = g.autotune(prec=prec, reps=5)
+    flops = g.info["flops_per_matvec"]
+    x0 = torch.from_numpy(np.stack([seeded_normal(1000 * rank + b, sb.dim) for b in range(sb.batch)])).to(dev)
+
+    def step():
+        return g.lanczos_ground(x0, tol=args.mixed_tol, max_iter=args.max_iter, prec=prec, refine=args.refine,
+                                refine_tol=args.tol, graph_iters=8, grad=True)
+    for _ in range(3):
+        step()
+    n_t = 5
+    ms, (e0, psi, infos, st, dE) = event_ms(torch, stream, dev, step, n_t)
+    mv = max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
+    t64, (e64, p64, i64, s64, dE64) = event_ms(torch, stream, dev, lambda: g.lanczos_ground(
+        x0, tol=args.tol, max_iter=max(600, args.max_iter), prec="fp64", refine="none", graph_iters=8, grad=True))
+    e0, e64 = np.asarray(e0, dtype=np.float64), np.asarray(e64, dtype=np.float64)
+    mv_ms = product_ms(torch, g, x0, stream, dev, prec, 20)
+    ldos = measure_ldos(binding, torch, inp, psi, e0, prec, dev, stream)
+    out = {"workload": "hubbard_ladder_2x32_m1000_isogrown_U4-12_batch16",
+           "source": "isometry-grown superblock (random q-preserving isometries beyond m; workloads/grown.py)",
+           "D": sb.dim, "sectors": sb.n_sectors, "pairs": len(sb.pairs), "autotune": tune,
+           "step_ms": ms, "step_tflops": mv * flops / (ms / 1e3) / 1e12, "status": st,
+           "lanczos_iters": max(i["iters"] for i in infos),
+           "matvec_ms": mv_ms, "matvec_tflops": flops / (mv_ms / 1e3) / 1e12,
+           "accuracy": {"reference": f"float64 GPU solve of the same members (tol {args.tol:g}), status {s64}",
+                        "dE0_rel_max": float(np.max(np.abs(e0 - e64) / np.abs(e64))),
+                        "dpsi_max": dpsi_max(torch, psi, p64), "fp64_solve_ms": t64,
+                        "fp64_solve_iters": max(i["iters"] for i in i64),
+                        "speedup_mixed_vs_fp64_solve": t64 / ms},
+           "ldos": ldos}
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
+_ONE_THREAD_REAL = r"""
+import sys, time
+sys.path.insert(0, sys.argv[1])
+import bench
+from workloads.superblock import Superblock
+sb = Superblock.load(sys.argv[2])
+n, sec = bench._oracle_products(sb, float(sys.argv[3]), int(sys.argv[4]))
+print(n, sec)
+"""
+
+
+def cpu_baseline_real(sb):
+    """The oracle's blocked float64 product on the headline superblock (saved
+    to a temporary npz for a child process whose BLAS threads are pinned to 1
+    before NumPy loads), and in this process with NumPy's default threading."""
+    import tempfile
+    from oracle import superblock as osb
+    flops = osb.matvec_flops(sb)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sb.npz")
+        sb.save(path)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", _ONE_THREAD_REAL, ROOT, path, "10.0", "50"],
+                           env=env, capture_output=True, text=True, timeout=900)
+        n1, s1 = r.stdout.split()[-2:]
+    n1, s1 = int(n1), float(s1)
+    n, sec = _oracle_products(sb, 5.0, 50)
+    return {"value": n1 * flops / s1 / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n1} blocked float64 products (one member each, NumPy, one thread) of the headline "
+                      f"superblock, {s1:.1f} s",
+            "value_all_cores": n * flops / sec / 1e12, "host_cores": len(os.sched_getaffinity(0)),
+            "sample_all_cores": f"{n} products with NumPy's default BLAS threading, {sec:.1f} s"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -445,10 +479,11 @@ def main():
     dev = torch.device("cuda", local)
     from paper_0902_3185_gb300 import binding
     from workloads.superblock import seeded_normal
+    stream = torch.cuda.current_stream(dev)
+    peaks, kind = measured_peaks()
 
-    from workloads.grown import ladder_m1000_ldos
-    ldos_inp = ladder_m1000_ldos(batch=args.batch, seed=rank)  # the bench superblock and its N -/+ 1 partners
-    sb = ldos_inp["N"]
+    # config 5 from the device DMRG driver (setup, outside the timed region)
+    sb, dmrg_stats = build_real(binding, args.batch, rank)
     g = binding.GpuSuperblock(sb, device=dev)
     prec = args.prec
     if prec == "auto":
@@ -458,17 +493,14 @@ def main():
             prec = "bf16x3"
         except binding.DmrgError:
             pass
-    tune = None
-    if prec != "fp64":  # pick the tensor-core tiling for this superblock (outside the timed region)
-        tune = g.autotune(prec=prec, reps=5)
+    tune = g.autotune(prec=prec, reps=5) if prec != "fp64" else None
     flops_mv = g.info["flops_per_matvec"]
-    X0 = np.stack([seeded_normal(1000 * rank + b, sb.dim) for b in range(sb.batch)])
+    X0 = np.stack([seeded_normal(1000 * rank + 5000 + b, sb.dim) for b in range(sb.batch)])
     x0 = torch.from_numpy(X0).to(dev)
-    stream = torch.cuda.current_stream(dev)
 
     def step(x):
         # ground state and its Hellmann-Feynman gradient (with the Newton
-        # refinement the gradient comes out of its last float64 product)
+        # refinement the gradient comes out of its last residual product)
         e0, psi, infos, st, dEdc = g.lanczos_ground(x, tol=args.tol if prec == "fp64" else args.mixed_tol,
                                                     max_iter=args.max_iter, prec=prec, refine=args.refine,
                                                     refine_tol=args.tol, graph_iters=8, grad=True)
@@ -486,9 +518,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     ev = []
-    mv_count = 0
-    it_count = 0
-    launches = 0
+    mv_count = it_count = launches = 0
     for k in range(args.steps):
         flush.fill_(float(k))  # L2 flush between timed steps
         a = torch.cuda.Event(enable_timing=True)
@@ -508,56 +538,33 @@ def main():
     ms_per_step = ms / args.steps
     value = job_value(world, mv_count, flops_mv, ms)
     e_step, psi_step, dE_step = np.asarray(e0, dtype=np.float64), psi, dEdc
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
 
-    # where the step goes: the mixed Lanczos alone, then the refinement
     def timed(fn):
-        a_ = torch.cuda.Event(enable_timing=True)
-        b_ = torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        r_ = fn()
-        b_.record(stream)
-        torch.cuda.synchronize(dev)
-        return a_.elapsed_time(b_), r_
+        return event_ms(torch, stream, dev, fn)
+    # where the step goes: the mixed Lanczos alone, then with the refinement
     t_lz, (_, _, info_lz, _) = timed(lambda: g.lanczos_ground(
         x0, tol=args.tol if prec == "fp64" else args.mixed_tol, max_iter=args.max_iter, prec=prec,
         refine="none", graph_iters=8))
     t_full, (_, _, info_full, _) = timed(lambda: g.lanczos_ground(
         x0, tol=args.tol if prec == "fp64" else args.mixed_tol, max_iter=args.max_iter, prec=prec,
         refine=args.refine, refine_tol=args.tol, graph_iters=8))
-    # the same Lanczos iteration with float64 products (20 iterations, no early stop)
-    n64 = 20
-    t_64, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=n64, prec="fp64", refine="none",
-                                             graph_iters=10))
     lz_iters = max(i["iters"] for i in info_lz)
     breakdown = {"lanczos_ms": t_lz, "refine_ms": t_full - t_lz, "solve_status": step.status,
                  "mixed_lanczos_steps_per_s": lz_iters / (t_lz / 1e3),
-                 "fp64_lanczos_steps_per_s_first20": n64 / (t_64 / 1e3),
                  "lanczos_iters": max(i["iters"] for i in info_full),
                  "fp64_products": max(i["fp64_matvecs"] for i in info_full),
                  "mixed_products": max(i["mixed_matvecs"] for i in info_full),
                  "residual_max": max(i["residual"] for i in info_full)}
 
     # kernel-only product timing (events on the launching stream)
-    y = g.empty()
-    reps = 20
-    for _ in range(3):
-        g.apply_H(x0, y, prec=prec)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
-        g.apply_H(x0, y, prec=prec)
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    mv_ms = a.elapsed_time(b) / reps
-    mv64_ms = mv_ms
-    if prec != "fp64":
-        a.record(stream)
-        for _ in range(3):
-            g.apply_H(x0, y, prec="fp64")
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        mv64_ms = a.elapsed_time(b) / 3
+    mv_ms = product_ms(torch, g, x0, stream, dev, prec, 20)
+    mv64_ms = product_ms(torch, g, x0, stream, dev, "fp64", 2) if prec != "fp64" else mv_ms
+    df = prec != "fp64" and args.refine == "newton_df64"
+    rprec = "df64" if df else "fp64"  # arithmetic of the refinement's residual products
+    mvr_ms = product_ms(torch, g, x0, stream, dev, "df64", 3) if df else mv64_ms
+    t_pdot, _ = timed(lambda: g.apply_H_term_dots(x0, prec=rprec))
+    t_grad, _ = timed(lambda: g.energy_grad(psi))
 
     # end to end through the public API with host buffers
     xh = torch.from_numpy(X0).pin_memory()
@@ -566,72 +573,52 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         xd = xh.to(dev, non_blocking=True)
-        e0h, psi, infos, dEdc = step(xd)
-        ph.copy_(psi, non_blocking=True)
-        dh = dEdc.cpu()
+        e0h, psi_e, infos_e, dEdc_e = step(xd)
+        ph.copy_(psi_e, non_blocking=True)
+        dh = dEdc_e.cpu()
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e = {"value": world * mv_count / args.steps * flops_mv / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(X0.nbytes), "d2h_bytes_per_step": int(X0.nbytes + dh.numel() * 8)}
 
-    # Hellmann-Feynman gradient alone (float64 per-term dots), and the float64
-    # product that also gives the per-term dots
-    t_grad, _ = timed(lambda: g.energy_grad(psi))
-    df = prec != "fp64" and args.refine == "newton_df64"
-    rprec = "df64" if df else "fp64"  # arithmetic of the refinement's residual products
-    t_pdot, _ = timed(lambda: g.apply_H_term_dots(x0, prec=rprec))
-    mvr_ms = mv64_ms
-    if df:
-        for _ in range(2):
-            g.apply_H(x0, y, prec="df64")
-        a.record(stream)
-        for _ in range(5):
-            g.apply_H(x0, y, prec="df64")
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        mvr_ms = a.elapsed_time(b) / 5
     # Lanczos iteration rate at fixed Krylov length j (no early stop)
     fixed_j = {}
-    for pj in ([prec, "fp64"] if prec != "fp64" else ["fp64"]):
-        for j in (20, 100):
+    for pj, js in ([(prec, (20, 100)), ("fp64", (20,))] if prec != "fp64" else [("fp64", (20,))]):
+        for j in js:
             t_j, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=j, prec=pj, refine="none",
                                                     graph_iters=10))
             fixed_j[f"{pj}_j{j}_steps_per_s"] = j / (t_j / 1e3)
-    # accuracy leg: the same batch solved with float64 products (plain float64
-    # GPU path: float64 Lanczos to the same tolerance, gradient after the
-    # solve), against the timed step's mixed + refined result
+    for j in (20, 100):  # one full Gram-Schmidt pass reads the Krylov basis twice (dots, then update)
+        fixed_j[f"reorth_bytes_per_step_j{j}"] = 2 * (j + 1) * sb.batch * sb.dim * 8
+
+    # accuracy leg: a float64 certificate of every returned state (the
+    # residual recomputed with the float64 product bounds |theta - E0| by |r|,
+    # Weinstein) and the float64 GPU solve of the same batch from the same
+    # start vectors (float64 products and Lanczos to the same tolerance)
     accuracy = None
     if prec != "fp64":
-        t_f64, (e64, psi64, info64, st64, dE64) = timed(lambda: g.lanczos_ground(
-            x0, tol=args.tol, max_iter=max(600, args.max_iter), prec="fp64", refine="none", graph_iters=8,
-            grad=True))
-        e64 = np.asarray(e64, dtype=np.float64)
-        pm = psi_step / psi_step.norm(dim=1, keepdim=True)
-        p6 = psi64 / psi64.norm(dim=1, keepdim=True)
-        dpsi = torch.minimum((pm - p6).norm(dim=1), (pm + p6).norm(dim=1)).cpu().numpy()
-        dE_rel = np.abs(e_step - e64) / np.abs(e64)
-        dg = (dE_step - dE64).abs().max().item()
-        accuracy = {"reference": "float64 GPU solve of the same 16 members (float64 products and Lanczos, "
-                                 f"tol {args.tol:g}), status {st64}",
-                    "dE0_rel_max": float(dE_rel.max()), "dE0_rel_per_member": [float(v) for v in dE_rel],
-                    "dpsi_max": float(dpsi.max()), "dE_dc_max_abs_diff": float(dg),
-                    "meets_1e-8": bool(dE_rel.max() <= 1e-8),
-                    "fp64_solve_ms": t_f64, "fp64_solve_iters": max(i["iters"] for i in info64),
-                    "fp64_lanczos_steps_per_s": max(i["iters"] for i in info64) / (t_f64 / 1e3),
-                    "mixed_solve_ms": ms_per_step,
-                    "speedup_mixed_vs_fp64_solve": t_f64 / ms_per_step}
-    # local density of states from the refined ground states (paper: continued fractions)
-    ldos = measure_ldos(binding, torch, ldos_inp, psi, np.asarray(e0h, dtype=np.float64), prec, dev, stream)
-    peaks, kind = measured_peaks()
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    real = None
-    if prec == "bf16x3" and not args.no_real:
-        del g
-        torch.cuda.empty_cache()
-        real = measure_real(binding, torch, args, dev, stream, peaks, kind, sm_mhz)
-    # one full Gram-Schmidt pass reads the Krylov basis twice (dots, then update)
-    for j in (20, 100):
-        fixed_j[f"reorth_bytes_per_step_j{j}"] = 2 * (j + 1) * sb.batch * sb.dim * 8
+        hp = g.apply_H(psi_step, prec="fp64")
+        nrm = psi_step.norm(dim=1)
+        theta = ((psi_step * hp).sum(dim=1) / nrm ** 2)
+        res = ((hp - theta[:, None] * psi_step).norm(dim=1) / nrm).cpu().numpy()
+        th = theta.cpu().numpy()
+        accuracy = {"fp64_certificate": {"residual_rel_max": float(np.max(res / np.abs(th))),
+                                         "weinstein_bound_dE0_rel_max": float(np.max(res / np.abs(th))),
+                                         "theta_fp64_vs_e0_rel_max": float(np.max(np.abs(th - e_step) / np.abs(th)))}}
+        if not args.no_fp64_solve:
+            t_f64, (e64, psi64, info64, st64, dE64) = timed(lambda: g.lanczos_ground(
+                x0, tol=args.tol, max_iter=600, prec="fp64", refine="none", graph_iters=8, grad=True))
+            e64 = np.asarray(e64, dtype=np.float64)
+            dE_rel = np.abs(e_step - e64) / np.abs(e64)
+            accuracy.update({
+                "reference": "float64 GPU solve of the same 16 members from the same start vectors (float64 "
+                             f"products and Lanczos, tol {args.tol:g}, at most 600 iterations), status {st64}",
+                "dE0_rel_max": float(dE_rel.max()), "dE0_rel_per_member": [float(v) for v in dE_rel],
+                "dpsi_max": dpsi_max(torch, psi_step, psi64), "dE_dc_max_abs_diff": float((dE_step - dE64).abs().max()),
+                "meets_1e-8": bool(dE_rel.max() <= 1e-8),
+                "fp64_solve_ms": t_f64, "fp64_solve_iters": max(i["iters"] for i in info64),
+                "fp64_lanczos_steps_per_s": max(i["iters"] for i in info64) / (t_f64 / 1e3),
+                "mixed_solve_ms": ms_per_step, "speedup_mixed_vs_fp64_solve": t_f64 / ms_per_step})
 
     n_mixed = mv_count / args.steps - max(i["fp64_matvecs"] for i in infos) if prec != "fp64" else 0
     n_f64 = max(i["fp64_matvecs"] for i in infos) if prec != "fp64" else mv_count / args.steps
@@ -666,42 +653,46 @@ def main():
     a_r = flops_mv / (mvr_ms / 1e3) / 1e12
     kernels[f"{name_r}_product"] = {
         "bound": "alu", "achieved": a_r, "peak": pk_r, "unit": "TFLOP/s", "frac": a_r / pk_r,
-        "traffic": recorded_traffic(f"{name_r}_product"),
-        "kernel": kern_r, "peak_source": src_r,
+        "traffic": recorded_traffic(f"{name_r}_product"), "kernel": kern_r, "peak_source": src_r,
         "ms_per_step": (n_f64 - n_dots) * mvr_ms + (0.0 if newton else t_grad)}
     if n_dots:
         a_d = flops_mv / (t_pdot / 1e3) / 1e12
         kernels[f"{name_r}_product_with_dots"] = {
             "bound": "alu", "achieved": a_d, "peak": pk_r, "unit": "TFLOP/s", "frac": a_d / pk_r,
-            "traffic": None, "kernel": kern_d, "peak_source": src_r,
-            "ms_per_step": n_dots * t_pdot}
+            "traffic": None, "kernel": kern_d, "peak_source": src_r, "ms_per_step": n_dots * t_pdot}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     roof = dict(kernels[dom])
     roof["share_of_step"] = roof["ms_per_step"] / ms_per_step
     for k in kernels:
         kernels[k]["share_of_step"] = kernels[k]["ms_per_step"] / ms_per_step
-    achieved = flops_mv / (mv_ms / 1e3) / 1e12
+    sb_info = {"D": sb.dim, "sectors": sb.n_sectors, "pairs": len(sb.pairs),
+               "max_sector": int(max(sb.r.max(), sb.c.max()))}
+    del g, step
+    torch.cuda.empty_cache()
+
+    grown = measure_grown(binding, torch, args, prec, dev, stream, rank) if (prec != "fp64" and not args.no_grown) \
+        else None
 
     out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if prec == "fp64" else f"{prec}+f32acc (products), f64 (Lanczos)",
-           "data": "synthetic (seeded isometry-grown superblocks)",
-           "config": {"workload": WORKLOAD, "batch": sb.batch, "D": sb.dim, "m": 1000,
-                      "sectors": sb.n_sectors, "pairs": len(sb.pairs), "prec": prec, "tol": args.tol,
-                      "l2": "256 MB flush between timed steps; Krylov basis > L2",
-                      "autotune": tune},
+           "data": "synthetic (the model's own DMRG superblock from the device driver; no dataset)",
+           "config": dict({"workload": WORKLOAD, "batch": sb.batch, "m": 1000, "prec": prec, "tol": args.tol,
+                           "l2": "256 MB flush between timed steps; Krylov basis > L2", "autotune": tune},
+                          **sb_info),
+           "dmrg_setup": dmrg_stats,
            "lanczos_steps_per_s": world * it_count / (ms / 1e3),
-           "matvec_ms": mv_ms, "matvec_tflops": achieved, "matvec_fp64_ms": mv64_ms,
+           "matvec_ms": mv_ms, "matvec_tflops": flops_mv / (mv_ms / 1e3) / 1e12, "matvec_fp64_ms": mv64_ms,
            "matvec_fp64_tflops": flops_mv / (mv64_ms / 1e3) / 1e12,
            "residual_products": rprec, "matvec_residual_ms": mvr_ms,
            "speedup_mixed_vs_fp64_matvec": mv64_ms / mv_ms,
-           "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e0[:4]],
+           "iters_per_step": it_count / args.steps, "e0": [float(v) for v in e_step[:4]],
            "breakdown": dict(breakdown, energy_grad_ms=t_grad, residual_product_with_dots_ms=t_pdot),
-           "lanczos_fixed_j": fixed_j, "ldos": ldos, "accuracy": accuracy, "real_superblock": real,
+           "lanczos_fixed_j": fixed_j, "accuracy": accuracy, "isometry_grown": grown,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline_sample(sb)
+        out["cpu_baseline"] = cpu_baseline_real(sb)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
