@@ -628,7 +628,7 @@ def main():
         a_t = flops_mv / (mv_ms / 1e3) / 1e12
         kernels["tensor_product"] = {
             "bound": "tensor", "achieved": a_t, "peak": pk, "unit": "TFLOP/s", "frac": a_t / pk,
-            "traffic": recorded_traffic(f"tensor_product_{prec}"),
+            "traffic": recorded_traffic(f"tensor_product_{prec}_real"),
             "kernel": f"tcgen05 product, {prec} (staging + 3 grouped launches per dmrg_apply_H)",
             "peak_source": (f"{kind} bf16 peak / 3 (three bf16 MMAs per algorithmic product)" if prec == "bf16x3"
                             else f"{kind} bf16 peak x nominal 1100/2250"),
@@ -653,7 +653,7 @@ def main():
     a_r = flops_mv / (mvr_ms / 1e3) / 1e12
     kernels[f"{name_r}_product"] = {
         "bound": "alu", "achieved": a_r, "peak": pk_r, "unit": "TFLOP/s", "frac": a_r / pk_r,
-        "traffic": recorded_traffic(f"{name_r}_product"), "kernel": kern_r, "peak_source": src_r,
+        "traffic": recorded_traffic(f"{name_r}_product_real"), "kernel": kern_r, "peak_source": src_r,
         "ms_per_step": (n_f64 - n_dots) * mvr_ms + (0.0 if newton else t_grad)}
     if n_dots:
         a_d = flops_mv / (t_pdot / 1e3) / 1e12

@@ -2,6 +2,16 @@
 
 python -m paper_0902_3185_gb300.prof --workload ladder_m1000 --prec bf16x3 --reps 3
 
+The real config-5 superblock (the device DMRG's m = 1000 ladder, as bench.py
+builds it), saved once and then profiled without the DMRG run:
+
+python -m paper_0902_3185_gb300.prof --save-real /tmp/real.npz
+python -m paper_0902_3185_gb300.prof --workload npz:/tmp/real.npz --prec bf16x3 --reps 3 [--step]
+
+--step runs, after the products, one bench step (mixed solve with double-float
+refinement and the gradient) inside the NVTX range "step" (ncu --nvtx
+--nvtx-include "step/" captures exactly its launches).
+
 Recording the DRAM traffic of one product from an ncu capture of exactly its
 launches (``ncu -i <rep> --page raw --csv > raw.csv``) for bench.py:
 
@@ -24,6 +34,10 @@ if ROOT not in sys.path:
 TRAFFIC_SOURCES = {
     "tensor_product_bf16x3": ["paper_0902_3185_gb300/csrc/matvec_tc.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
     "tensor_product_tf32": ["paper_0902_3185_gb300/csrc/matvec_tc.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
+    "tensor_product_bf16x3_real": ["paper_0902_3185_gb300/csrc/matvec_tc.cu",
+                                   "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
+    "df64_product_real": ["paper_0902_3185_gb300/csrc/matvec_df.cu", "paper_0902_3185_gb300/csrc/df.cuh",
+                          "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
     "fp64_product": ["paper_0902_3185_gb300/csrc/matvec_f64.cu"],
     "df64_product": ["paper_0902_3185_gb300/csrc/matvec_df.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
 }
@@ -68,7 +82,9 @@ def main():
     if len(sys.argv) >= 4 and sys.argv[1] == "--record-traffic":
         return record_traffic(sys.argv[2], sys.argv[3], " ".join(sys.argv[4:]))
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="ladder_m1000", choices=["ladder_m1000", "random64"])
+    ap.add_argument("--workload", default="ladder_m1000", help="ladder_m1000, random64 or npz:<path>")
+    ap.add_argument("--save-real", default=None, help="build the real m = 1000 superblock and save it here")
+    ap.add_argument("--step", action="store_true", help="one bench step inside the NVTX range 'step'")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3", "df64"])
     ap.add_argument("--reps", type=int, default=3)
@@ -77,8 +93,17 @@ def main():
     a = ap.parse_args()
     import torch
     from paper_0902_3185_gb300.binding import GpuSuperblock
-    from workloads.superblock import seeded_normal
-    if a.workload == "ladder_m1000":
+    from workloads.superblock import Superblock, seeded_normal
+    if a.save_real:
+        import bench
+        from paper_0902_3185_gb300 import binding
+        sb, stats = bench.build_real(binding, a.batch, 0)
+        sb.save(a.save_real)
+        print(f"saved D={sb.dim} pairs={len(sb.pairs)} dmrg {stats['s']:.1f} s")
+        return
+    if a.workload.startswith("npz:"):
+        sb = Superblock.load(a.workload[4:])
+    elif a.workload == "ladder_m1000":
         from workloads.grown import ladder_m1000
         sb = ladder_m1000(batch=a.batch)
     else:
@@ -122,6 +147,17 @@ def main():
         print(json.dumps(rep))
     if a.lanczos_iters:
         g.lanczos_ground(x, tol=1e-300, max_iter=a.lanczos_iters, prec=a.prec, refine=False)
+    if a.step:
+        def step():
+            return g.lanczos_ground(x, tol=2e-4, max_iter=300, prec=a.prec, refine="newton_df64", refine_tol=1e-10,
+                                    graph_iters=8, grad=True)
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("step")
+        e0, _, infos, st, _ = step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(f"step status {st} launches {infos[0]['kernel_launches']} iters {infos[0]['iters']}")
     torch.cuda.synchronize()
     print(f"D={sb.dim} batch={sb.batch} pairs={len(sb.pairs)} flops/product={g.info['flops_per_matvec']:.4g}")
 
