@@ -537,6 +537,10 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   sb->lz_cap = cap;
 }
 
+// Krylov basis storage: float64 for float64 solves, double-float pairs (and
+// double-float Gram-Schmidt passes) for the mixed-precision solves
+bool lz_pair(int prec) { return prec != DMRG_FP64; }
+
 // one Lanczos iteration for every running member (all on stream st)
 void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   const int64_t D = sb->D;
@@ -552,19 +556,20 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   double* nB = sb->lz_npart + (size_t)B * nch;
   double* nC = sb->lz_npart + (size_t)2 * B * nch;
   const int ndot = lz_dot_nchunk(D);
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st);
+  const bool pair = lz_pair(prec);  // the Krylov basis as double-float pairs (mixed-precision solves)
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st, nullptr, nullptr, pair);
   lz_launch_reduce_rows(sb->lz_partial, hA, ctl, ndot, cap, B, 2, nullptr, st);
   // pass A's update runs inside pass B's dot sweep (norm partials per dot chunk)
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA, pair);
   lz_launch_reduce_rows(sb->lz_partial, hB, ctl, ndot, cap, B, 0, nullptr, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st, pair);
   lz_launch_dgks(nA, nB, sb->lz_gate, ctl, B, ndot, nch, st);
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st);
+  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st, nullptr, nullptr, pair);
   lz_launch_reduce_rows(sb->lz_partial, hC, ctl, ndot, cap, B, 0, sb->lz_gate, st);
-  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st);
+  lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st, pair);
   lz_launch_finalize_ab(sb->lz_h, nB, nC, sb->lz_gate, sb->lz_ab, ctl, B, cap, nch, st);
   lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, ctl, sb->lz_out + 4 * B, B, cap, D, st);  // tol at out[4B]
-  lz_launch_next_vector(sb->lz_w, sb->lz_ab, sb->lz_V, sb->lz_vcur, ctl, D, B, cap, st);
+  lz_launch_next_vector(sb->lz_w, sb->lz_ab, sb->lz_V, sb->lz_vcur, ctl, D, B, cap, st, pair);
   lz_launch_advance(ctl, B, st);
   CK(cudaGetLastError());
 }
@@ -627,7 +632,7 @@ LzRun lz_run(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double 
   double* nrm2 = sb->d_scratch;
   lz_launch_sumsq(psi0, part, D, B, nch, st);
   lz_launch_sum_chunks(part, nrm2, nch, B, st);
-  lz_launch_scale_unit(psi0, nrm2, sb->lz_V, sb->lz_vcur, D, B, st);
+  lz_launch_scale_unit(psi0, nrm2, sb->lz_V, sb->lz_vcur, D, B, st, lz_pair(prec));
   std::vector<int32_t> hc(LZ_CTL_MEMBER + 2 * B, 0);
   hc[LZ_CTL_MAXIT] = max_iter;
   hc[LZ_CTL_CHECK] = std::max(1, check_every);
@@ -650,7 +655,7 @@ LzRun lz_run(dmrg_sb* sb, const double* psi0, double* psi_out, int prec, double 
   // float64 eigenpairs of the members that stopped on the float32 test, side by side
   lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, sb->lz_ctl, sb->lz_out + 4 * B, B, cap, D, st, 1);
   CK(cudaMemcpyAsync(sb->h_ctl, sb->lz_ctl, sizeof(int32_t) * (LZ_CTL_MEMBER + 2 * B), cudaMemcpyDeviceToHost, st));
-  lz_launch_ritz(sb->lz_V, sb->lz_s, sb->lz_ctl, psi_out, D, B, cap, st);
+  lz_launch_ritz(sb->lz_V, sb->lz_s, sb->lz_ctl, psi_out, D, B, cap, st, lz_pair(prec));
   lz_launch_sumsq(psi_out, part, D, B, nch, st);
   lz_launch_sum_chunks(part, nrm2, nch, B, st);
   lz_launch_scale_unit(psi_out, nrm2, psi_out, nullptr, D, B, st);

@@ -10,6 +10,14 @@
 // are small, so pass B rarely shrinks w and pass C is rarely run; each full
 // pass costs 2 (j+1) D float64 FMAs per member.
 //
+// Storage of the Krylov basis: float64 for float64 solves; for the
+// mixed-precision solves each element is stored as a double-float pair
+// (hi, lo) of float32 values in the same 8 bytes (about 48 significant bits,
+// split once when the vector is written), and the full Gram-Schmidt passes
+// run in double-float arithmetic on the float32 pipes: reading a pair needs
+// no split, so a pass is bound by HBM instead of GB300's float64 issue rate
+// (2 fused multiply-adds per clock per SM, about 5 TB/s of 8-byte operands).
+//
 // Paper Sec. 3.3: each targeted symmetry block is diagonalised with Lanczos,
 // which needs only x += H y.  Everything here runs on the device for all batch
 // members at once and reads the iteration index from device memory, so one
@@ -26,6 +34,7 @@
 
 #include <cfloat>
 
+#include "df.cuh"
 #include "internal.h"
 #include "lanczos.h"
 
@@ -54,6 +63,16 @@ __device__ __forceinline__ bool member_skip(const int32_t* ctl, const int32_t* g
   return member_done(ctl, b) || (gate && gate[b] == 0);
 }
 
+// a Krylov element stored as a double-float pair
+__device__ __forceinline__ float2 ld_pair(const double* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st_pair(double* p, double v) { *reinterpret_cast<float2*>(p) = df_split(v); }
+__device__ __forceinline__ double pair_value(float2 a) { return tc::f2d_exact(a.x) + tc::f2d_exact(a.y); }
+// element d of Krylov row i in either storage
+template <bool PAIR>
+__device__ __forceinline__ double v_value(const double* p) {
+  return PAIR ? pair_value(ld_pair(p)) : *p;
+}
+
 // first Krylov row of a pass: the last `win` rows, or all (win = 0)
 __device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j - win + 1) : 0; }
 
@@ -68,7 +87,8 @@ __device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j
 // w -= h_pre[j-1] v_{j-1} + h_pre[j] v_j, in that order) is applied first,
 // written back to w, and its per-chunk sum of squares stored in npart_pre:
 // one sweep instead of an update sweep followed by a dot sweep.
-__global__ void __launch_bounds__(LZ_THREADS)
+template <bool PAIR>
+__global__ void __launch_bounds__(LZ_THREADS, PAIR ? 2 : 3)
 k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restrict__ partial,
            const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk, int win,
            const int32_t* __restrict__ gate, const double* __restrict__ h_pre, double* __restrict__ npart_pre) {
@@ -77,7 +97,8 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double wv[LZ_DOT_EPT];
+  double wv[LZ_DOT_EPT];  // w (float64 basis)
+  float2 wf[LZ_DOT_EPT];  // w split into double-float pairs (pair basis)
   const int64_t base = (int64_t)chunk * LZ_DOT_CHUNK + threadIdx.x;
   // the pre-update's rows (j - 1 when it exists, then j) and coefficients
   const bool two = j >= 1;
@@ -93,13 +114,14 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
     if (d < D) {
       x = w[(int64_t)b * D + d];
       if (h_pre) {
-        if (two) x = fma(-v0[d], h0, x);
-        x = fma(-v1[d], h1, x);
+        if (two) x = fma(-v_value<PAIR>(v0 + d), h0, x);
+        x = fma(-v_value<PAIR>(v1 + d), h1, x);
         w[(int64_t)b * D + d] = x;
         nrm = fma(x, x, nrm);
       }
     }
-    wv[e] = x;
+    if (PAIR) wf[e] = df_split(x);
+    else wv[e] = x;
   }
   if (h_pre) {
 #pragma unroll
@@ -117,17 +139,32 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
     double p[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      p[q] = 0.0;
       const int i = i0 + q;
-      if (i <= j) {
-        const double* v = V + ((int64_t)i * batch + b) * D + base;
-        if (full) {
+      const double* v = V + ((int64_t)i * batch + b) * D + base;
+      if (PAIR) {  // double-float dot of the stored pairs with the split w
+        float ps = 0.0f, pc = 0.0f;
+        if (i <= j) {
+          if (full) {
 #pragma unroll
-          for (int e = 0; e < LZ_DOT_EPT; ++e) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
-        } else {
+            for (int e = 0; e < LZ_DOT_EPT; ++e) df_fma(ld_pair(v + e * LZ_THREADS), wf[e], ps, pc);
+          } else {
 #pragma unroll
-          for (int e = 0; e < LZ_DOT_EPT; ++e)
-            if (base + e * LZ_THREADS < D) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
+            for (int e = 0; e < LZ_DOT_EPT; ++e)
+              if (base + e * LZ_THREADS < D) df_fma(ld_pair(v + e * LZ_THREADS), wf[e], ps, pc);
+          }
+        }
+        p[q] = df_value(ps, pc);
+      } else {
+        p[q] = 0.0;
+        if (i <= j) {
+          if (full) {
+#pragma unroll
+            for (int e = 0; e < LZ_DOT_EPT; ++e) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < LZ_DOT_EPT; ++e)
+              if (base + e * LZ_THREADS < D) p[q] = fma(v[e * LZ_THREADS], wv[e], p[q]);
+          }
         }
       }
     }
@@ -202,17 +239,22 @@ k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h, const 
 
 // w[b] -= sum_{i0<=i<=j} V[i][b] h[b][i] (i0 = first_row(j, win)); with
 // norm_partial != NULL also the per-chunk sum of squares of the new w.
+template <bool PAIR>
 __global__ void __launch_bounds__(LZ_THREADS)
 k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* __restrict__ h,
             double* __restrict__ norm_partial, const int32_t* __restrict__ ctl, int64_t D, int batch,
             int cap, int nchunk, int win, const int32_t* __restrict__ gate) {
-  extern __shared__ double sh[];
+  extern __shared__ double sh[];  // the coefficients (pair basis: split into double-float pairs)
+  float2* shf = reinterpret_cast<float2*>(sh);
   __shared__ double red[LZ_THREADS / 32];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
   const int i0 = first_row(j, win);
-  for (int i = i0 + threadIdx.x; i <= j; i += blockDim.x) sh[i] = h[(int64_t)b * cap + i];
+  for (int i = i0 + threadIdx.x; i <= j; i += blockDim.x) {
+    if (PAIR) shf[i] = df_split(h[(int64_t)b * cap + i]);
+    else sh[i] = h[(int64_t)b * cap + i];
+  }
   __syncthreads();
   double nrm = 0.0;
 #pragma unroll
@@ -220,7 +262,13 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
     const int64_t d = (int64_t)chunk * LZ_CHUNK + e * LZ_THREADS + threadIdx.x;
     if (d >= D) continue;
     double acc = w[(int64_t)b * D + d];
-    for (int i = i0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
+    if (PAIR) {  // sum_i V[i] h[i] in double-float arithmetic, subtracted in float64
+      float ss = 0.0f, sc = 0.0f;
+      for (int i = i0; i <= j; ++i) df_fma(ld_pair(V + ((int64_t)i * batch + b) * D + d), shf[i], ss, sc);
+      acc -= df_value(ss, sc);
+    } else {
+      for (int i = i0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
+    }
     w[(int64_t)b * D + d] = acc;
     nrm = fma(acc, acc, nrm);
   }
@@ -533,6 +581,7 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
 }
 
 // v_{j+1} = w / beta_j for running members (into the basis and the current vector)
+template <bool PAIR>
 __global__ void k_next_vector(const double* __restrict__ w, const double* __restrict__ ab,
                               double* __restrict__ V, double* __restrict__ vcur,
                               const int32_t* __restrict__ ctl, int64_t D, int batch, int cap) {
@@ -547,7 +596,8 @@ __global__ void k_next_vector(const double* __restrict__ w, const double* __rest
   double* vn = V + ((int64_t)(j + 1) * batch + b) * D;
   for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
     const double v = w[(int64_t)b * D + d] * inv;
-    vn[d] = v;
+    if (PAIR) st_pair(vn + d, v);
+    else vn[d] = v;
     vcur[(int64_t)b * D + d] = v;
   }
 }
@@ -603,6 +653,7 @@ __global__ void k_sum_chunks(const double* __restrict__ part, double* __restrict
 }
 
 // y[b] = x[b] / sqrt(nrm2[b]); also into y2 if given
+template <bool PAIR>
 __global__ void k_scale_unit(const double* __restrict__ x, const double* __restrict__ nrm2,
                              double* __restrict__ y, double* __restrict__ y2, int64_t D) {
   __shared__ double s_inv;
@@ -612,12 +663,14 @@ __global__ void k_scale_unit(const double* __restrict__ x, const double* __restr
   const double inv = s_inv;
   for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
     const double v = x[(int64_t)b * D + d] * inv;
-    y[(int64_t)b * D + d] = v;
+    if (PAIR) st_pair(y + (int64_t)b * D + d, v);  // y is a Krylov row
+    else y[(int64_t)b * D + d] = v;
     if (y2) y2[(int64_t)b * D + d] = v;
   }
 }
 
 // out[b] = sum_{i < n_b} s[b][i] V[i][b]
+template <bool PAIR>
 __global__ void k_ritz(const double* __restrict__ V, const double* __restrict__ s,
                        const int32_t* __restrict__ ctl, double* __restrict__ out, int64_t D, int batch,
                        int cap) {
@@ -625,9 +678,16 @@ __global__ void k_ritz(const double* __restrict__ V, const double* __restrict__ 
   if (ctl[LZ_CTL_MEMBER + b] == LZ_HOLD) return;  // its result came from an earlier run
   const int n = ctl[LZ_CTL_MEMBER + batch + b];
   for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) t = fma(s[(int64_t)b * cap + i], V[((int64_t)i * batch + b) * D + d], t);
-    out[(int64_t)b * D + d] = t;
+    if (PAIR) {  // double-float sum of the stored pairs
+      float ts = 0.0f, tc2 = 0.0f;
+      for (int i = 0; i < n; ++i)
+        df_fma(ld_pair(V + ((int64_t)i * batch + b) * D + d), df_split(s[(int64_t)b * cap + i]), ts, tc2);
+      out[(int64_t)b * D + d] = df_value(ts, tc2);
+    } else {
+      double t = 0.0;
+      for (int i = 0; i < n; ++i) t = fma(s[(int64_t)b * cap + i], V[((int64_t)i * batch + b) * D + d], t);
+      out[(int64_t)b * D + d] = t;
+    }
   }
 }
 
@@ -694,9 +754,14 @@ void lz_launch_cfrac(const double* norm2, const double* alpha, const double* bet
 }
 void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int win, const int32_t* gate, cudaStream_t st, const double* h_pre,
-                        double* npart_pre) {
-  k_multidot<<<dim3(lz_dot_nchunk(D), batch), LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap,
-                                                                  lz_dot_nchunk(D), win, gate, h_pre, npart_pre);
+                        double* npart_pre, bool pair) {
+  const dim3 g(lz_dot_nchunk(D), batch);
+  if (pair)
+    k_multidot<true><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D), win, gate, h_pre,
+                                               npart_pre);
+  else
+    k_multidot<false><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D), win, gate,
+                                                h_pre, npart_pre);
 }
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st) {
@@ -705,9 +770,13 @@ void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl,
 }
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
                          const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, int win,
-                         const int32_t* gate, cudaStream_t st) {
-  k_multiaxpy<<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl, D,
-                                                                            batch, cap, nchunk, win, gate);
+                         const int32_t* gate, cudaStream_t st, bool pair) {
+  if (pair)
+    k_multiaxpy<true><<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl, D,
+                                                                                   batch, cap, nchunk, win, gate);
+  else
+    k_multiaxpy<false><<<dim3(nchunk, batch), LZ_THREADS, cap * sizeof(double), st>>>(V, w, h, norm_partial, ctl,
+                                                                                    D, batch, cap, nchunk, win, gate);
 }
 void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate, const int32_t* ctl, int batch,
                     int nchunk_a, int nchunk, cudaStream_t st) {
@@ -727,8 +796,9 @@ static int vec_blocks(int64_t D) {
   return (int)(nb < 2048 ? (nb < 1 ? 1 : nb) : 2048);
 }
 void lz_launch_next_vector(const double* w, const double* ab, double* V, double* vcur, const int32_t* ctl,
-                           int64_t D, int batch, int cap, cudaStream_t st) {
-  k_next_vector<<<dim3(vec_blocks(D), batch), 256, 0, st>>>(w, ab, V, vcur, ctl, D, batch, cap);
+                           int64_t D, int batch, int cap, cudaStream_t st, bool pair) {
+  if (pair) k_next_vector<true><<<dim3(vec_blocks(D), batch), 256, 0, st>>>(w, ab, V, vcur, ctl, D, batch, cap);
+  else k_next_vector<false><<<dim3(vec_blocks(D), batch), 256, 0, st>>>(w, ab, V, vcur, ctl, D, batch, cap);
 }
 void lz_launch_advance(int32_t* ctl, int batch, cudaStream_t st) { k_advance<<<1, 32, 0, st>>>(ctl, batch); }
 void lz_launch_sumsq(const double* x, double* part, int64_t D, int batch, int nchunk, cudaStream_t st) {
@@ -742,12 +812,14 @@ void lz_launch_sum_chunks(const double* part, double* res, int nchunk, int batch
   k_sum_chunks<<<(batch + 127) / 128, 128, 0, st>>>(part, res, nchunk, batch);
 }
 void lz_launch_scale_unit(const double* x, const double* nrm2, double* y, double* y2, int64_t D, int batch,
-                          cudaStream_t st) {
-  k_scale_unit<<<dim3(vec_blocks(D), batch), 256, 0, st>>>(x, nrm2, y, y2, D);
+                          cudaStream_t st, bool pair) {
+  if (pair) k_scale_unit<true><<<dim3(vec_blocks(D), batch), 256, 0, st>>>(x, nrm2, y, y2, D);
+  else k_scale_unit<false><<<dim3(vec_blocks(D), batch), 256, 0, st>>>(x, nrm2, y, y2, D);
 }
 void lz_launch_ritz(const double* V, const double* s, const int32_t* ctl, double* out, int64_t D, int batch,
-                    int cap, cudaStream_t st) {
-  k_ritz<<<dim3(vec_blocks(D), batch), 256, 0, st>>>(V, s, ctl, out, D, batch, cap);
+                    int cap, cudaStream_t st, bool pair) {
+  if (pair) k_ritz<true><<<dim3(vec_blocks(D), batch), 256, 0, st>>>(V, s, ctl, out, D, batch, cap);
+  else k_ritz<false><<<dim3(vec_blocks(D), batch), 256, 0, st>>>(V, s, ctl, out, D, batch, cap);
 }
 void lz_launch_div_rows(double* v, const double* nrm2, int n_terms, int batch, cudaStream_t st) {
   const int n = n_terms * batch;

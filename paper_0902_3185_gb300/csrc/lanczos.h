@@ -34,15 +34,17 @@ inline int lz_dot_nchunk(int64_t D) { return (int)((D + LZ_DOT_CHUNK - 1) / LZ_D
 // Gram-Schmidt passes over the Krylov rows first_row(j, win)..j (win = 0: all
 // rows); members with gate != NULL and gate[b] == 0 are skipped.
 // h_pre / npart_pre: apply the three-term update with coefficients h_pre
-// first (written back to w, per-chunk norm partials into npart_pre)
+// first (written back to w, per-chunk norm partials into npart_pre).
+// pair: the Krylov basis V is stored as double-float pairs (mixed-precision
+// solves; the passes run in double-float arithmetic), else float64
 void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int win, const int32_t* gate, cudaStream_t st,
-                        const double* h_pre = nullptr, double* npart_pre = nullptr);
+                        const double* h_pre, double* npart_pre, bool pair);
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st);
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
                          const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, int win,
-                         const int32_t* gate, cudaStream_t st);
+                         const int32_t* gate, cudaStream_t st, bool pair);
 void lz_launch_dgks(const double* npart_a, const double* npart_b, int32_t* gate, const int32_t* ctl, int batch,
                     int nchunk_a, int nchunk, cudaStream_t st);
 void lz_launch_finalize_ab(const double* h, const double* npart_b, const double* npart_c, const int32_t* gate,
@@ -54,16 +56,18 @@ void lz_launch_cfrac(const double* norm2, const double* alpha, const double* bet
 void lz_launch_tridiag(const double* ab, double* s, double* out, int32_t* ctl, const double* tol, int batch,
                        int cap, int64_t D, cudaStream_t st, int final_pass = 0);
 void lz_launch_next_vector(const double* w, const double* ab, double* V, double* vcur, const int32_t* ctl,
-                           int64_t D, int batch, int cap, cudaStream_t st);
+                           int64_t D, int batch, int cap, cudaStream_t st, bool pair);
 void lz_launch_advance(int32_t* ctl, int batch, cudaStream_t st);
 void lz_launch_sumsq(const double* x, double* part, int64_t D, int batch, int nchunk, cudaStream_t st);
 void lz_launch_dot(const double* x, const double* y, double* part, int64_t D, int batch, int nchunk,
                    cudaStream_t st);
 void lz_launch_sum_chunks(const double* part, double* res, int nchunk, int batch, cudaStream_t st);
+// y = x / |x| (pair: y is a Krylov row stored as double-float pairs); y2, if
+// not NULL, gets the float64 values
 void lz_launch_scale_unit(const double* x, const double* nrm2, double* y, double* y2, int64_t D, int batch,
-                          cudaStream_t st);
+                          cudaStream_t st, bool pair = false);
 void lz_launch_ritz(const double* V, const double* s, const int32_t* ctl, double* out, int64_t D, int batch,
-                    int cap, cudaStream_t st);
+                    int cap, cudaStream_t st, bool pair);
 void lz_launch_div_rows(double* v, const double* nrm2, int n_terms, int batch, cudaStream_t st);
 void lz_launch_reduce_terms(const double* part, const int32_t* ptr, const int32_t* idx, double* out, int n,
                             cudaStream_t st);
