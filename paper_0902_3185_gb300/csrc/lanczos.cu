@@ -256,21 +256,40 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
     else sh[i] = h[(int64_t)b * cap + i];
   }
   __syncthreads();
+  // the rows in the outer loop and the thread's LZ_EPT elements inside it:
+  // independent accumulators, so every row issues LZ_EPT loads at once
+  const int64_t d0 = (int64_t)chunk * LZ_CHUNK + threadIdx.x;
+  const bool full = d0 + (LZ_EPT - 1) * LZ_THREADS < D;
+  double acc[LZ_EPT];
+  float ss[LZ_EPT], sc[LZ_EPT];
+#pragma unroll
+  for (int e = 0; e < LZ_EPT; ++e) {
+    acc[e] = 0.0;
+    ss[e] = sc[e] = 0.0f;
+  }
+#pragma unroll 2
+  for (int i = i0; i <= j; ++i) {
+    const double* vi = V + ((int64_t)i * batch + b) * D + d0;
+    if (PAIR) {  // sum_i V[i] h[i] in double-float arithmetic
+      const float2 hi = shf[i];
+#pragma unroll
+      for (int e = 0; e < LZ_EPT; ++e)
+        if (full || d0 + e * LZ_THREADS < D) df_fma(ld_pair(vi + e * LZ_THREADS), hi, ss[e], sc[e]);
+    } else {
+      const double hi = sh[i];
+#pragma unroll
+      for (int e = 0; e < LZ_EPT; ++e)
+        if (full || d0 + e * LZ_THREADS < D) acc[e] = fma(vi[e * LZ_THREADS], hi, acc[e]);
+    }
+  }
   double nrm = 0.0;
 #pragma unroll
   for (int e = 0; e < LZ_EPT; ++e) {
-    const int64_t d = (int64_t)chunk * LZ_CHUNK + e * LZ_THREADS + threadIdx.x;
+    const int64_t d = d0 + e * LZ_THREADS;
     if (d >= D) continue;
-    double acc = w[(int64_t)b * D + d];
-    if (PAIR) {  // sum_i V[i] h[i] in double-float arithmetic, subtracted in float64
-      float ss = 0.0f, sc = 0.0f;
-      for (int i = i0; i <= j; ++i) df_fma(ld_pair(V + ((int64_t)i * batch + b) * D + d), shf[i], ss, sc);
-      acc -= df_value(ss, sc);
-    } else {
-      for (int i = i0; i <= j; ++i) acc = fma(-V[((int64_t)i * batch + b) * D + d], sh[i], acc);
-    }
-    w[(int64_t)b * D + d] = acc;
-    nrm = fma(acc, acc, nrm);
+    const double x = w[(int64_t)b * D + d] - (PAIR ? df_value(ss[e], sc[e]) : acc[e]);
+    w[(int64_t)b * D + d] = x;
+    nrm = fma(x, x, nrm);
   }
   if (norm_partial) {
     const double t = block_sum(nrm, red);
