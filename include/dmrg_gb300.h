@@ -253,6 +253,18 @@ typedef struct {
 } dmrg_tune_info;
 dmrg_status dmrg_autotune(dmrg_sb* sb, int32_t prec, int32_t reps, void* stream, dmrg_tune_info* info);
 
+/* Measurement hook (no paper counterpart): event-timed average of `reps`
+ * full Gram-Schmidt passes of the Lanczos solver at Krylov index j (dots of w
+ * against rows 0..j, their reduction, and the update w -= V h) for every
+ * member of this superblock, in the basis storage of `prec` (float64 for
+ * DMRG_FP64, double-float pairs otherwise).  Allocates the Lanczos buffers
+ * for j + 1 rows if needed; the rows and w hold arbitrary values (the time
+ * does not depend on them).  *ms = milliseconds per pass; *bytes = the bytes
+ * one pass must move, (2 (j + 1) + 3) D batch 8.  Synchronises the stream.
+ * DMRG_EINVAL for j outside [0, 767], reps < 1 or NULL outputs. */
+dmrg_status dmrg_time_reorth(dmrg_sb* sb, int32_t prec, int32_t j, int32_t reps, double* ms, double* bytes,
+                             void* stream);
+
 /* Synchronise `stream` and report device-side failures of earlier calls on
  * this superblock: DMRG_ETIMEOUT if a bounded wait inside a tensor-core
  * kernel gave up (the kernel then skipped its output and released its

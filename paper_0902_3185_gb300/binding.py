@@ -29,7 +29,8 @@ SYMBOLS = ["dmrg_create_superblock", "dmrg_destroy_superblock", "dmrg_last_error
            "dmrg_energy_grad", "dmrg_apply_H_static_scratch", "dmrg_autotune", "dmrg_sync_status",
            "dmrg_test_inject", "dmrg_lanczos_ground_grad", "dmrg_apply_H_term_dots", "dmrg_lanczos_coeffs",
            "dmrg_continued_fraction", "dmrg_sys_create", "dmrg_sys_destroy", "dmrg_sys_last_error",
-           "dmrg_sys_infinite", "dmrg_sys_sweeps", "dmrg_sys_last_superblock", "dmrg_sym_eig_batched"]
+           "dmrg_sys_infinite", "dmrg_sys_sweeps", "dmrg_sys_last_superblock", "dmrg_sym_eig_batched",
+           "dmrg_time_reorth"]
 
 
 class DmrgError(RuntimeError):
@@ -153,6 +154,7 @@ def load(build_if_missing: bool = True):
     lib.dmrg_sys_sweeps.argtypes = [vp, i32, C.POINTER(StepInfo), C.POINTER(C.c_int32)]
     lib.dmrg_sys_last_superblock.argtypes = [vp, C.POINTER(_SbView), dp]
     lib.dmrg_sym_eig_batched.argtypes = [i32, vp, vp, vp, vp, vp]
+    lib.dmrg_time_reorth.argtypes = [vp, i32, i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     for name in SYMBOLS:
         if name not in ("dmrg_destroy_superblock", "dmrg_last_error", "dmrg_sys_destroy", "dmrg_sys_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -308,6 +310,13 @@ class GpuSuperblock:
         if grad:
             return e0, psi_out, infos, st, dE
         return e0, psi_out, infos, st
+
+    def time_reorth(self, j, prec="bf16x3", reps=5, stream=None):
+        """Event-timed full Gram-Schmidt pass at Krylov index j: (ms, bytes moved)."""
+        ms, nbytes = C.c_double(), C.c_double()
+        self._check(self.lib.dmrg_time_reorth(self.h, _prec(prec), int(j), int(reps), C.byref(ms), C.byref(nbytes),
+                                              _stream(stream)))
+        return ms.value, nbytes.value
 
     def apply_H_term_dots(self, psi, prec="fp64", stream=None):
         """y = H psi and dots[b][k] = <psi_b, (A_k (x) B_k) psi_b>, one pass

@@ -1377,6 +1377,55 @@ dmrg_status dmrg_lanczos_coeffs(dmrg_sb* sb, const double* phi0, int32_t n_max, 
   });
 }
 
+dmrg_status dmrg_time_reorth(dmrg_sb* sb, int32_t prec, int32_t j, int32_t reps, double* ms, double* bytes,
+                             void* stream) {
+  if (!sb || !ms || !bytes || prec < DMRG_FP64 || prec > DMRG_BF16X3 || j < 0 || j > 767 || reps < 1) {
+    if (sb) sb->err = "time_reorth: bad arguments";
+    return DMRG_EINVAL;
+  }
+  return guard(sb, [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t D = sb->D;
+    const int B = sb->batch;
+    lz_alloc(sb, j + 1);
+    const int cap = sb->lz_cap, nch = sb->lz_nchunk, ndot = lz_dot_nchunk(D);
+    const bool pair = lz_pair(prec);
+    // every member running at Krylov index j; the basis rows and w hold whatever
+    // the last solve left (the timing does not depend on the values)
+    std::vector<int32_t> hc(LZ_CTL_MEMBER + 2 * B, 0);
+    hc[LZ_CTL_J] = j;
+    hc[LZ_CTL_MAXIT] = cap;
+    hc[LZ_CTL_CHECK] = 1;
+    CK(cudaMemcpyAsync(sb->lz_ctl, hc.data(), hc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(sb->lz_w, 0, sizeof(double) * (size_t)B * D, st));
+    double* hB = sb->lz_h + (size_t)B * cap;
+    double* nB = sb->lz_npart + (size_t)B * nch;
+    auto pass = [&] {
+      lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, sb->lz_ctl, D, B, cap, 0, nullptr, st, nullptr, nullptr,
+                         pair);
+      lz_launch_reduce_rows(sb->lz_partial, hB, sb->lz_ctl, ndot, cap, B, 0, nullptr, st);
+      lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, sb->lz_ctl, D, B, cap, nch, 0, nullptr, st, pair);
+    };
+    pass();
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CK(cudaEventRecord(a, st));
+    for (int r = 0; r < reps; ++r) pass();
+    CK(cudaEventRecord(b, st));
+    CK(cudaEventSynchronize(b));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CK(cudaGetLastError());
+    *ms = (double)t / reps;
+    // the dots read rows 0..j and w; the update reads rows 0..j, reads and writes w
+    *bytes = (2.0 * (j + 1) + 3.0) * (double)D * B * 8.0;
+    return DMRG_OK;
+  });
+}
+
 dmrg_status dmrg_continued_fraction(const double* norm2, const double* alpha, const double* beta, const int32_t* n,
                                     int32_t batch, int32_t ld, const double* z_re, const double* z_im, int32_t n_z,
                                     double* g_re, double* g_im, void* stream) {

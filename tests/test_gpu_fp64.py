@@ -336,3 +336,22 @@ def test_set_coeffs_is_ordered_on_the_callers_stream(dev):
         for y in ys:
             assert close(y.cpu().numpy()[b], ref_old)
         assert close(y_new.cpu().numpy()[b], ref_new)
+
+
+def test_time_reorth_hook(dev):
+    """The Gram-Schmidt timing hook: positive time, the documented byte count,
+    bad arguments rejected; a solve afterwards is unaffected."""
+    from paper_0902_3185_gb300 import binding
+    sb = grown_hubbard_superblock(12, "ladder", 5, 5, m=60, cut=6, U_values=[4.0, 8.0])
+    g = gpu_sb(sb)
+    for prec in ("fp64", "bf16x3"):
+        ms, nbytes = g.time_reorth(10, prec=prec, reps=3)
+        assert ms > 0 and nbytes == (2 * 11 + 3) * sb.dim * sb.batch * 8
+    with pytest.raises(binding.DmrgError):
+        g.time_reorth(-1)
+    X = np.stack([seeded_normal(50 + b, sb.dim) for b in range(sb.batch)])
+    e0, _, _, st = g.lanczos_ground(to_dev(X), tol=1e-12, max_iter=300)
+    assert st == 0
+    for b in range(sb.batch):
+        ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v, b), X[b], tol=1e-12, max_iter=300)
+        assert abs(e0[b] - ref.e0) <= 1e-10 * abs(ref.e0)
