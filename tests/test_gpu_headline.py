@@ -20,6 +20,7 @@ N_up = N_dn = 28, 16 members (U = 4 .. 12) in one batch:
   refined states of the benchmark's step certified by the oracle (its own
   float64 Rayleigh quotient and residual of the returned state, and its
   gradient formula).
+"""
 import numpy as np
 import pytest
 
