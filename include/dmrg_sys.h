@@ -109,6 +109,8 @@ typedef struct {      /* one per DMRG step */
                          assembly and creation, the Lanczos solve, density matrices to W^T O W */
   int32_t max_sector; /* largest symmetry sector of the truncated block(s) (eigensolve size) */
   int32_t guessed;    /* 1: the Lanczos solve started from the transformed previous ground state */
+  double ms_eig, ms_select, ms_transform; /* parts of ms_truncate: density matrices and their
+                         eigensolves; the global choice of the kept states; W^T O W */
 } dmrg_step_info;
 
 /* A DMRG run on a lattice of L (even, >= 4) sites keeping m states.  Builds

@@ -99,7 +99,8 @@ class StepInfo(C.Structure):
                 ("gap_S", C.c_double), ("gap_E", C.c_double), ("iters", C.c_int32), ("kept_S", C.c_int32),
                 ("kept_E", C.c_int32), ("n_terms", C.c_int32), ("ms", C.c_double), ("ms_grow", C.c_double),
                 ("ms_superblock", C.c_double), ("ms_solve", C.c_double), ("ms_truncate", C.c_double),
-                ("max_sector", C.c_int32), ("guessed", C.c_int32)]
+                ("max_sector", C.c_int32), ("guessed", C.c_int32), ("ms_eig", C.c_double),
+                ("ms_select", C.c_double), ("ms_transform", C.c_double)]
 
 
 class _SbView(C.Structure):

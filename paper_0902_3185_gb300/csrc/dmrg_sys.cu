@@ -666,7 +666,12 @@ struct TruncOut {
   BlkP blk;
   double eps = 0.0, gap = 0.0;
   int kept = 0;
+  double ms_eig = 0.0, ms_select = 0.0, ms_transform = 0.0;  // density matrices and eigensolves; choice; W^T O W
 };
+
+double host_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 // Keep the m most probable states of the grown block G (side S: rows of the
 // target blocks, rho = Psi Psi^T; side E: columns, rho = Psi^T Psi) and carry
@@ -683,6 +688,7 @@ TruncOut truncate(const Model& M, const Blk& G, bool sideS, const SbView& V, con
     woff[z + 1] = woff[z] + (n > EIG_SMEM_MAX_N ? 2 * n * (n + 1) : 0);
   }
   const int64_t ncand = coff[nz];
+  const double t0 = host_ms();
   DBuf rho((size_t)roff[nz]);
   auto Vv = std::make_shared<DBuf>((size_t)roff[nz]);
   DBuf lam((size_t)ncand), work((size_t)std::max<int64_t>(woff[nz], 1));
@@ -725,6 +731,8 @@ TruncOut truncate(const Model& M, const Blk& G, bool sideS, const SbView& V, con
     ej.push_back(j);
   }
   launch_eig(ej, st);
+  SYS_CK(cudaStreamSynchronize(st));
+  const double t1 = host_ms();
   // global selection
   std::vector<int32_t> hsec((size_t)ncand), hidx((size_t)ncand);
   for (int z = 0; z < nz; ++z)
@@ -743,6 +751,7 @@ TruncOut truncate(const Model& M, const Blk& G, bool sideS, const SbView& V, con
   SYS_CK(cudaMemcpyAsync(keep.data(), dkeep.p, ncand * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SYS_CK(cudaMemcpyAsync(hst, stats.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   SYS_CK(cudaStreamSynchronize(st));
+  const double t2 = host_ms();
   auto tr = std::make_shared<Trunc>();
   tr->grown = b;
   tr->comps = G.comps;
@@ -822,6 +831,9 @@ TruncOut truncate(const Model& M, const Blk& G, bool sideS, const SbView& V, con
   SYS_CK(cudaStreamSynchronize(st));
   N->trunc = tr;
   TruncOut out;
+  out.ms_eig = t1 - t0;
+  out.ms_select = t2 - t1;
+  out.ms_transform = host_ms() - t2;
   out.blk = N;
   out.eps = std::max(0.0, hst[0]);
   out.gap = hst[1];
@@ -1240,6 +1252,9 @@ dmrg_status dmrg_sys_infinite(dmrg_sys* sys, dmrg_step_info* steps, int32_t* n_s
       TruncOut ts = truncate(M, *Sp, true, sys->view, psi, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
       TruncOut te = truncate(M, *Ep, false, sys->view, psi, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
       info.ms_truncate = now_ms() - t2;
+      info.ms_eig = ts.ms_eig + te.ms_eig;
+      info.ms_select = ts.ms_select + te.ms_select;
+      info.ms_transform = ts.ms_transform + te.ms_transform;
       info.max_sector = std::max(max_dim(*Sp), max_dim(*Ep));
       S = ts.blk;
       E = te.blk;
@@ -1317,12 +1332,18 @@ dmrg_status dmrg_sys_sweeps(dmrg_sys* sys, int32_t n_sweeps, dmrg_step_info* ste
       if (dir > 0) {
         TruncOut ts = truncate(M, *Sp, true, sys->view, psi, sys->m, sys->opts.tie_tol, Sp->n - M.reach, st);
         sys->left[Sp->n] = ts.blk;
+        info.ms_eig = ts.ms_eig;
+        info.ms_select = ts.ms_select;
+        info.ms_transform = ts.ms_transform;
         info.eps_S = ts.eps;
         info.gap_S = ts.gap;
         info.kept_S = ts.kept;
       } else {
         TruncOut te = truncate(M, *Ep, false, sys->view, psi, sys->m, sys->opts.tie_tol, Ep->n - M.reach, st);
         sys->right[Ep->n] = te.blk;
+        info.ms_eig = te.ms_eig;
+        info.ms_select = te.ms_select;
+        info.ms_transform = te.ms_transform;
         info.eps_E = te.eps;
         info.gap_E = te.gap;
         info.kept_E = te.kept;

@@ -58,5 +58,5 @@ def test_dmrg_sys_struct_layouts_match_header():
     assert ctypes.sizeof(binding._BondTerm) == 8 + 4 * 4
     assert ctypes.sizeof(binding._ModelDesc) == 136
     assert ctypes.sizeof(binding.SysOpts) == 8 + 4 * 4 + 8 + 8 + 8
-    assert ctypes.sizeof(binding.StepInfo) == 4 * 4 + 8 + 8 * 5 + 4 * 4 + 8 + 8 * 4 + 4 * 2
+    assert ctypes.sizeof(binding.StepInfo) == 4 * 4 + 8 + 8 * 5 + 4 * 4 + 8 + 8 * 4 + 4 * 2 + 8 * 3
     assert ctypes.sizeof(binding._SbView) == ctypes.sizeof(binding._Desc) + 8 * 3 + 4 * 2
