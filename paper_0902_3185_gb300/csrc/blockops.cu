@@ -176,8 +176,11 @@ void launch_gemm(const std::vector<GemmJob>& jobs, cudaStream_t st) {
 // so all of them are applied at once -- rows p, q of A for every pair, then
 // columns p, q of A and of V -- as A <- J^T A J, V <- V J.  The rotation that
 // zeroes a_pq: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
-// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c.  Sweeps stop when the
-// off-diagonal mass is below (1e-15)^2 of the diagonal's (at most 40).
+// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c.  A rotation is skipped
+// when |a_pq| <= 4 eps |A|_F (threshold Jacobi: rounding leaves off-diagonal
+// elements near eps |A|, so a tighter test would never pass), and the sweeps
+// stop after one without a rotation (at most 40).  The eigenvalues are then
+// accurate to a few eps |A| in absolute terms, as a LAPACK solver's.
 constexpr int EIG_THREADS = 256;
 constexpr int EIG_MAX_N = 4096;
 
@@ -222,17 +225,14 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig(const EigJob* __restrict__ 
   }
   __syncthreads();
   if (n > 1) {
+    double fro = 0.0;
+    for (int e = tid; e < n * n; e += EIG_THREADS) {
+      const double x = a[(e / n) * ld + e % n];
+      fro = fma(x, x, fro);
+    }
+    const double thr = 4.0 * 2.220446049250313e-16 * sqrt(eig_block_sum(fro, red));
     for (int sweep = 0; sweep < 40; ++sweep) {
-      double off = 0.0, dg = 0.0;
-      for (int e = tid; e < n * n; e += EIG_THREADS) {
-        const int i = e / n, j = e % n;
-        const double x = a[i * ld + j];
-        if (i == j) dg = fma(x, x, dg);
-        else off = fma(x, x, off);
-      }
-      off = eig_block_sum(off, red);
-      dg = eig_block_sum(dg, red);
-      if (off <= 1e-30 * dg || off <= 1e-300) break;
+      double rot = 0.0;  // rotations applied by this thread in the sweep
       for (int r = 0; r < n2 - 1; ++r) {
         for (int k = tid; k < np; k += EIG_THREADS) {
           int p = rr_player(k, r, n2), q = rr_player(n2 - 1 - k, r, n2);
@@ -240,13 +240,14 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig(const EigJob* __restrict__ 
           double c = 1.0, s = 0.0;
           if (q < n) {
             const double apq = a[p * ld + q];
-            if (apq != 0.0) {
+            if (fabs(apq) > thr) {
               const double tau = (a[q * ld + q] - a[p * ld + p]) / (2.0 * apq);
               double t;
               if (fabs(tau) > 1e150) t = 0.5 / tau;
               else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
               c = 1.0 / sqrt(1.0 + t * t);
               s = t * c;
+              rot += 1.0;
             }
           }
           pp[k] = p;
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig(const EigJob* __restrict__ 
         }
         __syncthreads();
       }
+      if (eig_block_sum(rot, red) == 0.0) break;  // the same sum in every thread
     }
   }
   // decreasing order (ties by index)
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_cluster(const EigJob* __res
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   __shared__ double red[EIG_THREADS / 32];
-  __shared__ double sums[2];
+  __shared__ double sums[1];
   __shared__ int n_own;
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -342,30 +344,24 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_cluster(const EigJob* __res
     a[li * n + j] = jb.A[(int64_t)i * n + j];
     v[li * n + j] = i == j ? 1.0 : 0.0;
   }
-  cl.sync();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, dgs = 0.0;
-    for (int e = tid; e < rows * n; e += EIG_THREADS) {
-      const int li = e / n, j = e % n, i = rank + C * li;
-      const double x = a[li * n + j];
-      if (i == j) dgs = fma(x, x, dgs);
-      else off = fma(x, x, off);
-    }
-    off = eig_block_sum(off, red);
-    dgs = eig_block_sum(dgs, red);
-    if (tid == 0) {
-      sums[0] = off;
-      sums[1] = dgs;
-    }
+  // sum over the cluster of one value per block, in the same order in every block
+  auto cluster_sum = [&](double v) -> double {
+    v = eig_block_sum(v, red);
+    if (tid == 0) sums[0] = v;
     cl.sync();
-    double to = 0.0, td = 0.0;
-    for (int b = 0; b < C; ++b) {  // the same order in every block
-      const double* rs = cl.map_shared_rank(sums, b);
-      to += rs[0];
-      td += rs[1];
-    }
-    cl.sync();  // the sums are read before any block writes the next ones
-    if (to <= 1e-30 * td || to <= 1e-300) break;
+    double t = 0.0;
+    for (int b = 0; b < C; ++b) t += cl.map_shared_rank(sums, b)[0];
+    cl.sync();  // read before any block writes the next one
+    return t;
+  };
+  double fro = 0.0;
+  for (int e = tid; e < rows * n; e += EIG_THREADS) {
+    const double x = a[(e / n) * n + e % n];
+    fro = fma(x, x, fro);
+  }
+  const double thr = 4.0 * 2.220446049250313e-16 * sqrt(cluster_sum(fro));
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double rot = 0.0;  // rotations this block computed in the sweep
     for (int r = 0; r < n2 - 1; ++r) {
       if (tid == 0) n_own = 0;
       __syncthreads();
@@ -376,7 +372,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_cluster(const EigJob* __res
         double c = 1.0, s = 0.0;
         if (q < n) {
           const double apq = a[(p / C) * n + q];
-          if (apq != 0.0) {
+          if (fabs(apq) > thr) {
             const double* ra = cl.map_shared_rank(a, q % C);
             const double aqq = ra[(q / C) * n + q];
             const double tau = (aqq - a[(p / C) * n + p]) / (2.0 * apq);
@@ -385,6 +381,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_cluster(const EigJob* __res
             else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
             s = t * c;
+            rot += 1.0;
           }
         }
         par[2 * k] = c;
@@ -430,6 +427,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_cluster(const EigJob* __res
       }
       cl.sync();
     }
+    if (cluster_sum(rot) == 0.0) break;  // every block leaves together
   }
   // decreasing order: every block gathers the diagonal, ranks it, and writes its own rows of V
   for (int i = tid; i < n; i += EIG_THREADS) {
