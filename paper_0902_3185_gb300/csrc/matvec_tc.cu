@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <stdexcept>
 #include <vector>
 
@@ -940,12 +941,15 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     const int s1 = (int)B.segs.size();
     int64_t kw = 0;
     for (const TcSeg& g : sg) kw += g.kchunks;
+    // N split into tiles of (nearly) equal width, multiples of 16, at most max_ntile
+    const int64_t n_tiles = cdiv(o.N, max_ntile);
+    const int64_t width = cdiv(cdiv(o.N, n_tiles), 16) * 16;
     for (int m0 = 0; m0 < o.M; m0 += 128)
-      for (int n0 = 0; n0 < o.N; n0 += max_ntile) {
+      for (int n0 = 0; n0 < o.N; n0 += (int)width) {
         TcTile t{};
         t.m0 = m0;
         t.n0 = n0;
-        t.ntile = (int)std::min<int64_t>(max_ntile, cdiv(o.N - n0, 16) * 16);
+        t.ntile = (int)std::min<int64_t>(width, cdiv(o.N - n0, 16) * 16);
         t.la = (int)std::min<int64_t>(16, cdiv(o.M - m0, 8));
         t.ra = (int)std::min<int64_t>(t.ntile / 8, cdiv(o.N - n0, 8));
         t.seg_begin = s0;
@@ -1134,11 +1138,21 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     }
   }
   auto finish = [&](Build& B, Launch& L) {
-    // heaviest tiles first, dealt round-robin over the persistent CTAs
+    // heaviest first, dealt round-robin over the persistent CTAs, by groups of
+    // the tiles of one output and first row: the N tiles of a row of tiles
+    // share their L operand tiles, the rows of one output their R operands, so
+    // a group's tiles (and the rows of one output, of equal group weight) stay
+    // neighbours in the order and run on neighbouring CTAs at about the same
+    // time, where the second read of a shared operand tile hits L2
     std::vector<size_t> perm(B.tiles.size());
     for (size_t i = 0; i < perm.size(); ++i) perm[i] = i;
-    if (tune.heavy_first)
-      std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return B.weight[a] > B.weight[b]; });
+    if (tune.heavy_first) {
+      std::map<std::pair<int, int>, int64_t> gw;
+      for (size_t i = 0; i < B.tiles.size(); ++i) gw[{B.tiles[i].out, B.tiles[i].m0}] += B.weight[i];
+      std::vector<int64_t> w(B.tiles.size());
+      for (size_t i = 0; i < B.tiles.size(); ++i) w[i] = gw[{B.tiles[i].out, B.tiles[i].m0}];
+      std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return w[a] > w[b]; });
+    }
     std::vector<TcTile> t(B.tiles.size());
     for (size_t i = 0; i < perm.size(); ++i) t[i] = B.tiles[perm[i]];
     L.tiles = up(t);
