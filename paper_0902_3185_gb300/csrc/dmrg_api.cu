@@ -1115,7 +1115,13 @@ dmrg_status dmrg_set_coeffs(dmrg_sb* sb, const double* coeffs, void* stream) {
     memcpy(sb->h_coeffs_pinned, coeffs, n * sizeof(double));
     CK(cudaMemcpyAsync(sb->d_coeffs, sb->h_coeffs_pinned, n * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
-    tc_set_coeffs(sb);
+    if (tc_set_coeffs(sb))  // tensor-core panels with folded coefficients were rebuilt
+      for (int i = 0; i < 8; ++i)
+        if (sb->lz_graphs[i]) {
+          cudaGraphExecDestroy((cudaGraphExec_t)sb->lz_graphs[i]);
+          sb->lz_graphs[i] = nullptr;
+          sb->lz_graph_key[i] = 0;
+        }
     return DMRG_OK;
   });
 }

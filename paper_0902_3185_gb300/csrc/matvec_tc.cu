@@ -36,6 +36,7 @@
 // hi*hi + hi*lo + lo*hi in kind::f16 with an FP32 accumulator.
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -745,6 +746,7 @@ struct State {
   std::vector<double> host_ops;               // float64 blocks (forward)
   std::vector<std::vector<double>> trans;     // transposed blocks (H^T)
   std::vector<EPair> fw, bw;
+  std::vector<double> built_coeffs;           // the coefficient table the panels were built with
 };
 
 void free_launch(Launch& l) {
@@ -822,12 +824,33 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   // wavefunction panel; otherwise the term gets a coefficient-scaled copy.
   // slot_of[i]: slot of identity pair i (0 = scaled copy or not an identity pair)
   std::vector<int> slot_of(np, 0);
+  // An identity term whose coefficient is the same for every member (e.g. a
+  // hopping class at fixed t while U is swept) needs no per-member scaling:
+  // the diagonal identity pairs of one output sector and group with such
+  // coefficients are folded into one operator panel, sum_k c_k B_k (or
+  // sum_k c_k A_k), read against the unscaled wavefunction panel into the
+  // main accumulator (their coefficients are in the panel).  folded[i]: pair
+  // i is one of them; fold[s][grp]: the pairs folded for sector s.
+  const int nt = sb->n_terms;
+  auto uniform = [&](int term) {
+    for (int64_t b = 1; b < nb; ++b)
+      if (sb->coeffs[(size_t)b * nt + term] != sb->coeffs[term]) return false;
+    return true;
+  };
+  std::vector<char> folded(np, 0);
+  std::vector<std::array<std::vector<size_t>, 2>> fold((size_t)S);
+  for (size_t i = 0; i < np; ++i) {
+    const EPair& e = P[i];
+    if (!(e.flags & (DMRG_ID_A | DMRG_ID_B)) || e.s_out != e.s_in || !uniform(e.term)) continue;
+    folded[i] = 1;
+    fold[(size_t)e.s_out][(e.flags & DMRG_ID_A) ? 0 : 1].push_back(i);
+  }
   for (int s = 0; s < S; ++s) {
     for (int grp = 0; grp < 2; ++grp) {  // 0: 1 (x) B terms (group E), 1: A (x) 1 terms (group S)
       const int flag = grp == 0 ? DMRG_ID_A : DMRG_ID_B;
       std::vector<int> terms;
       for (size_t i : by_out[s])
-        if ((P[i].flags & flag) && std::find(terms.begin(), terms.end(), P[i].term) == terms.end())
+        if ((P[i].flags & flag) && !folded[i] && std::find(terms.begin(), terms.end(), P[i].term) == terms.end())
           terms.push_back(P[i].term);
       if (terms.empty()) continue;
       const int64_t Nout = grp == 0 ? c[s] : r[s];
@@ -835,15 +858,27 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       const int nslot = 1 + (int)terms.size();
       if (nslot > TC_MAX_SLOTS || nslot * ntile > 256) continue;
       for (size_t i : by_out[s])
-        if (P[i].flags & flag)
+        if ((P[i].flags & flag) && !folded[i])
           slot_of[i] = 1 + (int)(std::find(terms.begin(), terms.end(), P[i].term) - terms.begin());
     }
   }
   std::vector<Panel> pA(np), pB(np), pX(np), pS(np);  // operator A, B; intermediate; scaled psi copy
   std::vector<Panel> psiP(S), psiPT(S);
   std::vector<char> needP(S, 0), needPT(S, 0);
+  std::vector<Panel> pF((size_t)S * 2);  // folded operator panels: [s][0] sum c B (group E), [s][1] sum c A (group S)
+  for (int s = 0; s < S; ++s) {
+    if (!fold[(size_t)s][0].empty()) {
+      pF[(size_t)s * 2] = alloc(c[s], c[s]);
+      needP[s] = 1;
+    }
+    if (!fold[(size_t)s][1].empty()) {
+      pF[(size_t)s * 2 + 1] = alloc(r[s], r[s]);
+      needPT[s] = 1;
+    }
+  }
   for (size_t i = 0; i < np; ++i) {
     const EPair& e = P[i];
+    if (folded[i]) continue;
     const int64_t ro = r[e.s_out], ri = r[e.s_in], co = c[e.s_out], ci = c[e.s_in];
     if (!(e.flags & DMRG_ID_A)) pA[i] = alloc(ro, ri);
     if (!(e.flags & DMRG_ID_B)) pB[i] = alloc(co, ci);
@@ -868,6 +903,19 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     if (pA[i].off >= 0) pack(hi, lo, pA[i], e.A, r[e.s_in], prec);
     if (pB[i].off >= 0) pack(hi, lo, pB[i], e.B, c[e.s_in], prec);
   }
+  for (int s = 0; s < S; ++s)
+    for (int grp = 0; grp < 2; ++grp) {
+      const std::vector<size_t>& f = fold[(size_t)s][grp];
+      if (f.empty()) continue;
+      const int64_t n = grp == 0 ? c[s] : r[s];
+      std::vector<double> M((size_t)(n * n), 0.0);
+      for (size_t i : f) {
+        const double ck = sb->coeffs[P[i].term];
+        const double* X = grp == 0 ? P[i].B : P[i].A;
+        for (int64_t k = 0; k < n * n; ++k) M[(size_t)k] += ck * X[k];
+      }
+      pack(hi, lo, pF[(size_t)s * 2 + grp], M.data(), n, prec);
+    }
   auto dptr = [&](const Panel& p) { return d_hi + p.off; };
 
   // ---- staging: the panels each sector block feeds, then its tiles
@@ -883,7 +931,7 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
   }
   for (size_t i = 0; i < np; ++i) {
     const EPair& e = P[i];
-    if (slot_of[i]) continue;
+    if (slot_of[i] || folded[i]) continue;
     if (e.flags & DMRG_ID_A) add_feed(e.s_in, 0, e.term, pS[i]);
     else if (e.flags & DMRG_ID_B) add_feed(e.s_in, 1, e.term, pS[i]);
   }
@@ -1089,8 +1137,11 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
     if ((int64_t)r[s] * c[s] == 0) continue;
     std::vector<TcSeg> sE, sS;
     std::vector<int> tE, tS;  // terms of slots 1, 2, ...
+    if (pF[(size_t)s * 2].off >= 0) sE.push_back(seg(psiP[s], pF[(size_t)s * 2]));          // folded 1 (x) B terms
+    if (pF[(size_t)s * 2 + 1].off >= 0) sS.push_back(seg(psiPT[s], pF[(size_t)s * 2 + 1]));  // folded A (x) 1 terms
     for (size_t i : by_out[s]) {
       const EPair& e = P[i];
+      if (folded[i]) continue;
       if (e.flags & DMRG_ID_A) {
         TcSeg g = slot_of[i] ? seg(psiP[e.s_in], pB[i]) : seg(pS[i], pB[i]);
         g.slot = slot_of[i];
@@ -1208,7 +1259,32 @@ double tc_operand_bytes(const dmrg_sb* sb) {
   return s ? s->op_bytes_tf32 : 0.0;
 }
 
-void tc_set_coeffs(dmrg_sb*) {}  // coefficients are read from the shared table at run time
+static void build_fmt(dmrg_sb* sb, State* s, int fi);
+
+// Coefficients are read from the shared table at run time, except those of
+// identity terms uniform over the batch, folded into operator panels at build
+// time: the panels are rebuilt when the set of such terms or their values
+// change.  Returns true when it rebuilt (captured graphs then hold stale task
+// lists).
+bool tc_set_coeffs(dmrg_sb* sb) {
+  State* s = st_of(sb);
+  if (!s || !s->ok) return false;
+  const int nt = sb->n_terms;
+  const int64_t nb = sb->batch;
+  auto uniform = [&](const std::vector<double>& cf, int term) {
+    for (int64_t b = 1; b < nb; ++b)
+      if (cf[(size_t)b * nt + term] != cf[term]) return false;
+    return true;
+  };
+  bool same = true;
+  for (int k = 0; k < nt && same; ++k) {
+    const bool uo = uniform(s->built_coeffs, k), un = uniform(sb->coeffs, k);
+    same = uo == un && (!uo || s->built_coeffs[k] == sb->coeffs[k]);
+  }
+  if (same) return false;
+  for (int fi = 0; fi < 2; ++fi) build_fmt(sb, s, fi);
+  return true;
+}
 
 int tc_launches(const dmrg_sb* sb, int prec) {
   const State* s = st_of(sb);
@@ -1242,6 +1318,7 @@ static void build_fmt(dmrg_sb* sb, State* s, int fi) {
   TCK(cudaMemcpy(F.arena, hi.data(), hi.size(), cudaMemcpyHostToDevice));
   if (prec == DMRG_BF16X3) TCK(cudaMemcpy(F.arena + lo_delta, lo.data(), lo.size(), cudaMemcpyHostToDevice));
   if (fi == 0) s->op_bytes_tf32 = (double)a;
+  s->built_coeffs = sb->coeffs;
 }
 
 void tc_build(dmrg_sb* sb) {

@@ -12,7 +12,7 @@ namespace dmrg {
 void tc_build(dmrg_sb* sb);      // operand panels and task lists (no-op when unsupported)
 void tc_free(dmrg_sb* sb);
 bool tc_available(const dmrg_sb* sb);
-void tc_set_coeffs(dmrg_sb* sb);
+bool tc_set_coeffs(dmrg_sb* sb);  // true: operand panels rebuilt (captured graphs are stale)
 double tc_operand_bytes(const dmrg_sb* sb);
 int tc_launches(const dmrg_sb* sb, int prec);  // kernels one product launches
 void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,

@@ -144,3 +144,42 @@ def test_full_size_ladder_m1000_mixed(dev, prec):
         ref = osb.apply_H(sb, X[b], b)
         bound = osb.apply_H(asb, np.abs(X[b]), b)
         assert within_model(y[b], ref, bound, GAMMA[prec])
+
+
+def test_folded_uniform_terms_follow_set_coeffs(dev):
+    """Identity terms whose coefficient is the same for every member are
+    folded into the tensor-core operator panels; the BF16x3 product stays
+    within its error model after coefficient changes that keep a term
+    uniform with a new value, that make it member-dependent, and that make it
+    uniform again, and a Lanczos graph captured before the change is not
+    reused with stale panels."""
+    from paper_0902_3185_gb300 import binding
+    sb0 = grown_hubbard_superblock(12, "ladder", 5, 5, m=60, cut=6, U_values=[4.0, 8.0, 6.0])
+    g = gpu_sb(sb0)
+    X = np.stack([seeded_normal(80 + b, sb0.dim) for b in range(sb0.batch)])
+    x = to_dev(X)
+    try:
+        g.apply_H(x, prec="bf16x3")
+    except binding.DmrgError as e:
+        if e.status == 8:
+            pytest.skip("tensor-core path not available")
+        raise
+    it = sb0.class_names.index("t")
+    e_first, _, _, st = g.lanczos_ground(x, tol=1e-4, max_iter=200, prec="bf16x3", refine="newton_df64",
+                                         refine_tol=1e-11)
+    assert st == 0
+    for tvals in ([1.3, 1.3, 1.3], [1.0, 0.8, 1.2], [0.9, 0.9, 0.9]):
+        cp = sb0.couplings.copy()
+        cp[:, it] = tvals
+        sb = sb0.with_coeffs(sb0.coeffs_from_couplings(cp))
+        g.set_coeffs(sb.coeffs)
+        y = g.apply_H(x, prec="bf16x3").cpu().numpy()
+        for b in range(sb.batch):
+            ref = osb.apply_H(sb, X[b], b)
+            assert within_model(y[b], ref, osb.apply_H(abs_sb(sb), np.abs(X[b]), b), GAMMA["bf16x3"]), tvals
+        e0, _, _, st = g.lanczos_ground(x, tol=1e-4, max_iter=200, prec="bf16x3", refine="newton_df64",
+                                        refine_tol=1e-11)
+        assert st == 0
+        for b in range(sb.batch):
+            ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v, b), X[b], tol=1e-12, max_iter=300)
+            assert abs(e0[b] - ref.e0) <= 1e-8 * abs(ref.e0), (tvals, b)
