@@ -140,6 +140,14 @@ def max_over_ranks(ms, dist, device):
     return float(t.item())
 
 
+def member_products(infos):
+    """Products of one solve in units of whole-batch products: the members'
+    own product counts summed over the batch, divided by its size.  Members
+    stop at different iterations and a stopped member gets no more products,
+    so the batch's longest member overstates the work."""
+    return sum(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos) / len(infos)
+
+
 def job_value(world, products, flops, ms_total):
     """Whole-job algorithmic TFLOP/s: every rank ran `products` products of
     `flops` flops within the max-over-ranks time."""
@@ -409,7 +417,7 @@ def measure_grown(binding, torch, args, prec, dev, stream, rank):
         step()
     n_t = 5
     ms, (e0, psi, infos, st, dE) = event_ms(torch, stream, dev, step, n_t)
-    mv = max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
+    mv = member_products(infos)
     t64, (e64, p64, i64, s64, dE64) = event_ms(torch, stream, dev, lambda: g.lanczos_ground(
         x0, tol=args.tol, max_iter=max(600, args.max_iter), prec="fp64", refine="none", graph_iters=8, grad=True))
     e0, e64 = np.asarray(e0, dtype=np.float64), np.asarray(e64, dtype=np.float64)
@@ -527,7 +535,7 @@ def main():
         e0, psi, infos, dEdc = step(x0)
         b.record(stream)
         ev.append((a, b))
-        mv_count += max(i["mixed_matvecs"] + i["fp64_matvecs"] for i in infos)
+        mv_count += member_products(infos)
         it_count += max(i["iters"] + i["refine_iters"] for i in infos)
         launches += infos[0]["kernel_launches"]
     torch.cuda.synchronize(dev)

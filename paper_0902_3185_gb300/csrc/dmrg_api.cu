@@ -433,8 +433,11 @@ void build_f64_tasks(dmrg_sb* sb) {
 }
 
 // ------------------------------------------------------------- products
+// member_done (tensor-core precisions only, may be null): device [batch]
+// flags; members whose flag is nonzero are skipped (their rows of y are left
+// as they are)
 void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
-            cudaStream_t st) {
+            cudaStream_t st, const int32_t* member_done = nullptr) {
   if (prec == DMRG_FP64) {
     Bufs bufs{{const_cast<double*>(x), y, sb->d_T, sb->d_ops, nullptr}};
     launch_seg_gemm_f64(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, skip, st);
@@ -446,7 +449,7 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
     launch_seg_gemm_df(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
     launch_seg_gemm_df(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
   } else {
-    tc_matvec(sb, prec, x, y, accumulate, skip, st);
+    tc_matvec(sb, prec, x, y, accumulate, skip, st, member_done);
   }
   CK(cudaGetLastError());
 }
@@ -546,7 +549,8 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   const int64_t D = sb->D;
   const int B = sb->batch, cap = sb->lz_cap, nch = sb->lz_nchunk;
   int32_t* ctl = sb->lz_ctl;
-  matvec(sb, prec, sb->lz_vcur, sb->lz_w, 0, ctl + LZ_CTL_ALLDONE, st);
+  // members that have stopped (converged, pending, or held from an earlier run) get no product
+  matvec(sb, prec, sb->lz_vcur, sb->lz_w, 0, ctl + LZ_CTL_ALLDONE, st, ctl + LZ_CTL_MEMBER);
   // reorthogonalisation: (A) three-term step, (B) full pass, (C) second full
   // pass where the DGKS test asks for it (see lanczos.cu)
   double* hA = sb->lz_h;
@@ -728,7 +732,7 @@ void rf_enqueue_inner(dmrg_sb* sb, int prec, cudaStream_t st) {
   int32_t* stop = ctl + 2 * B;
   double* sc = sb->rf_sc;
   const float* psi = sb->rf_psi32;  // the current iterate, rounded for the inner solve
-  tc_matvec_f32in(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st);  // q = H p (mixed)
+  tc_matvec_f32in(sb, prec, sb->rf_p, sb->rf_q, 0, stop, st, ctl);  // q = H p (mixed); done members skipped
   rf_launch_dots4(sb->rf_q, sb->rf_p, psi, sb->rf_hp, sc, ctl, sb->rf_part, D, B, stop, st);
   rf_launch_alpha4(sb->rf_part, sc, ctl, D, B, stop, st);
   rf_launch_update(sb->rf_t, sb->rf_res, sb->rf_p, sb->rf_hp, psi, sb->rf_minv, sc, ctl, sb->rf_part, D, B, stop,

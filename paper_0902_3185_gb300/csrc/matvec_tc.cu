@@ -149,7 +149,7 @@ template <int PREC, class TIn>
 __global__ void __launch_bounds__(256)
 tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict__ outs, const TIn* __restrict__ x,
                 int64_t D, int64_t p_lo, const double* __restrict__ coef, int n_terms,
-                const int32_t* __restrict__ skip) {
+                const int32_t* __restrict__ skip, const int32_t* __restrict__ member_done) {
   constexpr int G = PREC == DMRG_TF32 ? 4 : 8;  // values per 16-byte granule
   constexpr int es = PREC == DMRG_TF32 ? 4 : 2;
   constexpr int NKG = STAGE_T / G;              // granules per tile row
@@ -157,6 +157,7 @@ tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict_
   if (skip && *skip) return;
   const StageTile tl = tiles[blockIdx.x];
   const int b = blockIdx.y;
+  if (member_done && member_done[b]) return;  // a member whose solve has stopped
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int rows_t = min(STAGE_T, tl.r - tl.r0), cols_t = min(STAGE_T, tl.c - tl.c0);
   // 32-bit offsets inside the sector block (r * c < 2^31)
@@ -216,13 +217,25 @@ constexpr int PANEL_EPI_BYTES = TC_EPI_WARPS * 16 * 40 * 4;
 constexpr int TC_COEF_MAX = 512;                    // coefficients cached in shared memory (float)
 constexpr int TC_CTRL_BYTES = 256 + 4 * TC_COEF_MAX;  // barriers etc., then the coefficient cache
 
+// A tile whose rows all belong to members whose solve has stopped
+// (member_done[b] != 0: converged Lanczos or CG members of a batch) is
+// skipped by all three roles alike: no copies, no MMAs, no output.  Rows are
+// member-stacked: row m belongs to member m / Rm.
+__device__ __forceinline__ bool tile_done(const TcTile& tl, const int32_t* __restrict__ member_done) {
+  if (!member_done || tl.o.Rm <= 0) return false;
+  const int last = min(tl.m0 + tl.la * 8, tl.o.M) - 1;
+  for (int b = tl.m0 / tl.o.Rm; b <= last / tl.o.Rm; ++b)
+    if (!member_done[b]) return false;
+  return true;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __restrict__ segs,
                const TcOut* __restrict__ seg_outs, double* __restrict__ y, int64_t D, const double* __restrict__ coef, int n_terms, int n_coef,
-               int accumulate, const int32_t* __restrict__ skip, int32_t* __restrict__ err,
-               int stages, int stage_bytes, int r_tile_bytes, int tmem_cols, int epi_bytes, int acc_stride,
-               int n_acc, int tile_split, int stall) {
+               int accumulate, const int32_t* __restrict__ skip, const int32_t* __restrict__ member_done,
+               int32_t* __restrict__ err, int stages, int stage_bytes, int r_tile_bytes, int tmem_cols,
+               int epi_bytes, int acc_stride, int n_acc, int tile_split, int stall) {
   if (skip && *skip) return;
   extern __shared__ __align__(1024) char smem_raw[];
   // control block, then 1024-aligned stage ring
@@ -285,6 +298,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
         tl = tl_n;
         const int tn = t + gridDim.x;
         if (tn < n_tiles) tl_n = tiles[tn];
+        if (tile_done(tl, member_done)) continue;
         const uint32_t lb = (uint32_t)tl.la * ATOM_BYTES, rb = (uint32_t)tl.ra * ATOM_BYTES;
         if (tl.pieced) {
           // one L tile and every piece's R rows per K chunk
@@ -372,7 +386,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const TcTile tl = tl_n;
         if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
-        if (tl.seg_begin == tl.seg_end) continue;
+        if (tl.seg_begin == tl.seg_end || tile_done(tl, member_done)) continue;
         int kch_n = segs[tl.seg_begin].kchunks, slot_n = segs[tl.seg_begin].slot;  // in flight during the wait
         const int acc = kk % n_acc;
         const uint32_t acc_phase = (uint32_t)(kk / n_acc) & 1u;
@@ -454,6 +468,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
       const TcTile tl = tl_n;
       if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
+      if (tile_done(tl, member_done)) continue;
       const TcOut& o = tl.o;
       const bool empty_tile = tl.seg_begin == tl.seg_end;
       const int acc = kk % n_acc;
@@ -1369,7 +1384,7 @@ void tc_build(dmrg_sb* sb) {
 // ------------------------------------------------------------- launching
 template <int PREC>
 static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* sb, int accumulate,
-                     const int32_t* skip, cudaStream_t st) {
+                     const int32_t* skip, const int32_t* member_done, cudaStream_t st) {
   if (L.n_tiles == 0) return;
   const int r_tile = L.ntile_max * PANEL_ROW_BYTES;
   const int stage_bytes = (L_TILE_BYTES + r_tile) * (PREC == DMRG_TF32 ? 1 : 2);
@@ -1393,27 +1408,27 @@ static void run_gemm(const State* s, const Launch& L, double* y, const dmrg_sb* 
       const int b0 = L.out_begin[o], n = L.out_begin[o + 1] - b0;
       tc_gemm_kernel<PREC><<<std::min(n, s->num_sms), TC_THREADS, smem, st>>>(
           L.tiles_by_out + b0, n, L.segs, L.seg_outs, y, sb->D, sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms, accumulate, skip,
-          sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, n_acc, 0, sb->test_stall);
+          member_done, sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi, L.acc_cols, n_acc, 0, sb->test_stall);
     }
     return;
   }
   const int grid = std::min(L.n_tiles, s->num_sms);
   tc_gemm_kernel<PREC><<<grid, TC_THREADS, smem, st>>>(L.tiles, L.n_tiles, L.segs, L.seg_outs, y, sb->D,
                                                        sb->d_coeffs, sb->n_terms, sb->batch * sb->n_terms,
-                                                       accumulate, skip,
+                                                       accumulate, skip, member_done,
                                                        sb->d_tc_err, stages, stage_bytes, r_tile, tmem_cols, epi,
                                                        L.acc_cols, n_acc, tile_split, sb->test_stall);
 }
 
 template <int PREC, class TIn>
 static void run_set(const State* s, const PairSet& ps, const TIn* x, double* y, const dmrg_sb* sb,
-                    int accumulate, const int32_t* skip, cudaStream_t st) {
+                    int accumulate, const int32_t* skip, cudaStream_t st, const int32_t* member_done = nullptr) {
   if (ps.n_stage_tiles > 0)
     tc_stage_kernel<PREC, TIn><<<dim3((unsigned)ps.n_stage_tiles, sb->batch), 256, 0, st>>>(
-        ps.stage_tiles, ps.stage_outs, x, sb->D, ps.p_lo, sb->d_coeffs, sb->n_terms, skip);
-  run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, st);
-  run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, st);
-  run_gemm<PREC>(s, ps.grpS, y, sb, accumulate, skip, st);
+        ps.stage_tiles, ps.stage_outs, x, sb->D, ps.p_lo, sb->d_coeffs, sb->n_terms, skip, member_done);
+  run_gemm<PREC>(s, ps.ph1, y, sb, 0, skip, member_done, st);
+  run_gemm<PREC>(s, ps.grpE, y, sb, accumulate, skip, member_done, st);
+  run_gemm<PREC>(s, ps.grpS, y, sb, accumulate, skip, member_done, st);
 }
 
 // Time the product under each candidate tuning on this superblock and keep
@@ -1482,20 +1497,20 @@ void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out) 
 }
 
 void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
-               cudaStream_t st) {
+               cudaStream_t st, const int32_t* member_done) {
   const State* s = st_of(sb);
   if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
-  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st);
-  else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st);
+  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st, member_done);
+  else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st, member_done);
   sb->test_stall = 0;  // the hook applies to one product
 }
 
 void tc_matvec_f32in(dmrg_sb* sb, int prec, const float* x, double* y, int accumulate, const int32_t* skip,
-                     cudaStream_t st) {
+                     cudaStream_t st, const int32_t* member_done) {
   const State* s = st_of(sb);
   if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
-  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st);
-  else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st);
+  if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st, member_done);
+  else run_set<DMRG_BF16X3>(s, s->f[1].fwd, x, y, sb, accumulate, skip, st, member_done);
   sb->test_stall = 0;
 }
 
