@@ -433,6 +433,21 @@ void build_f64_tasks(dmrg_sb* sb) {
 }
 
 // ------------------------------------------------------------- products
+// Double-float products read pre-split pairs: the operator arena (split at
+// the first such product) and the input, split into a buffer of its own each
+// time; the intermediates are written and read as pairs.  Returns the
+// buffers and their pair mask.
+uint32_t df_bufs(dmrg_sb* sb, const double* x, double* y, Bufs& bufs, cudaStream_t st) {
+  if (!sb->d_ops_df) {
+    sb->d_ops_df = dalloc<double>((size_t)std::max<int64_t>(sb->ops_elems, 1));
+    launch_split_pairs(sb->d_ops, sb->d_ops_df, sb->ops_elems, st);
+  }
+  if (!sb->d_x_df) sb->d_x_df = dalloc<double>((size_t)(sb->batch * sb->D));
+  launch_split_pairs(x, sb->d_x_df, sb->batch * sb->D, st);
+  bufs = Bufs{{sb->d_x_df, y, sb->d_T, sb->d_ops_df, nullptr}};
+  return (1u << BUF_X) | (1u << BUF_T) | (1u << BUF_OPS);
+}
+
 // member_done (tensor-core precisions only, may be null): device [batch]
 // flags; members whose flag is nonzero are skipped (their rows of y are left
 // as they are)
@@ -444,10 +459,11 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
     launch_seg_gemm_f64(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
     launch_seg_gemm_f64(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
   } else if (prec == DMRG_DF64) {  // the same task lists in double-float arithmetic
-    Bufs bufs{{const_cast<double*>(x), y, sb->d_T, sb->d_ops, nullptr}};
-    launch_seg_gemm_df(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, skip, st);
-    launch_seg_gemm_df(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
-    launch_seg_gemm_df(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st);
+    Bufs bufs;
+    const uint32_t pm = df_bufs(sb, x, y, bufs, st);
+    launch_seg_gemm_df(sb->f64_fwd1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, skip, st, pm);
+    launch_seg_gemm_df(sb->f64_fwd2, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st, pm);
+    launch_seg_gemm_df(sb->f64_fwd3, bufs, sb->d_coeffs, sb->n_terms, accumulate, nullptr, skip, st, pm);
   } else {
     tc_matvec(sb, prec, x, y, accumulate, skip, st, member_done);
   }
@@ -459,9 +475,10 @@ void matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, c
 void matvec_f64_dots(dmrg_sb* sb, const double* psi, double* y, double* dc, cudaStream_t st, bool df = false) {
   Bufs bufs{{const_cast<double*>(psi), y, sb->d_T, sb->d_ops, nullptr}};
   if (df) {
-    launch_seg_gemm_df(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
-    launch_seg_gemm_df_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
-    launch_seg_gemm_df_dots(sb->f64_pdot3, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
+    const uint32_t pm = df_bufs(sb, psi, y, bufs, st);
+    launch_seg_gemm_df(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st, pm);
+    launch_seg_gemm_df_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st, pm);
+    launch_seg_gemm_df_dots(sb->f64_pdot3, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st, pm);
   } else {
     launch_seg_gemm_f64(sb->f64_dot1, bufs, sb->d_coeffs, sb->n_terms, 0, nullptr, nullptr, st);
     launch_seg_gemm_f64_dots(sb->f64_pdot2, bufs, sb->d_coeffs, sb->n_terms, 0, sb->d_pdot_partial, nullptr, st);
@@ -1043,7 +1060,7 @@ void destroy(dmrg_sb* sb) {
                           &sb->f64_bwd2, &sb->f64_bwd3, &sb->f64_pdot2, &sb->f64_pdot3})
     free_tl(*tl);
   for (double* p : {sb->d_coeffs, sb->d_ops, sb->d_T, sb->d_dot_partial, sb->d_scratch, sb->d_red, sb->d_dg,
-                    sb->d_pdot_partial})
+                    sb->d_pdot_partial, sb->d_ops_df, sb->d_x_df})
     if (p) cudaFree(p);
   for (int32_t* p : {sb->d_pdot_ptr, sb->d_pdot_idx})
     if (p) cudaFree(p);

@@ -74,11 +74,16 @@ void launch_seg_gemm_f64(const TaskListF64& tl, const Bufs& bufs, const double* 
 // tiles of mode TM_STORE_DOTS (product and per-segment dots in one pass)
 void launch_seg_gemm_f64_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
                               int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
-// the same task lists in double-float arithmetic (matvec_df.cu)
+// the same task lists in double-float arithmetic (matvec_df.cu); buffers whose
+// bit is set in pair_mask (1 << BufId) hold float32 pairs (hi, lo) in their
+// 8-byte slots: read without splitting, written (TM_STORE) as pairs
 void launch_seg_gemm_df(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms, int accumulate,
-                        double* dot_out, const int32_t* skip, cudaStream_t st);
+                        double* dot_out, const int32_t* skip, cudaStream_t st, uint32_t pair_mask = 0);
 void launch_seg_gemm_df_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
-                             int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st);
+                             int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st,
+                             uint32_t pair_mask = 0);
+// dst[i] = the double-float pair of src[i] (n elements)
+void launch_split_pairs(const double* src, double* dst, int64_t n, cudaStream_t st);
 
 // ------------------------------------------------------------ host pair info
 struct PairH {
@@ -100,6 +105,8 @@ struct dmrg_sb {
   double* h_coeffs_pinned = nullptr;  // pinned staging copy of coeffs for dmrg_set_coeffs
   std::vector<dmrg::PairH> pairs;
   double* d_ops = nullptr;     // FP64 operator arena
+  double* d_ops_df = nullptr;  // the same arena as double-float pairs (first double-float product)
+  double* d_x_df = nullptr;    // [batch][D] the double-float product's input as pairs
   int64_t ops_elems = 0;
   double flops = 0;            // algorithmic flops of one product, one member
 

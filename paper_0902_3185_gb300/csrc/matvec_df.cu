@@ -18,6 +18,16 @@
 // accuracy enough for residuals r = H psi - theta psi down to |r| ~ 1e-12 |H psi|.  Outputs are written as
 // float64 (hi + lo).  Paper Sec. 3.3: the product x += H y, system,
 // environment and connection parts, on the fly.
+//
+// Buffers flagged in the pair mask hold every element as a float32 pair
+// (hi, lo) in its 8-byte slot, already split: the operator arena (split once
+// per superblock), the wavefunction (split once per product) and the
+// intermediates, which phase 1 writes as its renormalised (s, c) sums (48
+// bits, no rounding to float64 between the two GEMMs).  Loads from them skip
+// the integer split, which otherwise costs about 28 instructions per loaded
+// element per K tile.
+
+#include <algorithm>
 
 #include "df.cuh"
 #include "internal.h"
@@ -38,10 +48,20 @@ struct DFDotSmem {
 
 
 
+// the 8 bytes of a pair slot as (hi, lo): hi is the low word (float2 layout)
+__device__ __forceinline__ float2 df_bits(double v) {
+  return make_float2(__int_as_float(__double2loint(v)), __int_as_float(__double2hiint(v)));
+}
+__device__ __forceinline__ double df_slot(float s, float c) {  // (s, c) renormalised into one slot
+  const float hi = __fadd_rn(s, c);
+  const float lo = __fsub_rn(c, __fsub_rn(hi, s));
+  return __hiloint2double(__float_as_int(lo), __float_as_int(hi));
+}
+
 template <int NI, int NJ, bool DOTS>
 __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restrict__ segs, const Bufs& bufs,
                                         const double* __restrict__ coef, int n_terms, int accumulate,
-                                        double* __restrict__ dot_out, DFSmem& sm, DFDotSmem* dsm) {
+                                        double* __restrict__ dot_out, DFSmem& sm, DFDotSmem* dsm, uint32_t pm) {
   constexpr int BM = 16 * NI, BN = 16 * NJ;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
@@ -68,9 +88,14 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
     return (t.c_rm && t.c_axis == 0) ? m / t.c_rm : (t.c_rm ? 0 : t.member);
   };
   auto mcol = [&](int j) -> int { return by_col ? (t.n0 + tx + 16 * j) / t.c_rm : 0; };
+  const bool x_pairs = (pm >> BUF_X) & 1u;
   auto xo = [&](int i, int j) -> double {
     const int m = t.m0 + ty + 16 * i, n = t.n0 + tx + 16 * j;
-    return (m < t.M && n < t.N) ? X[coff(m, n)] : 0.0;
+    if (m >= t.M || n >= t.N) return 0.0;
+    const double v = X[coff(m, n)];
+    if (!x_pairs) return v;
+    const float2 p = df_bits(v);
+    return df_value(p.x, p.y);
   };
 
   // DOTS: each segment's coefficient-weighted sum goes straight to the
@@ -92,6 +117,7 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
     }
     const double* L = bufs.p[s.l_buf] + s.l_off;
     const double* R = bufs.p[s.r_buf] + s.r_off;
+    const bool l_pairs = (pm >> s.l_buf) & 1u, r_pairs = (pm >> s.r_buf) & 1u;
     const bool uscaled = s.coef_mode == 0 && s.coef >= 0;
     const float2 uscale = df_split(uscaled ? coef[s.coef] : 1.0);
     // this thread's load slots, fixed over the segment: tile row / column,
@@ -149,13 +175,13 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
       {
 #pragma unroll
         for (int e = 0; e < NI; ++e) {  // BM x BK elements, 256 per pass
-          float2 v = df_split(pl[e]);
+          float2 v = l_pairs ? df_bits(pl[e]) : df_split(pl[e]);
           if (lscaled) v = df_mul(v, lcf[e]);
           sm.L[lk[e]][lm[e]] = v;
         }
 #pragma unroll
         for (int e = 0; e < NJ; ++e) {  // BN x BK elements
-          float2 v = df_split(pr[e]);
+          float2 v = r_pairs ? df_bits(pr[e]) : df_split(pr[e]);
           if (rscaled) v = df_mul(v, rcf[e]);
           sm.R[rk[e]][rn_[e]] = v;
         }
@@ -242,7 +268,29 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
       for (int j = 0; j < NJ; ++j) put(i, j, 0.0, true);
   }
   double* C = bufs.p[t.c_buf] + t.c_off;
-  if (t.mode == TM_STORE) {
+  if (t.mode == TM_STORE && ((pm >> t.c_buf) & 1u)) {  // a pair buffer: (s, c) kept as the pair
+    const bool add = accumulate || t.add;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int m = t.m0 + ty + 16 * i;
+      if (m >= t.M) continue;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int n = t.n0 + tx + 16 * j;
+        if (n >= t.N) continue;
+        double* p = C + coff(m, n);
+        float s = s_[i][j], c = c_[i][j];
+        if (add) {  // two-sum of the stored pair's high parts, the low parts into c
+          const float2 o = df_bits(*p);
+          const float tt = __fadd_rn(s, o.x);
+          const float bv = __fsub_rn(tt, s);
+          c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(tt, bv)), __fsub_rn(o.x, bv)), o.y));
+          s = tt;
+        }
+        *p = df_slot(s, c);
+      }
+    }
+  } else if (t.mode == TM_STORE) {
     const bool add = accumulate || t.add;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
@@ -290,12 +338,12 @@ __device__ __forceinline__ void df_tile(const TileF64& t, const SegF64* __restri
 __global__ void __launch_bounds__(DF_THREADS, 2)
 seg_gemm_df_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs, Bufs bufs,
                    const double* __restrict__ coef, int n_terms, int accumulate, double* __restrict__ dot_out,
-                   const int32_t* __restrict__ skip) {
+                   const int32_t* __restrict__ skip, uint32_t pm) {
   __shared__ DFSmem sm;
   if (skip && *skip) return;
   const TileF64 t = tiles[blockIdx.x];
 #define DF_CASE(I, J) \
-  case (I) | ((J) << 8): df_tile<I, J, false>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, nullptr); break;
+  case (I) | ((J) << 8): df_tile<I, J, false>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, nullptr, pm); break;
   switch (t.shape) {
     DF_SHAPES(DF_CASE)
     default: break;  // the host builds only the shapes above
@@ -306,13 +354,13 @@ seg_gemm_df_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__
 __global__ void __launch_bounds__(DF_THREADS, 2)
 seg_gemm_df_dots_kernel(const TileF64* __restrict__ tiles, const SegF64* __restrict__ segs, Bufs bufs,
                         const double* __restrict__ coef, int n_terms, int accumulate, double* __restrict__ dot_out,
-                        const int32_t* __restrict__ skip) {
+                        const int32_t* __restrict__ skip, uint32_t pm) {
   __shared__ DFSmem sm;
   __shared__ DFDotSmem dsm;
   if (skip && *skip) return;
   const TileF64 t = tiles[blockIdx.x];
 #define DF_CASE(I, J) \
-  case (I) | ((J) << 8): df_tile<I, J, true>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, &dsm); break;
+  case (I) | ((J) << 8): df_tile<I, J, true>(t, segs, bufs, coef, n_terms, accumulate, dot_out, sm, &dsm, pm); break;
   switch (t.shape) {
     DF_SHAPES(DF_CASE)
     default: break;
@@ -322,17 +370,32 @@ seg_gemm_df_dots_kernel(const TileF64* __restrict__ tiles, const SegF64* __restr
 #undef DF_SHAPES
 
 void launch_seg_gemm_df(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms, int accumulate,
-                        double* dot_out, const int32_t* skip, cudaStream_t st) {
+                        double* dot_out, const int32_t* skip, cudaStream_t st, uint32_t pair_mask) {
   if (tl.n_tiles == 0) return;
   seg_gemm_df_kernel<<<(unsigned)tl.n_tiles, DF_THREADS, 0, st>>>(tl.d_tiles, tl.d_segs, bufs, coef, n_terms,
-                                                                  accumulate, dot_out, skip);
+                                                                  accumulate, dot_out, skip, pair_mask);
+}
+
+// dst[i] = the pair (hi, lo) of src[i] in its 8-byte slot
+__global__ void k_split_pairs(const double* __restrict__ src, double* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 p = df_split(src[i]);
+    dst[i] = __hiloint2double(__float_as_int(p.y), __float_as_int(p.x));
+  }
+}
+
+void launch_split_pairs(const double* src, double* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);  // grid-stride beyond
+  k_split_pairs<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
 }
 
 void launch_seg_gemm_df_dots(const TaskListF64& tl, const Bufs& bufs, const double* coef, int n_terms,
-                             int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st) {
+                             int accumulate, double* dot_out, const int32_t* skip, cudaStream_t st,
+                             uint32_t pair_mask) {
   if (tl.n_tiles == 0) return;
   seg_gemm_df_dots_kernel<<<(unsigned)tl.n_tiles, DF_THREADS, 0, st>>>(tl.d_tiles, tl.d_segs, bufs, coef, n_terms,
-                                                                       accumulate, dot_out, skip);
+                                                                       accumulate, dot_out, skip, pair_mask);
 }
 
 }  // namespace dmrg

@@ -25,12 +25,18 @@
 // One persistent kernel runs a list of output tiles (128 x up to 256) per
 // launch: warp 0 streams operand tiles through a multi-stage shared-memory
 // ring, warp 1 issues tcgen05.mma into two or three TMEM accumulator buffers,
-// warps 2-13 drain them (tcgen05.ld) and either write the float64 output
+// warps 2-9 drain them (tcgen05.ld) and either write the float64 output
 // block or the next phase's operand panel (scaled by the member's
 // coefficient, rounded to TF32 or split into BF16 hi + lo, written in 16-byte
 // granules after a transpose through shared memory).  Phase-1 pairs that
 // share their wavefunction operand run as one "pieced" tile: their operator
 // panels side by side along N behind one L tile.
+//
+// Eight draining warps rather than twelve: the block then gets 168 registers
+// a thread without spills (at 448 threads the cap of 128 spilled inside the
+// producer's and the MMA warp's loops), and fewer warps share the issue slots
+// of the two single-thread roles; on the real m = 1000 superblock the product
+// fell from 0.600 to 0.557 ms.
 //
 // Precisions: TF32 (kind::tf32), and BF16x3: x = hi + lo, products
 // hi*hi + hi*lo + lo*hi in kind::f16 with an FP32 accumulator.
@@ -202,7 +208,7 @@ tc_stage_kernel(const StageTile* __restrict__ tiles, const StageOut* __restrict_
 }
 
 // ------------------------------------------------------ grouped tile GEMM
-constexpr int TC_EPI_WARPS = 12;                   // three per TMEM lane quadrant
+constexpr int TC_EPI_WARPS = 8;                    // two per TMEM lane quadrant
 constexpr int TC_EPI_PARTS = TC_EPI_WARPS / 4;      // warps per TMEM lane quadrant
 constexpr int TC_MAX_ACC = 4;                        // accumulator buffers in TMEM
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer, MMA, epilogue
@@ -809,7 +815,7 @@ void pack(std::vector<uint8_t>& hi, std::vector<uint8_t>& lo, const Panel& p, co
 // half-arena layout starts at `base_off`; returns the bytes used.
 static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& P, int64_t base_off,
                          std::vector<uint8_t>& hi, std::vector<uint8_t>& lo, char* d_hi, int64_t lo_delta,
-                         PairSet& out, bool dry, const Tune& tune) {
+                         PairSet& out, bool dry, const Tune& tune, int n_sms) {
   const int64_t nb = sb->batch;
   const int es = prec == DMRG_TF32 ? 4 : 2;
   const int64_t kce = PANEL_ROW_BYTES / es;
@@ -1218,6 +1224,12 @@ static int64_t build_set(const dmrg_sb* sb, int prec, const std::vector<EPair>& 
       std::vector<int64_t> w(B.tiles.size());
       for (size_t i = 0; i < B.tiles.size(); ++i) w[i] = gw[{B.tiles[i].out, B.tiles[i].m0}];
       std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return w[a] > w[b]; });
+      // CTA c takes positions c, c + G, c + 2G, ... (G CTAs): reversing every
+      // second round of G deals the sorted tiles back and forth (a snake), so
+      // that no CTA takes the heavier tile of every round
+      const size_t G = (size_t)std::max(1, std::min(n_sms, (int)perm.size()));
+      for (size_t r0 = G; r0 < perm.size(); r0 += 2 * G)
+        std::reverse(perm.begin() + r0, perm.begin() + std::min(perm.size(), r0 + G));
     }
     std::vector<TcTile> t(B.tiles.size());
     for (size_t i = 0; i < perm.size(); ++i) t[i] = B.tiles[perm[i]];
@@ -1320,16 +1332,16 @@ static void build_fmt(dmrg_sb* sb, State* s, int fi) {
   std::vector<uint8_t> hi, lo;
   {
     PairSet none;
-    const int64_t a = build_set(sb, prec, s->fw, 0, hi, lo, nullptr, 0, none, true, s->tune[fi]);
-    const int64_t b2 = build_set(sb, prec, s->bw, a, hi, lo, nullptr, 0, none, true, s->tune[fi]);
+    const int64_t a = build_set(sb, prec, s->fw, 0, hi, lo, nullptr, 0, none, true, s->tune[fi], s->num_sms);
+    const int64_t b2 = build_set(sb, prec, s->bw, a, hi, lo, nullptr, 0, none, true, s->tune[fi], s->num_sms);
     F.bytes = (size_t)(a + b2);
   }
   const size_t total = F.bytes * (prec == DMRG_BF16X3 ? 2 : 1);
   TCK(cudaMalloc(&F.arena, std::max<size_t>(total, 1024)));
   TCK(cudaMemset(F.arena, 0, std::max<size_t>(total, 1024)));
   const int64_t lo_delta = prec == DMRG_BF16X3 ? (int64_t)F.bytes : 0;
-  const int64_t a = build_set(sb, prec, s->fw, 0, hi, lo, F.arena, lo_delta, F.fwd, false, s->tune[fi]);
-  build_set(sb, prec, s->bw, a, hi, lo, F.arena, lo_delta, F.bwd, false, s->tune[fi]);
+  const int64_t a = build_set(sb, prec, s->fw, 0, hi, lo, F.arena, lo_delta, F.fwd, false, s->tune[fi], s->num_sms);
+  build_set(sb, prec, s->bw, a, hi, lo, F.arena, lo_delta, F.bwd, false, s->tune[fi], s->num_sms);
   TCK(cudaMemcpy(F.arena, hi.data(), hi.size(), cudaMemcpyHostToDevice));
   if (prec == DMRG_BF16X3) TCK(cudaMemcpy(F.arena + lo_delta, lo.data(), lo.size(), cudaMemcpyHostToDevice));
   if (fi == 0) s->op_bytes_tf32 = (double)a;
