@@ -389,11 +389,13 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
       constexpr uint32_t fmt = PREC == DMRG_TF32 ? tc::FMT_TF32 : tc::FMT_BF16;
       TcTile tl_n{};
       if (blockIdx.x < n_tiles) tl_n = tiles[blockIdx.x];
+      int nt_seg = -1, nt_kch = 0, nt_slot = 0;  // the next tile's first segment, loaded during this tile
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const TcTile tl = tl_n;
         if (t + (int)gridDim.x < n_tiles) tl_n = tiles[t + gridDim.x];  // one tile ahead
         if (tl.seg_begin == tl.seg_end || tile_done(tl, member_done)) continue;
-        int kch_n = segs[tl.seg_begin].kchunks, slot_n = segs[tl.seg_begin].slot;  // in flight during the wait
+        int kch_n = nt_seg == tl.seg_begin ? nt_kch : segs[tl.seg_begin].kchunks;
+        int slot_n = nt_seg == tl.seg_begin ? nt_slot : segs[tl.seg_begin].slot;
         const int acc = kk % n_acc;
         const uint32_t acc_phase = (uint32_t)(kk / n_acc) & 1u;
         ++kk;
@@ -409,6 +411,10 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int n_tiles, const TcSeg* __res
           if (s + 1 < s_end) {  // one segment ahead
             kch_n = segs[s + 1].kchunks;
             slot_n = segs[s + 1].slot;
+          } else if (t + (int)gridDim.x < n_tiles && tl_n.seg_begin < tl_n.seg_end) {
+            nt_seg = tl_n.seg_begin;  // the next tile's first: in flight during this last segment
+            nt_kch = segs[nt_seg].kchunks;
+            nt_slot = segs[nt_seg].slot;
           }
           const uint32_t d_tmem = d_acc + (uint32_t)(slot * tl.ntile);
           uint32_t accum = (started >> slot) & 1u;
