@@ -59,4 +59,21 @@ __device__ __forceinline__ void df_fma(float2 a, float2 b, float& s, float& c) {
 
 __device__ __forceinline__ double df_value(float s, float c) { return tc::f2d_exact(s) + tc::f2d_exact(c); }
 
+// s + c as a pair (hi, lo) by Knuth's two-sum (no ordering of |s|, |c| assumed)
+__device__ __forceinline__ float2 df_two_sum(float s, float c) {
+  const float hi = __fadd_rn(s, c);
+  const float bv = __fsub_rn(hi, s);
+  return make_float2(hi, __fadd_rn(__fsub_rn(s, __fsub_rn(hi, bv)), __fsub_rn(c, bv)));
+}
+
+// a + b of two pairs: two-sum of the high parts, the low parts and its error
+// added into the low part, then the two-sum again (renormalised)
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 h = df_two_sum(a.x, b.x);
+  return df_two_sum(h.x, __fadd_rn(h.y, __fadd_rn(a.y, b.y)));
+}
+
+// (s, c) of df_fma as a renormalised pair
+__device__ __forceinline__ float2 df_pair(float s, float c) { return df_two_sum(s, c); }
+
 }  // namespace dmrg

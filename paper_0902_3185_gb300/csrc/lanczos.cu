@@ -93,6 +93,7 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
            const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk, int win,
            const int32_t* __restrict__ gate, const double* __restrict__ h_pre, double* __restrict__ npart_pre) {
   __shared__ double red[LZ_THREADS / 32][8];
+  __shared__ float2 red2[LZ_THREADS / 32][8];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
@@ -136,7 +137,9 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
   }
   const bool full = base + (LZ_DOT_EPT - 1) * LZ_THREADS < D;
   for (int i0 = first_row(j, win); i0 <= j; i0 += 8) {
+    // per-thread sums of 8 rows: float64, or double-float pairs (pair basis)
     double p[8];
+    float2 p2[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int i = i0 + q;
@@ -153,7 +156,7 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
               if (base + e * LZ_THREADS < D) df_fma(ld_pair(v + e * LZ_THREADS), wf[e], ps, pc);
           }
         }
-        p[q] = df_value(ps, pc);
+        p2[q] = df_pair(ps, pc);
       } else {
         p[q] = 0.0;
         if (i <= j) {
@@ -170,41 +173,65 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
     }
     // butterfly: after the step with offset 16 a lane holds 4 partial rows,
     // after 8 two rows, after 4 one row; offsets 2 and 1 finish that row.
-    {
-      const bool up = lane & 16;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const double send = up ? p[q] : p[q + 4];
-        const double keep = up ? p[q + 4] : p[q];
-        p[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-    }
-    {
-      const bool up = lane & 8;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const double send = up ? p[q] : p[q + 2];
-        const double keep = up ? p[q + 2] : p[q];
-        p[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-    }
-    {
-      const bool up = lane & 4;
-      const double send = up ? p[0] : p[1];
-      const double keep = up ? p[1] : p[0];
-      p[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    p[0] += __shfl_xor_sync(0xffffffffu, p[0], 2);
-    p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
-    // lane holds row ((lane>>4)&1)*4 + ((lane>>3)&1)*2 + ((lane>>2)&1)
+    // The pair basis adds pairs (float32 work: float64 issues at 1/64 of the
+    // float32 rate, and float64 adds here had cost a third of the sweep).
     const int row = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-    __syncthreads();
-    if ((lane & 3) == 0) red[wid][row] = p[0];
+    if (PAIR) {
+#pragma unroll
+      for (int h = 4; h >= 1; h >>= 1) {  // offsets 16, 8, 4: halve the rows held
+        const int off = 4 * h;
+        const bool up = lane & off;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+          const float2 send = up ? p2[q] : p2[q + h];
+          const float2 keep = up ? p2[q + h] : p2[q];
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, off),
+                                         __shfl_xor_sync(0xffffffffu, send.y, off));
+          p2[q] = df_add(keep, got);
+        }
+      }
+#pragma unroll
+      for (int off = 2; off >= 1; off >>= 1)
+        p2[0] = df_add(p2[0], make_float2(__shfl_xor_sync(0xffffffffu, p2[0].x, off),
+                                          __shfl_xor_sync(0xffffffffu, p2[0].y, off)));
+      __syncthreads();
+      if ((lane & 3) == 0) red2[wid][row] = p2[0];
+    } else {
+      {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double send = up ? p[q] : p[q + 4];
+          const double keep = up ? p[q + 4] : p[q];
+          p[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+      }
+      {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const double send = up ? p[q] : p[q + 2];
+          const double keep = up ? p[q + 2] : p[q];
+          p[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+      }
+      {
+        const bool up = lane & 4;
+        const double send = up ? p[0] : p[1];
+        const double keep = up ? p[1] : p[0];
+        p[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      p[0] += __shfl_xor_sync(0xffffffffu, p[0], 2);
+      p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
+      __syncthreads();
+      if ((lane & 3) == 0) red[wid][row] = p[0];
+    }
     __syncthreads();
     if (threadIdx.x < 8 && i0 + (int)threadIdx.x <= j) {
       double t = 0.0;
 #pragma unroll
-      for (int w2 = 0; w2 < LZ_THREADS / 32; ++w2) t += red[w2][threadIdx.x];
+      for (int w2 = 0; w2 < LZ_THREADS / 32; ++w2)
+        t += PAIR ? df_value(red2[w2][threadIdx.x].x, red2[w2][threadIdx.x].y) : red[w2][threadIdx.x];
       partial[((int64_t)b * nchunk + chunk) * cap + i0 + threadIdx.x] = t;
     }
   }
