@@ -531,7 +531,8 @@ void lz_alloc(dmrg_sb* sb, int cap) {
   sb->lz_V = dalloc<double>((size_t)(cap * B * D));
   sb->lz_w = dalloc<double>((size_t)(B * D));
   sb->lz_vcur = dalloc<double>((size_t)(B * D));
-  sb->lz_partial = dalloc<double>((size_t)(B * sb->lz_nchunk * cap));
+  // per-chunk partials of the vector kernels, or per-warp dot partials of every Krylov row
+  sb->lz_partial = dalloc<double>((size_t)B * std::max(sb->lz_nchunk, lz_dot_nparts(sb->D)) * cap);
   sb->lz_h = dalloc<double>((size_t)(3 * B * cap));
   sb->lz_npart = dalloc<double>((size_t)(3 * B * sb->lz_nchunk));
   sb->lz_gate = dalloc<int32_t>((size_t)B);
@@ -579,14 +580,14 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   const int ndot = lz_dot_nchunk(D);
   const bool pair = lz_pair(prec);  // the Krylov basis as double-float pairs (mixed-precision solves)
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st, nullptr, nullptr, pair);
-  lz_launch_reduce_rows(sb->lz_partial, hA, ctl, ndot, cap, B, 2, nullptr, st);
+  lz_launch_reduce_rows(sb->lz_partial, hA, ctl, lz_dot_nparts(D), cap, B, 2, nullptr, st);
   // pass A's update runs inside pass B's dot sweep (norm partials per dot chunk)
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA, pair);
-  lz_launch_reduce_rows(sb->lz_partial, hB, ctl, ndot, cap, B, 0, nullptr, st);
+  lz_launch_reduce_rows(sb->lz_partial, hB, ctl, lz_dot_nparts(D), cap, B, 0, nullptr, st);
   lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, ctl, D, B, cap, nch, 0, nullptr, st, pair);
   lz_launch_dgks(nA, nB, sb->lz_gate, ctl, B, ndot, nch, st);
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, sb->lz_gate, st, nullptr, nullptr, pair);
-  lz_launch_reduce_rows(sb->lz_partial, hC, ctl, ndot, cap, B, 0, sb->lz_gate, st);
+  lz_launch_reduce_rows(sb->lz_partial, hC, ctl, lz_dot_nparts(D), cap, B, 0, sb->lz_gate, st);
   lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hC, nC, ctl, D, B, cap, nch, 0, sb->lz_gate, st, pair);
   lz_launch_finalize_ab(sb->lz_h, nB, nC, sb->lz_gate, sb->lz_ab, ctl, B, cap, nch, st);
   lz_launch_tridiag(sb->lz_ab, sb->lz_s, sb->lz_out, ctl, sb->lz_out + 4 * B, B, cap, D, st);  // tol at out[4B]
@@ -1415,7 +1416,7 @@ dmrg_status dmrg_time_reorth(dmrg_sb* sb, int32_t prec, int32_t j, int32_t reps,
     const int64_t D = sb->D;
     const int B = sb->batch;
     lz_alloc(sb, j + 1);
-    const int cap = sb->lz_cap, nch = sb->lz_nchunk, ndot = lz_dot_nchunk(D);
+    const int cap = sb->lz_cap, nch = sb->lz_nchunk;
     const bool pair = lz_pair(prec);
     // every member running at Krylov index j; the basis rows and w hold whatever
     // the last solve left (the timing does not depend on the values)
@@ -1430,7 +1431,7 @@ dmrg_status dmrg_time_reorth(dmrg_sb* sb, int32_t prec, int32_t j, int32_t reps,
     auto pass = [&] {
       lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, sb->lz_ctl, D, B, cap, 0, nullptr, st, nullptr, nullptr,
                          pair);
-      lz_launch_reduce_rows(sb->lz_partial, hB, sb->lz_ctl, ndot, cap, B, 0, nullptr, st);
+      lz_launch_reduce_rows(sb->lz_partial, hB, sb->lz_ctl, lz_dot_nparts(D), cap, B, 0, nullptr, st);
       lz_launch_multiaxpy(sb->lz_V, sb->lz_w, hB, nB, sb->lz_ctl, D, B, cap, nch, 0, nullptr, st, pair);
     };
     pass();

@@ -76,8 +76,10 @@ __device__ __forceinline__ double v_value(const double* p) {
 // first Krylov row of a pass: the last `win` rows, or all (win = 0)
 __device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j - win + 1) : 0; }
 
-// partial[(b*nchunk + chunk)*cap + i] = sum_{d in chunk} V[i][b][d] * w[b][d], i0 <= i <= j
-// (i0 = first_row(j, win)).
+// partial[((b*nchunk + chunk)*LZ_DOT_WARPS + warp)*cap + i] = sum over the warp's
+// elements d of the chunk of V[i][b][d] * w[b][d], i0 <= i <= j (i0 =
+// first_row(j, win)): one partial per warp, so that no block barrier stands
+// between the row groups and the other warps keep loading while one reduces.
 // GB300 issues float64 at 1/64 of the float32 rate, so the reduction must not
 // cost more float64 work than the dot products: every thread keeps
 // LZ_DOT_EPT elements of w in registers, takes 8 rows at a time, and the 8
@@ -93,7 +95,6 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
            const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk, int win,
            const int32_t* __restrict__ gate, const double* __restrict__ h_pre, double* __restrict__ npart_pre) {
   __shared__ double red[LZ_THREADS / 32][8];
-  __shared__ float2 red2[LZ_THREADS / 32][8];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
@@ -194,8 +195,6 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
       for (int off = 2; off >= 1; off >>= 1)
         p2[0] = df_add(p2[0], make_float2(__shfl_xor_sync(0xffffffffu, p2[0].x, off),
                                           __shfl_xor_sync(0xffffffffu, p2[0].y, off)));
-      __syncthreads();
-      if ((lane & 3) == 0) red2[wid][row] = p2[0];
     } else {
       {
         const bool up = lane & 16;
@@ -223,17 +222,10 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
       }
       p[0] += __shfl_xor_sync(0xffffffffu, p[0], 2);
       p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
-      __syncthreads();
-      if ((lane & 3) == 0) red[wid][row] = p[0];
     }
-    __syncthreads();
-    if (threadIdx.x < 8 && i0 + (int)threadIdx.x <= j) {
-      double t = 0.0;
-#pragma unroll
-      for (int w2 = 0; w2 < LZ_THREADS / 32; ++w2)
-        t += PAIR ? df_value(red2[w2][threadIdx.x].x, red2[w2][threadIdx.x].y) : red[w2][threadIdx.x];
-      partial[((int64_t)b * nchunk + chunk) * cap + i0 + threadIdx.x] = t;
-    }
+    if ((lane & 3) == 0 && i0 + row <= j)
+      partial[(((int64_t)b * nchunk + chunk) * LZ_DOT_WARPS + wid) * cap + i0 + row] =
+          PAIR ? df_value(p2[0].x, p2[0].y) : p[0];
   }
 }
 

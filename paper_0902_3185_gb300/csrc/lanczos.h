@@ -14,6 +14,7 @@ constexpr int LZ_ROWS = 4;        // Krylov rows reduced together in k_multidot
 constexpr int LZ_TRI = 32;        // threads of the tridiagonal multisection (one warp)
 constexpr int LZ_DOT_EPT = 16;    // elements per thread in the reorthogonalisation dots
 constexpr int LZ_DOT_CHUNK = LZ_THREADS * LZ_DOT_EPT;
+constexpr int LZ_DOT_WARPS = LZ_THREADS / 32;  // dot partials per chunk (one per warp)
 
 // LZ_CTL_FORCE (testing hook): nonzero makes the float32 test pass at its first check
 enum LzCtl : int {
@@ -30,6 +31,8 @@ enum LzCode : int {
 
 inline int lz_nchunk(int64_t D) { return (int)((D + LZ_CHUNK - 1) / LZ_CHUNK); }
 inline int lz_dot_nchunk(int64_t D) { return (int)((D + LZ_DOT_CHUNK - 1) / LZ_DOT_CHUNK); }
+// dot partials per member and Krylov row written by one k_multidot launch
+inline int lz_dot_nparts(int64_t D) { return lz_dot_nchunk(D) * LZ_DOT_WARPS; }
 
 // Gram-Schmidt passes over the Krylov rows first_row(j, win)..j (win = 0: all
 // rows); members with gate != NULL and gate[b] == 0 are skipped.

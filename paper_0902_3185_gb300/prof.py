@@ -12,6 +12,10 @@ python -m paper_0902_3185_gb300.prof --workload npz:/tmp/real.npz --prec bf16x3 
 refinement and the gradient) inside the NVTX range "step" (ncu --nvtx
 --nvtx-include "step/" captures exactly its launches).
 
+--reorth J times only full Gram-Schmidt passes at Krylov index J (the
+Lanczos kernels k_multidot, k_reduce_rows, k_multiaxpy; one untimed pass,
+then --reps passes).
+
 Recording the DRAM traffic of one product from an ncu capture of exactly its
 launches (``ncu -i <rep> --page raw --csv > raw.csv``) for bench.py:
 
@@ -39,6 +43,8 @@ TRAFFIC_SOURCES = {
     "df64_product_real": ["paper_0902_3185_gb300/csrc/matvec_df.cu", "paper_0902_3185_gb300/csrc/df.cuh",
                           "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
     "fp64_product": ["paper_0902_3185_gb300/csrc/matvec_f64.cu"],
+    "gram_schmidt_pass_bf16x3_real": ["paper_0902_3185_gb300/csrc/lanczos.cu", "paper_0902_3185_gb300/csrc/lanczos.h",
+                                      "paper_0902_3185_gb300/csrc/df.cuh"],
     "df64_product": ["paper_0902_3185_gb300/csrc/matvec_df.cu", "paper_0902_3185_gb300/csrc/tc_kernel.cuh"],
 }
 
@@ -90,6 +96,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--lanczos-iters", type=int, default=0, help="also run a fixed-length Lanczos")
     ap.add_argument("--autotune", action="store_true", help="autotune, then time eager and graph-captured products")
+    ap.add_argument("--reorth", type=int, default=-1,
+                    help="only time full Gram-Schmidt passes at this Krylov index (one untimed pass, then --reps)")
     a = ap.parse_args()
     import torch
     from paper_0902_3185_gb300.binding import GpuSuperblock
@@ -110,6 +118,11 @@ def main():
         from workloads.synthetic import random_sectored
         sb = random_sectored(seed=0, batch=a.batch)
     g = GpuSuperblock(sb)
+    if a.reorth >= 0:
+        ms, nbytes = g.time_reorth(a.reorth, prec=a.prec, reps=a.reps)
+        print(f"D={sb.dim} batch={sb.batch} Gram-Schmidt pass at j={a.reorth}: {ms:.4f} ms, "
+              f"{nbytes / ms / 1e6:.1f} GB/s")
+        return
     x = torch.from_numpy(np.stack([seeded_normal(b, sb.dim) for b in range(sb.batch)])).cuda()
     y = g.empty()
     for _ in range(a.reps):
