@@ -76,10 +76,12 @@ __device__ __forceinline__ double v_value(const double* p) {
 // first Krylov row of a pass: the last `win` rows, or all (win = 0)
 __device__ __forceinline__ int first_row(int j, int win) { return win ? max(0, j - win + 1) : 0; }
 
-// partial[((b*nchunk + chunk)*LZ_DOT_WARPS + warp)*cap + i] = sum over the warp's
+// partial[(b*cap + i)*nparts + chunk*LZ_DOT_WARPS + warp] = sum over the warp's
 // elements d of the chunk of V[i][b][d] * w[b][d], i0 <= i <= j (i0 =
-// first_row(j, win)): one partial per warp, so that no block barrier stands
-// between the row groups and the other warps keep loading while one reduces.
+// first_row(j, win), nparts = nchunk * LZ_DOT_WARPS): one partial per warp,
+// so that no block barrier stands between the row groups and the other warps
+// keep loading while one reduces; a row's partials are contiguous for the
+// reduction.
 // GB300 issues float64 at 1/64 of the float32 rate, so the reduction must not
 // cost more float64 work than the dot products: every thread keeps
 // LZ_DOT_EPT elements of w in registers, takes 8 rows at a time, and the 8
@@ -224,36 +226,38 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
       p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
     }
     if ((lane & 3) == 0 && i0 + row <= j)
-      partial[(((int64_t)b * nchunk + chunk) * LZ_DOT_WARPS + wid) * cap + i0 + row] =
+      partial[((int64_t)b * cap + i0 + row) * ((int64_t)nchunk * LZ_DOT_WARPS) + chunk * LZ_DOT_WARPS + wid] =
           PAIR ? df_value(p2[0].x, p2[0].y) : p[0];
   }
 }
 
-// h[b*cap + i] = sum over chunks of the partials, first_row(j, win) <= i <= j.  Block (32 x 8):
-// lane x owns row i0 + x, warp y sums chunks y, y + 8, ...; the 8 warp sums
-// are then added in a fixed order (deterministic).
+// h[b*cap + i] = sum of row i's nparts partials, first_row(j, win) <= i <= j:
+// one warp per row (8 rows per block), lane l summing partials l, l + 32, ...
+// in four interleaved accumulators (loads in flight), then a fixed shuffle
+// tree: the same order on every call (deterministic).
 __global__ void __launch_bounds__(256)
 k_reduce_rows(const double* __restrict__ partial, double* __restrict__ h, const int32_t* __restrict__ ctl,
-              int nchunk, int cap, int win, const int32_t* __restrict__ gate) {
-  __shared__ double red[8][33];
+              int nparts, int cap, int win, const int32_t* __restrict__ gate) {
   const int b = blockIdx.x;
   if (member_skip(ctl, gate, b)) return;
   const int j = ctl[LZ_CTL_J];
-  const int i0 = first_row(j, win) + blockIdx.y * 32;
-  if (i0 > j) return;
-  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
-  const int i = i0 + x;
-  double t = 0.0;
-  if (i <= j)
-    for (int ch = y; ch < nchunk; ch += 8) t += partial[((int64_t)b * nchunk + ch) * cap + i];
-  red[y][x] = t;
-  __syncthreads();
-  if (y == 0 && i <= j) {
-    double u = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) u += red[k][x];
-    h[(int64_t)b * cap + i] = u;
+  const int lane = threadIdx.x & 31;
+  const int i = first_row(j, win) + blockIdx.y * 8 + (int)(threadIdx.x >> 5);
+  if (i > j) return;
+  const double* row = partial + ((int64_t)b * cap + i) * nparts;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int s = lane;
+  for (; s + 96 < nparts; s += 128) {
+    a0 += row[s];
+    a1 += row[s + 32];
+    a2 += row[s + 64];
+    a3 += row[s + 96];
   }
+  for (; s < nparts; s += 32) a0 += row[s];
+  double t = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) h[(int64_t)b * cap + i] = t;
 }
 
 // w[b] -= sum_{i0<=i<=j} V[i][b] h[b][i] (i0 = first_row(j, win)); with
@@ -804,7 +808,7 @@ void lz_launch_multidot(const double* V, double* w, double* partial, const int32
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st) {
   const int rows = win ? win : cap;
-  k_reduce_rows<<<dim3(batch, (rows + 31) / 32), 256, 0, st>>>(partial, h, ctl, nchunk, cap, win, gate);
+  k_reduce_rows<<<dim3(batch, (rows + 7) / 8), 256, 0, st>>>(partial, h, ctl, nchunk, cap, win, gate);
 }
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
                          const int32_t* ctl, int64_t D, int batch, int cap, int nchunk, int win,
