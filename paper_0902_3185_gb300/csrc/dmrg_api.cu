@@ -600,6 +600,8 @@ cudaGraphExec_t lz_graph(dmrg_sb* sb, int prec, int K) {
   const int key = 1 + prec * 1024 + K;
   for (int i = 0; i < 8; ++i)
     if (sb->lz_graphs[i] && sb->lz_graph_key[i] == key) return (cudaGraphExec_t)sb->lz_graphs[i];
+  // the products' panels must exist before the capture (building them allocates)
+  if (prec == DMRG_TF32 || prec == DMRG_BF16X3) tc_prepare(sb, prec);
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
@@ -766,6 +768,8 @@ cudaGraphExec_t rf_graph(dmrg_sb* sb, int prec, int K) {
   const int key = (1 << 20) + 1 + prec * 1024 + K;
   for (int i = 0; i < 8; ++i)
     if (sb->lz_graphs[i] && sb->lz_graph_key[i] == key) return (cudaGraphExec_t)sb->lz_graphs[i];
+  // the products' panels must exist before the capture (building them allocates)
+  if (prec == DMRG_TF32 || prec == DMRG_BF16X3) tc_prepare(sb, prec);
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;

@@ -748,6 +748,8 @@ struct Fmt {
   char* arena = nullptr;
   size_t bytes = 0;   // per hi/lo half
   PairSet fwd, bwd;
+  bool built = false;                // panels and task lists exist (built at the first use of the precision)
+  std::vector<double> built_coeffs;  // the coefficient table its panels were built with
 };
 
 // A pair as the product sees it (forward, or transposed for H^T)
@@ -773,7 +775,6 @@ struct State {
   std::vector<double> host_ops;               // float64 blocks (forward)
   std::vector<std::vector<double>> trans;     // transposed blocks (H^T)
   std::vector<EPair> fw, bw;
-  std::vector<double> built_coeffs;           // the coefficient table the panels were built with
 };
 
 void free_launch(Launch& l) {
@@ -1309,14 +1310,27 @@ bool tc_set_coeffs(dmrg_sb* sb) {
       if (cf[(size_t)b * nt + term] != cf[term]) return false;
     return true;
   };
-  bool same = true;
-  for (int k = 0; k < nt && same; ++k) {
-    const bool uo = uniform(s->built_coeffs, k), un = uniform(sb->coeffs, k);
-    same = uo == un && (!uo || s->built_coeffs[k] == sb->coeffs[k]);
+  bool rebuilt = false;
+  for (int fi = 0; fi < 2; ++fi) {
+    const Fmt& F = s->f[fi];
+    if (!F.built) continue;  // built later with the coefficients current then
+    bool same = true;
+    for (int k = 0; k < nt && same; ++k) {
+      const bool uo = uniform(F.built_coeffs, k), un = uniform(sb->coeffs, k);
+      same = uo == un && (!uo || F.built_coeffs[k] == sb->coeffs[k]);
+    }
+    if (same) continue;
+    build_fmt(sb, s, fi);
+    rebuilt = true;
   }
-  if (same) return false;
-  for (int fi = 0; fi < 2; ++fi) build_fmt(sb, s, fi);
-  return true;
+  return rebuilt;
+}
+
+void tc_prepare(dmrg_sb* sb, int prec) {
+  State* s = st_of(sb);
+  if (!s || !s->ok) return;
+  const int fi = prec == DMRG_TF32 ? 0 : 1;
+  if (!s->f[fi].built) build_fmt(sb, s, fi);
 }
 
 int tc_launches(const dmrg_sb* sb, int prec) {
@@ -1350,8 +1364,8 @@ static void build_fmt(dmrg_sb* sb, State* s, int fi) {
   build_set(sb, prec, s->bw, a, hi, lo, F.arena, lo_delta, F.bwd, false, s->tune[fi], s->num_sms);
   TCK(cudaMemcpy(F.arena, hi.data(), hi.size(), cudaMemcpyHostToDevice));
   if (prec == DMRG_BF16X3) TCK(cudaMemcpy(F.arena + lo_delta, lo.data(), lo.size(), cudaMemcpyHostToDevice));
-  if (fi == 0) s->op_bytes_tf32 = (double)a;
-  s->built_coeffs = sb->coeffs;
+  F.built_coeffs = sb->coeffs;
+  F.built = true;
 }
 
 void tc_build(dmrg_sb* sb) {
@@ -1393,7 +1407,14 @@ void tc_build(dmrg_sb* sb) {
     }
     s->bw.push_back(t);
   }
-  for (int fi = 0; fi < 2; ++fi) build_fmt(sb, s, fi);
+  // the panels of a precision are built at its first use (tc_prepare); the
+  // TF32 layout's operand bytes come from a dry run of its forward set
+  {
+    std::vector<uint8_t> hi, lo;
+    PairSet none;
+    s->op_bytes_tf32 = (double)build_set(sb, DMRG_TF32, s->fw, 0, hi, lo, nullptr, 0, none, true, s->tune[0],
+                                         s->num_sms);
+  }
   TCK(cudaFuncSetAttribute(tc_gemm_kernel<DMRG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   TCK(cudaFuncSetAttribute(tc_gemm_kernel<DMRG_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   s->ok = true;
@@ -1516,6 +1537,7 @@ void tc_autotune(dmrg_sb* sb, int prec, int reps, cudaStream_t st, double* out) 
 
 void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate, const int32_t* skip,
                cudaStream_t st, const int32_t* member_done) {
+  tc_prepare(sb, prec);
   const State* s = st_of(sb);
   if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
   if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st, member_done);
@@ -1525,6 +1547,7 @@ void tc_matvec(dmrg_sb* sb, int prec, const double* x, double* y, int accumulate
 
 void tc_matvec_f32in(dmrg_sb* sb, int prec, const float* x, double* y, int accumulate, const int32_t* skip,
                      cudaStream_t st, const int32_t* member_done) {
+  tc_prepare(sb, prec);
   const State* s = st_of(sb);
   if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
   if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].fwd, x, y, sb, accumulate, skip, st, member_done);
@@ -1533,6 +1556,7 @@ void tc_matvec_f32in(dmrg_sb* sb, int prec, const float* x, double* y, int accum
 }
 
 void tc_matvec_T(dmrg_sb* sb, int prec, const double* g, double* dpsi, cudaStream_t st) {
+  tc_prepare(sb, prec);
   const State* s = st_of(sb);
   if (!s || !s->ok) throw CudaFail("tensor-core path unavailable");
   if (prec == DMRG_TF32) run_set<DMRG_TF32>(s, s->f[0].bwd, g, dpsi, sb, 0, nullptr, st);

@@ -9,7 +9,10 @@ struct dmrg_sb;
 
 namespace dmrg {
 
-void tc_build(dmrg_sb* sb);      // operand panels and task lists (no-op when unsupported)
+void tc_build(dmrg_sb* sb);      // pair lists (no-op when unsupported); panels are built per precision at first use
+// build the operand panels and task lists of `prec` now if they do not exist
+// (allocates and copies: call it before a stream capture that runs products)
+void tc_prepare(dmrg_sb* sb, int prec);
 void tc_free(dmrg_sb* sb);
 bool tc_available(const dmrg_sb* sb);
 bool tc_set_coeffs(dmrg_sb* sb);  // true: operand panels rebuilt (captured graphs are stale)
