@@ -120,8 +120,11 @@ typedef struct {     /* one per batch member */
 } dmrg_lanczos_info;
 
 /* Sec. 3.2-3.3: build the sector tables, the (term, sector pair) task lists,
- * device copies of every operator block (float64 and tensor-core layouts)
- * and the workspace.  batch >= 1 superblocks share all blocks and differ only
+ * device copies of every operator block (float64 layout) and the workspace.
+ * The operator layouts of the other precisions (the tensor-core panels of
+ * DMRG_TF32 and DMRG_BF16X3, the double-float pairs of DMRG_DF64) are built
+ * at the first product in that precision: that call allocates and copies, so
+ * make it before capturing such products in a CUDA graph of your own.  batch >= 1 superblocks share all blocks and differ only
  * in coeffs.  Returns DMRG_EINVAL for inconsistent shapes (identity flag with
  * r_out != r_in, sector out of range, ld too small, NULL block). */
 dmrg_status dmrg_create_superblock(const dmrg_sb_desc* d, int32_t batch, dmrg_sb** out);
@@ -173,7 +176,9 @@ dmrg_status dmrg_apply_H_backward(dmrg_sb* sb, const double* psi, const double* 
  * the iteration captured in CUDA graphs.  A member stops when a float32
  * estimate of its residual passes at half the tolerance; the float64 test
  * after the loop confirms it, and a member that misses it restarts from its
- * Ritz vector with the iterations it has left (DMRG_ENOCONV only at max_iter).  psi0: device [batch][D] start vectors;
+ * Ritz vector with the iterations it has left (DMRG_ENOCONV only at max_iter).
+ * Tolerances below 1e-5 are finer than the float32 estimate resolves: near
+ * convergence those members are tested in float64 at every check instead.  psi0: device [batch][D] start vectors;
  * psi_out: device [batch][D], normalised; e0: host [batch]; info: host
  * [batch] or NULL.  Returns the worst member status (DMRG_OK if all met the
  * tolerance; DMRG_EBREAKDOWN is reported in info only). */

@@ -496,7 +496,10 @@ __device__ void inverse_iteration(const T* a, const T* e, int n, T sigma, T* z, 
 //    its Ritz vector) and stores s for the Ritz vector: the members' float64 solves
 //    run side by side in one launch instead of each in the launch where its
 //    member converged;
-//  - at breakdown or the cap the float64 eigenpair is computed at once.
+//  - at breakdown or the cap the float64 eigenpair is computed at once;
+//  - tolerances below 1e-5 are beyond the float32 estimate's resolution:
+//    near convergence (estimate <= 1e-2 |T|) those members take the float64
+//    eigenpair and test at every check instead of stopping as pending.
 // GB300 issues float64 at 1/64 of the float32 rate, which is why the per-
 // iteration test runs in float32.
 __global__ void __launch_bounds__(32)
@@ -571,8 +574,14 @@ k_tridiag(const double* __restrict__ ab, double* __restrict__ s_out, double* __r
                            false);
   __syncwarp();
   const double est = beta * fabs((double)z32[n - 1]);
-  const bool pass32 = est <= 0.5 * tol * fmax(1.0, fabs((double)th32)) || ctl[LZ_CTL_FORCE] != 0;
-  if (!final_pass && !(small_beta || last)) {
+  const bool force = ctl[LZ_CTL_FORCE] != 0;
+  const bool pass32 = est <= 0.5 * tol * fmax(1.0, fabs((double)th32)) || force;
+  // The float32 last component is accurate only to about eps32 |T| / gap
+  // (absolute), so the float32 estimate cannot resolve tolerances much below
+  // 1e-5: such solves take the float64 eigenpair at every check once the
+  // estimate has come within 1e-2 |T|, and stop on the float64 test.
+  const bool check64 = !final_pass && tol < 1e-5 && !force && est <= 1e-2 * scale_t;
+  if (!final_pass && !(small_beta || last) && !check64) {
     if (lane == 0) {
       out[b * 4 + 0] = th32;
       out[b * 4 + 1] = est;

@@ -176,11 +176,13 @@ def test_lanczos_cap_reports_noconv(dev):
 
 @pytest.mark.parametrize("check_every", [1, 3])
 def test_lanczos_members_stop_apart(dev, check_every):
-    """Members that pass the float32 test at different iterations stop as
-    pending; the float64 eigenpairs computed after the loop meet the
-    tolerance: status 0, the reported residual within tol, the true residual
-    |H psi - E psi| of the returned state within a few tol, energies equal to
-    the oracle's."""
+    """Members converge at different iterations and stop apart: status 0,
+    the reported residual within tol, the true residual |H psi - E psi| of
+    the returned state within a few tol, energies equal to the oracle's.  At
+    tol = 1e-10, below what the float32 estimate resolves, members are tested
+    in float64 at each check near convergence, so they stop at a check point
+    no later than the oracle's own stopping iteration (tolerance 1e-12), not
+    at the cap."""
     sb = CASES["hub_ladder_grown"]()
     g = gpu_sb(sb)
     X = np.stack([seeded_normal(40 + b, sb.dim) for b in range(sb.batch)])
@@ -191,11 +193,11 @@ def test_lanczos_members_stop_apart(dev, check_every):
     for b in range(sb.batch):
         scale = max(1.0, abs(e0[b]))
         assert infos[b]["status"] == 0 and infos[b]["residual"] <= tol * scale
-        if check_every > 1:
-            assert infos[b]["iters"] % check_every == 0 or infos[b]["iters"] >= 400
+        assert infos[b]["iters"] % check_every == 0
         r = osb.apply_H(sb, P[b], b) - e0[b] * P[b]
         assert np.linalg.norm(r) <= 10 * tol * scale
         ref = olz.lanczos_ground(lambda v: osb.apply_H(sb, v, b), X[b], tol=1e-12, max_iter=400)
+        assert ref.converged and infos[b]["iters"] <= ref.iters + check_every, (b, infos[b]["iters"], ref.iters)
         assert abs(e0[b] - ref.e0) <= 1e-10 * abs(ref.e0)
 
 
