@@ -579,7 +579,7 @@ void lz_enqueue_iteration(dmrg_sb* sb, int prec, cudaStream_t st) {
   double* nC = sb->lz_npart + (size_t)2 * B * nch;
   const int ndot = lz_dot_nchunk(D);
   const bool pair = lz_pair(prec);  // the Krylov basis as double-float pairs (mixed-precision solves)
-  lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 2, nullptr, st, nullptr, nullptr, pair);
+  lz_launch_dots_local(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, st, pair);
   lz_launch_reduce_rows(sb->lz_partial, hA, ctl, lz_dot_nparts(D), cap, B, 2, nullptr, st);
   // pass A's update runs inside pass B's dot sweep (norm partials per dot chunk)
   lz_launch_multidot(sb->lz_V, sb->lz_w, sb->lz_partial, ctl, D, B, cap, 0, nullptr, st, hA, nA, pair);

@@ -65,6 +65,10 @@ __device__ __forceinline__ bool member_skip(const int32_t* ctl, const int32_t* g
 
 // a Krylov element stored as a double-float pair
 __device__ __forceinline__ float2 ld_pair(const double* p) { return *reinterpret_cast<const float2*>(p); }
+// the pair held in the 8 bytes of a loaded element (hi in the low word)
+__device__ __forceinline__ float2 pair_bits(double v) {
+  return make_float2(__int_as_float(__double2loint(v)), __int_as_float(__double2hiint(v)));
+}
 __device__ __forceinline__ void st_pair(double* p, double v) { *reinterpret_cast<float2*>(p) = df_split(v); }
 __device__ __forceinline__ double pair_value(float2 a) { return tc::f2d_exact(a.x) + tc::f2d_exact(a.y); }
 // element d of Krylov row i in either storage
@@ -228,6 +232,74 @@ k_multidot(const double* __restrict__ V, double* __restrict__ w, double* __restr
     if ((lane & 3) == 0 && i0 + row <= j)
       partial[((int64_t)b * cap + i0 + row) * ((int64_t)nchunk * LZ_DOT_WARPS) + chunk * LZ_DOT_WARPS + wid] =
           PAIR ? df_value(p2[0].x, p2[0].y) : p[0];
+  }
+}
+
+// Pass A's dots: w with v_{j-1} and v_j (v_0 alone at j = 0), in the
+// partial layout of k_multidot with win = 2.  A pass over two rows does too
+// little arithmetic to hide memory latency behind it, so every thread issues
+// all of its loads -- its LZ_DOT_EPT elements of w and of both rows -- before
+// any arithmetic: one memory round trip per block instead of one for w
+// followed by one for the rows.
+template <bool PAIR>
+__global__ void __launch_bounds__(LZ_THREADS, 2)
+k_dots_local(const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ partial,
+             const int32_t* __restrict__ ctl, int64_t D, int batch, int cap, int nchunk) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (member_done(ctl, b)) return;
+  const int j = ctl[LZ_CTL_J];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t base = (int64_t)chunk * LZ_DOT_CHUNK + threadIdx.x;
+  const bool two = j >= 1;
+  const double* wb = w + (int64_t)b * D + base;
+  const double* r0 = V + ((int64_t)(two ? j - 1 : j) * batch + b) * D + base;
+  const double* r1 = V + ((int64_t)j * batch + b) * D + base;
+  double x[LZ_DOT_EPT], a0[LZ_DOT_EPT], a1[LZ_DOT_EPT];  // w, rows j-1 and j (pairs in their 8 bytes)
+#pragma unroll
+  for (int e = 0; e < LZ_DOT_EPT; ++e) {
+    const bool in = base + e * LZ_THREADS < D;
+    x[e] = in ? wb[e * LZ_THREADS] : 0.0;
+    a0[e] = in && two ? r0[e * LZ_THREADS] : 0.0;
+    a1[e] = in ? r1[e * LZ_THREADS] : 0.0;
+  }
+  double d0, d1;
+  if (PAIR) {
+    float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < LZ_DOT_EPT; ++e) {
+      const float2 wf = df_split(x[e]);
+      df_fma(pair_bits(a0[e]), wf, s0, c0);
+      df_fma(pair_bits(a1[e]), wf, s1, c1);
+    }
+    // fixed butterfly over the warp in double-float adds (deterministic)
+    float2 p0 = df_pair(s0, c0), p1 = df_pair(s1, c1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      p0 = df_add(p0, make_float2(__shfl_xor_sync(0xffffffffu, p0.x, o), __shfl_xor_sync(0xffffffffu, p0.y, o)));
+      p1 = df_add(p1, make_float2(__shfl_xor_sync(0xffffffffu, p1.x, o), __shfl_xor_sync(0xffffffffu, p1.y, o)));
+    }
+    d0 = df_value(p0.x, p0.y);
+    d1 = df_value(p1.x, p1.y);
+  } else {
+    double q0 = 0.0, q1 = 0.0;
+#pragma unroll
+    for (int e = 0; e < LZ_DOT_EPT; ++e) {
+      q0 = fma(a0[e], x[e], q0);
+      q1 = fma(a1[e], x[e], q1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+      q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+    }
+    d0 = q0;
+    d1 = q1;
+  }
+  if (lane == 0) {
+    const int64_t nparts = (int64_t)nchunk * LZ_DOT_WARPS;
+    const int64_t slot = (int64_t)chunk * LZ_DOT_WARPS + wid;
+    if (two) partial[((int64_t)b * cap + j - 1) * nparts + slot] = d0;
+    partial[((int64_t)b * cap + j) * nparts + slot] = d1;
   }
 }
 
@@ -813,6 +885,14 @@ void lz_launch_multidot(const double* V, double* w, double* partial, const int32
   else
     k_multidot<false><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D), win, gate,
                                                 h_pre, npart_pre);
+}
+void lz_launch_dots_local(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
+                          int batch, int cap, cudaStream_t st, bool pair) {
+  const dim3 g(lz_dot_nchunk(D), batch);
+  if (pair)
+    k_dots_local<true><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D));
+  else
+    k_dots_local<false><<<g, LZ_THREADS, 0, st>>>(V, w, partial, ctl, D, batch, cap, lz_dot_nchunk(D));
 }
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st) {

@@ -43,6 +43,9 @@ inline int lz_dot_nparts(int64_t D) { return lz_dot_nchunk(D) * LZ_DOT_WARPS; }
 void lz_launch_multidot(const double* V, double* w, double* partial, const int32_t* ctl, int64_t D,
                         int batch, int cap, int win, const int32_t* gate, cudaStream_t st,
                         const double* h_pre, double* npart_pre, bool pair);
+// pass A's dots (w with v_{j-1} and v_j) into the partials of a win = 2 pass
+void lz_launch_dots_local(const double* V, const double* w, double* partial, const int32_t* ctl, int64_t D,
+                          int batch, int cap, cudaStream_t st, bool pair);
 void lz_launch_reduce_rows(const double* partial, double* h, const int32_t* ctl, int nchunk, int cap,
                            int batch, int win, const int32_t* gate, cudaStream_t st);
 void lz_launch_multiaxpy(const double* V, double* w, const double* h, double* norm_partial,
