@@ -566,7 +566,9 @@ def main():
                  "lanczos_iters": max(i["iters"] for i in info_full),
                  "fp64_products": max(i["fp64_matvecs"] for i in info_full),
                  "mixed_products": max(i["mixed_matvecs"] for i in info_full),
-                 "residual_max": max(i["residual"] for i in info_full)}
+                 "residual_max": max(i["residual"] for i in info_full),
+                 "lanczos_iters_per_member": [int(i["iters"]) for i in info_full],
+                 "lanczos_restarts": sum(int(i["restarts"]) for i in info_full)}
 
     # kernel-only product timing (events on the launching stream)
     mv_ms = product_ms(torch, g, x0, stream, dev, prec, 20)

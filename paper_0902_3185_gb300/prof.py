@@ -170,7 +170,8 @@ def main():
         e0, _, infos, st, _ = step()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(f"step status {st} launches {infos[0]['kernel_launches']} iters {infos[0]['iters']}")
+        print(f"step status {st} launches {infos[0]['kernel_launches']} iters {[i['iters'] for i in infos]} "
+              f"restarts {[i['restarts'] for i in infos]}")
     torch.cuda.synchronize()
     print(f"D={sb.dim} batch={sb.batch} pairs={len(sb.pairs)} flops/product={g.info['flops_per_matvec']:.4g}")
 
