@@ -596,7 +596,7 @@ def main():
 
     # Lanczos iteration rate at fixed Krylov length j (no early stop)
     fixed_j = {}
-    for pj, js in ([(prec, (20, 100)), ("fp64", (20,))] if prec != "fp64" else [("fp64", (20,))]):
+    for pj, js in ([(prec, (20, 100)), ("fp64", (20, 100))] if prec != "fp64" else [("fp64", (20, 100))]):
         for j in js:
             t_j, _ = timed(lambda: g.lanczos_ground(x0, tol=1e-300, max_iter=j, prec=pj, refine="none",
                                                     graph_iters=10))
