@@ -355,12 +355,15 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
   // independent accumulators, so every row issues LZ_EPT loads at once
   const int64_t d0 = (int64_t)chunk * LZ_CHUNK + threadIdx.x;
   const bool full = d0 + (LZ_EPT - 1) * LZ_THREADS < D;
-  double acc[LZ_EPT];
+  double acc[LZ_EPT], wv[LZ_EPT];
   float ss[LZ_EPT], sc[LZ_EPT];
 #pragma unroll
   for (int e = 0; e < LZ_EPT; ++e) {
     acc[e] = 0.0;
     ss[e] = sc[e] = 0.0f;
+    // w is loaded before the rows, so that its memory round trip overlaps theirs
+    const int64_t d = d0 + e * LZ_THREADS;
+    wv[e] = d < D ? w[(int64_t)b * D + d] : 0.0;
   }
 #pragma unroll 2
   for (int i = i0; i <= j; ++i) {
@@ -382,7 +385,7 @@ k_multiaxpy(const double* __restrict__ V, double* __restrict__ w, const double* 
   for (int e = 0; e < LZ_EPT; ++e) {
     const int64_t d = d0 + e * LZ_THREADS;
     if (d >= D) continue;
-    const double x = w[(int64_t)b * D + d] - (PAIR ? df_value(ss[e], sc[e]) : acc[e]);
+    const double x = wv[e] - (PAIR ? df_value(ss[e], sc[e]) : acc[e]);
     w[(int64_t)b * D + d] = x;
     nrm = fma(x, x, nrm);
   }
