@@ -62,7 +62,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=300)
-    ap.add_argument("--mixed-tol", type=float, default=2e-4)
+    ap.add_argument("--mixed-tol", type=float, default=3e-4,
+                    help="Lanczos tolerance of the mixed solve on the headline superblock (measured there: 1e-4 "
+                         "458 ms, 2e-4 440, 3e-4 430, 4e-4 423, 6e-4 461 ms: a fourth residual product)")
     ap.add_argument("--refine", default="newton_df64", choices=["newton", "newton_df64", "lanczos", "none"])
     ap.add_argument("--no-grown", action="store_true", help="skip the isometry-grown stand-in leg")
     ap.add_argument("--no-fp64-solve", action="store_true",
@@ -182,6 +184,7 @@ def source_sha(files):
 
 
 GS_TRAFFIC_J = 60  # Krylov index of the recorded Gram-Schmidt pass capture
+GROWN_MIXED_TOL = 2e-4  # mixed Lanczos tolerance of the isometry-grown stand-in leg
 
 
 def recorded_traffic(name):
@@ -413,8 +416,8 @@ def measure_grown(binding, torch, args, prec, dev, stream, rank):
     flops = g.info["flops_per_matvec"]
     x0 = torch.from_numpy(np.stack([seeded_normal(1000 * rank + b, sb.dim) for b in range(sb.batch)])).to(dev)
 
-    def step():
-        return g.lanczos_ground(x0, tol=args.mixed_tol, max_iter=args.max_iter, prec=prec, refine=args.refine,
+    def step():  # the stand-in keeps the tolerance of its own measured history
+        return g.lanczos_ground(x0, tol=GROWN_MIXED_TOL, max_iter=args.max_iter, prec=prec, refine=args.refine,
                                 refine_tol=args.tol, graph_iters=8, grad=True)
     for _ in range(3):
         step()
@@ -711,7 +714,7 @@ def main():
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if prec == "fp64" else f"{prec}+f32acc (products), f64 (Lanczos)",
            "data": "synthetic (the model's own DMRG superblock from the device driver; no dataset)",
-           "config": dict({"workload": WORKLOAD, "batch": sb.batch, "m": 1000, "prec": prec, "tol": args.tol,
+           "config": dict({"workload": WORKLOAD, "batch": sb.batch, "m": 1000, "prec": prec, "tol": args.tol, "mixed_tol": args.mixed_tol,
                            "l2": "256 MB flush between timed steps; Krylov basis > L2", "autotune": tune},
                           **sb_info),
            "dmrg_setup": dmrg_stats,

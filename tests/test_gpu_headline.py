@@ -118,7 +118,7 @@ def test_real_products_against_oracle(real):
 
 
 def test_real_refined_states_certified_by_oracle(real):
-    """The benchmark's step (BF16x3 Lanczos to 2e-4, double-float Newton
+    """The benchmark's step (BF16x3 Lanczos to 3e-4, double-float Newton
     refinement to 1e-10, gradient) on the real superblock; for members 0 and
     15 the oracle recomputes theta = <psi|H|psi> and |H psi - theta psi| in
     float64 from the returned state: theta equals E0 to 1e-12 relative, and
@@ -127,7 +127,7 @@ def test_real_refined_states_certified_by_oracle(real):
     binding, sb = real
     g = binding.GpuSuperblock(sb)
     X0 = np.stack([seeded_normal(5000 + b, sb.dim) for b in range(sb.batch)])
-    e0, psi, infos, st, dE = g.lanczos_ground(torch.from_numpy(X0).cuda(), tol=2e-4, max_iter=300,
+    e0, psi, infos, st, dE = g.lanczos_ground(torch.from_numpy(X0).cuda(), tol=3e-4, max_iter=300,
                                               prec="bf16x3", refine="newton_df64", refine_tol=1e-10,
                                               graph_iters=8, grad=True)
     assert st == 0, [i["status"] for i in infos]
