@@ -728,7 +728,8 @@ def main():
            "lanczos_fixed_j": fixed_j, "accuracy": accuracy, "isometry_grown": grown,
            "roofline": roof, "roofline_kernels": kernels, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline_real(sb)
+        # the oracle baseline is timed at N = 1 only (host cores shared by N ranks would not be the same baseline)
+        out["cpu_baseline"] = cpu_baseline_real(sb) if world == 1 else None
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
