@@ -652,20 +652,23 @@ def main():
     pk64 = FP64_FMA_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
     pkdf = FP32_OPS_PER_CLK / DF_OPS_PER_FMA * 2 * sm_mhz * 1e6 / 1e12
     newton = prec != "fp64" and args.refine.startswith("newton")
-    n_dots = max(0, n_f64 - 1) if newton else 0
+    # the refinement computes the per-term dots with the residual product it
+    # expects to be the last (one per step, unless a residual met the
+    # tolerance earlier than expected)
+    n_dots = 1 if newton and n_f64 >= 2 else 0
     if df:
         pk_r, name_r = pkdf, "df64"
         src_r = (f"{FP32_OPS_PER_CLK} float32 ops/clock / {DF_OPS_PER_FMA} per double-float FMA x 2 x "
                  f"{sm_mhz:.0f} MHz (median SM clock of the timed region)")
         kern_r = "grouped double-float product, seg_gemm_df_kernel (3 launches per product)"
         kern_d = ("double-float product with the per-term dots (unscaled intermediates + seg_gemm_df_dots_kernel, "
-                  "the refinement's residuals after the first)")
+                  "the refinement's residual expected to be the last)")
     else:
         pk_r, name_r = pk64, "fp64"
         src_r = f"304 float64 FMA/clock x 2 x {sm_mhz:.0f} MHz (median SM clock of the timed region)"
         kern_r = "grouped float64 product, seg_gemm_f64_kernel (3 launches per dmrg_apply_H)"
         kern_d = ("float64 product with the per-term dots (unscaled intermediates + seg_gemm_f64_dots_kernel, "
-                  "the refinement's residuals after the first)")
+                  "the refinement's residual expected to be the last)")
     a_r = flops_mv / (mvr_ms / 1e3) / 1e12
     kernels[f"{name_r}_product"] = {
         "bound": "alu", "achieved": a_r, "peak": pk_r, "unit": "TFLOP/s", "frac": a_r / pk_r,

@@ -189,10 +189,12 @@ dmrg_status dmrg_lanczos_ground(dmrg_sb* sb, const double* psi0, double* psi_out
 /* dmrg_lanczos_ground, then the Hellmann-Feynman gradient of the returned
  * state, dE_dc[b][k] = <psi_b, (A_k (x) B_k) psi_b> / <psi_b, psi_b> (device
  * [batch][n_terms], as dmrg_energy_grad).  With refine = 2 (3) the
- * refinement's float64 (double-float) residual products after the first give
- * H psi and the per-term dots in one pass, so the gradient of the final state
- * costs no extra pass;
- * otherwise it is computed after the solve.  Same statuses as
+ * refinement's float64 (double-float) residual product that is expected to
+ * be the last (the previous step's requested accuracy, or the mixed product's
+ * error floor, meets the tolerance for every member) gives H psi and the
+ * per-term dots in one pass, so the gradient of the final state costs no
+ * extra pass; otherwise (also when a residual meets the tolerance earlier
+ * than expected) it is computed after the solve.  Same statuses as
  * dmrg_lanczos_ground; DMRG_EINVAL for dE_dc == NULL. */
 dmrg_status dmrg_lanczos_ground_grad(dmrg_sb* sb, const double* psi0, double* psi_out, double* e0,
                                      double* dE_dc, const dmrg_lanczos_opts* opts,

@@ -800,6 +800,10 @@ cudaGraphExec_t rf_graph(dmrg_sb* sb, int prec, int K) {
   return ge;
 }
 
+// the smallest residual reduction factor one Newton step is counted on when
+// predicting the last residual product (the mixed products' error bounds it)
+constexpr double RF_STEP_FLOOR = 1.0 / 4000.0;
+
 struct RfRun {
   std::vector<int32_t> code;  // LZ_CONVERGED or LZ_CAP
   std::vector<double> theta, resid;
@@ -833,10 +837,12 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, int rprec, double tol, int ma
   rf_launch_diag(sb->d_dg, sb->d_dg_terms, (int)sb->dg_terms.size(), sb->d_coeffs, sb->n_terms, sb->rf_diag, D, B,
                  st);
   ++r.launches;
+  // whether the next residual product is expected to be the last one (its
+  // per-term dots are then the gradient of the returned psi); the first is
+  // never the last in practice: the mixed solve stops far above the tolerance
+  bool expect_last = false;
   for (int o = 0; o < max_outer; ++o) {
-    // float64 residual of the current iterate (the first outer step is never
-    // the last in practice: the mixed solve stops far above the tolerance)
-    const bool with_dots = dc && o >= 1;
+    const bool with_dots = dc && o >= 1 && (expect_last || o + 1 == max_outer);
     if (with_dots) matvec_f64_dots(sb, cur, sb->lz_w, dc, st, rprec == DMRG_DF64);
     else matvec(sb, rprec, cur, sb->lz_w, 0, nullptr, st);
     r.dots_final = with_dots;
@@ -885,6 +891,14 @@ RfRun rf_solve(dmrg_sb* sb, double* psi, int prec, int rprec, double tol, int ma
       const double need = 0.25 * tol * std::max(1.0, std::fabs(r.theta[b])) / std::max(r.resid[b], 1e-300);
       eps = std::min(eps, std::max(o == 0 ? std::sqrt(need) : need, 1e-5));
     }
+    // the step shrinks a residual by about eps, but by no more than the mixed
+    // product's own error allows (about 1/4000 per step on the ladder): the
+    // next residual is expected to be the last when that meets the tolerance
+    // for every member still refining
+    expect_last = true;
+    for (int b = 0; b < B; ++b)
+      if (!conv[b] && r.resid[b] * std::max(eps, RF_STEP_FLOOR) > tol * std::max(1.0, std::fabs(r.theta[b])))
+        expect_last = false;
     CK(cudaMemcpyAsync(sb->rf_ctl, hctl.data(), sizeof(int32_t) * (2 * B + 2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(sb->rf_sc + RF_NSC * B, &eps, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
